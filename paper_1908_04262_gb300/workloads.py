@@ -1,0 +1,192 @@
+"""Seeded synthetic workloads: lattice configurations, nucleus sites, initial
+perturbations.
+
+This module produces inputs only.  It holds none of the method's arithmetic,
+so the CUDA path and the CPU oracle can both start from exactly the same
+bytes.  The workloads stand in for the paper's foaming cases (Sec. 4.4:
+nucleated bubbles in a liquid below a headspace); the paper used no public
+dataset.
+
+Conventions: cells are indexed ``n = x + nx*(y + ny*z)``; the up axis is y
+in 2D and z in 3D; ``walls`` is a bitmask over the faces -x,+x,-y,+y,-z,+z.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+DEFAULT_SEED = 20190812
+
+BASE = dict(
+    nx=32, ny=32, nz=1, storage="fp64",
+    tau=0.8, rho0=1.0, accel=(0.0, 0.0, 0.0),
+    rheo=0, rheo_n=1.0, rheo_k=0.0, rheo_lambda=0.0, rheo_a=2.0,
+    tau0=0.8, tau_inf=0.505, tau_min=0.505, tau_max=2.0,
+    sigma=0.0, k_pi=0.0, d_max=4.0,
+    D=0.05, kH=0.0, RT=1.0, c0=0.0, q=0.0, p0=1.0 / 3.0,
+    fill_height=1e9, walls=0, wall_u=(0.0, 0.0, 0.0),
+    atmosphere=1, eps=1e-3, bubble_capacity=4096,
+)
+
+RHEO = {"newtonian": 0, "powerlaw": 1, "carreau": 2}
+
+
+def config(**kw) -> dict:
+    c = dict(BASE)
+    c.update(kw)
+    return c
+
+
+def powerlaw_k(n: float, tau_ref: float = 0.7, shear_ref: float = 1e-3) -> float:
+    """Consistency k of a power-law fluid whose relaxation time is ``tau_ref``
+    at shear rate ``shear_ref`` (lattice units, c_s^2 = 1/3)."""
+    return (tau_ref - 0.5) / 3.0 * shear_ref ** (1.0 - n)
+
+
+# ---------------------------------------------------------------------------
+# nucleus placement
+
+
+def uniform_spheres(rng, n, box_lo, box_hi, rmin, rmax, min_spacing, max_tries=200000):
+    """Uniform random centres by rejection with a minimum centre spacing."""
+    lo, hi = np.asarray(box_lo, float), np.asarray(box_hi, float)
+    pts, rad = [], []
+    tries = 0
+    while len(pts) < n and tries < max_tries:
+        tries += 1
+        r = rng.uniform(rmin, rmax)
+        p = lo + r + rng.random(lo.size) * (hi - lo - 2 * r)
+        if all(np.linalg.norm(p - q) >= min_spacing for q in pts):
+            pts.append(p)
+            rad.append(r)
+    if len(pts) < n:
+        raise RuntimeError("could not place %d spheres" % n)
+    return np.array(pts), np.array(rad)
+
+
+def poisson_disk(rng, n, box_lo, box_hi, min_dist, rmin, rmax, max_tries=2000000):
+    """Dart-throwing Poisson-disk sampling (minimum distance ``min_dist``)
+    with a uniform grid for neighbour look-up; radii uniform in [rmin, rmax]
+    and every sphere kept inside the box."""
+    lo, hi = np.asarray(box_lo, float), np.asarray(box_hi, float)
+    dim = lo.size
+    cell = min_dist / math.sqrt(dim)
+    shape = np.maximum(1, np.ceil((hi - lo) / cell).astype(int))
+    grid = {}
+    pts, rad = [], []
+    tries = 0
+    reach = int(math.ceil(min_dist / cell))
+    while len(pts) < n and tries < max_tries:
+        tries += 1
+        r = rng.uniform(rmin, rmax)
+        p = lo + r + rng.random(dim) * (hi - lo - 2 * r)
+        g = tuple(np.minimum(((p - lo) / cell).astype(int), shape - 1))
+        ok = True
+        ranges = [range(max(0, g[d] - reach), min(shape[d], g[d] + reach + 1)) for d in range(dim)]
+        for idx in np.stack(np.meshgrid(*ranges, indexing="ij"), -1).reshape(-1, dim):
+            j = grid.get(tuple(idx))
+            if j is not None and np.linalg.norm(pts[j] - p) < min_dist:
+                ok = False
+                break
+        if not ok:
+            continue
+        if tuple(g) in grid:
+            continue
+        grid[tuple(g)] = len(pts)
+        pts.append(p)
+        rad.append(r)
+    if len(pts) < n:
+        raise RuntimeError("poisson_disk placed %d of %d" % (len(pts), n))
+    return np.array(pts), np.array(rad)
+
+
+def as3(pts):
+    pts = np.asarray(pts, float)
+    if pts.shape[1] == 2:
+        pts = np.concatenate([pts, np.zeros((len(pts), 1))], axis=1)
+    return pts
+
+
+# ---------------------------------------------------------------------------
+# the workloads
+
+
+def c1_2d_128_fp64() -> tuple[dict, np.ndarray, np.ndarray]:
+    """2D D2Q9, 128x128, FP64: free surface at y = 112, one bubble of radius 8
+    at the domain centre; tau 0.8, sigma 0.01, D2Q5 gas with c0 = 1, kH = 0.5,
+    D = 0.05."""
+    cfg = config(nx=128, ny=128, nz=1, storage="fp64", tau=0.8, sigma=0.01, k_pi=0.0,
+                 D=0.05, kH=0.5, c0=1.0, RT=0.1, fill_height=112.0, walls=0xF)
+    return cfg, np.array([[64.0, 64.0, 0.0]]), np.array([8.0])
+
+
+def _c2_physics(**kw):
+    n = 0.6
+    return config(storage="fp32", rheo=RHEO["powerlaw"], rheo_n=n, rheo_k=powerlaw_k(n),
+                  tau=0.7, sigma=5e-3, d_max=3.0, k_pi=1e-3 / 3.0, D=0.02, kH=0.5, c0=1.0,
+                  RT=0.1, walls=0x3F, **kw)
+
+
+def c2_3d_128_fp32(seed=DEFAULT_SEED):
+    """3D D3Q19, 128^3, FP32: 8 bubbles, uniform random centres (spacing >= 20),
+    radii U[4,6]; power-law n = 0.6 with tau = 0.7 at shear rate 1e-3;
+    disjoining pressure (Pi_max 1e-3, cutoff 3); D3Q7 gas c0 = 1, kH = 0.5,
+    D = 0.02.  Liquid fills 3/4 of the height."""
+    n = 128
+    cfg = _c2_physics(nx=n, ny=n, nz=n, fill_height=0.75 * n)
+    rng = np.random.default_rng(seed)
+    pts, rad = uniform_spheres(rng, 8, (3, 3, 3), (n - 3, n - 3, 0.75 * n - 3), 4.0, 6.0, 20.0)
+    return cfg, pts, rad
+
+
+def c2_crop_3d_32(seed=DEFAULT_SEED, storage="fp32"):
+    """32^3 lattice with the physics of the 128^3 case and one bubble of
+    radius 5, for element-wise comparison with the oracle."""
+    n = 32
+    cfg = _c2_physics(nx=n, ny=n, nz=n, fill_height=0.75 * n)
+    cfg["storage"] = storage
+    rng = np.random.default_rng(seed)
+    c = np.array([[16.0, 16.0, 12.0]]) + rng.uniform(-0.5, 0.5, (1, 3))
+    return cfg, c, np.array([5.0])
+
+
+def c3_3d_256_fp16s(seed=DEFAULT_SEED):
+    """3D D3Q19, 256^3, shifted-FP16 storage: 200 Poisson-disk nuclei (min
+    distance 8), radii U[2,4], nucleation times U[0,5000]; Carreau fluid
+    n = 0.5, lambda = 50 (a = 2, tau0 = 0.8, tau_inf = 0.505)."""
+    n = 256
+    cfg = config(nx=n, ny=n, nz=n, storage="fp16s", rheo=RHEO["carreau"], rheo_n=0.5,
+                 rheo_lambda=50.0, rheo_a=2.0, tau0=0.8, tau_inf=0.505, tau=0.8,
+                 sigma=5e-3, d_max=3.0, k_pi=1e-3 / 3.0, D=0.02, kH=0.5, c0=1.0, RT=0.1,
+                 walls=0x3F, fill_height=0.75 * n)
+    rng = np.random.default_rng(seed)
+    pts, rad = poisson_disk(rng, 200, (2, 2, 2), (n - 2, n - 2, 0.75 * n - 3), 8.0, 2.0, 4.0)
+    times = np.sort(rng.integers(0, 5001, size=200))
+    return cfg, pts, rad, times
+
+
+def c5_3d_512x512x384_bf16s(seed=DEFAULT_SEED):
+    """3D D3Q19, 512x512x384, shifted-BF16 storage: 2000 Poisson-disk nuclei
+    (min distance 10), radii U[2,4]; power-law n = 0.7."""
+    nx, ny, nz = 512, 512, 384
+    n = 0.7
+    cfg = config(nx=nx, ny=ny, nz=nz, storage="bf16s", rheo=RHEO["powerlaw"], rheo_n=n,
+                 rheo_k=powerlaw_k(n), tau=0.7, sigma=5e-3, d_max=3.0, k_pi=1e-3 / 3.0,
+                 D=0.02, kH=0.5, c0=1.0, RT=0.1, walls=0x3F, fill_height=0.75 * nz)
+    rng = np.random.default_rng(seed)
+    pts, rad = poisson_disk(rng, 2000, (2, 2, 2), (nx - 2, ny - 2, 0.75 * nz - 3), 10.0, 2.0, 4.0)
+    return cfg, pts, rad
+
+
+def random_flow_state(cfg: dict, seed: int, du: float = 0.02, drho: float = 0.01):
+    """Seeded random density/velocity perturbation of an all-liquid lattice,
+    for driving every population through the collision."""
+    rng = np.random.default_rng(seed)
+    N = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    rho = cfg["rho0"] + drho * (rng.random(N) - 0.5)
+    u = du * (rng.random((N, 3)) - 0.5)
+    if cfg["nz"] == 1:
+        u[:, 2] = 0.0
+    conc = cfg["c0"] + 0.1 * rng.random(N)
+    return rho, u, conc
