@@ -1,0 +1,308 @@
+#!/usr/bin/env python3
+"""Throughput of the full free-surface foaming step on GB300.
+
+One step = the whole per-timestep sweep: interface mass exchange, fused
+stream/collide/reconstruct/ADE, conversion with excess redistribution,
+union-find bubble labelling, bubble table update (ideal gas), normals /
+curvature / PLIC, disjoining pressure.
+
+Workload: the 128^3 D3Q19 + D3Q7 case (FP32 storage, 8 bubbles, power-law
+fluid, disjoining pressure on), seeded synthetic inputs.  Metric: MLUPS over
+all lattice cells.  Populations (217 MB) exceed the 129 MB L2, so no flush
+is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (the step has no
+cross-GPU exchange); value = cells x steps of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (D3Q19 FSLBM + D3Q7 ADE) and % HBM roofline; FP16+learned-κ vs FP32 plain"
+WORKLOAD = "3D D3Q19 FSLBM + D3Q7 ADE, 128^3, FP32 storage, 8 bubbles (R 4-6), power-law n=0.6, disjoining on"
+KERNELS_PER_STEP = 14  # exchange 1, sweep 1, conversion 4, labelling 5, bubble update 1, geometry 1, disjoining 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+def start_clocks(gpu: int):
+    fd, path = tempfile.mkstemp(suffix=".csv")
+    os.close(fd)
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except Exception:
+        proc = None
+    return proc, path
+
+
+def stop_clocks(proc, path):
+    if proc is not None:
+        time.sleep(0.25)
+        proc.terminate()
+        try:
+            proc.wait(timeout=5)
+        except Exception:
+            proc.kill()
+    rows = []
+    try:
+        for line in open(path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(path)
+    except Exception:
+        pass
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes_sweep(counts, storage_bytes, arith_bytes, Q=19, QA=7):
+    """Bytes the fused sweep must move in one launch: every liquid or
+    interface cell reads and writes its Q + QA populations once; every cell's
+    flag byte is read; interface cells also read u_I (3), kappa, Pi, M, alpha
+    and write alpha and their flag byte."""
+    gas, liq, ifc, wall = [float(x) for x in counts]
+    N = gas + liq + ifc + wall
+    fluid = liq + ifc
+    return fluid * 2 * (Q + QA) * storage_bytes + N * 1 + ifc * (8 * arith_bytes + 1)
+
+
+def reduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def cpu_baseline_oracle(cfg, pts, rad, steps=1):
+    """The FP64 CPU oracle, as it stands, on the same 128^3 workload:
+    construction and nucleation untimed, `steps` full steps timed."""
+    import oracle
+
+    ora = oracle.OracleSim(cfg)
+    ora.nucleate(pts, rad)
+    t0 = time.perf_counter()
+    ora.step(steps)
+    dt = time.perf_counter() - t0
+    N = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    return {"value": N * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%d full step(s) of the 128^3 workload (%.1f s, single thread)" % (steps, dt)}
+
+
+def reference_sample_cfg():
+    """Bounded sample of the workload for the oracle: the same physics on a
+    64^3 lattice with one bubble (same seed)."""
+    from paper_1908_04262_gb300 import workloads as W
+
+    cfg, c, r = W.c2_crop_3d_32()
+    n = 64
+    cfg.update(nx=n, ny=n, nz=n, fill_height=0.75 * n)
+    return cfg, [[32.0 + c[0][0] - 16.0, 32.0 + c[0][1] - 16.0, 24.0 + c[0][2] - 12.0]], list(r)
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    cfg, c, r = reference_sample_cfg()
+    ora = oracle.OracleSim(cfg)
+    ora.nucleate(c, r)
+    ora.step(args.warmup)
+    t0 = time.perf_counter()
+    ora.step(args.steps)
+    dt = time.perf_counter() - t0
+    N = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    v = N * args.steps / dt / 1e6
+    sample = "each step: one oracle step of the workload's physics on a 64^3 lattice with one bubble"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    from paper_1908_04262_gb300 import build as B
+
+    if rank == 0:
+        B.build()
+    barrier(world)
+    from paper_1908_04262_gb300 import lbf
+    from paper_1908_04262_gb300 import workloads as W
+
+    cfg, pts, rad = W.c2_3d_128_fp32()
+    N = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    stream = torch.cuda.Stream()
+    sim = lbf.Sim(cfg, stream=stream.cuda_stream)
+    sim.nucleate(pts, rad)
+    sim.step(args.warmup)
+    counts0 = sim.cell_counts()
+
+    # --- timed region: device-resident state, CUDA-graph step ------------
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = start_clocks(local_rank)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = stop_clocks(*clk)
+    ms = reduce_max(e0.elapsed_time(e1), world)
+    counts1 = sim.cell_counts()
+    value = N * args.steps * world / (ms / 1e3) / 1e6
+
+    # --- kernel timing (CUDA events around every kernel group) -----------
+    kp = max(50, min(args.steps, 400))
+    sim.timing_enable(True)
+    ca = sim.cell_counts()
+    sim.step(kp)
+    groups = sim.timing_read()
+    cb = sim.cell_counts()
+    sim.timing_enable(False)
+    sweep_ms, sweep_n = groups["stream_collide"]
+    avg_counts = (np.asarray(ca, float) + np.asarray(cb, float)) / 2
+    bytes_sweep = algorithmic_bytes_sweep(avg_counts, 4, 4)
+    achieved = bytes_sweep / (sweep_ms / sweep_n / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    total_ms = sum(v[0] for v in groups.values())
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_stream_collide<3,float> (fused sweep)",
+                "bytes_per_launch": bytes_sweep, "launch_ms": sweep_ms / sweep_n,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                "sweep_share_of_step": sweep_ms / total_ms if total_ms > 0 else None}
+    kernel_ms = {k: v[0] / max(v[1], 1) for k, v in groups.items()}
+
+    # --- end to end through the public API with host buffers -------------
+    f = sim.fields(["flags", "rho", "u", "alpha", "conc"])
+    pinned = {}
+    for k, v in f.items():
+        t = torch.empty(v.size, dtype=torch.uint8 if k == "flags" else torch.float64, pin_memory=True)
+        t.numpy()[:] = v.reshape(-1).astype(np.uint8 if k == "flags" else np.float64)
+        pinned[k] = t.numpy()
+    h2d = N * (1 + 8 + 24 + 8 + 8)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    sim.set_cells(pinned["flags"], pinned["rho"], pinned["u"], pinned["alpha"], pinned["conc"])
+    nb_rows = 0
+    for _ in range(args.steps):
+        sim.step(1)
+        nb_rows = len(sim.bubbles()["id"])
+    out = sim.fields(["rho", "alpha", "flags"])
+    torch.cuda.synchronize()
+    t_e2e = reduce_max(time.perf_counter() - t0, world)
+    e2e = {"value": N * args.steps * world / t_e2e / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": h2d / args.steps,
+           "d2h_bytes_per_step": 40 * nb_rows + N * (8 + 8 + 4) / args.steps,
+           "note": "lbf_set_cells from pinned host arrays, then per step lbf_step(1) + lbf_bubbles, "
+                   "then lbf_fields(rho, alpha, flags) to host"}
+    del out
+
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": N, "seed": W.DEFAULT_SEED,
+                       "l2": "inputs larger than L2: 217 MB of populations per replica",
+                       "parallelism": "replicas x%d" % world,
+                       "cells_gas_liquid_interface_wall": [int(x) for x in counts1]},
+            "roofline": roofline, "kernel_ms": kernel_ms,
+            "fluid_mlups": (counts0[1] + counts0[2]) * args.steps * world / (ms / 1e3) / 1e6,
+            "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clocks, "e2e": e2e}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_oracle(cfg, pts, rad)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * lbf.h -- C ABI of the GB300 (sm_103a) free-surface lattice Boltzmann
+ * foaming step (LBfoam, arXiv 1908.04262).
+ *
+ * One lbf_sim owns one lattice on one GPU: populations of the flow
+ * (D2Q9 / D3Q19, Sec. 2) and of the dissolved gas (D2Q5 / D3Q7, Sec. 3.1),
+ * cell types and fill levels (Sec. 2.1), bubble labels and the bubble table
+ * (Sec. 2.2 Eq. idealgas, Sec. 3.5), curvature and disjoining pressure
+ * (Sec. 2.2 Eq. rhob, Sec. 3.3).  All device memory is owned by the library.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: 0 on success, a negative LBF_E* code on failure; the
+ *    message of the last failure on the calling thread is lbf_last_error().
+ *  - Cells are indexed n = x + nx*(y + ny*z); the up axis is y in 2D
+ *    (nz == 1) and z in 3D.  Every face is periodic unless its bit is set in
+ *    cfg.walls (bit 0 -x, 1 +x, 2 -y, 3 +y, 4 -z, 5 +z), which turns the
+ *    outermost layer of that face into half-way bounce-back walls (Sec. 2).
+ *  - Work is queued on cfg.stream (a cudaStream_t; NULL = the legacy default
+ *    stream).  Calls that return host data synchronise that stream.
+ *  - A lbf_sim is not thread-safe; distinct lbf_sim objects are independent.
+ *  - Host pointers are plain pageable or pinned memory owned by the caller;
+ *    device pointers must be on the lbf_sim's device and stay valid for the
+ *    duration of the call (work on them is complete when the call returns).
+ */
+#ifndef LBF_H
+#define LBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define LBF_OK 0
+#define LBF_EINVAL (-1)     /* bad argument or configuration                  */
+#define LBF_ENOMEM (-2)     /* device allocation failed                       */
+#define LBF_ECUDA (-3)      /* a CUDA runtime call failed                     */
+#define LBF_ENOTCONV (-4)   /* union-find iteration cap reached               */
+#define LBF_ENONFINITE (-5) /* non-finite populations found by lbf_ledger     */
+#define LBF_ECAPACITY (-6)  /* more bubbles than cfg.bubble_capacity          */
+
+typedef struct lbf_sim lbf_sim;
+
+/* population storage (the arithmetic type follows in brackets):
+ * FP64 [f64], FP32 [f32], FP16S / BF16S: populations stored as f - w_i
+ * (and g - w_i c0) in binary16 / bfloat16 [f32] */
+typedef enum { LBF_FP64 = 0, LBF_FP32 = 1, LBF_FP16S = 2, LBF_BF16S = 3 } lbf_storage;
+typedef enum { LBF_NEWTONIAN = 0, LBF_POWERLAW = 1, LBF_CARREAU_YASUDA = 2 } lbf_rheology;
+
+typedef struct {
+  int nx, ny, nz;           /* lattice; nz == 1 selects D2Q9 + D2Q5            */
+  int storage;              /* lbf_storage                                      */
+  double tau, rho0;         /* Newtonian relaxation time (Sec. 2.3 Eq. tau)     */
+  double accel[3];          /* body acceleration (Guo forcing)                  */
+  int rheo;                 /* lbf_rheology (Sec. 2.3)                           */
+  double rheo_n, rheo_k;    /* power law: nu = k gamma_dot^(n-1)                */
+  double rheo_lambda, rheo_a, tau0, tau_inf; /* Carreau-Yasuda, Eq. carreauTau */
+  double tau_min, tau_max;  /* clamp of the local relaxation time               */
+  double sigma;             /* surface tension gamma (Eq. rhob)                  */
+  double k_pi, d_max;       /* disjoining pressure slope and range (Sec. 3.3)   */
+  double D, kH, RT, c0, q, p0; /* diffusivity, Henry constant, gas constant x
+                                  temperature, initial concentration, source,
+                                  ambient pressure (Sec. 3.1-3.2)               */
+  double fill_height;       /* initial liquid below this height (up axis)      */
+  int walls;                /* bounce-back faces, see above                     */
+  double wall_u[3];         /* velocity of the walls of the +y face             */
+  int atmosphere;           /* 1: gas touching the top interior layer is held
+                               at p0 (the headspace)                            */
+  double eps;               /* conversion margin: fill when alpha > 1 + eps,
+                               empty when alpha < -eps (Sec. 2.1)               */
+  int bubble_capacity;      /* maximum number of bubbles (<= 16384)             */
+  void *stream;             /* cudaStream_t used by every call                  */
+} lbf_config;
+
+/* one row of the bubble table */
+typedef struct {
+  int32_t id;        /* stable id: kept through growth; merges keep the
+                        smallest id, the largest piece of a split keeps it  */
+  int32_t atm;       /* 1 for the atmosphere (held at p0)                   */
+  int64_t label;     /* canonical label: smallest linear index of its gas  */
+  double volume;     /* gas cells + sum of (1 - alpha) of interface cells   */
+  double gas_mass;   /* m_g (Eq. idealgas)                                  */
+  double pressure;   /* p_g = m_g RT / V (Eq. idealgas)                     */
+} lbf_bubble;
+
+/* Sec. 2-3: allocate and initialise a lattice: liquid below fill_height
+ * at rest (f = f_eq(rho0, 0), g = g_eq(c0, 0)), walls, headspace; labels
+ * bubbles and computes the geometry.  *out receives the handle.
+ * Errors: LBF_EINVAL (sizes <= 0, more than 2^31-1 cells, bad enums, tau or
+ * tau_min <= 1/2, capacity outside [1, 16384]), LBF_ENOMEM, LBF_ECUDA. */
+int lbf_create(const lbf_config *cfg, lbf_sim **out);
+
+/* Release every resource; NULL is ignored. */
+void lbf_destroy(lbf_sim *s);
+
+/* Sec. 3.4: nucleate n gas spheres (disks in 2D).  centres: host, n x 3
+ * doubles (lattice coordinates, z ignored in 2D); radii: host, n doubles.
+ * at_step: host, n step numbers at which each nucleus appears, or NULL for
+ * "now".  Only liquid cells are carved; a cell's fill level is the fraction
+ * of its 4^d sub-cell points outside the sphere.  A new bubble starts in
+ * Laplace equilibrium, p = p0 + (d-1) sigma / R_eq.
+ * Errors: LBF_EINVAL (n < 0, NULL arrays, radius <= 0, step in the past). */
+int lbf_nucleate(lbf_sim *s, int n, const double *centres, const double *radii,
+                 const long long *at_step);
+
+/* Replace the state from host arrays of N cells: type (0 gas, 1 liquid,
+ * 2 interface, 3 wall), rho, u (3 doubles per cell), alpha (fill level of
+ * interface cells), c (dissolved gas).  Populations are set to equilibrium;
+ * liquid touching gas becomes interface with alpha = 1; every bubble is
+ * new (Laplace equilibrium).  Errors: LBF_EINVAL, LBF_ECUDA. */
+int lbf_set_cells(lbf_sim *s, const uint8_t *type, const double *rho, const double *u,
+                  const double *alpha, const double *c);
+
+/* Advance nsteps full steps: stream/collide/reconstruct/exchange/ADE
+ * (Sec. 2, 2.1, 2.2, 3.1, 3.2), conversion (Sec. 2.1), labelling and bubble
+ * update (Sec. 3.5, Eq. idealgas), curvature and disjoining pressure
+ * (Sec. 2.2, 3.3); nuclei due in the interval are carved at their step.
+ * Synchronises at the end and returns the sticky device error, if any
+ * (LBF_ECAPACITY, LBF_ENOTCONV).  Errors: LBF_EINVAL (nsteps < 0). */
+int lbf_step(lbf_sim *s, int nsteps);
+
+/* Copy the bubble table to host memory: out has room for capacity rows;
+ * *count receives the number of bubbles (rows beyond capacity are dropped).
+ * Synchronises.  Errors: LBF_EINVAL (NULL pointers, capacity < 0). */
+int lbf_bubbles(lbf_sim *s, lbf_bubble *out, int capacity, int *count);
+
+/* field bits for lbf_fields; dst[k] receives the k-th requested field in
+ * bit order; vector fields (U, NORMAL) hold 3 values per cell (x fastest
+ * inside the cell).  RHO, U, CONC are zero outside liquid and interface
+ * cells; FLAGS and LABEL are int32 whatever dtype says. */
+#define LBF_F_RHO (1u << 0)    /* density sum f (Sec. 2)                       */
+#define LBF_F_U (1u << 1)      /* velocity, force-shifted (Sec. 2)             */
+#define LBF_F_ALPHA (1u << 2)  /* fill level (Sec. 2.1 Eq. alpha)              */
+#define LBF_F_MASS (1u << 3)   /* liquid mass M (rho in liquid cells)          */
+#define LBF_F_FLAGS (1u << 4)  /* cell type 0..3                               */
+#define LBF_F_CONC (1u << 5)   /* dissolved gas sum g (Sec. 3.1)               */
+#define LBF_F_KAPPA (1u << 6)  /* curvature (Eq. rhob)                         */
+#define LBF_F_LABEL (1u << 7)  /* bubble index into the table, or -1           */
+#define LBF_F_PI (1u << 8)     /* disjoining pressure (Sec. 3.3)               */
+#define LBF_F_NORMAL (1u << 9) /* interface normal, into the liquid            */
+#define LBF_F_DSTAR (1u << 10) /* PLIC offset of the interface plane           */
+/* Copy the requested fields.  dst_is_device: 1 if every dst[k] is device
+ * memory, 0 for host memory (the call then synchronises).  dtype: 0 float,
+ * 1 double for the floating-point fields.  Errors: LBF_EINVAL. */
+int lbf_fields(lbf_sim *s, unsigned mask, void *const *dst, int dst_is_device, int dtype);
+
+/* FP64 ledgers (synchronises): [0] liquid mass on the lattice (sum of rho
+ * over liquid cells + M over interface cells), [1] excess mass that found
+ * no interface neighbour, [2] liquid removed by nucleation, [3] dissolved
+ * gas, [4] gas in bubbles, [5] gas exchanged with the outside, [6] gas added
+ * by the source term, [7] count of non-finite populations.
+ * Returns LBF_ENONFINITE when [7] > 0. */
+int lbf_ledger(lbf_sim *s, double *out8);
+
+/* Kernel timing for measurements: while enabled, lbf_step launches its
+ * kernels one by one (no CUDA graph) and brackets each with CUDA events on
+ * cfg.stream.  lbf_timing_read sums the device time of every kernel group
+ * since the last enable: out_ms[k] and out_launches[k] for k < nmax, in the
+ * order of lbf_timing_name(k).  Returns the number of groups. */
+int lbf_timing_enable(lbf_sim *s, int enable);
+int lbf_timing_read(lbf_sim *s, double *out_ms, long long *out_launches, int nmax);
+const char *lbf_timing_name(int k);
+
+/* Counts of gas, liquid, interface and wall cells (synchronises). */
+int lbf_cell_counts(lbf_sim *s, long long *out4);
+
+/* Number of completed steps. */
+long long lbf_step_count(const lbf_sim *s);
+
+const char *lbf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,639 @@
+// lbf_abi.cu -- host runtime behind the C ABI of include/lbf.h: device
+// state, the per-step launch sequence (captured once per AA parity into a
+// CUDA graph), the nucleation queue, exports, ledgers and kernel timing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbf.h"
+#include "lbf_ops_api.h"
+
+using namespace lbf;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail(LBF_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+// kernel groups of one step, in launch order
+enum { G_EXCHANGE = 0, G_STREAM, G_CONVERT, G_LABEL, G_BUBBLE, G_GEOMETRY, G_DISJOIN, G_COUNT };
+const char *kGroupNames[G_COUNT] = {"exchange",      "stream_collide", "convert",   "label",
+                                    "bubble_update", "geometry",       "disjoining"};
+
+struct Nucleus {
+  long long step;
+  double c[3], r;
+};
+
+}  // namespace
+
+struct lbf_sim {
+  lbf_config cfg;
+  int dim = 0, Q = 0, QA = 0;
+  long long N = 0;
+  size_t ssz = 0, rsz = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  Ops *ops = nullptr;
+  std::vector<void *> allocs;
+  // device state
+  void *f = nullptr, *g = nullptr;
+  uint8_t *flags[2] = {nullptr, nullptr};
+  void *M = nullptr, *phi = nullptr, *uI = nullptr, *kappa = nullptr, *Pi = nullptr, *nrm = nullptr,
+       *dst = nullptr, *ex = nullptr;
+  int *label[2] = {nullptr, nullptr}, *parent = nullptr, *roots = nullptr, *nroots = nullptr;
+  unsigned long long *hash = nullptr;
+  int hash_size = 0, cap = 0;
+  Table tab[2];
+  int *gpar, *gnold, *gnnew, *gatm, *gminid, *gheir;
+  double *gmold, *gvnew;
+  unsigned long long *gvmax;
+  int *next_id = nullptr;
+  double *led = nullptr;
+  unsigned long long *fluid_updates = nullptr;
+  int *err = nullptr;
+  double *acc = nullptr;
+  unsigned long long *counts = nullptr;
+  void *staging = nullptr;
+  long long step = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  std::vector<Nucleus> queue;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;
+  double t_ms[G_COUNT] = {0};
+  long long t_n[G_COUNT] = {0};
+};
+
+namespace {
+
+int dev_alloc(lbf_sim *s, void **p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) return fail(LBF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  s->allocs.push_back(*p);
+  return 0;
+}
+
+template <class T> int dalloc(lbf_sim *s, T **p, size_t count) {
+  return dev_alloc(s, (void **)p, count * sizeof(T));
+}
+
+// parameters for work at step `step`: par = population parity, flags[par]
+// current, flags[1-par] written by the conversion, labels and tables likewise
+Params make_params(lbf_sim *s, long long step) {
+  const int par = (int)(step & 1);
+  const lbf_config &c = s->cfg;
+  Params p;
+  memset(&p, 0, sizeof p);
+  p.nx = c.nx; p.ny = c.ny; p.nz = c.nz; p.dim = s->dim; p.N = s->N;
+  p.f = s->f; p.g = s->g;
+  p.flags = s->flags[par];
+  p.flags_out = s->flags[1 - par];
+  p.M = s->M; p.phi = s->phi; p.uI = s->uI; p.kappa = s->kappa; p.Pi = s->Pi; p.nrm = s->nrm;
+  p.dst = s->dst; p.ex = s->ex;
+  p.label_old = s->label[par];
+  p.label_new = s->label[1 - par];
+  p.parent = s->parent;
+  p.told = s->tab[par];
+  p.tnew = s->tab[1 - par];
+  p.roots = s->roots; p.nroots = s->nroots; p.hash = s->hash; p.hash_size = s->hash_size; p.cap = s->cap;
+  p.gpar = s->gpar; p.gnold = s->gnold; p.gnnew = s->gnnew; p.gatm = s->gatm; p.gminid = s->gminid;
+  p.gheir = s->gheir; p.gmold = s->gmold; p.gvnew = s->gvnew; p.gvmax = s->gvmax;
+  p.next_id = s->next_id; p.led = s->led; p.fluid_updates = s->fluid_updates; p.err = s->err;
+  p.tau = c.tau; p.rho0 = c.rho0; p.ax = c.accel[0]; p.ay = c.accel[1]; p.az = c.accel[2];
+  p.has_force = (c.accel[0] != 0.0 || c.accel[1] != 0.0 || c.accel[2] != 0.0);
+  p.rheo = c.rheo; p.rn = c.rheo_n; p.rk = c.rheo_k; p.rlam = c.rheo_lambda; p.ra = c.rheo_a;
+  p.tau0 = c.tau0; p.tau_inf = c.tau_inf; p.tau_min = c.tau_min; p.tau_max = c.tau_max;
+  p.sigma = c.sigma; p.k_pi = c.k_pi; p.d_max = c.d_max;
+  p.taug = 0.5 + c.D / (s->dim == 2 ? 1.0 / 3.0 : 0.25);
+  p.kH = c.kH; p.RT = c.RT; p.c0 = c.c0; p.q = c.q; p.p0 = c.p0; p.eps = c.eps;
+  p.uwx = c.wall_u[0]; p.uwy = c.wall_u[1]; p.uwz = c.wall_u[2];
+  p.walls = c.walls; p.atmosphere = c.atmosphere;
+  const int up = s->dim - 1;
+  const int n_up = up == 1 ? c.ny : c.nz;
+  p.top_layer = n_up - 1 - ((c.walls >> (2 * up + 1)) & 1);
+  p.ray_steps = (int)std::ceil(c.d_max) + 1;
+  return p;
+}
+
+// labelling + bubble update + geometry outside the step (create, set_cells,
+// nucleation): the results are copied back into the current buffers
+int relabel_in_place(lbf_sim *s) {
+  const int par = (int)(s->step & 1);
+  Params p = make_params(s, s->step);
+  p.flags_out = s->flags[par];
+  s->ops->uf_init(p, s->st);
+  s->ops->label(p, s->st);
+  s->ops->bubble_update(p, s->st);
+  const size_t cap = (size_t)s->cap;
+  Table &a = s->tab[par], &b = s->tab[1 - par];
+  CK(cudaMemcpyAsync(s->label[par], s->label[1 - par], sizeof(int) * s->N, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaMemcpyAsync(a.m, b.m, sizeof(double) * cap, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaMemcpyAsync(a.p, b.p, sizeof(double) * cap, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaMemcpyAsync(a.V, b.V, sizeof(double) * cap, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaMemcpyAsync(a.dm, b.dm, sizeof(double) * cap, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaMemcpyAsync(a.id, b.id, sizeof(int) * cap, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaMemcpyAsync(a.atm, b.atm, sizeof(int) * cap, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaMemcpyAsync(a.root, b.root, sizeof(int) * cap, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaMemcpyAsync(a.count, b.count, sizeof(int), cudaMemcpyDeviceToDevice, s->st));
+  p.label_new = s->label[par];
+  s->ops->geometry(p, s->st);
+  s->ops->disjoining(p, s->st);
+  CK(cudaGetLastError());
+  return 0;
+}
+
+int separate_and_relabel(lbf_sim *s) {
+  const int par = (int)(s->step & 1);
+  Params p = make_params(s, s->step);
+  s->ops->separate(p, par, s->st);
+  CK(cudaGetLastError());
+  return relabel_in_place(s);
+}
+
+cudaEvent_t next_event(lbf_sim *s) {
+  if (s->ev_used == s->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    s->ev_pool.push_back(e);
+  }
+  return s->ev_pool[s->ev_used++];
+}
+
+// the launch sequence of one step
+void enqueue_step(lbf_sim *s, const Params &p, int par, bool timed) {
+  auto group = [&](int gidx, auto &&fn) {
+    if (timed) {
+      cudaEvent_t a = next_event(s), b = next_event(s);
+      cudaEventRecord(a, s->st);
+      fn();
+      cudaEventRecord(b, s->st);
+      s->ev_marks.push_back({gidx, {a, b}});
+    } else {
+      fn();
+    }
+  };
+  group(G_EXCHANGE, [&] { s->ops->exchange(p, par, s->st); });
+  group(G_STREAM, [&] { s->ops->stream_collide(p, par, s->st); });
+  group(G_CONVERT, [&] { s->ops->convert(p, par, s->st); });
+  group(G_LABEL, [&] { s->ops->label(p, s->st); });
+  group(G_BUBBLE, [&] { s->ops->bubble_update(p, s->st); });
+  group(G_GEOMETRY, [&] { s->ops->geometry(p, s->st); });
+  group(G_DISJOIN, [&] { s->ops->disjoining(p, s->st); });
+}
+
+int harvest_timing(lbf_sim *s) {
+  if (s->ev_marks.empty()) return 0;
+  CK(cudaStreamSynchronize(s->st));
+  for (auto &m : s->ev_marks) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, m.second.first, m.second.second));
+    s->t_ms[m.first] += ms;
+    s->t_n[m.first] += 1;
+  }
+  s->ev_marks.clear();
+  s->ev_used = 0;
+  return 0;
+}
+
+int run_one_step(lbf_sim *s) {
+  const int par = (int)(s->step & 1);
+  Params p = make_params(s, s->step);
+  if (s->timing) {
+    enqueue_step(s, p, par, true);
+    CK(cudaGetLastError());
+    if (s->ev_marks.size() > 4096) {
+      int rc = harvest_timing(s);
+      if (rc) return rc;
+    }
+    return 0;
+  }
+  if (!s->graph[par]) {
+    cudaGraph_t gr;
+    CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+    enqueue_step(s, p, par, false);
+    CK(cudaStreamEndCapture(s->st, &gr));
+    cudaError_t e = cudaGraphInstantiate(&s->graph[par], gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return fail(LBF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  CK(cudaGraphLaunch(s->graph[par], s->st));
+  return 0;
+}
+
+int carve_due_nuclei(lbf_sim *s) {
+  bool any = false;
+  const int par = (int)(s->step & 1);
+  Params p = make_params(s, s->step);
+  std::vector<Nucleus> keep;
+  for (auto &nu : s->queue) {
+    if (nu.step <= s->step) {
+      s->ops->nucleate(p, par, nu.c, nu.r, s->st);
+      any = true;
+    } else {
+      keep.push_back(nu);
+    }
+  }
+  s->queue.swap(keep);
+  if (!any) return 0;
+  CK(cudaGetLastError());
+  return separate_and_relabel(s);
+}
+
+int check_device_error(lbf_sim *s) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  if (e & ERR_CAPACITY) return fail(LBF_ECAPACITY, "more bubbles than bubble_capacity");
+  if (e & ERR_NOTCONV) return fail(LBF_ENOTCONV, "union-find iteration cap reached");
+  if (e & ERR_HASH) return fail(LBF_ECAPACITY, "bubble overlap table full");
+  return 0;
+}
+
+int validate(const lbf_config *c) {
+  if (!c) return fail(LBF_EINVAL, "cfg is NULL");
+  if (c->nx <= 0 || c->ny <= 0 || c->nz <= 0) return fail(LBF_EINVAL, "lattice sizes must be positive");
+  if ((long long)c->nx * c->ny * c->nz > 2147483647LL) return fail(LBF_EINVAL, "more than 2^31-1 cells");
+  if (c->nx < 3 || c->ny < 3 || (c->nz != 1 && c->nz < 3)) return fail(LBF_EINVAL, "each extent must be >= 3 (nz == 1 for 2D)");
+  if (c->storage < 0 || c->storage > 3) return fail(LBF_EINVAL, "bad storage");
+  if (c->rheo < 0 || c->rheo > 2) return fail(LBF_EINVAL, "bad rheology");
+  if (!(c->tau > 0.5)) return fail(LBF_EINVAL, "tau must exceed 1/2");
+  if (c->rheo != 0 && !(c->tau_min > 0.5 && c->tau_max > c->tau_min)) return fail(LBF_EINVAL, "need 1/2 < tau_min < tau_max");
+  if (!(c->D > 0.0)) return fail(LBF_EINVAL, "D must be positive");
+  if (!(c->RT > 0.0) || !(c->rho0 > 0.0)) return fail(LBF_EINVAL, "RT and rho0 must be positive");
+  if (c->bubble_capacity < 1 || c->bubble_capacity > 16384) return fail(LBF_EINVAL, "bubble_capacity must be in [1, 16384]");
+  if (c->k_pi != 0.0 && !(c->d_max > 0.0 && c->d_max <= 64.0)) return fail(LBF_EINVAL, "d_max must be in (0, 64]");
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbf_last_error(void) { return g_err.c_str(); }
+
+void lbf_destroy(lbf_sim *s) {
+  if (!s) return;
+  if (s->st) cudaStreamSynchronize(s->st);
+  for (int k = 0; k < 2; ++k)
+    if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
+  for (auto e : s->ev_pool) cudaEventDestroy(e);
+  for (void *p : s->allocs) cudaFree(p);
+  if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+  delete s->ops;
+  delete s;
+}
+
+int lbf_create(const lbf_config *cfg, lbf_sim **out) {
+  if (!out) return fail(LBF_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc) return rc;
+  lbf_sim *s = new lbf_sim();
+  s->cfg = *cfg;
+  s->dim = cfg->nz == 1 ? 2 : 3;
+  s->Q = s->dim == 2 ? 9 : 19;
+  s->QA = s->dim == 2 ? 5 : 7;
+  s->N = (long long)cfg->nx * cfg->ny * cfg->nz;
+  static const size_t ssz[4] = {8, 4, 2, 2};
+  s->ssz = ssz[cfg->storage];
+  s->rsz = cfg->storage == LBF_FP64 ? 8 : 4;
+  switch (cfg->storage) {
+    case LBF_FP64: s->ops = make_ops_f64(s->dim); break;
+    case LBF_FP32: s->ops = make_ops_f32(s->dim); break;
+    case LBF_FP16S: s->ops = make_ops_f16(s->dim); break;
+    default: s->ops = make_ops_bf16(s->dim); break;
+  }
+  if (cfg->stream) {
+    s->st = (cudaStream_t)cfg->stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete s->ops;
+      delete s;
+      return fail(LBF_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    s->own_stream = true;
+  }
+  const size_t N = (size_t)s->N;
+  s->cap = cfg->bubble_capacity;
+  int hs = 1024;
+  while (hs < 4 * s->cap) hs <<= 1;
+  s->hash_size = hs;
+#define AL(expr)       \
+  do {                 \
+    rc = (expr);       \
+    if (rc) {          \
+      lbf_destroy(s);  \
+      return rc;       \
+    }                  \
+  } while (0)
+  AL(dev_alloc(s, &s->f, N * s->Q * s->ssz));
+  AL(dev_alloc(s, &s->g, N * s->QA * s->ssz));
+  AL(dalloc(s, &s->flags[0], N));
+  AL(dalloc(s, &s->flags[1], N));
+  AL(dev_alloc(s, &s->M, N * s->rsz));
+  AL(dev_alloc(s, &s->phi, N * s->rsz));
+  AL(dev_alloc(s, &s->uI, 3 * N * s->rsz));
+  AL(dev_alloc(s, &s->kappa, N * s->rsz));
+  AL(dev_alloc(s, &s->Pi, N * s->rsz));
+  AL(dev_alloc(s, &s->nrm, 3 * N * s->rsz));
+  AL(dev_alloc(s, &s->dst, N * s->rsz));
+  AL(dev_alloc(s, &s->ex, N * s->rsz));
+  AL(dalloc(s, &s->label[0], N));
+  AL(dalloc(s, &s->label[1], N));
+  AL(dalloc(s, &s->parent, N));
+  AL(dalloc(s, &s->roots, (size_t)s->cap));
+  AL(dalloc(s, &s->nroots, 1));
+  AL(dalloc(s, &s->hash, (size_t)hs));
+  for (int k = 0; k < 2; ++k) {
+    Table &t = s->tab[k];
+    AL(dalloc(s, &t.m, s->cap));
+    AL(dalloc(s, &t.p, s->cap));
+    AL(dalloc(s, &t.V, s->cap));
+    AL(dalloc(s, &t.dm, s->cap));
+    AL(dalloc(s, &t.id, s->cap));
+    AL(dalloc(s, &t.atm, s->cap));
+    AL(dalloc(s, &t.root, s->cap));
+    AL(dalloc(s, &t.count, 1));
+  }
+  const size_t G2 = 2 * (size_t)s->cap;
+  AL(dalloc(s, &s->gpar, G2));
+  AL(dalloc(s, &s->gnold, G2));
+  AL(dalloc(s, &s->gnnew, G2));
+  AL(dalloc(s, &s->gatm, G2));
+  AL(dalloc(s, &s->gminid, G2));
+  AL(dalloc(s, &s->gheir, G2));
+  AL(dalloc(s, &s->gmold, G2));
+  AL(dalloc(s, &s->gvnew, G2));
+  AL(dalloc(s, &s->gvmax, G2));
+  AL(dalloc(s, &s->next_id, 1));
+  AL(dalloc(s, &s->led, 8));
+  AL(dalloc(s, &s->fluid_updates, 1));
+  AL(dalloc(s, &s->err, 1));
+  AL(dalloc(s, &s->acc, 4));
+  AL(dalloc(s, &s->counts, 4));
+#undef AL
+  // zero everything that is read before being written
+  auto zero = [&](void *p, size_t b) { return cudaMemsetAsync(p, 0, b, s->st); };
+  cudaError_t e = cudaSuccess;
+  e = e ? e : zero(s->f, N * s->Q * s->ssz);
+  e = e ? e : zero(s->g, N * s->QA * s->ssz);
+  e = e ? e : zero(s->kappa, N * s->rsz);
+  e = e ? e : zero(s->Pi, N * s->rsz);
+  e = e ? e : zero(s->uI, 3 * N * s->rsz);
+  e = e ? e : zero(s->ex, N * s->rsz);
+  e = e ? e : cudaMemsetAsync(s->label[0], 0xff, sizeof(int) * N, s->st);
+  e = e ? e : cudaMemsetAsync(s->label[1], 0xff, sizeof(int) * N, s->st);
+  e = e ? e : cudaMemsetAsync(s->hash, 0xff, sizeof(unsigned long long) * hs, s->st);
+  for (int k = 0; k < 2; ++k) {
+    e = e ? e : zero(s->tab[k].count, sizeof(int));
+    e = e ? e : zero(s->tab[k].dm, sizeof(double) * s->cap);
+  }
+  e = e ? e : zero(s->next_id, sizeof(int));
+  e = e ? e : zero(s->led, 8 * sizeof(double));
+  e = e ? e : zero(s->fluid_updates, sizeof(unsigned long long));
+  e = e ? e : zero(s->err, sizeof(int));
+  if (e != cudaSuccess) {
+    lbf_destroy(s);
+    return fail(LBF_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  }
+  Params p = make_params(s, 0);
+  s->ops->init_fill(p, 0, cfg->fill_height, s->st);
+  s->ops->nearwall(p, s->st);
+  rc = separate_and_relabel(s);
+  if (!rc) rc = check_device_error(s);
+  if (rc) {
+    std::string msg = g_err;
+    lbf_destroy(s);
+    return fail(rc, msg);
+  }
+  *out = s;
+  return 0;
+}
+
+int lbf_nucleate(lbf_sim *s, int n, const double *centres, const double *radii, const long long *at_step) {
+  if (!s || n < 0 || (n > 0 && (!centres || !radii))) return fail(LBF_EINVAL, "bad arguments");
+  for (int k = 0; k < n; ++k) {
+    if (!(radii[k] > 0.0)) return fail(LBF_EINVAL, "radius must be positive");
+    if (at_step && at_step[k] < s->step) return fail(LBF_EINVAL, "nucleation step is in the past");
+  }
+  for (int k = 0; k < n; ++k) {
+    Nucleus nu;
+    nu.step = at_step ? at_step[k] : s->step;
+    nu.c[0] = centres[3 * k];
+    nu.c[1] = centres[3 * k + 1];
+    nu.c[2] = s->dim == 3 ? centres[3 * k + 2] : 0.0;
+    nu.r = radii[k];
+    s->queue.push_back(nu);
+  }
+  std::stable_sort(s->queue.begin(), s->queue.end(),
+                   [](const Nucleus &a, const Nucleus &b) { return a.step < b.step; });
+  int rc = carve_due_nuclei(s);
+  if (rc) return rc;
+  return check_device_error(s);
+}
+
+int lbf_set_cells(lbf_sim *s, const uint8_t *type, const double *rho, const double *u, const double *alpha,
+                  const double *c) {
+  if (!s || !type || !rho || !u || !alpha || !c) return fail(LBF_EINVAL, "NULL argument");
+  const size_t N = (size_t)s->N;
+  void *buf = nullptr;
+  const size_t bytes = N + N * 8 * 6 + 64;
+  CK(cudaMallocAsync(&buf, bytes, s->st));
+  uint8_t *dt = (uint8_t *)buf;
+  double *drho = (double *)((char *)buf + ((N + 15) / 16) * 16);
+  double *du = drho + N, *da = du + 3 * N, *dc = da + N;
+  CK(cudaMemcpyAsync(dt, type, N, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(drho, rho, 8 * N, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(du, u, 24 * N, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(da, alpha, 8 * N, cudaMemcpyHostToDevice, s->st));
+  CK(cudaMemcpyAsync(dc, c, 8 * N, cudaMemcpyHostToDevice, s->st));
+  const int par = (int)(s->step & 1);
+  Params p = make_params(s, s->step);
+  s->ops->init_cells(p, par, dt, drho, du, da, dc, s->st);
+  s->ops->nearwall(p, s->st);
+  CK(cudaFreeAsync(buf, s->st));
+  CK(cudaMemsetAsync(s->label[par], 0xff, sizeof(int) * N, s->st));
+  CK(cudaMemsetAsync(s->tab[par].count, 0, sizeof(int), s->st));
+  int rc = separate_and_relabel(s);
+  if (rc) return rc;
+  return check_device_error(s);
+}
+
+int lbf_step(lbf_sim *s, int nsteps) {
+  if (!s || nsteps < 0) return fail(LBF_EINVAL, "bad arguments");
+  for (int k = 0; k < nsteps; ++k) {
+    int rc = carve_due_nuclei(s);
+    if (rc) return rc;
+    rc = run_one_step(s);
+    if (rc) return rc;
+    ++s->step;
+  }
+  return check_device_error(s);
+}
+
+long long lbf_step_count(const lbf_sim *s) { return s ? s->step : -1; }
+
+int lbf_bubbles(lbf_sim *s, lbf_bubble *out, int capacity, int *count) {
+  if (!s || !count || capacity < 0 || (capacity > 0 && !out)) return fail(LBF_EINVAL, "bad arguments");
+  const Table &t = s->tab[s->step & 1];
+  int nb = 0;
+  CK(cudaMemcpyAsync(&nb, t.count, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  *count = nb;
+  const int k = std::min(nb, capacity);
+  if (k > 0) {
+    std::vector<double> m(k), p(k), V(k);
+    std::vector<int> id(k), atm(k), root(k);
+    CK(cudaMemcpyAsync(m.data(), t.m, sizeof(double) * k, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(p.data(), t.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(V.data(), t.V, sizeof(double) * k, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(id.data(), t.id, sizeof(int) * k, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(atm.data(), t.atm, sizeof(int) * k, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(root.data(), t.root, sizeof(int) * k, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    for (int i = 0; i < k; ++i) {
+      out[i].id = id[i];
+      out[i].atm = atm[i];
+      out[i].label = root[i];
+      out[i].volume = V[i];
+      out[i].gas_mass = m[i];
+      out[i].pressure = p[i];
+    }
+  }
+  return 0;
+}
+
+int lbf_fields(lbf_sim *s, unsigned mask, void *const *dst, int dst_is_device, int dtype) {
+  if (!s || !dst || (dtype != 0 && dtype != 1)) return fail(LBF_EINVAL, "bad arguments");
+  if (mask >> 11) return fail(LBF_EINVAL, "unknown field bit");
+  const int par = (int)(s->step & 1);
+  Params p = make_params(s, s->step);
+  p.label_new = s->label[par];
+  const size_t N = (size_t)s->N;
+  int k = 0;
+  for (int bit = 0; bit < 11; ++bit) {
+    if (!(mask & (1u << bit))) continue;
+    void *out = dst[k++];
+    if (!out) return fail(LBF_EINVAL, "NULL destination");
+    const bool is_int = bit == FLD_FLAGS || bit == FLD_LABEL;
+    const int width = (bit == FLD_U || bit == FLD_NORMAL) ? 3 : 1;
+    const size_t bytes = N * width * (is_int ? 4 : (dtype ? 8 : 4));
+    if (dst_is_device) {
+      s->ops->field(p, par, bit, out, dtype, s->st);
+      CK(cudaGetLastError());
+    } else {
+      if (!s->staging) {
+        int rc = dev_alloc(s, &s->staging, N * 3 * 8);
+        if (rc) return rc;
+      }
+      s->ops->field(p, par, bit, s->staging, dtype, s->st);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(out, s->staging, bytes, cudaMemcpyDeviceToHost, s->st));
+      CK(cudaStreamSynchronize(s->st));
+    }
+  }
+  return 0;
+}
+
+static int run_ledger(lbf_sim *s, double *acc3, unsigned long long *cnt4) {
+  const int par = (int)(s->step & 1);
+  Params p = make_params(s, s->step);
+  CK(cudaMemsetAsync(s->acc, 0, 4 * sizeof(double), s->st));
+  CK(cudaMemsetAsync(s->counts, 0, 4 * sizeof(unsigned long long), s->st));
+  s->ops->ledger(p, par, s->acc, s->counts, s->st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(acc3, s->acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(cnt4, s->counts, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return 0;
+}
+
+int lbf_ledger(lbf_sim *s, double *out) {
+  if (!s || !out) return fail(LBF_EINVAL, "bad arguments");
+  double acc[3];
+  unsigned long long cnt[4];
+  int rc = run_ledger(s, acc, cnt);
+  if (rc) return rc;
+  double led[8];
+  unsigned long long upd = 0;
+  CK(cudaMemcpyAsync(led, s->led, sizeof led, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemcpyAsync(&upd, s->fluid_updates, sizeof upd, cudaMemcpyDeviceToHost, s->st));
+  const Table &t = s->tab[s->step & 1];
+  int nb = 0;
+  CK(cudaMemcpyAsync(&nb, t.count, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  double gas = 0.0;
+  if (nb > 0) {
+    std::vector<double> m(nb);
+    CK(cudaMemcpyAsync(m.data(), t.m, sizeof(double) * nb, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    for (double v : m) gas += v;
+  }
+  out[0] = acc[0];
+  out[1] = led[1];
+  out[2] = led[2];
+  out[3] = acc[1];
+  out[4] = gas;
+  out[5] = led[5];
+  out[6] = s->cfg.q * (double)upd;
+  out[7] = acc[2];
+  if (acc[2] > 0.0) return fail(LBF_ENONFINITE, "non-finite populations");
+  return 0;
+}
+
+int lbf_cell_counts(lbf_sim *s, long long *out4) {
+  if (!s || !out4) return fail(LBF_EINVAL, "bad arguments");
+  double acc[3];
+  unsigned long long cnt[4];
+  int rc = run_ledger(s, acc, cnt);
+  if (rc) return rc;
+  for (int k = 0; k < 4; ++k) out4[k] = (long long)cnt[k];
+  return 0;
+}
+
+int lbf_timing_enable(lbf_sim *s, int enable) {
+  if (!s) return fail(LBF_EINVAL, "NULL sim");
+  int rc = harvest_timing(s);
+  if (rc) return rc;
+  s->timing = enable != 0;
+  for (int k = 0; k < G_COUNT; ++k) {
+    s->t_ms[k] = 0.0;
+    s->t_n[k] = 0;
+  }
+  return 0;
+}
+
+int lbf_timing_read(lbf_sim *s, double *out_ms, long long *out_launches, int nmax) {
+  if (!s) return fail(LBF_EINVAL, "NULL sim");
+  int rc = harvest_timing(s);
+  if (rc) return rc;
+  for (int k = 0; k < G_COUNT && k < nmax; ++k) {
+    if (out_ms) out_ms[k] = s->t_ms[k];
+    if (out_launches) out_launches[k] = s->t_n[k];
+  }
+  return G_COUNT;
+}
+
+const char *lbf_timing_name(int k) { return (k >= 0 && k < G_COUNT) ? kGroupNames[k] : ""; }
+
+}  // extern "C"

@@ -1,0 +1,229 @@
+// lbf_common.cuh -- lattice definitions, storage codecs, the in-place AA
+// population layout and the launch parameter block shared by every kernel of
+// the GB300 free-surface foaming step.
+//
+// Populations are SoA, one plane of N cells per direction, updated in place
+// with the AA access pattern: a step that starts from parity 0 reads and
+// writes only the cell's own slots; a step that starts from parity 1 reads
+// from and writes to the neighbours' slots.  Each (cell, direction) outgoing
+// population owns exactly one slot in either parity, so no two threads write
+// the same slot.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbf {
+
+// cell types (bits 0-1 of the flag byte), conversion marks (bits 2-4) and a
+// static bit for cells with a wall among their lattice neighbours (bit 5)
+enum : int { T_GAS = 0, T_LIQ = 1, T_IFC = 2, T_WALL = 3 };
+enum : int { MK_NONE = 0, MK_FILL = 1, MK_EMPTY = 2, MK_GI = 3, MK_LI = 4 };
+constexpr uint8_t NEARWALL = 0x20;
+__device__ __forceinline__ int ftype(uint8_t f) { return f & 3; }
+__device__ __forceinline__ int fmark(uint8_t f) { return (f >> 2) & 7; }
+
+// fields of the export kernel (bit order of the public field mask)
+enum : int { FLD_RHO = 0, FLD_U = 1, FLD_ALPHA = 2, FLD_MASS = 3, FLD_FLAGS = 4, FLD_CONC = 5,
+             FLD_KAPPA = 6, FLD_LABEL = 7, FLD_PI = 8, FLD_NORMAL = 9, FLD_DSTAR = 10 };
+
+// sticky device error bits
+enum : int { ERR_CAPACITY = 1, ERR_NOTCONV = 2, ERR_HASH = 4 };
+
+// ---------------------------------------------------------------------------
+// velocity sets (Sec. 2: D2Q9 / D3Q19 with the paper's weights; Sec. 3.1:
+// D2Q5 / D3Q7 are the first 5 / 7 vectors).  Opposite vectors are adjacent.
+
+template <int D> struct Lat;
+template <> struct Lat<2> {
+  static constexpr int Q = 9, QA = 5;
+  __host__ __device__ static constexpr int cx(int i) { return i == 1 || i == 5 || i == 7 ? 1 : (i == 2 || i == 6 || i == 8 ? -1 : 0); }
+  __host__ __device__ static constexpr int cy(int i) { return i == 3 || i == 5 || i == 8 ? 1 : (i == 4 || i == 6 || i == 7 ? -1 : 0); }
+  __host__ __device__ static constexpr int cz(int) { return 0; }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+  __host__ __device__ static constexpr double wa(int i) { return i == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
+  static constexpr double csa2 = 1.0 / 3.0;
+};
+template <> struct Lat<3> {
+  static constexpr int Q = 19, QA = 7;
+  __host__ __device__ static constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 13 || i == 15) ? 1 : ((i == 2 || i == 8 || i == 10 || i == 14 || i == 16) ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 11 || i == 14 || i == 17) ? 1 : ((i == 4 || i == 8 || i == 12 || i == 13 || i == 18) ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int cz(int i) {
+    return (i == 5 || i == 9 || i == 11 || i == 16 || i == 18) ? 1 : ((i == 6 || i == 10 || i == 12 || i == 15 || i == 17) ? -1 : 0);
+  }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+  __host__ __device__ static constexpr double wa(int i) { return i == 0 ? 0.25 : 0.125; }
+  static constexpr double csa2 = 0.25;
+};
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// ---------------------------------------------------------------------------
+// storage codecs: the arithmetic type R and the shifted reduced-precision
+// forms (stored value = population - shift, shift = w_i rho0 or wa_i c0)
+
+template <class S> struct ST;
+template <> struct ST<double> { using R = double; };
+template <> struct ST<float> { using R = float; };
+template <> struct ST<__half> { using R = float; };
+template <> struct ST<__nv_bfloat16> { using R = float; };
+
+__device__ __forceinline__ double ld(const double *p, size_t k, double) { return p[k]; }
+__device__ __forceinline__ float ld(const float *p, size_t k, float) { return p[k]; }
+__device__ __forceinline__ float ld(const __half *p, size_t k, float sh) { return __half2float(p[k]) + sh; }
+__device__ __forceinline__ float ld(const __nv_bfloat16 *p, size_t k, float sh) { return __bfloat162float(p[k]) + sh; }
+__device__ __forceinline__ void st(double *p, size_t k, double v, double) { p[k] = v; }
+__device__ __forceinline__ void st(float *p, size_t k, float v, float) { p[k] = v; }
+__device__ __forceinline__ void st(__half *p, size_t k, float v, float sh) { p[k] = __float2half_rn(v - sh); }
+__device__ __forceinline__ void st(__nv_bfloat16 *p, size_t k, float v, float sh) { p[k] = __float2bfloat16_rn(v - sh); }
+
+// ---------------------------------------------------------------------------
+// bubble table (one of two, swapped every step)
+
+struct Table {
+  double *m, *p, *V, *dm;  // gas mass, pressure, volume, gas gained this step
+  int *id, *atm, *root;    // stable id, atmosphere flag, canonical label
+  int *count;              // number of rows (device)
+};
+
+// everything a kernel may need; passed by value
+struct Params {
+  int nx, ny, nz, dim;
+  long long N;
+  void *f, *g;           // populations (storage type)
+  uint8_t *flags;        // current flags (marks are written in place)
+  uint8_t *flags_out;    // flags after conversion
+  void *M, *phi;         // liquid mass, fill level (arithmetic type)
+  void *uI;              // 3N: velocity of interface cells from the last step
+  void *kappa, *Pi, *nrm, *dst, *ex;
+  int *label_old, *label_new, *parent;
+  Table told, tnew;
+  int *roots, *nroots;
+  unsigned long long *hash;
+  int hash_size, cap;
+  // K10 scratch (2*cap each)
+  int *gpar, *gnold, *gnnew, *gatm, *gminid, *gheir;
+  double *gmold, *gvnew;
+  unsigned long long *gvmax;
+  int *next_id;
+  double *led;                   // 8 ledger accumulators
+  unsigned long long *fluid_updates;
+  int *err;
+  // physics
+  double tau, rho0, ax, ay, az;
+  int has_force, rheo;
+  double rn, rk, rlam, ra, tau0, tau_inf, tau_min, tau_max;
+  double sigma, k_pi, d_max, taug, kH, RT, c0, q, p0, eps;
+  double uwx, uwy, uwz;
+  int walls, atmosphere, top_layer, ray_steps;
+};
+
+// ---------------------------------------------------------------------------
+// indexing
+
+struct Cell {
+  int x, y, z;
+  int xm, xp, ym, yp, zm, zp;  // wrapped neighbour coordinates
+};
+
+__device__ __forceinline__ Cell make_cell(const Params &p, long long n) {
+  Cell c;
+  const long long nxy = (long long)p.nx * p.ny;
+  c.z = (int)(n / nxy);
+  const long long r = n - (long long)c.z * nxy;
+  c.y = (int)(r / p.nx);
+  c.x = (int)(r - (long long)c.y * p.nx);
+  c.xm = c.x == 0 ? p.nx - 1 : c.x - 1;
+  c.xp = c.x == p.nx - 1 ? 0 : c.x + 1;
+  c.ym = c.y == 0 ? p.ny - 1 : c.y - 1;
+  c.yp = c.y == p.ny - 1 ? 0 : c.y + 1;
+  c.zm = c.z == 0 ? p.nz - 1 : c.z - 1;
+  c.zp = c.z == p.nz - 1 ? 0 : c.z + 1;
+  return c;
+}
+
+// cell at offset (dx,dy,dz) in {-1,0,1}^3
+__device__ __forceinline__ long long at(const Params &p, const Cell &c, int dx, int dy, int dz) {
+  const int xx = dx < 0 ? c.xm : (dx > 0 ? c.xp : c.x);
+  const int yy = dy < 0 ? c.ym : (dy > 0 ? c.yp : c.y);
+  const int zz = dz < 0 ? c.zm : (dz > 0 ? c.zp : c.z);
+  return xx + (long long)p.nx * (yy + (long long)p.ny * zz);
+}
+
+// general periodic offset (any distance)
+__device__ __forceinline__ long long at_far(const Params &p, int x, int y, int z) {
+  x %= p.nx; if (x < 0) x += p.nx;
+  y %= p.ny; if (y < 0) y += p.ny;
+  z %= p.nz; if (z < 0) z += p.nz;
+  return x + (long long)p.nx * (y + (long long)p.ny * z);
+}
+
+template <int D> __device__ __forceinline__ long long nb(const Params &p, const Cell &c, int i) {
+  return at(p, c, Lat<D>::cx(i), Lat<D>::cy(i), Lat<D>::cz(i));
+}
+template <int D> __device__ __forceinline__ long long src(const Params &p, const Cell &c, int i) {
+  return at(p, c, -Lat<D>::cx(i), -Lat<D>::cy(i), -Lat<D>::cz(i));
+}
+
+// AA slots.  Parity 0: slot (i, n) holds the population arriving at n along
+// e_i.  Parity 1: slot (opp(i), n) holds n's own outgoing population along e_i.
+template <int D> __device__ __forceinline__ size_t slot_out(const Params &p, const Cell &c, long long n, int i, int par) {
+  return par == 0 ? (size_t)i * p.N + nb<D>(p, c, i) : (size_t)opp(i) * p.N + n;
+}
+template <int D> __device__ __forceinline__ size_t slot_in(const Params &p, const Cell &c, long long n, int i, int par) {
+  return par == 0 ? (size_t)i * p.N + n : (size_t)opp(i) * p.N + src<D>(p, c, i);
+}
+
+template <class R, int D> __device__ __forceinline__ R feq(int i, R rho, R ux, R uy, R uz) {
+  const R eu = (R)Lat<D>::cx(i) * ux + (R)Lat<D>::cy(i) * uy + (R)Lat<D>::cz(i) * uz;
+  const R uu = ux * ux + uy * uy + uz * uz;
+  return (R)Lat<D>::w(i) * rho * ((R)1 + eu * (R)3 + eu * eu * (R)4.5 - uu * (R)1.5);
+}
+
+template <class R, int D> __device__ __forceinline__ R geq(int i, R c, R ux, R uy, R uz) {
+  const R eu = (R)Lat<D>::cx(i) * ux + (R)Lat<D>::cy(i) * uy + (R)Lat<D>::cz(i) * uz;
+  return (R)Lat<D>::wa(i) * c * ((R)1 + eu / (R)Lat<D>::csa2);
+}
+
+template <class S, int D> __device__ __forceinline__ typename ST<S>::R fshift(const Params &p, int i) {
+  return (typename ST<S>::R)(Lat<D>::w(i) * p.rho0);
+}
+template <class S, int D> __device__ __forceinline__ typename ST<S>::R gshift(const Params &p, int i) {
+  return (typename ST<S>::R)(Lat<D>::wa(i) * p.c0);
+}
+
+// post-conversion type from a flag byte carrying marks
+__device__ __forceinline__ int post_type(uint8_t f) {
+  const int m = fmark(f);
+  if (m == MK_FILL) return T_LIQ;
+  if (m == MK_EMPTY) return T_GAS;
+  if (m == MK_GI || m == MK_LI) return T_IFC;
+  return ftype(f);
+}
+
+// warp-aggregated FP64 atomic add keyed by a bubble index: lanes holding the
+// same key are summed in lane order by their lowest lane.  Must be reached by
+// all 32 lanes of the warp; lanes with key < 0 contribute nothing.
+__device__ __forceinline__ void agg_add(double *base, int key, double v, double *wbuf) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  wbuf[lane] = v;
+  __syncwarp();
+  if (key >= 0 && lane == __ffs(peers) - 1) {
+    double s = 0.0;
+    unsigned m = peers;
+    while (m) {
+      const int l = __ffs(m) - 1;
+      s += wbuf[l];
+      m &= m - 1;
+    }
+    atomicAdd(base + key, s);
+  }
+  __syncwarp();
+}
+
+}  // namespace lbf

@@ -1,0 +1,455 @@
+// lbf_convert.cuh -- cell conversion with excess-mass redistribution
+// (Sec. 2.1), lattice initialisation, nucleation (Sec. 3.4), field export and
+// the FP64 ledgers.  All kernels run one thread per cell.
+//
+// Conversion (after the sweep has marked interface cells whose fill level
+// left [-eps, 1+eps]):
+//   k_conv_unmark     an emptying cell next to a filling cell stays interface
+//   k_conv_neighbours gas next to a filling cell and liquid next to an
+//                     emptying cell become interface (liquid never meets gas)
+//   k_conv_compute    excess mass of converting cells, split equally over the
+//                     neighbours that are interface afterwards; new interface
+//                     cells from gas start at the mean equilibrium of their
+//                     interface neighbours; dissolved gas moves between the
+//                     liquid and the cell's bubble
+//   k_conv_apply      interface cells collect the excess; new types written
+//                     to the second flag buffer; union-find roots initialised
+#pragma once
+#include "lbf_common.cuh"
+
+namespace lbf {
+
+template <int D, class S>
+__device__ __forceinline__ typename ST<S>::R sum_out_f(const Params &p, const Cell &c, long long n, int par,
+                                                       typename ST<S>::R *u) {
+  using R = typename ST<S>::R;
+  const S *f = (const S *)p.f;
+  R rho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int i = 0; i < Lat<D>::Q; ++i) {
+    const R v = ld(f, slot_out<D>(p, c, n, i, par), fshift<S, D>(p, i));
+    rho += v;
+    jx += v * (R)Lat<D>::cx(i);
+    jy += v * (R)Lat<D>::cy(i);
+    jz += v * (R)Lat<D>::cz(i);
+  }
+  if (u) {
+    u[0] = (jx - (R)0.5 * rho * (R)p.ax) / rho;
+    u[1] = (jy - (R)0.5 * rho * (R)p.ay) / rho;
+    u[2] = (jz - (R)0.5 * rho * (R)p.az) / rho;
+  }
+  return rho;
+}
+
+template <int D, class S>
+__device__ __forceinline__ typename ST<S>::R sum_out_g(const Params &p, const Cell &c, long long n, int par) {
+  using R = typename ST<S>::R;
+  const S *g = (const S *)p.g;
+  R s = 0;
+#pragma unroll
+  for (int i = 0; i < Lat<D>::QA; ++i) s += ld(g, slot_out<D>(p, c, n, i, par), gshift<S, D>(p, i));
+  return s;
+}
+
+template <int D, class S>
+__device__ __forceinline__ void write_equilibrium(const Params &p, const Cell &c, long long n, int par,
+                                                  typename ST<S>::R rho, const typename ST<S>::R *u,
+                                                  typename ST<S>::R conc) {
+  using R = typename ST<S>::R;
+  S *f = (S *)p.f;
+  S *g = (S *)p.g;
+#pragma unroll
+  for (int i = 0; i < Lat<D>::Q; ++i)
+    st(f, slot_out<D>(p, c, n, i, par), feq<R, D>(i, rho, u[0], u[1], u[2]), fshift<S, D>(p, i));
+#pragma unroll
+  for (int i = 0; i < Lat<D>::QA; ++i)
+    st(g, slot_out<D>(p, c, n, i, par), geq<R, D>(i, conc, u[0], u[1], u[2]), gshift<S, D>(p, i));
+}
+
+template <int D>
+__global__ void k_conv_unmark(Params p) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  const uint8_t fl = p.flags[n];
+  if (fmark(fl) != MK_EMPTY) return;
+  const Cell c = make_cell(p, n);
+#pragma unroll
+  for (int i = 1; i < Lat<D>::Q; ++i)
+    if (fmark(p.flags[nb<D>(p, c, i)]) == MK_FILL) {
+      p.flags[n] = (uint8_t)(fl & ~(7 << 2));
+      return;
+    }
+}
+
+template <int D>
+__global__ void k_conv_neighbours(Params p) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  const uint8_t fl = p.flags[n];
+  const int t = ftype(fl);
+  if (t != T_GAS && t != T_LIQ) return;
+  const Cell c = make_cell(p, n);
+  const int want = t == T_GAS ? MK_FILL : MK_EMPTY;
+#pragma unroll
+  for (int i = 1; i < Lat<D>::Q; ++i)
+    if (fmark(p.flags[nb<D>(p, c, i)]) == want) {
+      p.flags[n] = (uint8_t)(fl | ((t == T_GAS ? MK_GI : MK_LI) << 2));
+      return;
+    }
+}
+
+// par: parity of the populations after the sweep
+template <int D, class S>
+__global__ void __launch_bounds__(256) k_conv_compute(Params p, int par) {
+  using R = typename ST<S>::R;
+  __shared__ double wbuf[256];
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const bool inr = n < p.N;
+  const uint8_t fl = inr ? p.flags[n] : (uint8_t)0;
+  const int mk = fmark(fl);
+  double dmv = 0.0;
+  int lab = -1;
+  if (inr && mk != MK_NONE) {
+    const Cell c = make_cell(p, n);
+    R *M = (R *)p.M;
+    if (mk == MK_FILL || mk == MK_EMPTY) {
+      const R rho = sum_out_f<D, S>(p, c, n, par, nullptr);
+      const R excess = mk == MK_FILL ? M[n] - rho : M[n];
+      int cnt = 0;
+#pragma unroll
+      for (int i = 1; i < Lat<D>::Q; ++i) cnt += post_type(p.flags[nb<D>(p, c, i)]) == T_IFC;
+      R *ex = (R *)p.ex;
+      if (cnt > 0)
+        ex[n] = excess / (R)cnt;
+      else
+        atomicAdd(p.led + 1, (double)excess);
+      if (mk == MK_EMPTY) {
+        const double cg = (double)sum_out_g<D, S>(p, c, n, par);
+        lab = p.label_old[n];
+        if (lab >= 0)
+          dmv = cg;
+        else
+          atomicAdd(p.led + 5, cg);
+      }
+    } else if (mk == MK_GI) {
+      R rs = 0, us[3] = {0, 0, 0}, cs = 0;
+      int cnt = 0;
+#pragma unroll
+      for (int i = 1; i < Lat<D>::Q; ++i) {
+        const long long m = nb<D>(p, c, i);
+        const uint8_t fm = p.flags[m];
+        if (ftype(fm) == T_IFC && (fmark(fm) == MK_NONE || fmark(fm) == MK_FILL)) {
+          const Cell cm = make_cell(p, m);
+          R u[3];
+          rs += sum_out_f<D, S>(p, cm, m, par, u);
+          us[0] += u[0];
+          us[1] += u[1];
+          us[2] += u[2];
+          cs += sum_out_g<D, S>(p, cm, m, par);
+          ++cnt;
+        }
+      }
+      const R inv = (R)cnt;
+      rs /= inv;
+      us[0] /= inv;
+      us[1] /= inv;
+      us[2] /= inv;
+      cs /= inv;
+      write_equilibrium<D, S>(p, c, n, par, rs, us, cs);
+      M[n] = 0;
+      lab = p.label_old[n];
+      if (lab >= 0)
+        dmv = -(double)cs;
+      else
+        atomicAdd(p.led + 5, -(double)cs);
+    } else if (mk == MK_LI) {
+      M[n] = sum_out_f<D, S>(p, c, n, par, nullptr);
+    }
+  }
+  if (__any_sync(0xffffffffu, lab >= 0)) agg_add(p.told.dm, lab, dmv, wbuf + (threadIdx.x & ~31));
+}
+
+template <int D, class S>
+__global__ void k_conv_apply(Params p, int par) {
+  using R = typename ST<S>::R;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  const uint8_t fl = p.flags[n];
+  const int pt = post_type(fl);
+  const int mk = fmark(fl);
+  if (pt == T_IFC) {
+    const Cell c = make_cell(p, n);
+    const R *ex = (const R *)p.ex;
+    R *M = (R *)p.M;
+    R recv = 0;
+    bool has = false;
+#pragma unroll
+    for (int i = 1; i < Lat<D>::Q; ++i) {
+      const long long m = nb<D>(p, c, i);
+      const int fm = fmark(p.flags[m]);
+      if (fm == MK_FILL || fm == MK_EMPTY) {
+        recv += ex[m];
+        has = true;
+      }
+    }
+    if (has || mk == MK_GI || mk == MK_LI) {
+      const R Mv = M[n] + recv;
+      M[n] = Mv;
+      ((R *)p.phi)[n] = Mv / sum_out_f<D, S>(p, c, n, par, nullptr);
+    }
+  } else if (mk == MK_FILL) {
+    ((R *)p.phi)[n] = 1;
+    ((R *)p.M)[n] = 0;
+  } else if (mk == MK_EMPTY) {
+    ((R *)p.phi)[n] = 0;
+    ((R *)p.M)[n] = 0;
+  }
+  p.flags_out[n] = (uint8_t)(pt | (fl & NEARWALL));
+  if (pt == T_GAS) p.parent[n] = (int)n;
+}
+
+// ---------------------------------------------------------------------------
+// initialisation
+
+template <int D> __device__ __forceinline__ bool is_wall_cell(const Params &p, const Cell &c) {
+  const int w = p.walls;
+  if ((w & 1) && c.x == 0) return true;
+  if ((w & 2) && c.x == p.nx - 1) return true;
+  if ((w & 4) && c.y == 0) return true;
+  if ((w & 8) && c.y == p.ny - 1) return true;
+  if (D == 3 && (w & 16) && c.z == 0) return true;
+  if (D == 3 && (w & 32) && c.z == p.nz - 1) return true;
+  return false;
+}
+
+// liquid below fill_height at rest, walls, gas above
+template <int D, class S>
+__global__ void k_init_fill(Params p, int par, double fill_height) {
+  using R = typename ST<S>::R;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  const Cell c = make_cell(p, n);
+  R *M = (R *)p.M, *phi = (R *)p.phi;
+  if (is_wall_cell<D>(p, c)) {
+    p.flags[n] = T_WALL;
+    phi[n] = 0;
+    M[n] = 0;
+    return;
+  }
+  const double h = D == 2 ? c.y : c.z;
+  double a = fill_height - (h - 0.5);
+  a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+  const int t = a >= 1.0 ? T_LIQ : (a <= 0.0 ? T_GAS : T_IFC);
+  p.flags[n] = (uint8_t)t;
+  phi[n] = (R)a;
+  M[n] = 0;
+  if (t != T_GAS) {
+    const R u[3] = {0, 0, 0};
+    write_equilibrium<D, S>(p, c, n, par, (R)p.rho0, u, (R)p.c0);
+    if (t == T_IFC) M[n] = (R)a * (R)p.rho0;
+  }
+}
+
+// state from per-cell arrays (already on the device)
+template <int D, class S>
+__global__ void k_init_cells(Params p, int par, const uint8_t *type, const double *rho, const double *u,
+                             const double *alpha, const double *conc) {
+  using R = typename ST<S>::R;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  const Cell c = make_cell(p, n);
+  const int t = type[n] & 3;
+  R *M = (R *)p.M, *phi = (R *)p.phi;
+  p.flags[n] = (uint8_t)t;
+  M[n] = 0;
+  phi[n] = t == T_LIQ ? (R)1 : (t == T_IFC ? (R)alpha[n] : (R)0);
+  if (t == T_LIQ || t == T_IFC) {
+    const R uu[3] = {(R)u[3 * n], (R)u[3 * n + 1], (R)u[3 * n + 2]};
+    write_equilibrium<D, S>(p, c, n, par, (R)rho[n], uu, (R)conc[n]);
+    if (t == T_IFC) M[n] = (R)alpha[n] * (R)rho[n];
+  }
+}
+
+// liquid next to gas becomes interface with alpha = 1 (two passes)
+template <int D>
+__global__ void k_separate_mark(Params p) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  const uint8_t fl = p.flags[n];
+  if (ftype(fl) != T_LIQ) return;
+  const Cell c = make_cell(p, n);
+#pragma unroll
+  for (int i = 1; i < Lat<D>::Q; ++i)
+    if (ftype(p.flags[nb<D>(p, c, i)]) == T_GAS) {
+      p.flags[n] = (uint8_t)(fl | (MK_LI << 2));
+      return;
+    }
+}
+
+template <int D, class S>
+__global__ void k_separate_apply(Params p, int par) {
+  using R = typename ST<S>::R;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  const uint8_t fl = p.flags[n];
+  if (fmark(fl) != MK_LI) return;
+  const Cell c = make_cell(p, n);
+  p.flags[n] = (uint8_t)(T_IFC | (fl & NEARWALL));
+  ((R *)p.phi)[n] = 1;
+  ((R *)p.M)[n] = sum_out_f<D, S>(p, c, n, par, nullptr);
+}
+
+template <int D>
+__global__ void k_nearwall(Params p) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  const Cell c = make_cell(p, n);
+  bool w = false;
+#pragma unroll
+  for (int i = 1; i < Lat<D>::Q; ++i) w |= ftype(p.flags[nb<D>(p, c, i)]) == T_WALL;
+  const uint8_t fl = p.flags[n];
+  p.flags[n] = (uint8_t)(w ? (fl | NEARWALL) : (fl & ~NEARWALL));
+}
+
+// Sec. 3.4: carve one nucleus (sphere or disk of radius R at (cx,cy,cz))
+// into liquid cells of its bounding box [x0,x0+bx) x [y0,..) x [z0,..)
+template <int D, class S>
+__global__ void k_nucleate(Params p, int par, double cx, double cy, double cz, double R0, int x0, int y0,
+                           int z0, int bx, int by, int bz) {
+  using R = typename ST<S>::R;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)bx * by * bz) return;
+  const int X = x0 + (int)(t % bx);
+  const int Y = y0 + (int)((t / bx) % by);
+  const int Z = z0 + (int)(t / ((long long)bx * by));
+  const long long n = at_far(p, X, Y, Z);
+  if (ftype(p.flags[n]) != T_LIQ) return;
+  const int total = D == 3 ? 64 : 16;
+  int nout = 0;
+  for (int k = 0; k < (D == 3 ? 4 : 1); ++k)
+    for (int b = 0; b < 4; ++b)
+      for (int a = 0; a < 4; ++a) {
+        const double px = X + (a + 0.5) / 4.0 - 0.5 - cx;
+        const double py = Y + (b + 0.5) / 4.0 - 0.5 - cy;
+        const double pz = D == 3 ? Z + (k + 0.5) / 4.0 - 0.5 - cz : 0.0;
+        nout += px * px + py * py + pz * pz >= R0 * R0;
+      }
+  if (nout == total) return;
+  const Cell c = make_cell(p, n);
+  const double rho = (double)sum_out_f<D, S>(p, c, n, par, nullptr);
+  R *M = (R *)p.M, *phi = (R *)p.phi;
+  const uint8_t keep = p.flags[n] & NEARWALL;
+  if (nout == 0) {
+    p.flags[n] = (uint8_t)(T_GAS | keep);
+    phi[n] = 0;
+    M[n] = 0;
+    atomicAdd(p.led + 2, rho);
+    atomicAdd(p.led + 5, (double)sum_out_g<D, S>(p, c, n, par));
+  } else {
+    const double al = (double)nout / total;
+    p.flags[n] = (uint8_t)(T_IFC | keep);
+    phi[n] = (R)al;
+    M[n] = (R)(al * rho);
+    atomicAdd(p.led + 2, rho - al * rho);
+  }
+}
+
+template <int D>
+__global__ void k_uf_init(Params p) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  if (ftype(p.flags_out[n]) == T_GAS) p.parent[n] = (int)n;
+}
+
+// ---------------------------------------------------------------------------
+// export and ledgers
+
+template <int D, class S>
+__global__ void k_fields(Params p, int par, int which, void *out, int dtype) {
+  using R = typename ST<S>::R;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  const int t = ftype(p.flags[n]);
+  const bool fluid = t == T_LIQ || t == T_IFC;
+  double v[3] = {0.0, 0.0, 0.0};
+  int width = 1;
+  const Cell c = make_cell(p, n);
+  switch (which) {
+    case FLD_RHO: if (fluid) v[0] = (double)sum_out_f<D, S>(p, c, n, par, nullptr); break;
+    case FLD_U:
+      width = 3;
+      if (fluid) {
+        R u[3];
+        sum_out_f<D, S>(p, c, n, par, u);
+        v[0] = u[0]; v[1] = u[1]; v[2] = u[2];
+      }
+      break;
+    case FLD_ALPHA: v[0] = (double)((const R *)p.phi)[n]; break;
+    case FLD_MASS:
+      if (t == T_IFC) v[0] = (double)((const R *)p.M)[n];
+      else if (t == T_LIQ) v[0] = (double)sum_out_f<D, S>(p, c, n, par, nullptr);
+      break;
+    case FLD_CONC: if (fluid) v[0] = (double)sum_out_g<D, S>(p, c, n, par); break;
+    case FLD_KAPPA: if (t == T_IFC) v[0] = (double)((const R *)p.kappa)[n]; break;
+    case FLD_PI: if (t == T_IFC) v[0] = (double)((const R *)p.Pi)[n]; break;
+    case FLD_DSTAR: if (t == T_IFC) v[0] = (double)((const R *)p.dst)[n]; break;
+    case FLD_NORMAL:
+      width = 3;
+      if (t == T_IFC) {
+        const R *nr = (const R *)p.nrm;
+        v[0] = nr[n]; v[1] = nr[p.N + n]; v[2] = nr[2 * p.N + n];
+      }
+      break;
+    case FLD_FLAGS: ((int *)out)[n] = t; return;
+    case FLD_LABEL: ((int *)out)[n] = (t == T_GAS || t == T_IFC) ? p.label_new[n] : -1; return;
+  }
+  for (int k = 0; k < width; ++k) {
+    if (dtype == 1)
+      ((double *)out)[width * n + k] = v[k];
+    else
+      ((float *)out)[width * n + k] = (float)v[k];
+  }
+}
+
+// [0] liquid mass, [1] dissolved gas, [2] non-finite populations, plus cell
+// counts of the four types
+template <int D, class S>
+__global__ void __launch_bounds__(256) k_ledger(Params p, int par, double *acc, unsigned long long *counts) {
+  using R = typename ST<S>::R;
+  __shared__ double sm[3][256];
+  __shared__ unsigned long long sc[4];
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (threadIdx.x < 4) sc[threadIdx.x] = 0;
+  double mass = 0.0, gas = 0.0, bad = 0.0;
+  __syncthreads();
+  if (n < p.N) {
+    const int t = ftype(p.flags[n]);
+    atomicAdd(&sc[t], 1ull);
+    if (t == T_LIQ || t == T_IFC) {
+      const Cell c = make_cell(p, n);
+      const S *f = (const S *)p.f;
+      double rho = 0.0;
+      for (int i = 0; i < Lat<D>::Q; ++i) {
+        const double v = (double)ld(f, slot_out<D>(p, c, n, i, par), fshift<S, D>(p, i));
+        rho += v;
+        if (!isfinite(v)) bad += 1.0;
+      }
+      mass = t == T_LIQ ? rho : (double)((const R *)p.M)[n];
+      gas = (double)sum_out_g<D, S>(p, c, n, par);
+    }
+  }
+  sm[0][threadIdx.x] = mass;
+  sm[1][threadIdx.x] = gas;
+  sm[2][threadIdx.x] = bad;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < 3; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 3; ++k) atomicAdd(acc + k, sm[k][0]);
+  if (threadIdx.x < 4 && sc[threadIdx.x]) atomicAdd(counts + threadIdx.x, sc[threadIdx.x]);
+}
+
+}  // namespace lbf

@@ -1,0 +1,39 @@
+// lbf_ops_api.h -- the launch interface seen by the host runtime: one Ops
+// object per (lattice, storage) pair, created by the factory of the
+// translation unit that holds that storage type's kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lbf_common.cuh"
+
+namespace lbf {
+
+struct Ops {
+  virtual ~Ops() {}
+  virtual void init_fill(const Params &p, int par, double h, cudaStream_t s) = 0;
+  virtual void init_cells(const Params &p, int par, const uint8_t *t, const double *rho, const double *u,
+                          const double *a, const double *c, cudaStream_t s) = 0;
+  virtual void separate(const Params &p, int par, cudaStream_t s) = 0;
+  virtual void nearwall(const Params &p, cudaStream_t s) = 0;
+  virtual void nucleate(const Params &p, int par, const double *c, double R, cudaStream_t s) = 0;
+  virtual void uf_init(const Params &p, cudaStream_t s) = 0;
+  // step pieces (par = parity of the populations when the step starts)
+  virtual void exchange(const Params &p, int par, cudaStream_t s) = 0;
+  virtual void stream_collide(const Params &p, int par, cudaStream_t s) = 0;
+  virtual void convert(const Params &p, int par, cudaStream_t s) = 0;
+  virtual void label(const Params &p, cudaStream_t s) = 0;
+  virtual void bubble_update(const Params &p, cudaStream_t s) = 0;
+  virtual void geometry(const Params &p, cudaStream_t s) = 0;
+  virtual void disjoining(const Params &p, cudaStream_t s) = 0;
+  // export
+  virtual void field(const Params &p, int par, int which, void *out, int dtype, cudaStream_t s) = 0;
+  virtual void ledger(const Params &p, int par, double *acc, unsigned long long *counts, cudaStream_t s) = 0;
+};
+
+// defined in one translation unit per storage type
+Ops *make_ops_f64(int dim);
+Ops *make_ops_f32(int dim);
+Ops *make_ops_f16(int dim);
+Ops *make_ops_bf16(int dim);
+
+}  // namespace lbf

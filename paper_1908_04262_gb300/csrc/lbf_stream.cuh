@@ -1,0 +1,273 @@
+// lbf_stream.cuh -- the per-step lattice sweep.
+//
+// k_exchange (interface cells only) runs first: it reads the cell's own
+// outgoing populations of the last step and the incoming ones from liquid
+// and interface neighbours while no slot is being rewritten, and applies the
+// mass exchange of Sec. 2.1 Eq. massexchange (Theta = 1 towards liquid,
+// (alpha_x + alpha_nb)/2 towards interface, 0 towards gas and walls).  It
+// also keeps the cell's last velocity u_I for the reconstruction.
+//
+// k_stream_collide (every liquid and interface cell) then streams in place
+// (Sec. 2 Eq. streamingstep), bounces back at walls, rebuilds populations
+// arriving from gas cells (Sec. 2.2 Eq. reconstruct with the gas density of
+// Eq. rhob / rhobplusdisjoining), relaxes with BGK plus Guo forcing
+// (Sec. 2 Eq. collision/equilibrium) at a per-cell tau from the local shear
+// rate (Sec. 2.3 Eq. tau/carreauTau), updates the fill level
+// (Sec. 2.1 Eq. alpha) and marks interface cells that fill or empty.  The
+// same thread advances the dissolved gas on D2Q5/D3Q7 (Sec. 3.1
+// Eq. diffusion) with Henry's law at gas links (Sec. 3.2 Eq. henryslaw /
+// reconstructdiffusion) and adds the cell's gas current (Sec. 3.1
+// Eq. gascurrent) to its bubble.
+#pragma once
+#include "lbf_common.cuh"
+
+namespace lbf {
+
+template <class R> struct Prec;
+template <> struct Prec<double> { static constexpr double tol = 1e-13; static constexpr int iters = 60; };
+template <> struct Prec<float> { static constexpr float tol = 2e-6f; static constexpr int iters = 24; };
+
+// tau of the rheology model at shear rate gd, and d tau / d gd
+template <class R> __device__ __forceinline__ R tau_model(const Params &p, R gd, R &dtau) {
+  if (p.rheo == 1) {
+    const R t = (R)3 * (R)p.rk * pow(gd, (R)p.rn - (R)1);
+    dtau = t * ((R)p.rn - (R)1) / gd;
+    return (R)0.5 + t;
+  }
+  const R lg = pow((R)p.rlam * gd, (R)p.ra);
+  const R base = (R)1 + lg;
+  const R fac = pow(base, ((R)p.rn - (R)1) / (R)p.ra);
+  dtau = (R)(p.tau0 - p.tau_inf) * fac * ((R)p.rn - (R)1) / base * lg / gd;
+  return (R)p.tau_inf + (R)(p.tau0 - p.tau_inf) * fac;
+}
+
+// Sec. 2.3: tau solves tau = tau_model(A / tau) (shear rate A / tau from the
+// non-equilibrium stress); safeguarded Newton on [tau_min, tau_max].
+template <class R> __device__ __forceinline__ R solve_tau(const Params &p, R A) {
+  R lo = (R)p.tau_min, hi = (R)p.tau_max, d;
+  if (!(hi - tau_model<R>(p, A / hi, d) > (R)0)) return hi;
+  if (!(lo - tau_model<R>(p, A / lo, d) < (R)0)) return lo;
+  // Newton from the upper end of the bracket, falling back to bisection
+  // whenever a step leaves the bracket; h(t) = t - tau_model(A / t)
+  R t = hi;
+  for (int it = 0; it < Prec<R>::iters; ++it) {
+    R dm;
+    const R h = t - tau_model<R>(p, A / t, dm);
+    if (h > (R)0) hi = t; else lo = t;
+    const R deriv = (R)1 + dm * A / (t * t);
+    R tn = t - h / deriv;
+    if (!(tn > lo && tn < hi)) tn = (R)0.5 * (lo + hi);
+    const R step = tn - t;
+    t = tn;
+    if (fabs(step) <= Prec<R>::tol * t) break;
+  }
+  return t;
+}
+
+template <int D, class S, int PAR>
+__global__ void __launch_bounds__(256) k_exchange(Params p) {
+  using R = typename ST<S>::R;
+  constexpr int Q = Lat<D>::Q;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  if (ftype(p.flags[n]) != T_IFC) return;
+  const Cell c = make_cell(p, n);
+  const S *f = (const S *)p.f;
+  R *M = (R *)p.M;
+  const R *phi = (const R *)p.phi;
+  R fo[Q];
+  R rho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    fo[i] = ld(f, slot_out<D>(p, c, n, i, PAR), fshift<S, D>(p, i));
+    rho += fo[i];
+    jx += fo[i] * (R)Lat<D>::cx(i);
+    jy += fo[i] * (R)Lat<D>::cy(i);
+    jz += fo[i] * (R)Lat<D>::cz(i);
+  }
+  R *uI = (R *)p.uI;
+  uI[n] = (jx - (R)0.5 * rho * (R)p.ax) / rho;
+  uI[p.N + n] = (jy - (R)0.5 * rho * (R)p.ay) / rho;
+  uI[2 * p.N + n] = (jz - (R)0.5 * rho * (R)p.az) / rho;
+  R Mn = M[n];
+  const R ph = phi[n];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const long long m = nb<D>(p, c, i);
+    const int tn = ftype(p.flags[m]);
+    if (tn == T_LIQ || tn == T_IFC) {
+      // arriving along opp(i) from m: the slot holding m's outgoing f_opp(i)
+      const R fin = ld(f, slot_in<D>(p, c, n, opp(i), PAR), fshift<S, D>(p, opp(i)));
+      const R dm = fin - fo[i];
+      if (tn == T_LIQ)
+        Mn += dm;
+      else
+        Mn += (R)0.5 * (ph + phi[m]) * dm;
+    }
+  }
+  M[n] = Mn;
+}
+
+template <int D, class S, int PAR>
+__global__ void __launch_bounds__(256) k_stream_collide(Params p) {
+  using R = typename ST<S>::R;
+  constexpr int Q = Lat<D>::Q, QA = Lat<D>::QA;
+  __shared__ double wbuf[256];
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const bool inr = n < p.N;
+  const uint8_t fl = inr ? p.flags[n] : (uint8_t)T_GAS;
+  const int type = ftype(fl);
+  const bool active = inr && (type == T_LIQ || type == T_IFC);
+  const bool isI = active && type == T_IFC;
+  double flux = 0.0;
+  int lab = -1;
+  if (active) {
+    const Cell c = make_cell(p, n);
+    S *f = (S *)p.f;
+    S *g = (S *)p.g;
+    const bool simple = type == T_LIQ && !(fl & NEARWALL);
+    R fi[Q];
+    R uIx = 0, uIy = 0, uIz = 0, rhog = 0, kap = 0, pi = 0;
+    if (isI) {
+      const R *uI = (const R *)p.uI;
+      uIx = uI[n];
+      uIy = uI[p.N + n];
+      uIz = uI[2 * p.N + n];
+      kap = ((const R *)p.kappa)[n];
+      pi = ((const R *)p.Pi)[n];
+    }
+    int tsrc[Q];
+    fi[0] = ld(f, (size_t)n, fshift<S, D>(p, 0));
+    tsrc[0] = T_LIQ;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      tsrc[i] = simple ? T_LIQ : ftype(p.flags[src<D>(p, c, i)]);
+      const int ts = tsrc[i];
+      if (ts == T_LIQ || ts == T_IFC) {
+        fi[i] = ld(f, slot_in<D>(p, c, n, i, PAR), fshift<S, D>(p, i));
+      } else if (ts == T_WALL) {
+        // half-way bounce-back: the cell's own outgoing population towards
+        // the wall, reflected (the slot belongs to the wall cell)
+        R v = ld(f, slot_out<D>(p, c, n, opp(i), PAR), fshift<S, D>(p, opp(i)));
+        const int sy = Lat<D>::cy(i) > 0 ? c.ym : (Lat<D>::cy(i) < 0 ? c.yp : c.y);
+        if ((p.walls & 8) && sy == p.ny - 1) {
+          const R eu = (R)Lat<D>::cx(i) * (R)p.uwx + (R)Lat<D>::cy(i) * (R)p.uwy + (R)Lat<D>::cz(i) * (R)p.uwz;
+          v += (R)2 * (R)Lat<D>::w(i) * (R)p.rho0 * eu * (R)3;
+        }
+        fi[i] = v;
+      } else {
+        // Sec. 2.2 Eq. reconstruct: f_i = feq_i(rho_g,u_I) + feq_opp(rho_g,u_I) - f_opp
+        const int b = p.label_old[src<D>(p, c, i)];
+        const R pg = b >= 0 ? (R)p.told.p[b] : (R)p.p0;
+        rhog = (pg - (R)2 * (R)p.sigma * kap - pi) * (R)3;
+        const R fo = ld(f, slot_out<D>(p, c, n, opp(i), PAR), fshift<S, D>(p, opp(i)));
+        fi[i] = feq<R, D>(i, rhog, uIx, uIy, uIz) + feq<R, D>(opp(i), rhog, uIx, uIy, uIz) - fo;
+      }
+    }
+    // moments and Guo-shifted velocity
+    R rho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      rho += fi[i];
+      jx += fi[i] * (R)Lat<D>::cx(i);
+      jy += fi[i] * (R)Lat<D>::cy(i);
+      jz += fi[i] * (R)Lat<D>::cz(i);
+    }
+    const R ux = (jx + (R)0.5 * rho * (R)p.ax) / rho;
+    const R uy = (jy + (R)0.5 * rho * (R)p.ay) / rho;
+    const R uz = (jz + (R)0.5 * rho * (R)p.az) / rho;
+    R fe[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fe[i] = feq<R, D>(i, rho, ux, uy, uz);
+    R tau = (R)p.tau;
+    if (p.rheo != 0) {
+      R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const R fn = fi[i] - fe[i];
+        const R ex = (R)Lat<D>::cx(i), ey = (R)Lat<D>::cy(i), ez = (R)Lat<D>::cz(i);
+        pxx += ex * ex * fn;
+        pyy += ey * ey * fn;
+        pzz += ez * ez * fn;
+        pxy += ex * ey * fn;
+        pxz += ex * ez * fn;
+        pyz += ey * ez * fn;
+      }
+      const R nrm2 = pxx * pxx + pyy * pyy + pzz * pzz + (R)2 * (pxy * pxy + pxz * pxz + pyz * pyz);
+      tau = solve_tau<R>(p, sqrt(nrm2) / ((R)1.4142135623730951 * rho / (R)3));
+    }
+    const R om = (R)1 / tau;
+    if (p.has_force) {
+      const R ff = (R)1 - (R)0.5 * om;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const R ex = (R)Lat<D>::cx(i), ey = (R)Lat<D>::cy(i), ez = (R)Lat<D>::cz(i);
+        const R eu = ex * ux + ey * uy + ez * uz;
+        const R F = ((ex - ux) * (R)3 + eu * ex * (R)9) * rho * (R)p.ax +
+                    ((ey - uy) * (R)3 + eu * ey * (R)9) * rho * (R)p.ay +
+                    ((ez - uz) * (R)3 + eu * ez * (R)9) * rho * (R)p.az;
+        fi[i] = fi[i] - (fi[i] - fe[i]) * om + ff * (R)Lat<D>::w(i) * F;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) fi[i] = fi[i] - (fi[i] - fe[i]) * om;
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st(f, slot_out<D>(p, c, n, i, 1 - PAR), fi[i], fshift<S, D>(p, i));
+
+    R phin = 0, pho = 0;
+    if (isI) {
+      R *phi = (R *)p.phi;
+      const R Mn = ((const R *)p.M)[n];
+      pho = phi[n];
+      phin = Mn / rho;
+      phi[n] = phin;
+      int mk = MK_NONE;
+      if (Mn > ((R)1 + (R)p.eps) * rho)
+        mk = MK_FILL;
+      else if (Mn < -(R)p.eps * rho)
+        mk = MK_EMPTY;
+      if (mk) p.flags[n] = (uint8_t)(fl | (mk << 2));
+    }
+
+    // dissolved gas (Sec. 3.1-3.2)
+    R gi[QA];
+    R cgas = 0;
+    R fl_gas = 0;
+    gi[0] = ld(g, (size_t)n, gshift<S, D>(p, 0));
+#pragma unroll
+    for (int i = 1; i < QA; ++i) {
+      const int ts = tsrc[i];
+      if (ts == T_LIQ || ts == T_IFC) {
+        gi[i] = ld(g, slot_in<D>(p, c, n, i, PAR), gshift<S, D>(p, i));
+      } else if (ts == T_WALL) {
+        gi[i] = ld(g, slot_out<D>(p, c, n, opp(i), PAR), gshift<S, D>(p, opp(i)));
+      } else {
+        const int b = p.label_old[src<D>(p, c, i)];
+        const R cH = (R)p.kH * (b >= 0 ? (R)p.told.p[b] : (R)p.p0);
+        const R go = ld(g, slot_out<D>(p, c, n, opp(i), PAR), gshift<S, D>(p, opp(i)));
+        gi[i] = (R)2 * (R)Lat<D>::wa(i) * cH - go;
+        fl_gas += go - gi[i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < QA; ++i) cgas += gi[i];
+    const R omg = (R)1 / (R)p.taug;
+#pragma unroll
+    for (int i = 0; i < QA; ++i) {
+      const R v = gi[i] + (geq<R, D>(i, cgas, ux, uy, uz) - gi[i]) * omg + (R)Lat<D>::wa(i) * (R)p.q;
+      st(g, slot_out<D>(p, c, n, i, 1 - PAR), v, gshift<S, D>(p, i));
+    }
+    if (isI) {
+      flux = (double)(fl_gas - cgas * (phin - pho));
+      lab = p.label_old[n];
+      if (lab < 0) atomicAdd(p.led + 5, flux);
+    }
+  }
+  const int cnt = __syncthreads_count(active);
+  if (threadIdx.x == 0 && cnt) atomicAdd(p.fluid_updates, (unsigned long long)cnt);
+  if (__any_sync(0xffffffffu, isI && lab >= 0))
+    agg_add(p.told.dm, (isI && lab >= 0) ? lab : -1, flux, wbuf + (threadIdx.x & ~31));
+}
+
+}  // namespace lbf
