@@ -32,6 +32,7 @@ enum { GAS = 0, LIQ = 1, IFC = 2, WALL = 3 };
 enum { MK_NONE = 0, MK_FILL = 1, MK_EMPTY = 2, MK_GI = 3, MK_LI = 4 };
 enum { ERR_CAPACITY = -6 };
 static const double PI_ = 3.14159265358979323846;
+static const double LSQ_RIDGE = 1e-3;
 
 struct or_sim {
   or_config c;
@@ -805,7 +806,9 @@ static int solve_small(double *A, double *b, int k, double *x) {
   return 1;
 }
 
-/* least-squares fit of z = sum_j beta_j phi_j(x, y) */
+/* least-squares fit of z = sum_j beta_j phi_j(x, y), with a small ridge
+ * term so that point sets that cannot resolve every coefficient (cells next
+ * to walls, nearly axis-aligned planes) give a smooth, bounded answer */
 static int lsq_fit(const double (*pts)[3], int np, int k, int kind, double *beta) {
   double A[25] = {0}, b[5] = {0}, ph[5];
   int p, i, j;
@@ -823,6 +826,7 @@ static int lsq_fit(const double (*pts)[3], int np, int k, int kind, double *beta
       b[i] += ph[i] * pts[p][2];
     }
   }
+  for (i = 0; i < k; ++i) A[i * k + i] += LSQ_RIDGE;
   return solve_small(A, b, k, beta);
 }
 

@@ -140,7 +140,6 @@ int relabel_in_place(lbf_sim *s) {
   const int par = (int)(s->step & 1);
   Params p = make_params(s, s->step);
   p.flags_out = s->flags[par];
-  s->ops->uf_init(p, s->st);
   s->ops->label(p, s->st);
   s->ops->bubble_update(p, s->st);
   const size_t cap = (size_t)s->cap;
@@ -273,6 +272,7 @@ int validate(const lbf_config *c) {
   if (c->nx <= 0 || c->ny <= 0 || c->nz <= 0) return fail(LBF_EINVAL, "lattice sizes must be positive");
   if ((long long)c->nx * c->ny * c->nz > 2147483647LL) return fail(LBF_EINVAL, "more than 2^31-1 cells");
   if (c->nx < 3 || c->ny < 3 || (c->nz != 1 && c->nz < 3)) return fail(LBF_EINVAL, "each extent must be >= 3 (nz == 1 for 2D)");
+  if (c->ny > 65535 || c->nz > 65535) return fail(LBF_EINVAL, "ny and nz must be <= 65535");
   if (c->storage < 0 || c->storage > 3) return fail(LBF_EINVAL, "bad storage");
   if (c->rheo < 0 || c->rheo > 2) return fail(LBF_EINVAL, "bad rheology");
   if (!(c->tau > 0.5)) return fail(LBF_EINVAL, "tau must exceed 1/2");

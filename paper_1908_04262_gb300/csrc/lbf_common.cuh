@@ -123,35 +123,52 @@ struct Params {
 };
 
 // ---------------------------------------------------------------------------
-// indexing
+// indexing.  Full-lattice kernels run on a (ceil(nx/B), ny, nz) grid of
+// B-thread blocks along x, so a thread finds its cell without division; the
+// six periodic neighbour offsets are kept as index deltas.
 
 struct Cell {
   int x, y, z;
-  int xm, xp, ym, yp, zm, zp;  // wrapped neighbour coordinates
+  long long n;
+  int dxm, dxp;          // -1 / +1 along x, wrapped
+  long long dym, dyp;    // -nx / +nx along y, wrapped
+  long long dzm, dzp;    // -nx*ny / +nx*ny along z, wrapped
 };
 
-__device__ __forceinline__ Cell make_cell(const Params &p, long long n) {
+__device__ __forceinline__ Cell cell_at(const Params &p, int x, int y, int z) {
   Cell c;
-  const long long nxy = (long long)p.nx * p.ny;
-  c.z = (int)(n / nxy);
-  const long long r = n - (long long)c.z * nxy;
-  c.y = (int)(r / p.nx);
-  c.x = (int)(r - (long long)c.y * p.nx);
-  c.xm = c.x == 0 ? p.nx - 1 : c.x - 1;
-  c.xp = c.x == p.nx - 1 ? 0 : c.x + 1;
-  c.ym = c.y == 0 ? p.ny - 1 : c.y - 1;
-  c.yp = c.y == p.ny - 1 ? 0 : c.y + 1;
-  c.zm = c.z == 0 ? p.nz - 1 : c.z - 1;
-  c.zp = c.z == p.nz - 1 ? 0 : c.z + 1;
+  c.x = x; c.y = y; c.z = z;
+  const long long nx = p.nx, nxy = (long long)p.nx * p.ny;
+  c.n = x + nx * (y + (long long)p.ny * z);
+  c.dxm = x == 0 ? p.nx - 1 : -1;
+  c.dxp = x == p.nx - 1 ? 1 - p.nx : 1;
+  c.dym = y == 0 ? (long long)(p.ny - 1) * nx : -nx;
+  c.dyp = y == p.ny - 1 ? -(long long)(p.ny - 1) * nx : nx;
+  c.dzm = z == 0 ? (long long)(p.nz - 1) * nxy : -nxy;
+  c.dzp = z == p.nz - 1 ? -(long long)(p.nz - 1) * nxy : nxy;
   return c;
 }
 
+// the thread's cell in a full-lattice launch; false for padding threads
+__device__ __forceinline__ bool grid_cell(const Params &p, Cell &c) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  c = cell_at(p, x < p.nx ? x : p.nx - 1, blockIdx.y, blockIdx.z);
+  return x < p.nx;
+}
+
+// cell from a linear index (rare paths only: uses division)
+__device__ __forceinline__ Cell make_cell(const Params &p, long long n) {
+  const long long nxy = (long long)p.nx * p.ny;
+  const int z = (int)(n / nxy);
+  const long long r = n - (long long)z * nxy;
+  const int y = (int)(r / p.nx);
+  return cell_at(p, (int)(r - (long long)y * p.nx), y, z);
+}
+
 // cell at offset (dx,dy,dz) in {-1,0,1}^3
-__device__ __forceinline__ long long at(const Params &p, const Cell &c, int dx, int dy, int dz) {
-  const int xx = dx < 0 ? c.xm : (dx > 0 ? c.xp : c.x);
-  const int yy = dy < 0 ? c.ym : (dy > 0 ? c.yp : c.y);
-  const int zz = dz < 0 ? c.zm : (dz > 0 ? c.zp : c.z);
-  return xx + (long long)p.nx * (yy + (long long)p.ny * zz);
+__device__ __forceinline__ long long at(const Params &, const Cell &c, int dx, int dy, int dz) {
+  return c.n + (dx < 0 ? c.dxm : (dx > 0 ? c.dxp : 0)) + (dy < 0 ? c.dym : (dy > 0 ? c.dyp : 0)) +
+         (dz < 0 ? c.dzm : (dz > 0 ? c.dzp : 0));
 }
 
 // general periodic offset (any distance)

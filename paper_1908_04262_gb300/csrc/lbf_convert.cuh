@@ -13,7 +13,7 @@
 //                     interface neighbours; dissolved gas moves between the
 //                     liquid and the cell's bubble
 //   k_conv_apply      interface cells collect the excess; new types written
-//                     to the second flag buffer; union-find roots initialised
+//                     to the second flag buffer
 #pragma once
 #include "lbf_common.cuh"
 
@@ -68,11 +68,11 @@ __device__ __forceinline__ void write_equilibrium(const Params &p, const Cell &c
 
 template <int D>
 __global__ void k_conv_unmark(Params p) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
+  Cell c;
+  if (!grid_cell(p, c)) return;
+  const long long n = c.n;
   const uint8_t fl = p.flags[n];
   if (fmark(fl) != MK_EMPTY) return;
-  const Cell c = make_cell(p, n);
 #pragma unroll
   for (int i = 1; i < Lat<D>::Q; ++i)
     if (fmark(p.flags[nb<D>(p, c, i)]) == MK_FILL) {
@@ -83,12 +83,12 @@ __global__ void k_conv_unmark(Params p) {
 
 template <int D>
 __global__ void k_conv_neighbours(Params p) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
+  Cell c;
+  if (!grid_cell(p, c)) return;
+  const long long n = c.n;
   const uint8_t fl = p.flags[n];
   const int t = ftype(fl);
   if (t != T_GAS && t != T_LIQ) return;
-  const Cell c = make_cell(p, n);
   const int want = t == T_GAS ? MK_FILL : MK_EMPTY;
 #pragma unroll
   for (int i = 1; i < Lat<D>::Q; ++i)
@@ -103,15 +103,15 @@ template <int D, class S>
 __global__ void __launch_bounds__(256) k_conv_compute(Params p, int par) {
   using R = typename ST<S>::R;
   __shared__ double wbuf[256];
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const bool inr = n < p.N;
+  Cell c;
+  const bool inr = grid_cell(p, c);
+  const long long n = c.n;
   const uint8_t fl = inr ? p.flags[n] : (uint8_t)0;
   const int mk = fmark(fl);
   double dmv = 0.0;
   int lab = -1;
   if (inr && mk != MK_NONE) {
-    const Cell c = make_cell(p, n);
-    R *M = (R *)p.M;
+      R *M = (R *)p.M;
     if (mk == MK_FILL || mk == MK_EMPTY) {
       const R rho = sum_out_f<D, S>(p, c, n, par, nullptr);
       const R excess = mk == MK_FILL ? M[n] - rho : M[n];
@@ -172,14 +172,14 @@ __global__ void __launch_bounds__(256) k_conv_compute(Params p, int par) {
 template <int D, class S>
 __global__ void k_conv_apply(Params p, int par) {
   using R = typename ST<S>::R;
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
+  Cell c;
+  if (!grid_cell(p, c)) return;
+  const long long n = c.n;
   const uint8_t fl = p.flags[n];
   const int pt = post_type(fl);
   const int mk = fmark(fl);
   if (pt == T_IFC) {
-    const Cell c = make_cell(p, n);
-    const R *ex = (const R *)p.ex;
+      const R *ex = (const R *)p.ex;
     R *M = (R *)p.M;
     R recv = 0;
     bool has = false;
@@ -205,7 +205,6 @@ __global__ void k_conv_apply(Params p, int par) {
     ((R *)p.M)[n] = 0;
   }
   p.flags_out[n] = (uint8_t)(pt | (fl & NEARWALL));
-  if (pt == T_GAS) p.parent[n] = (int)n;
 }
 
 // ---------------------------------------------------------------------------
@@ -226,9 +225,9 @@ template <int D> __device__ __forceinline__ bool is_wall_cell(const Params &p, c
 template <int D, class S>
 __global__ void k_init_fill(Params p, int par, double fill_height) {
   using R = typename ST<S>::R;
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
-  const Cell c = make_cell(p, n);
+  Cell c;
+  if (!grid_cell(p, c)) return;
+  const long long n = c.n;
   R *M = (R *)p.M, *phi = (R *)p.phi;
   if (is_wall_cell<D>(p, c)) {
     p.flags[n] = T_WALL;
@@ -255,9 +254,9 @@ template <int D, class S>
 __global__ void k_init_cells(Params p, int par, const uint8_t *type, const double *rho, const double *u,
                              const double *alpha, const double *conc) {
   using R = typename ST<S>::R;
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
-  const Cell c = make_cell(p, n);
+  Cell c;
+  if (!grid_cell(p, c)) return;
+  const long long n = c.n;
   const int t = type[n] & 3;
   R *M = (R *)p.M, *phi = (R *)p.phi;
   p.flags[n] = (uint8_t)t;
@@ -273,11 +272,11 @@ __global__ void k_init_cells(Params p, int par, const uint8_t *type, const doubl
 // liquid next to gas becomes interface with alpha = 1 (two passes)
 template <int D>
 __global__ void k_separate_mark(Params p) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
+  Cell c;
+  if (!grid_cell(p, c)) return;
+  const long long n = c.n;
   const uint8_t fl = p.flags[n];
   if (ftype(fl) != T_LIQ) return;
-  const Cell c = make_cell(p, n);
 #pragma unroll
   for (int i = 1; i < Lat<D>::Q; ++i)
     if (ftype(p.flags[nb<D>(p, c, i)]) == T_GAS) {
@@ -289,11 +288,11 @@ __global__ void k_separate_mark(Params p) {
 template <int D, class S>
 __global__ void k_separate_apply(Params p, int par) {
   using R = typename ST<S>::R;
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
+  Cell c;
+  if (!grid_cell(p, c)) return;
+  const long long n = c.n;
   const uint8_t fl = p.flags[n];
   if (fmark(fl) != MK_LI) return;
-  const Cell c = make_cell(p, n);
   p.flags[n] = (uint8_t)(T_IFC | (fl & NEARWALL));
   ((R *)p.phi)[n] = 1;
   ((R *)p.M)[n] = sum_out_f<D, S>(p, c, n, par, nullptr);
@@ -301,9 +300,9 @@ __global__ void k_separate_apply(Params p, int par) {
 
 template <int D>
 __global__ void k_nearwall(Params p) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
-  const Cell c = make_cell(p, n);
+  Cell c;
+  if (!grid_cell(p, c)) return;
+  const long long n = c.n;
   bool w = false;
 #pragma unroll
   for (int i = 1; i < Lat<D>::Q; ++i) w |= ftype(p.flags[nb<D>(p, c, i)]) == T_WALL;
@@ -354,26 +353,19 @@ __global__ void k_nucleate(Params p, int par, double cx, double cy, double cz, d
   }
 }
 
-template <int D>
-__global__ void k_uf_init(Params p) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
-  if (ftype(p.flags_out[n]) == T_GAS) p.parent[n] = (int)n;
-}
-
 // ---------------------------------------------------------------------------
 // export and ledgers
 
 template <int D, class S>
 __global__ void k_fields(Params p, int par, int which, void *out, int dtype) {
   using R = typename ST<S>::R;
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
+  Cell c;
+  if (!grid_cell(p, c)) return;
+  const long long n = c.n;
   const int t = ftype(p.flags[n]);
   const bool fluid = t == T_LIQ || t == T_IFC;
   double v[3] = {0.0, 0.0, 0.0};
   int width = 1;
-  const Cell c = make_cell(p, n);
   switch (which) {
     case FLD_RHO: if (fluid) v[0] = (double)sum_out_f<D, S>(p, c, n, par, nullptr); break;
     case FLD_U:
@@ -414,19 +406,20 @@ __global__ void k_fields(Params p, int par, int which, void *out, int dtype) {
 // [0] liquid mass, [1] dissolved gas, [2] non-finite populations, plus cell
 // counts of the four types
 template <int D, class S>
-__global__ void __launch_bounds__(256) k_ledger(Params p, int par, double *acc, unsigned long long *counts) {
+__global__ void __launch_bounds__(128) k_ledger(Params p, int par, double *acc, unsigned long long *counts) {
   using R = typename ST<S>::R;
-  __shared__ double sm[3][256];
+  __shared__ double sm[3][128];
   __shared__ unsigned long long sc[4];
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  Cell c;
+  const bool inr = grid_cell(p, c);
+  const long long n = c.n;
   if (threadIdx.x < 4) sc[threadIdx.x] = 0;
   double mass = 0.0, gas = 0.0, bad = 0.0;
   __syncthreads();
-  if (n < p.N) {
+  if (inr) {
     const int t = ftype(p.flags[n]);
     atomicAdd(&sc[t], 1ull);
     if (t == T_LIQ || t == T_IFC) {
-      const Cell c = make_cell(p, n);
       const S *f = (const S *)p.f;
       double rho = 0.0;
       for (int i = 0; i < Lat<D>::Q; ++i) {
@@ -442,7 +435,7 @@ __global__ void __launch_bounds__(256) k_ledger(Params p, int par, double *acc, 
   sm[1][threadIdx.x] = gas;
   sm[2][threadIdx.x] = bad;
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
+  for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
     if (threadIdx.x < s)
       for (int k = 0; k < 3; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
     __syncthreads();

@@ -11,7 +11,8 @@
 // branches by the trigonometric formula, then one Newton polish).
 // Curvature: least-squares paraboloid through the PLIC points of the
 // interface cells of the stencil (each cut with the centre normal) in a frame
-// whose third axis is the normal; kappa = -(mean curvature), so a gas sphere
+// whose third axis is the normal (ridge-regularised normal equations);
+// kappa = -(mean curvature), so a gas sphere
 // has kappa = 1/R and a gas disk 1/(2R); limited to [-1, 1].
 // Disjoining pressure: march from the cell centre along the normal, cell
 // boundary by cell boundary (Algorithm 1, ties step diagonally), until an
@@ -163,12 +164,17 @@ __device__ __forceinline__ bool solve_small(R (&A)[K][K], R (&b)[K], R (&x)[K]) 
   return true;
 }
 
+// ridge added to the diagonal of the least-squares normal equations: point
+// sets that cannot resolve every coefficient (next to walls, nearly
+// axis-aligned planes) then give a smooth, bounded curvature
+constexpr double kLsqRidge = 1e-3;
+
 template <int D, class R>
 __global__ void __launch_bounds__(128) k_geometry(Params p) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
+  Cell c;
+  if (!grid_cell(p, c)) return;
+  const long long n = c.n;
   if (ftype(p.flags_out[n]) != T_IFC) return;
-  const Cell c = make_cell(p, n);
   const R *phi = (const R *)p.phi;
   R *kap = (R *)p.kappa, *nr = (R *)p.nrm, *ds = (R *)p.dst;
   constexpr int ZR = D == 3 ? 1 : 0;
@@ -271,6 +277,8 @@ __global__ void __launch_bounds__(128) k_geometry(Params p) {
       }
   R kv = 0;
   R beta[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) NA[i][i] += (R)kLsqRidge;
   const bool full = np >= (D == 3 ? 5 : 2) && solve_small<R, K>(NA, Nb, beta);
   if (full) {
     if constexpr (D == 3) {
@@ -280,16 +288,17 @@ __global__ void __launch_bounds__(128) k_geometry(Params p) {
     } else {
       kv = -beta[0] / pow((R)1 + beta[1] * beta[1], (R)1.5);
     }
-  } else if (np >= 1 && N1 >= (R)1e-9) {
-    kv = (D == 3 ? (R)-2 : (R)-1) * (b1 / N1);
+  } else if (np >= 1) {
+    kv = (D == 3 ? (R)-2 : (R)-1) * (b1 / (N1 + (R)kLsqRidge));
   }
   kap[n] = kv < (R)-1 ? (R)-1 : (kv > (R)1 ? (R)1 : kv);
 }
 
 template <int D, class R>
 __global__ void k_disjoining(Params p) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
+  Cell c;
+  if (!grid_cell(p, c)) return;
+  const long long n = c.n;
   if (ftype(p.flags_out[n]) != T_IFC) return;
   R *Pi = (R *)p.Pi;
   const int b = p.label_new[n];
@@ -299,7 +308,6 @@ __global__ void k_disjoining(Params p) {
     Pi[n] = 0;
     return;
   }
-  const Cell c = make_cell(p, n);
   R tmax[3], tdel[3];
   int step[3], off[3] = {0, 0, 0};
   for (int d = 0; d < 3; ++d) {

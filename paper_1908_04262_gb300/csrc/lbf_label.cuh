@@ -54,15 +54,96 @@ static __global__ void k_label_prep(Params p) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *p.nroots = 0;
 }
 
+// union-find tiles: the local pass joins gas cells of one tile in shared
+// memory, the merge pass joins tiles across their faces in global memory
+template <int D> struct Tile;
+template <> struct Tile<3> { static constexpr int TX = 32, TY = 8, TZ = 4; };
+template <> struct Tile<2> { static constexpr int TX = 32, TY = 32, TZ = 1; };
+constexpr int TILE_THREADS = 256;
+
+// parents only ever point to smaller indices, so a chain has at most TN
+// links; the caps below are never reached by a consistent forest
+__device__ __forceinline__ int sm_find(volatile int *lp, int a) {
+  for (int it = 0; it < 4096; ++it) {
+    const int b = lp[a];
+    if (b == a) break;
+    a = b;
+  }
+  return a;
+}
+
+__device__ __forceinline__ bool sm_union(int *lp, int a, int b) {
+  for (int it = 0; it < 65536; ++it) {
+    a = sm_find(lp, a);
+    b = sm_find(lp, b);
+    if (a == b) return true;
+    if (a > b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    const int old = atomicMin(lp + b, a);
+    if (old == b) return true;
+    b = old;
+  }
+  return false;
+}
+
 template <int D>
-__global__ void k_uf_hook(Params p) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
+__global__ void __launch_bounds__(TILE_THREADS) k_uf_local(Params p) {
+  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ;
+  __shared__ int lp[TN];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  const long long nx = p.nx, nxy = (long long)p.nx * p.ny;
+  for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
+    const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
+    bool gas = false;
+    if (x < p.nx && y < p.ny && z < p.nz) gas = ftype(p.flags_out[x + nx * y + nxy * z]) == T_GAS;
+    lp[t] = gas ? t : -1;
+  }
+  __syncthreads();
+  bool ok = true;
+  for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
+    if (lp[t] < 0) continue;
+    const int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
+#pragma unroll
+    for (int i = 1; i < Lat<D>::Q; i += 2) {  // one vector of each opposite pair
+      const int ax = lx + Lat<D>::cx(i), ay = ly + Lat<D>::cy(i), az = lz + Lat<D>::cz(i);
+      if (ax < 0 || ax >= TX || ay < 0 || ay >= TY || az < 0 || az >= TZ) continue;
+      const int u = ax + TX * (ay + TY * az);
+      if (lp[u] >= 0) ok &= sm_union(lp, t, u);
+    }
+  }
+  if (!ok) atomicOr(p.err, ERR_NOTCONV);
+  __syncthreads();
+  for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
+    if (lp[t] < 0) continue;
+    const int r = sm_find(lp, t);
+    const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
+    const int rx = x0 + r % TX, ry = y0 + (r / TX) % TY, rz = z0 + r / (TX * TY);
+    p.parent[x + nx * y + nxy * z] = (int)(rx + nx * ry + nxy * rz);
+  }
+}
+
+// gas cells join their gas neighbours in other tiles (or across the
+// periodic boundary)
+template <int D>
+__global__ void k_uf_merge(Params p) {
+  Cell c;
+  if (!grid_cell(p, c)) return;
+  const long long n = c.n;
   if (ftype(p.flags_out[n]) != T_GAS) return;
-  const Cell c = make_cell(p, n);
+  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
+  const int lx = c.x % TX, ly = c.y % TY, lz = c.z % TZ;
   bool ok = true;
 #pragma unroll
-  for (int i = 1; i < Lat<D>::Q; i += 2) {  // one vector of each opposite pair
+  for (int i = 1; i < Lat<D>::Q; i += 2) {
+    const int dx = Lat<D>::cx(i), dy = Lat<D>::cy(i), dz = Lat<D>::cz(i);
+    const int ax = c.x + dx, ay = c.y + dy, az = c.z + dz;
+    const bool wraps = ax < 0 || ax >= p.nx || ay < 0 || ay >= p.ny || az < 0 || az >= p.nz;
+    const bool crosses = wraps || lx + dx < 0 || lx + dx >= TX || ly + dy < 0 || ly + dy >= TY ||
+                         lz + dz < 0 || lz + dz >= TZ;
+    if (!crosses) continue;
     const long long m = nb<D>(p, c, i);
     if (ftype(p.flags_out[m]) == T_GAS) ok &= uf_union(p.parent, (int)n, (int)m);
   }
@@ -70,8 +151,9 @@ __global__ void k_uf_hook(Params p) {
 }
 
 static __global__ void k_uf_compress(Params p) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
+  Cell c;
+  if (!grid_cell(p, c)) return;
+  const long long n = c.n;
   if (ftype(p.flags_out[n]) != T_GAS) return;
   const int r = uf_find(p.parent, (int)n);
   p.parent[n] = r;
@@ -143,8 +225,9 @@ __device__ __forceinline__ void hash_insert(const Params &p, unsigned long long 
 template <int D, class R>
 __global__ void __launch_bounds__(256) k_relabel(Params p) {
   __shared__ double wbuf[256];
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const bool inr = n < p.N;
+  Cell c;
+  const bool inr = grid_cell(p, c);
+  const long long n = c.n;
   const int t = inr ? ftype(p.flags_out[n]) : T_WALL;
   const int cnt = *p.tnew.count;
   int knew = -1;
@@ -153,12 +236,10 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
     knew = root_index(p.roots, cnt, p.parent[n]);
     v = 1.0;
     if (p.atmosphere && knew >= 0) {
-      const Cell c = make_cell(p, n);
-      if ((D == 2 ? c.y : c.z) == p.top_layer) p.tnew.atm[knew] = 1;
+          if ((D == 2 ? c.y : c.z) == p.top_layer) p.tnew.atm[knew] = 1;
     }
   } else if (t == T_IFC) {
-    const Cell c = make_cell(p, n);
-#pragma unroll
+  #pragma unroll
     for (int i = 1; i < Lat<D>::Q; ++i) {
       const long long m = nb<D>(p, c, i);
       if (ftype(p.flags_out[m]) == T_GAS) {

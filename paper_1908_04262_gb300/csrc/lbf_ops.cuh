@@ -14,23 +14,30 @@ namespace lbf {
 
 inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// full-lattice launches: blocks of B threads along x, one block row per (y, z)
+inline int row_block(const Params &p) { return p.nx >= 96 ? 128 : (p.nx > 32 ? 64 : 32); }
+inline dim3 row_grid(const Params &p) {
+  const int b = row_block(p);
+  return dim3((unsigned)((p.nx + b - 1) / b), (unsigned)p.ny, (unsigned)p.nz);
+}
+
 template <int D, class S>
 struct OpsImpl final : Ops {
   using R = typename ST<S>::R;
   static constexpr int B = 256;
 
   void init_fill(const Params &p, int par, double h, cudaStream_t s) override {
-    k_init_fill<D, S><<<blocks_for(p.N, B), B, 0, s>>>(p, par, h);
+    k_init_fill<D, S><<<row_grid(p), row_block(p), 0, s>>>(p, par, h);
   }
   void init_cells(const Params &p, int par, const uint8_t *t, const double *rho, const double *u,
                   const double *a, const double *c, cudaStream_t s) override {
-    k_init_cells<D, S><<<blocks_for(p.N, B), B, 0, s>>>(p, par, t, rho, u, a, c);
+    k_init_cells<D, S><<<row_grid(p), row_block(p), 0, s>>>(p, par, t, rho, u, a, c);
   }
   void separate(const Params &p, int par, cudaStream_t s) override {
-    k_separate_mark<D><<<blocks_for(p.N, B), B, 0, s>>>(p);
-    k_separate_apply<D, S><<<blocks_for(p.N, B), B, 0, s>>>(p, par);
+    k_separate_mark<D><<<row_grid(p), row_block(p), 0, s>>>(p);
+    k_separate_apply<D, S><<<row_grid(p), row_block(p), 0, s>>>(p, par);
   }
-  void nearwall(const Params &p, cudaStream_t s) override { k_nearwall<D><<<blocks_for(p.N, B), B, 0, s>>>(p); }
+  void nearwall(const Params &p, cudaStream_t s) override { k_nearwall<D><<<row_grid(p), row_block(p), 0, s>>>(p); }
   void nucleate(const Params &p, int par, const double *c, double R0, cudaStream_t s) override {
     const int x0 = (int)floor(c[0] - R0 - 1.0), x1 = (int)ceil(c[0] + R0 + 1.0);
     const int y0 = (int)floor(c[1] - R0 - 1.0), y1 = (int)ceil(c[1] + R0 + 1.0);
@@ -40,47 +47,49 @@ struct OpsImpl final : Ops {
     k_nucleate<D, S><<<blocks_for(cnt, B), B, 0, s>>>(p, par, c[0], c[1], D == 3 ? c[2] : 0.0, R0, x0, y0,
                                                         z0, bx, by, bz);
   }
-  void uf_init(const Params &p, cudaStream_t s) override { k_uf_init<D><<<blocks_for(p.N, B), B, 0, s>>>(p); }
   void exchange(const Params &p, int par, cudaStream_t s) override {
     if (par)
-      k_exchange<D, S, 1><<<blocks_for(p.N, B), B, 0, s>>>(p);
+      k_exchange<D, S, 1><<<row_grid(p), row_block(p), 0, s>>>(p);
     else
-      k_exchange<D, S, 0><<<blocks_for(p.N, B), B, 0, s>>>(p);
+      k_exchange<D, S, 0><<<row_grid(p), row_block(p), 0, s>>>(p);
   }
   void stream_collide(const Params &p, int par, cudaStream_t s) override {
     if (par)
-      k_stream_collide<D, S, 1><<<blocks_for(p.N, B), B, 0, s>>>(p);
+      k_stream_collide<D, S, 1><<<row_grid(p), row_block(p), 0, s>>>(p);
     else
-      k_stream_collide<D, S, 0><<<blocks_for(p.N, B), B, 0, s>>>(p);
+      k_stream_collide<D, S, 0><<<row_grid(p), row_block(p), 0, s>>>(p);
   }
   void convert(const Params &p, int par, cudaStream_t s) override {
     const int post = 1 - par;
-    k_conv_unmark<D><<<blocks_for(p.N, B), B, 0, s>>>(p);
-    k_conv_neighbours<D><<<blocks_for(p.N, B), B, 0, s>>>(p);
-    k_conv_compute<D, S><<<blocks_for(p.N, B), B, 0, s>>>(p, post);
-    k_conv_apply<D, S><<<blocks_for(p.N, B), B, 0, s>>>(p, post);
+    k_conv_unmark<D><<<row_grid(p), row_block(p), 0, s>>>(p);
+    k_conv_neighbours<D><<<row_grid(p), row_block(p), 0, s>>>(p);
+    k_conv_compute<D, S><<<row_grid(p), row_block(p), 0, s>>>(p, post);
+    k_conv_apply<D, S><<<row_grid(p), row_block(p), 0, s>>>(p, post);
   }
   void label(const Params &p, cudaStream_t s) override {
     k_label_prep<<<blocks_for(p.cap, B), B, 0, s>>>(p);
-    k_uf_hook<D><<<blocks_for(p.N, B), B, 0, s>>>(p);
-    k_uf_compress<<<blocks_for(p.N, B), B, 0, s>>>(p);
+    const dim3 tg((unsigned)((p.nx + Tile<D>::TX - 1) / Tile<D>::TX), (unsigned)((p.ny + Tile<D>::TY - 1) / Tile<D>::TY),
+                  (unsigned)((p.nz + Tile<D>::TZ - 1) / Tile<D>::TZ));
+    k_uf_local<D><<<tg, TILE_THREADS, 0, s>>>(p);
+    k_uf_merge<D><<<row_grid(p), row_block(p), 0, s>>>(p);
+    k_uf_compress<<<row_grid(p), row_block(p), 0, s>>>(p);
     int P = 1;
     while (P < p.cap) P <<= 1;
     k_sort_roots<<<1, 1024, P * sizeof(int), s>>>(p);
-    k_relabel<D, R><<<blocks_for(p.N, B), B, 0, s>>>(p);
+    k_relabel<D, R><<<row_grid(p), row_block(p), 0, s>>>(p);
   }
   void bubble_update(const Params &p, cudaStream_t s) override { k_bubble_update<<<1, 1024, 0, s>>>(p); }
   void geometry(const Params &p, cudaStream_t s) override {
-    k_geometry<D, R><<<blocks_for(p.N, 128), 128, 0, s>>>(p);
+    k_geometry<D, R><<<row_grid(p), row_block(p), 0, s>>>(p);
   }
   void disjoining(const Params &p, cudaStream_t s) override {
-    k_disjoining<D, R><<<blocks_for(p.N, B), B, 0, s>>>(p);
+    k_disjoining<D, R><<<row_grid(p), row_block(p), 0, s>>>(p);
   }
   void field(const Params &p, int par, int which, void *out, int dtype, cudaStream_t s) override {
-    k_fields<D, S><<<blocks_for(p.N, B), B, 0, s>>>(p, par, which, out, dtype);
+    k_fields<D, S><<<row_grid(p), row_block(p), 0, s>>>(p, par, which, out, dtype);
   }
   void ledger(const Params &p, int par, double *acc, unsigned long long *counts, cudaStream_t s) override {
-    k_ledger<D, S><<<blocks_for(p.N, B), B, 0, s>>>(p, par, acc, counts);
+    k_ledger<D, S><<<row_grid(p), row_block(p), 0, s>>>(p, par, acc, counts);
   }
 };
 

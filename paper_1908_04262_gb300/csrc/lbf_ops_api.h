@@ -16,7 +16,6 @@ struct Ops {
   virtual void separate(const Params &p, int par, cudaStream_t s) = 0;
   virtual void nearwall(const Params &p, cudaStream_t s) = 0;
   virtual void nucleate(const Params &p, int par, const double *c, double R, cudaStream_t s) = 0;
-  virtual void uf_init(const Params &p, cudaStream_t s) = 0;
   // step pieces (par = parity of the populations when the step starts)
   virtual void exchange(const Params &p, int par, cudaStream_t s) = 0;
   virtual void stream_collide(const Params &p, int par, cudaStream_t s) = 0;

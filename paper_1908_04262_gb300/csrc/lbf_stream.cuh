@@ -65,13 +65,13 @@ template <class R> __device__ __forceinline__ R solve_tau(const Params &p, R A) 
 }
 
 template <int D, class S, int PAR>
-__global__ void __launch_bounds__(256) k_exchange(Params p) {
+__global__ void __launch_bounds__(128) k_exchange(Params p) {
   using R = typename ST<S>::R;
   constexpr int Q = Lat<D>::Q;
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
+  Cell c;
+  if (!grid_cell(p, c)) return;
+  const long long n = c.n;
   if (ftype(p.flags[n]) != T_IFC) return;
-  const Cell c = make_cell(p, n);
   const S *f = (const S *)p.f;
   R *M = (R *)p.M;
   const R *phi = (const R *)p.phi;
@@ -108,13 +108,18 @@ __global__ void __launch_bounds__(256) k_exchange(Params p) {
   M[n] = Mn;
 }
 
+template <class R> struct SweepOcc;
+template <> struct SweepOcc<double> { static constexpr int blocks = 3; };
+template <> struct SweepOcc<float> { static constexpr int blocks = 6; };
+
 template <int D, class S, int PAR>
-__global__ void __launch_bounds__(256) k_stream_collide(Params p) {
+__global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_stream_collide(Params p) {
   using R = typename ST<S>::R;
   constexpr int Q = Lat<D>::Q, QA = Lat<D>::QA;
-  __shared__ double wbuf[256];
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const bool inr = n < p.N;
+  __shared__ double wbuf[128];
+  Cell c;
+  const bool inr = grid_cell(p, c);
+  const long long n = c.n;
   const uint8_t fl = inr ? p.flags[n] : (uint8_t)T_GAS;
   const int type = ftype(fl);
   const bool active = inr && (type == T_LIQ || type == T_IFC);
@@ -122,46 +127,54 @@ __global__ void __launch_bounds__(256) k_stream_collide(Params p) {
   double flux = 0.0;
   int lab = -1;
   if (active) {
-    const Cell c = make_cell(p, n);
     S *f = (S *)p.f;
     S *g = (S *)p.g;
     const bool simple = type == T_LIQ && !(fl & NEARWALL);
-    R fi[Q];
-    R uIx = 0, uIy = 0, uIz = 0, rhog = 0, kap = 0, pi = 0;
-    if (isI) {
-      const R *uI = (const R *)p.uI;
-      uIx = uI[n];
-      uIy = uI[p.N + n];
-      uIz = uI[2 * p.N + n];
-      kap = ((const R *)p.kappa)[n];
-      pi = ((const R *)p.Pi)[n];
-    }
-    int tsrc[Q];
-    fi[0] = ld(f, (size_t)n, fshift<S, D>(p, 0));
-    tsrc[0] = T_LIQ;
+    // kinds of the source cells: bit i set when x - e_i is gas / a wall
+    unsigned gasm = 0, wallm = 0;
+    if (!simple) {
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      tsrc[i] = simple ? T_LIQ : ftype(p.flags[src<D>(p, c, i)]);
-      const int ts = tsrc[i];
-      if (ts == T_LIQ || ts == T_IFC) {
-        fi[i] = ld(f, slot_in<D>(p, c, n, i, PAR), fshift<S, D>(p, i));
-      } else if (ts == T_WALL) {
-        // half-way bounce-back: the cell's own outgoing population towards
-        // the wall, reflected (the slot belongs to the wall cell)
-        R v = ld(f, slot_out<D>(p, c, n, opp(i), PAR), fshift<S, D>(p, opp(i)));
-        const int sy = Lat<D>::cy(i) > 0 ? c.ym : (Lat<D>::cy(i) < 0 ? c.yp : c.y);
-        if ((p.walls & 8) && sy == p.ny - 1) {
-          const R eu = (R)Lat<D>::cx(i) * (R)p.uwx + (R)Lat<D>::cy(i) * (R)p.uwy + (R)Lat<D>::cz(i) * (R)p.uwz;
-          v += (R)2 * (R)Lat<D>::w(i) * (R)p.rho0 * eu * (R)3;
+      for (int i = 1; i < Q; ++i) {
+        const int ts = ftype(p.flags[src<D>(p, c, i)]);
+        gasm |= (ts == T_GAS ? 1u : 0u) << i;
+        wallm |= (ts == T_WALL ? 1u : 0u) << i;
+      }
+    }
+    R fi[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (i == 0 || !((gasm | wallm) >> i & 1u)) fi[i] = ld(f, slot_in<D>(p, c, n, i, PAR), fshift<S, D>(p, i));
+    }
+    if (gasm | wallm) {
+      R uIx = 0, uIy = 0, uIz = 0, kap = 0, pi = 0;
+      if (isI) {
+        const R *uI = (const R *)p.uI;
+        uIx = uI[n];
+        uIy = uI[p.N + n];
+        uIz = uI[2 * p.N + n];
+        kap = ((const R *)p.kappa)[n];
+        pi = ((const R *)p.Pi)[n];
+      }
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (wallm >> i & 1u) {
+          // half-way bounce-back: the cell's own outgoing population towards
+          // the wall, reflected (the slot belongs to the wall cell)
+          R v = ld(f, slot_out<D>(p, c, n, opp(i), PAR), fshift<S, D>(p, opp(i)));
+          const bool top = Lat<D>::cy(i) > 0 ? c.y == 0 : (Lat<D>::cy(i) < 0 ? c.y == p.ny - 2 : c.y == p.ny - 1);
+          if ((p.walls & 8) && top) {
+            const R eu = (R)Lat<D>::cx(i) * (R)p.uwx + (R)Lat<D>::cy(i) * (R)p.uwy + (R)Lat<D>::cz(i) * (R)p.uwz;
+            v += (R)2 * (R)Lat<D>::w(i) * (R)p.rho0 * eu * (R)3;
+          }
+          fi[i] = v;
+        } else if (gasm >> i & 1u) {
+          // Sec. 2.2 Eq. reconstruct with rho_g of Eq. rhob / rhobplusdisjoining
+          const int b = p.label_old[src<D>(p, c, i)];
+          const R pg = b >= 0 ? (R)p.told.p[b] : (R)p.p0;
+          const R rg = (pg - (R)2 * (R)p.sigma * kap - pi) * (R)3;
+          const R fo = ld(f, slot_out<D>(p, c, n, opp(i), PAR), fshift<S, D>(p, opp(i)));
+          fi[i] = feq<R, D>(i, rg, uIx, uIy, uIz) + feq<R, D>(opp(i), rg, uIx, uIy, uIz) - fo;
         }
-        fi[i] = v;
-      } else {
-        // Sec. 2.2 Eq. reconstruct: f_i = feq_i(rho_g,u_I) + feq_opp(rho_g,u_I) - f_opp
-        const int b = p.label_old[src<D>(p, c, i)];
-        const R pg = b >= 0 ? (R)p.told.p[b] : (R)p.p0;
-        rhog = (pg - (R)2 * (R)p.sigma * kap - pi) * (R)3;
-        const R fo = ld(f, slot_out<D>(p, c, n, opp(i), PAR), fshift<S, D>(p, opp(i)));
-        fi[i] = feq<R, D>(i, rhog, uIx, uIy, uIz) + feq<R, D>(opp(i), rhog, uIx, uIy, uIz) - fo;
       }
     }
     // moments and Guo-shifted velocity
@@ -176,15 +189,12 @@ __global__ void __launch_bounds__(256) k_stream_collide(Params p) {
     const R ux = (jx + (R)0.5 * rho * (R)p.ax) / rho;
     const R uy = (jy + (R)0.5 * rho * (R)p.ay) / rho;
     const R uz = (jz + (R)0.5 * rho * (R)p.az) / rho;
-    R fe[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) fe[i] = feq<R, D>(i, rho, ux, uy, uz);
     R tau = (R)p.tau;
     if (p.rheo != 0) {
       R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        const R fn = fi[i] - fe[i];
+        const R fn = fi[i] - feq<R, D>(i, rho, ux, uy, uz);
         const R ex = (R)Lat<D>::cx(i), ey = (R)Lat<D>::cy(i), ez = (R)Lat<D>::cz(i);
         pxx += ex * ex * fn;
         pyy += ey * ey * fn;
@@ -206,14 +216,16 @@ __global__ void __launch_bounds__(256) k_stream_collide(Params p) {
         const R F = ((ex - ux) * (R)3 + eu * ex * (R)9) * rho * (R)p.ax +
                     ((ey - uy) * (R)3 + eu * ey * (R)9) * rho * (R)p.ay +
                     ((ez - uz) * (R)3 + eu * ez * (R)9) * rho * (R)p.az;
-        fi[i] = fi[i] - (fi[i] - fe[i]) * om + ff * (R)Lat<D>::w(i) * F;
+        const R v = fi[i] - (fi[i] - feq<R, D>(i, rho, ux, uy, uz)) * om + ff * (R)Lat<D>::w(i) * F;
+        st(f, slot_out<D>(p, c, n, i, 1 - PAR), v, fshift<S, D>(p, i));
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) fi[i] = fi[i] - (fi[i] - fe[i]) * om;
+      for (int i = 0; i < Q; ++i) {
+        const R v = fi[i] - (fi[i] - feq<R, D>(i, rho, ux, uy, uz)) * om;
+        st(f, slot_out<D>(p, c, n, i, 1 - PAR), v, fshift<S, D>(p, i));
+      }
     }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) st(f, slot_out<D>(p, c, n, i, 1 - PAR), fi[i], fshift<S, D>(p, i));
 
     R phin = 0, pho = 0;
     if (isI) {
@@ -232,26 +244,22 @@ __global__ void __launch_bounds__(256) k_stream_collide(Params p) {
 
     // dissolved gas (Sec. 3.1-3.2)
     R gi[QA];
-    R cgas = 0;
-    R fl_gas = 0;
-    gi[0] = ld(g, (size_t)n, gshift<S, D>(p, 0));
+    R cgas = 0, fl_gas = 0;
 #pragma unroll
-    for (int i = 1; i < QA; ++i) {
-      const int ts = tsrc[i];
-      if (ts == T_LIQ || ts == T_IFC) {
-        gi[i] = ld(g, slot_in<D>(p, c, n, i, PAR), gshift<S, D>(p, i));
-      } else if (ts == T_WALL) {
+    for (int i = 0; i < QA; ++i) {
+      if (i > 0 && (wallm >> i & 1u)) {
         gi[i] = ld(g, slot_out<D>(p, c, n, opp(i), PAR), gshift<S, D>(p, opp(i)));
-      } else {
+      } else if (i > 0 && (gasm >> i & 1u)) {
         const int b = p.label_old[src<D>(p, c, i)];
         const R cH = (R)p.kH * (b >= 0 ? (R)p.told.p[b] : (R)p.p0);
         const R go = ld(g, slot_out<D>(p, c, n, opp(i), PAR), gshift<S, D>(p, opp(i)));
         gi[i] = (R)2 * (R)Lat<D>::wa(i) * cH - go;
         fl_gas += go - gi[i];
+      } else {
+        gi[i] = ld(g, slot_in<D>(p, c, n, i, PAR), gshift<S, D>(p, i));
       }
+      cgas += gi[i];
     }
-#pragma unroll
-    for (int i = 0; i < QA; ++i) cgas += gi[i];
     const R omg = (R)1 / (R)p.taug;
 #pragma unroll
     for (int i = 0; i < QA; ++i) {
@@ -264,8 +272,10 @@ __global__ void __launch_bounds__(256) k_stream_collide(Params p) {
       if (lab < 0) atomicAdd(p.led + 5, flux);
     }
   }
-  const int cnt = __syncthreads_count(active);
-  if (threadIdx.x == 0 && cnt) atomicAdd(p.fluid_updates, (unsigned long long)cnt);
+  if (p.q != 0.0) {
+    const unsigned b = __ballot_sync(0xffffffffu, active);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(p.fluid_updates, (unsigned long long)__popc(b));
+  }
   if (__any_sync(0xffffffffu, isI && lab >= 0))
     agg_add(p.told.dm, (isI && lab >= 0) ? lab : -1, flux, wbuf + (threadIdx.x & ~31));
 }
