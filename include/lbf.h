@@ -154,11 +154,12 @@ int lbf_fields(lbf_sim *s, unsigned mask, void *const *dst, int dst_is_device, i
  * Returns LBF_ENONFINITE when [7] > 0. */
 int lbf_ledger(lbf_sim *s, double *out8);
 
-/* Kernel timing for measurements: while enabled, lbf_step launches its
- * kernels one by one (no CUDA graph) and brackets each with CUDA events on
- * cfg.stream.  lbf_timing_read sums the device time of every kernel group
- * since the last enable: out_ms[k] and out_launches[k] for k < nmax, in the
- * order of lbf_timing_name(k).  Returns the number of groups. */
+/* Kernel timing for measurements: while enabled, lbf_step replays a second
+ * CUDA graph of the same step in which every kernel group is bracketed by
+ * CUDA event records on cfg.stream, and synchronises after each step to read
+ * them.  lbf_timing_read sums the device time of every kernel group since
+ * the last enable: out_ms[k] and out_launches[k] for k < nmax, in the order
+ * of lbf_timing_name(k).  Returns the number of groups. */
 int lbf_timing_enable(lbf_sim *s, int enable);
 int lbf_timing_read(lbf_sim *s, double *out_ms, long long *out_launches, int nmax);
 const char *lbf_timing_name(int k);

@@ -53,11 +53,17 @@ struct lbf_sim {
   std::vector<void *> allocs;
   // device state
   void *f = nullptr, *g = nullptr;
-  uint8_t *flags[2] = {nullptr, nullptr};
+  uint8_t *flags = nullptr;
+  int *ilist[2] = {nullptr, nullptr}, *icount[2] = {nullptr, nullptr}, *nlist = nullptr, *ncount = nullptr;
+  int list_blocks = 0;
   void *M = nullptr, *phi = nullptr, *uI = nullptr, *kappa = nullptr, *Pi = nullptr, *nrm = nullptr,
        *dst = nullptr, *ex = nullptr;
   int *label[2] = {nullptr, nullptr}, *parent = nullptr, *roots = nullptr, *nroots = nullptr;
+  int *lsize = nullptr;
+  uint8_t *tstat = nullptr;
+  int *troot = nullptr;
   unsigned long long *hash = nullptr;
+  int *hlist = nullptr, *hcount = nullptr;
   int hash_size = 0, cap = 0;
   Table tab[2];
   int *gpar, *gnold, *gnnew, *gatm, *gminid, *gheir;
@@ -72,12 +78,12 @@ struct lbf_sim {
   void *staging = nullptr;
   long long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t tgraph[2] = {nullptr, nullptr};  // with event records
+  cudaEvent_t tev[2][2 * G_COUNT];
+  bool tev_made = false;
   std::vector<Nucleus> queue;
   // timing
   bool timing = false;
-  std::vector<cudaEvent_t> ev_pool;
-  size_t ev_used = 0;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;
   double t_ms[G_COUNT] = {0};
   long long t_n[G_COUNT] = {0};
 };
@@ -96,8 +102,9 @@ template <class T> int dalloc(lbf_sim *s, T **p, size_t count) {
   return dev_alloc(s, (void **)p, count * sizeof(T));
 }
 
-// parameters for work at step `step`: par = population parity, flags[par]
-// current, flags[1-par] written by the conversion, labels and tables likewise
+// parameters for work at step `step`: par = population parity; labels,
+// bubble tables and interface lists [par] are current, [1-par] are written
+// during the step
 Params make_params(lbf_sim *s, long long step) {
   const int par = (int)(step & 1);
   const lbf_config &c = s->cfg;
@@ -105,16 +112,25 @@ Params make_params(lbf_sim *s, long long step) {
   memset(&p, 0, sizeof p);
   p.nx = c.nx; p.ny = c.ny; p.nz = c.nz; p.dim = s->dim; p.N = s->N;
   p.f = s->f; p.g = s->g;
-  p.flags = s->flags[par];
-  p.flags_out = s->flags[1 - par];
+  p.flags = s->flags;
+  p.ilist = s->ilist[par];
+  p.icount = s->icount[par];
+  p.inext = s->ilist[1 - par];
+  p.inext_count = s->icount[1 - par];
+  p.nlist = s->nlist;
+  p.ncount = s->ncount;
+  p.list_blocks = s->list_blocks;
   p.M = s->M; p.phi = s->phi; p.uI = s->uI; p.kappa = s->kappa; p.Pi = s->Pi; p.nrm = s->nrm;
   p.dst = s->dst; p.ex = s->ex;
   p.label_old = s->label[par];
   p.label_new = s->label[1 - par];
   p.parent = s->parent;
+  p.lsize = s->lsize;
+  p.tstat = s->tstat;
+  p.troot = s->troot;
   p.told = s->tab[par];
   p.tnew = s->tab[1 - par];
-  p.roots = s->roots; p.nroots = s->nroots; p.hash = s->hash; p.hash_size = s->hash_size; p.cap = s->cap;
+  p.roots = s->roots; p.nroots = s->nroots; p.hash = s->hash; p.hlist = s->hlist; p.hcount = s->hcount; p.hash_size = s->hash_size; p.cap = s->cap;
   p.gpar = s->gpar; p.gnold = s->gnold; p.gnnew = s->gnnew; p.gatm = s->gatm; p.gminid = s->gminid;
   p.gheir = s->gheir; p.gmold = s->gmold; p.gvnew = s->gvnew; p.gvmax = s->gvmax;
   p.next_id = s->next_id; p.led = s->led; p.fluid_updates = s->fluid_updates; p.err = s->err;
@@ -139,7 +155,7 @@ Params make_params(lbf_sim *s, long long step) {
 int relabel_in_place(lbf_sim *s) {
   const int par = (int)(s->step & 1);
   Params p = make_params(s, s->step);
-  p.flags_out = s->flags[par];
+  s->ops->build_ilist(p, s->st);
   s->ops->label(p, s->st);
   s->ops->bubble_update(p, s->st);
   const size_t cap = (size_t)s->cap;
@@ -168,48 +184,36 @@ int separate_and_relabel(lbf_sim *s) {
   return relabel_in_place(s);
 }
 
-cudaEvent_t next_event(lbf_sim *s) {
-  if (s->ev_used == s->ev_pool.size()) {
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    s->ev_pool.push_back(e);
-  }
-  return s->ev_pool[s->ev_used++];
-}
-
-// the launch sequence of one step
-void enqueue_step(lbf_sim *s, const Params &p, int par, bool timed) {
+// the launch sequence of one step; with `ev` every kernel group is
+// bracketed by event records (captured into the timing graph)
+void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
   auto group = [&](int gidx, auto &&fn) {
-    if (timed) {
-      cudaEvent_t a = next_event(s), b = next_event(s);
-      cudaEventRecord(a, s->st);
-      fn();
-      cudaEventRecord(b, s->st);
-      s->ev_marks.push_back({gidx, {a, b}});
-    } else {
-      fn();
-    }
+    if (ev) cudaEventRecordWithFlags(ev[2 * gidx], s->st, cudaEventRecordExternal);
+    fn();
+    if (ev) cudaEventRecordWithFlags(ev[2 * gidx + 1], s->st, cudaEventRecordExternal);
   };
   group(G_EXCHANGE, [&] { s->ops->exchange(p, par, s->st); });
   group(G_STREAM, [&] { s->ops->stream_collide(p, par, s->st); });
   group(G_CONVERT, [&] { s->ops->convert(p, par, s->st); });
   group(G_LABEL, [&] { s->ops->label(p, s->st); });
   group(G_BUBBLE, [&] { s->ops->bubble_update(p, s->st); });
-  group(G_GEOMETRY, [&] { s->ops->geometry(p, s->st); });
-  group(G_DISJOIN, [&] { s->ops->disjoining(p, s->st); });
+  // the geometry of the next step works on the interface list the
+  // conversion produced
+  Params pn = p;
+  pn.ilist = p.inext;
+  pn.icount = p.inext_count;
+  group(G_GEOMETRY, [&] { s->ops->geometry(pn, s->st); });
+  group(G_DISJOIN, [&] { s->ops->disjoining(pn, s->st); });
 }
 
-int harvest_timing(lbf_sim *s) {
-  if (s->ev_marks.empty()) return 0;
-  CK(cudaStreamSynchronize(s->st));
-  for (auto &m : s->ev_marks) {
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, m.second.first, m.second.second));
-    s->t_ms[m.first] += ms;
-    s->t_n[m.first] += 1;
-  }
-  s->ev_marks.clear();
-  s->ev_used = 0;
+int capture(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev, cudaGraphExec_t *out) {
+  cudaGraph_t gr;
+  CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+  enqueue_step(s, p, par, ev);
+  CK(cudaStreamEndCapture(s->st, &gr));
+  cudaError_t e = cudaGraphInstantiate(out, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return fail(LBF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
   return 0;
 }
 
@@ -217,22 +221,28 @@ int run_one_step(lbf_sim *s) {
   const int par = (int)(s->step & 1);
   Params p = make_params(s, s->step);
   if (s->timing) {
-    enqueue_step(s, p, par, true);
-    CK(cudaGetLastError());
-    if (s->ev_marks.size() > 4096) {
-      int rc = harvest_timing(s);
+    if (!s->tev_made) {
+      for (int k = 0; k < 2; ++k)
+        for (int j = 0; j < 2 * G_COUNT; ++j) CK(cudaEventCreate(&s->tev[k][j]));
+      s->tev_made = true;
+    }
+    if (!s->tgraph[par]) {
+      int rc = capture(s, p, par, s->tev[par], &s->tgraph[par]);
       if (rc) return rc;
+    }
+    CK(cudaGraphLaunch(s->tgraph[par], s->st));
+    CK(cudaStreamSynchronize(s->st));
+    for (int gidx = 0; gidx < G_COUNT; ++gidx) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, s->tev[par][2 * gidx], s->tev[par][2 * gidx + 1]));
+      s->t_ms[gidx] += ms;
+      s->t_n[gidx] += 1;
     }
     return 0;
   }
   if (!s->graph[par]) {
-    cudaGraph_t gr;
-    CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
-    enqueue_step(s, p, par, false);
-    CK(cudaStreamEndCapture(s->st, &gr));
-    cudaError_t e = cudaGraphInstantiate(&s->graph[par], gr, 0);
-    cudaGraphDestroy(gr);
-    if (e != cudaSuccess) return fail(LBF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    int rc = capture(s, p, par, nullptr, &s->graph[par]);
+    if (rc) return rc;
   }
   CK(cudaGraphLaunch(s->graph[par], s->st));
   return 0;
@@ -293,9 +303,13 @@ const char *lbf_last_error(void) { return g_err.c_str(); }
 void lbf_destroy(lbf_sim *s) {
   if (!s) return;
   if (s->st) cudaStreamSynchronize(s->st);
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < 2; ++k) {
     if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
-  for (auto e : s->ev_pool) cudaEventDestroy(e);
+    if (s->tgraph[k]) cudaGraphExecDestroy(s->tgraph[k]);
+  }
+  if (s->tev_made)
+    for (int k = 0; k < 2; ++k)
+      for (int j = 0; j < 2 * G_COUNT; ++j) cudaEventDestroy(s->tev[k][j]);
   for (void *p : s->allocs) cudaFree(p);
   if (s->own_stream && s->st) cudaStreamDestroy(s->st);
   delete s->ops;
@@ -334,6 +348,12 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     s->own_stream = true;
   }
   const size_t N = (size_t)s->N;
+  {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    s->list_blocks = 4 * (sms > 0 ? sms : 132);
+  }
   s->cap = cfg->bubble_capacity;
   int hs = 1024;
   while (hs < 4 * s->cap) hs <<= 1;
@@ -348,8 +368,13 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   } while (0)
   AL(dev_alloc(s, &s->f, N * s->Q * s->ssz));
   AL(dev_alloc(s, &s->g, N * s->QA * s->ssz));
-  AL(dalloc(s, &s->flags[0], N));
-  AL(dalloc(s, &s->flags[1], N));
+  AL(dalloc(s, &s->flags, N));
+  AL(dalloc(s, &s->ilist[0], N));
+  AL(dalloc(s, &s->ilist[1], N));
+  AL(dalloc(s, &s->icount[0], 1));
+  AL(dalloc(s, &s->icount[1], 1));
+  AL(dalloc(s, &s->nlist, N));
+  AL(dalloc(s, &s->ncount, 1));
   AL(dev_alloc(s, &s->M, N * s->rsz));
   AL(dev_alloc(s, &s->phi, N * s->rsz));
   AL(dev_alloc(s, &s->uI, 3 * N * s->rsz));
@@ -361,9 +386,19 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   AL(dalloc(s, &s->label[0], N));
   AL(dalloc(s, &s->label[1], N));
   AL(dalloc(s, &s->parent, N));
+  AL(dalloc(s, &s->lsize, N));
+  {
+    // union-find tiles: 32x8x4 in 3D, 32x32 in 2D
+    const size_t tx = (cfg->nx + 31) / 32, ty = (cfg->ny + (s->dim == 3 ? 7 : 31)) / (s->dim == 3 ? 8 : 32),
+                 tz = s->dim == 3 ? (cfg->nz + 3) / 4 : 1;
+    AL(dalloc(s, &s->tstat, tx * ty * tz));
+    AL(dalloc(s, &s->troot, tx * ty * tz));
+  }
   AL(dalloc(s, &s->roots, (size_t)s->cap));
   AL(dalloc(s, &s->nroots, 1));
   AL(dalloc(s, &s->hash, (size_t)hs));
+  AL(dalloc(s, &s->hlist, (size_t)hs));
+  AL(dalloc(s, &s->hcount, 1));
   for (int k = 0; k < 2; ++k) {
     Table &t = s->tab[k];
     AL(dalloc(s, &t.m, s->cap));
@@ -409,6 +444,10 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     e = e ? e : zero(s->tab[k].dm, sizeof(double) * s->cap);
   }
   e = e ? e : zero(s->next_id, sizeof(int));
+  e = e ? e : zero(s->icount[0], sizeof(int));
+  e = e ? e : zero(s->icount[1], sizeof(int));
+  e = e ? e : zero(s->ncount, sizeof(int));
+  e = e ? e : zero(s->hcount, sizeof(int));
   e = e ? e : zero(s->led, 8 * sizeof(double));
   e = e ? e : zero(s->fluid_updates, sizeof(unsigned long long));
   e = e ? e : zero(s->err, sizeof(int));
@@ -613,8 +652,6 @@ int lbf_cell_counts(lbf_sim *s, long long *out4) {
 
 int lbf_timing_enable(lbf_sim *s, int enable) {
   if (!s) return fail(LBF_EINVAL, "NULL sim");
-  int rc = harvest_timing(s);
-  if (rc) return rc;
   s->timing = enable != 0;
   for (int k = 0; k < G_COUNT; ++k) {
     s->t_ms[k] = 0.0;
@@ -625,8 +662,6 @@ int lbf_timing_enable(lbf_sim *s, int enable) {
 
 int lbf_timing_read(lbf_sim *s, double *out_ms, long long *out_launches, int nmax) {
   if (!s) return fail(LBF_EINVAL, "NULL sim");
-  int rc = harvest_timing(s);
-  if (rc) return rc;
   for (int k = 0; k < G_COUNT && k < nmax; ++k) {
     if (out_ms) out_ms[k] = s->t_ms[k];
     if (out_launches) out_launches[k] = s->t_n[k];

@@ -95,15 +95,22 @@ struct Params {
   int nx, ny, nz, dim;
   long long N;
   void *f, *g;           // populations (storage type)
-  uint8_t *flags;        // current flags (marks are written in place)
-  uint8_t *flags_out;    // flags after conversion
+  uint8_t *flags;        // cell flags (conversion marks written in place)
+  int *ilist, *icount;   // interface cells at the start of the step
+  int *inext, *inext_count;  // interface cells after the conversion
+  int *nlist, *ncount;   // gas/liquid cells turning interface this step
+  int list_blocks;       // persistent grid size of the list kernels
   void *M, *phi;         // liquid mass, fill level (arithmetic type)
   void *uI;              // 3N: velocity of interface cells from the last step
   void *kappa, *Pi, *nrm, *dst, *ex;
   int *label_old, *label_new, *parent;
+  int *lsize;            // size of each tile-local gas component, at its root
+  uint8_t *tstat;        // per union-find tile: 0 no gas, 1 one gas component, 2 several
+  int *troot;            // per tile with one component: its root cell
   Table told, tnew;
   int *roots, *nroots;
   unsigned long long *hash;
+  int *hlist, *hcount;   // occupied hash slots, in insertion order
   int hash_size, cap;
   // K10 scratch (2*cap each)
   int *gpar, *gnold, *gnnew, *gatm, *gminid, *gheir;
@@ -211,6 +218,21 @@ template <class S, int D> __device__ __forceinline__ typename ST<S>::R fshift(co
 }
 template <class S, int D> __device__ __forceinline__ typename ST<S>::R gshift(const Params &p, int i) {
   return (typename ST<S>::R)(Lat<D>::wa(i) * p.c0);
+}
+
+// lists of cells: grid-stride loop over n entries
+#define FOR_LIST(k, count) for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (count); k += gridDim.x * blockDim.x)
+
+// append to a list with one atomic per warp
+__device__ __forceinline__ void list_append(int *list, int *count, bool take, int value) {
+  const unsigned m = __ballot_sync(__activemask(), take);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(__activemask(), base, leader);
+  if (take) list[base + __popc(m & ((1u << lane) - 1u))] = value;
 }
 
 // post-conversion type from a flag byte carrying marks

@@ -12,8 +12,8 @@
 //                     cells from gas start at the mean equilibrium of their
 //                     interface neighbours; dissolved gas moves between the
 //                     liquid and the cell's bubble
-//   k_conv_apply      interface cells collect the excess; new types written
-//                     to the second flag buffer
+//   k_conv_apply      interface cells collect the excess and refresh alpha
+//   k_conv_finalize   new types replace the marks; the next interface list
 #pragma once
 #include "lbf_common.cuh"
 
@@ -66,145 +66,216 @@ __device__ __forceinline__ void write_equilibrium(const Params &p, const Cell &c
     st(g, slot_out<D>(p, c, n, i, par), geq<R, D>(i, conc, u[0], u[1], u[2]), gshift<S, D>(p, i));
 }
 
-template <int D>
-__global__ void k_conv_unmark(Params p) {
-  Cell c;
-  if (!grid_cell(p, c)) return;
-  const long long n = c.n;
-  const uint8_t fl = p.flags[n];
-  if (fmark(fl) != MK_EMPTY) return;
-#pragma unroll
-  for (int i = 1; i < Lat<D>::Q; ++i)
-    if (fmark(p.flags[nb<D>(p, c, i)]) == MK_FILL) {
-      p.flags[n] = (uint8_t)(fl & ~(7 << 2));
-      return;
-    }
-}
+// all conversion kernels walk the interface list of the step (every cell
+// that can fill or empty) and the list of cells they turn into interface;
+// persistent grids, one thread per listed cell
 
 template <int D>
-__global__ void k_conv_neighbours(Params p) {
-  Cell c;
-  if (!grid_cell(p, c)) return;
-  const long long n = c.n;
-  const uint8_t fl = p.flags[n];
-  const int t = ftype(fl);
-  if (t != T_GAS && t != T_LIQ) return;
-  const int want = t == T_GAS ? MK_FILL : MK_EMPTY;
+__global__ void k_conv_unmark(Params p) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *p.inext_count = 0;
+    *p.ncount = 0;
+  }
+  const int cnt = *p.icount;
+  FOR_LIST(k, cnt) {
+    const long long n = p.ilist[k];
+    const uint8_t fl = p.flags[n];
+    if (fmark(fl) != MK_EMPTY) continue;
+    const Cell c = make_cell(p, n);
 #pragma unroll
-  for (int i = 1; i < Lat<D>::Q; ++i)
-    if (fmark(p.flags[nb<D>(p, c, i)]) == want) {
-      p.flags[n] = (uint8_t)(fl | ((t == T_GAS ? MK_GI : MK_LI) << 2));
-      return;
+    for (int i = 1; i < Lat<D>::Q; ++i)
+      if (fmark(p.flags[nb<D>(p, c, i)]) == MK_FILL) {
+        p.flags[n] = (uint8_t)(fl & ~(7 << 2));
+        break;
+      }
+  }
+}
+
+// set a conversion mark on a neighbour's flag byte; true for the first writer
+__device__ __forceinline__ bool mark_byte(uint8_t *flags, long long m, int mk) {
+  const uintptr_t a = (uintptr_t)(flags + m);
+  unsigned *word = (unsigned *)(a & ~(uintptr_t)3);
+  const int sh = (int)(a & 3) * 8;
+  const unsigned old = atomicOr(word, (unsigned)(mk << 2) << sh);
+  return ((old >> sh) & (7u << 2)) == 0;
+}
+
+// gas next to a filling cell and liquid next to an emptying cell become
+// interface (liquid never meets gas); the first marker lists the cell
+template <int D>
+__global__ void k_conv_neighbours(Params p) {
+  const int cnt = *p.icount;
+  for (int base = blockIdx.x * blockDim.x; base < cnt; base += gridDim.x * blockDim.x) {
+    const int k = base + threadIdx.x;
+    int mk = MK_NONE;
+    long long n = 0;
+    if (k < cnt) {
+      n = p.ilist[k];
+      mk = fmark(p.flags[n]);
     }
+    if (mk == MK_FILL || mk == MK_EMPTY) {
+      const Cell c = make_cell(p, n);
+      const int want = mk == MK_FILL ? T_GAS : T_LIQ;
+      const int put = mk == MK_FILL ? MK_GI : MK_LI;
+#pragma unroll
+      for (int i = 1; i < Lat<D>::Q; ++i) {
+        const long long m = nb<D>(p, c, i);
+        const bool first = ftype(p.flags[m]) == want && mark_byte(p.flags, m, put);
+        if (first) {
+          const int pos = atomicAdd(p.ncount, 1);
+          p.nlist[pos] = (int)m;
+        }
+      }
+    }
+  }
+}
+
+// cell n of the interface list or of the new-interface list
+__device__ __forceinline__ long long list_cell(const Params &p, int k, int ni) {
+  return k < ni ? p.ilist[k] : p.nlist[k - ni];
 }
 
 // par: parity of the populations after the sweep
 template <int D, class S>
-__global__ void __launch_bounds__(256) k_conv_compute(Params p, int par) {
+__global__ void __launch_bounds__(128) k_conv_compute(Params p, int par) {
   using R = typename ST<S>::R;
-  __shared__ double wbuf[256];
-  Cell c;
-  const bool inr = grid_cell(p, c);
-  const long long n = c.n;
-  const uint8_t fl = inr ? p.flags[n] : (uint8_t)0;
-  const int mk = fmark(fl);
-  double dmv = 0.0;
-  int lab = -1;
-  if (inr && mk != MK_NONE) {
-      R *M = (R *)p.M;
-    if (mk == MK_FILL || mk == MK_EMPTY) {
-      const R rho = sum_out_f<D, S>(p, c, n, par, nullptr);
-      const R excess = mk == MK_FILL ? M[n] - rho : M[n];
-      int cnt = 0;
+  __shared__ double wbuf[128];
+  const int ni = *p.icount, total = ni + *p.ncount;
+  for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+    const int k = base + threadIdx.x;
+    double dmv = 0.0;
+    int lab = -1;
+    if (k < total) {
+      const long long n = list_cell(p, k, ni);
+      const uint8_t fl = p.flags[n];
+      const int mk = fmark(fl);
+      if (mk != MK_NONE) {
+        const Cell c = make_cell(p, n);
+        R *M = (R *)p.M;
+        if (mk == MK_FILL || mk == MK_EMPTY) {
+          const R rho = sum_out_f<D, S>(p, c, n, par, nullptr);
+          const R excess = mk == MK_FILL ? M[n] - rho : M[n];
+          int cnt = 0;
 #pragma unroll
-      for (int i = 1; i < Lat<D>::Q; ++i) cnt += post_type(p.flags[nb<D>(p, c, i)]) == T_IFC;
-      R *ex = (R *)p.ex;
-      if (cnt > 0)
-        ex[n] = excess / (R)cnt;
-      else
-        atomicAdd(p.led + 1, (double)excess);
-      if (mk == MK_EMPTY) {
-        const double cg = (double)sum_out_g<D, S>(p, c, n, par);
-        lab = p.label_old[n];
-        if (lab >= 0)
-          dmv = cg;
-        else
-          atomicAdd(p.led + 5, cg);
-      }
-    } else if (mk == MK_GI) {
-      R rs = 0, us[3] = {0, 0, 0}, cs = 0;
-      int cnt = 0;
+          for (int i = 1; i < Lat<D>::Q; ++i) cnt += post_type(p.flags[nb<D>(p, c, i)]) == T_IFC;
+          R *ex = (R *)p.ex;
+          if (cnt > 0)
+            ex[n] = excess / (R)cnt;
+          else
+            atomicAdd(p.led + 1, (double)excess);
+          if (mk == MK_EMPTY) {
+            const double cg = (double)sum_out_g<D, S>(p, c, n, par);
+            lab = p.label_old[n];
+            if (lab >= 0)
+              dmv = cg;
+            else
+              atomicAdd(p.led + 5, cg);
+          }
+        } else if (mk == MK_GI) {
+          R rs = 0, us[3] = {0, 0, 0}, cs = 0;
+          int cnt = 0;
 #pragma unroll
-      for (int i = 1; i < Lat<D>::Q; ++i) {
-        const long long m = nb<D>(p, c, i);
-        const uint8_t fm = p.flags[m];
-        if (ftype(fm) == T_IFC && (fmark(fm) == MK_NONE || fmark(fm) == MK_FILL)) {
-          const Cell cm = make_cell(p, m);
-          R u[3];
-          rs += sum_out_f<D, S>(p, cm, m, par, u);
-          us[0] += u[0];
-          us[1] += u[1];
-          us[2] += u[2];
-          cs += sum_out_g<D, S>(p, cm, m, par);
-          ++cnt;
+          for (int i = 1; i < Lat<D>::Q; ++i) {
+            const long long m = nb<D>(p, c, i);
+            const uint8_t fm = p.flags[m];
+            if (ftype(fm) == T_IFC && (fmark(fm) == MK_NONE || fmark(fm) == MK_FILL)) {
+              const Cell cm = make_cell(p, m);
+              R u[3];
+              rs += sum_out_f<D, S>(p, cm, m, par, u);
+              us[0] += u[0];
+              us[1] += u[1];
+              us[2] += u[2];
+              cs += sum_out_g<D, S>(p, cm, m, par);
+              ++cnt;
+            }
+          }
+          const R inv = (R)cnt;
+          rs /= inv;
+          us[0] /= inv;
+          us[1] /= inv;
+          us[2] /= inv;
+          cs /= inv;
+          write_equilibrium<D, S>(p, c, n, par, rs, us, cs);
+          M[n] = 0;
+          lab = p.label_old[n];
+          if (lab >= 0)
+            dmv = -(double)cs;
+          else
+            atomicAdd(p.led + 5, -(double)cs);
+        } else if (mk == MK_LI) {
+          M[n] = sum_out_f<D, S>(p, c, n, par, nullptr);
         }
       }
-      const R inv = (R)cnt;
-      rs /= inv;
-      us[0] /= inv;
-      us[1] /= inv;
-      us[2] /= inv;
-      cs /= inv;
-      write_equilibrium<D, S>(p, c, n, par, rs, us, cs);
-      M[n] = 0;
-      lab = p.label_old[n];
-      if (lab >= 0)
-        dmv = -(double)cs;
-      else
-        atomicAdd(p.led + 5, -(double)cs);
-    } else if (mk == MK_LI) {
-      M[n] = sum_out_f<D, S>(p, c, n, par, nullptr);
     }
+    if (__any_sync(0xffffffffu, lab >= 0)) agg_add(p.told.dm, lab, dmv, wbuf + (threadIdx.x & ~31));
   }
-  if (__any_sync(0xffffffffu, lab >= 0)) agg_add(p.told.dm, lab, dmv, wbuf + (threadIdx.x & ~31));
 }
 
+// interface cells after the conversion collect the excess of converting
+// neighbours and refresh their fill level
 template <int D, class S>
 __global__ void k_conv_apply(Params p, int par) {
   using R = typename ST<S>::R;
-  Cell c;
-  if (!grid_cell(p, c)) return;
-  const long long n = c.n;
-  const uint8_t fl = p.flags[n];
-  const int pt = post_type(fl);
-  const int mk = fmark(fl);
-  if (pt == T_IFC) {
+  const int ni = *p.icount, total = ni + *p.ncount;
+  FOR_LIST(k, total) {
+    const long long n = list_cell(p, k, ni);
+    const uint8_t fl = p.flags[n];
+    const int pt = post_type(fl);
+    const int mk = fmark(fl);
+    if (pt == T_IFC) {
+      const Cell c = make_cell(p, n);
       const R *ex = (const R *)p.ex;
-    R *M = (R *)p.M;
-    R recv = 0;
-    bool has = false;
+      R *M = (R *)p.M;
+      R recv = 0;
+      bool has = false;
 #pragma unroll
-    for (int i = 1; i < Lat<D>::Q; ++i) {
-      const long long m = nb<D>(p, c, i);
-      const int fm = fmark(p.flags[m]);
-      if (fm == MK_FILL || fm == MK_EMPTY) {
-        recv += ex[m];
-        has = true;
+      for (int i = 1; i < Lat<D>::Q; ++i) {
+        const long long m = nb<D>(p, c, i);
+        const int fm = fmark(p.flags[m]);
+        if (fm == MK_FILL || fm == MK_EMPTY) {
+          recv += ex[m];
+          has = true;
+        }
       }
+      if (has || mk == MK_GI || mk == MK_LI) {
+        const R Mv = M[n] + recv;
+        M[n] = Mv;
+        ((R *)p.phi)[n] = Mv / sum_out_f<D, S>(p, c, n, par, nullptr);
+      }
+    } else if (mk == MK_FILL) {
+      ((R *)p.phi)[n] = 1;
+      ((R *)p.M)[n] = 0;
+    } else if (mk == MK_EMPTY) {
+      ((R *)p.phi)[n] = 0;
+      ((R *)p.M)[n] = 0;
     }
-    if (has || mk == MK_GI || mk == MK_LI) {
-      const R Mv = M[n] + recv;
-      M[n] = Mv;
-      ((R *)p.phi)[n] = Mv / sum_out_f<D, S>(p, c, n, par, nullptr);
-    }
-  } else if (mk == MK_FILL) {
-    ((R *)p.phi)[n] = 1;
-    ((R *)p.M)[n] = 0;
-  } else if (mk == MK_EMPTY) {
-    ((R *)p.phi)[n] = 0;
-    ((R *)p.M)[n] = 0;
   }
-  p.flags_out[n] = (uint8_t)(pt | (fl & NEARWALL));
+}
+
+// new types replace the marks; the interface cells of the next step are listed
+static __global__ void k_conv_finalize(Params p) {
+  const int ni = *p.icount, total = ni + *p.ncount;
+  for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+    const int k = base + threadIdx.x;
+    bool take = false;
+    long long n = 0;
+    if (k < total) {
+      n = list_cell(p, k, ni);
+      const uint8_t fl = p.flags[n];
+      const int pt = post_type(fl);
+      p.flags[n] = (uint8_t)(pt | (fl & NEARWALL));
+      take = pt == T_IFC;
+    }
+    list_append(p.inext, p.inext_count, take, (int)n);
+  }
+}
+
+// list every interface cell (initialisation paths)
+static __global__ void k_build_ilist(Params p) {
+  Cell c;
+  const bool inr = grid_cell(p, c);
+  const bool take = inr && ftype(p.flags[c.n]) == T_IFC;
+  list_append(p.ilist, p.icount, take, (int)c.n);
 }
 
 // ---------------------------------------------------------------------------

@@ -171,10 +171,10 @@ constexpr double kLsqRidge = 1e-3;
 
 template <int D, class R>
 __global__ void __launch_bounds__(128) k_geometry(Params p) {
-  Cell c;
-  if (!grid_cell(p, c)) return;
-  const long long n = c.n;
-  if (ftype(p.flags_out[n]) != T_IFC) return;
+  const int cnt = *p.icount;
+  FOR_LIST(kk, cnt) {
+  const long long n = p.ilist[kk];
+  const Cell c = make_cell(p, n);
   const R *phi = (const R *)p.phi;
   R *kap = (R *)p.kappa, *nr = (R *)p.nrm, *ds = (R *)p.dst;
   constexpr int ZR = D == 3 ? 1 : 0;
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(128) k_geometry(Params p) {
     for (int dy = -1; dy <= 1; ++dy)
       for (int dx = -1; dx <= 1; ++dx) {
         const long long m = at(p, c, dx, dy, dz);
-        const int tm = ftype(p.flags_out[m]);
+        const int tm = ftype(p.flags[m]);
         R a;
         if (tm == T_LIQ) a = 1;
         else if (tm == T_GAS) a = 0;
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(128) k_geometry(Params p) {
     nr[n] = 0;
     nr[p.N + n] = 0;
     nr[2 * p.N + n] = 0;
-    return;
+    continue;
   }
   const R mx = gx / gn, my = gy / gn, mz = gz / gn;
   const R s0 = plic_offset<D, R>(mx, my, mz, ac);
@@ -292,22 +292,23 @@ __global__ void __launch_bounds__(128) k_geometry(Params p) {
     kv = (D == 3 ? (R)-2 : (R)-1) * (b1 / (N1 + (R)kLsqRidge));
   }
   kap[n] = kv < (R)-1 ? (R)-1 : (kv > (R)1 ? (R)1 : kv);
+  }
 }
 
 template <int D, class R>
 __global__ void k_disjoining(Params p) {
-  Cell c;
-  if (!grid_cell(p, c)) return;
-  const long long n = c.n;
-  if (ftype(p.flags_out[n]) != T_IFC) return;
+  const int cnt = *p.icount;
+  FOR_LIST(kk, cnt) {
+  const long long n = p.ilist[kk];
   R *Pi = (R *)p.Pi;
   const int b = p.label_new[n];
   const R *nr = (const R *)p.nrm, *ds = (const R *)p.dst;
   const R dir[3] = {nr[n], nr[p.N + n], nr[2 * p.N + n]};
   if (p.k_pi == 0.0 || b < 0 || (dir[0] == (R)0 && dir[1] == (R)0 && dir[2] == (R)0)) {
     Pi[n] = 0;
-    return;
+    continue;
   }
+  const Cell c = make_cell(p, n);
   R tmax[3], tdel[3];
   int step[3], off[3] = {0, 0, 0};
   for (int d = 0; d < 3; ++d) {
@@ -327,7 +328,7 @@ __global__ void k_disjoining(Params p) {
     const long long y = at_far(p, c.x + off[0], c.y + off[1], c.z + off[2]);
     const int ly = p.label_new[y];
     if (ly == b) continue;
-    const int ty = ftype(p.flags_out[y]);
+    const int ty = ftype(p.flags[y]);
     if (ty == T_WALL) break;
     if ((ty == T_IFC || ty == T_GAS) && ly >= 0) {
       const R ny0 = nr[y], ny1 = nr[p.N + y], ny2 = nr[2 * p.N + y];
@@ -343,6 +344,7 @@ __global__ void k_disjoining(Params p) {
     }
   }
   Pi[n] = (dist >= (R)0 && dist < (R)p.d_max) ? (R)p.k_pi * ((R)p.d_max - dist) : (R)0;
+  }
 }
 
 }  // namespace lbf

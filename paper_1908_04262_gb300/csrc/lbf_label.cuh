@@ -18,17 +18,52 @@ namespace lbf {
 constexpr unsigned long long HASH_EMPTY = ~0ull;
 constexpr int UF_ITERS = 1 << 22;
 
-__device__ __forceinline__ int uf_find(const int *par, int a) {
+// find with path halving: a node's parent is replaced by its grandparent
+// on the way up.  Parents only move towards smaller indices, so the writes
+// keep every node's parent an ancestor; a concurrent link that such a write
+// overwrites is retried by the union that made it (its atomicMin returns a
+// value other than the expected root).
+__device__ __forceinline__ int uf_find(int *par, int a) {
   for (int it = 0; it < UF_ITERS; ++it) {
     const int b = __ldcg(par + a);
+    if (b == a) return a;
+    const int c = __ldcg(par + b);
+    if (c == b) return b;
+    __stcg(par + a, c);
+    a = c;
+  }
+  return a;
+}
+
+// the same on arrays that may live in shared or global memory
+__device__ __forceinline__ int uf_find_any(const int *par, int a) {
+  for (int it = 0; it < UF_ITERS; ++it) {
+    const int b = *(const volatile int *)(par + a);
     if (b == a) return a;
     a = b;
   }
   return a;
 }
+__device__ __forceinline__ bool uf_union_any(int *par, int a, int b) {
+  for (int it = 0; it < UF_ITERS; ++it) {
+    a = uf_find_any(par, a);
+    b = uf_find_any(par, b);
+    if (a == b) return true;
+    if (a > b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    const int old = atomicMin(par + b, a);
+    if (old == b) return true;
+    b = old;
+  }
+  return false;
+}
 
-// returns false when the iteration cap was reached
-__device__ __forceinline__ bool uf_union(int *par, int a, int b) {
+// returns false when the iteration cap was reached (kept out of line: it is
+// called from unrolled direction loops)
+static __device__ __noinline__ bool uf_union(int *par, int a, int b) {
   for (int it = 0; it < UF_ITERS; ++it) {
     a = uf_find(par, a);
     b = uf_find(par, b);
@@ -72,7 +107,7 @@ __device__ __forceinline__ int sm_find(volatile int *lp, int a) {
   return a;
 }
 
-__device__ __forceinline__ bool sm_union(int *lp, int a, int b) {
+static __device__ __noinline__ bool sm_union(int *lp, int a, int b) {
   for (int it = 0; it < 65536; ++it) {
     a = sm_find(lp, a);
     b = sm_find(lp, b);
@@ -89,19 +124,71 @@ __device__ __forceinline__ bool sm_union(int *lp, int a, int b) {
   return false;
 }
 
+template <int D> struct TileGrid {
+  int ntx, nty, ntz;
+  __device__ __forceinline__ TileGrid(const Params &p)
+      : ntx((p.nx + Tile<D>::TX - 1) / Tile<D>::TX),
+        nty((p.ny + Tile<D>::TY - 1) / Tile<D>::TY),
+        ntz((p.nz + Tile<D>::TZ - 1) / Tile<D>::TZ) {}
+  __device__ __forceinline__ int id(int tx, int ty, int tz) const {
+    tx = (tx + ntx) % ntx;
+    ty = (ty + nty) % nty;
+    tz = (tz + ntz) % ntz;
+    return tx + ntx * (ty + nty * tz);
+  }
+};
+
+// one block per tile: status, local union-find in shared memory, parents
+// and local component sizes
 template <int D>
 __global__ void __launch_bounds__(TILE_THREADS) k_uf_local(Params p) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ;
   __shared__ int lp[TN];
+  __shared__ int lsz[TN];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
   const long long nx = p.nx, nxy = (long long)p.nx * p.ny;
+  __shared__ int sg, sc;
+  if (threadIdx.x == 0) {
+    sg = 0;
+    sc = 0;
+  }
+  __syncthreads();
+  int ngas = 0, ncell = 0;
   for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
     const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
     bool gas = false;
-    if (x < p.nx && y < p.ny && z < p.nz) gas = ftype(p.flags_out[x + nx * y + nxy * z]) == T_GAS;
+    if (x < p.nx && y < p.ny && z < p.nz) {
+      ++ncell;
+      gas = ftype(p.flags[x + nx * y + nxy * z]) == T_GAS;
+    }
+    ngas += gas;
     lp[t] = gas ? t : -1;
+    lsz[t] = 0;
   }
+  atomicAdd(&sg, ngas);
+  atomicAdd(&sc, ncell);
   __syncthreads();
+  const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const long long root0 = x0 + nx * y0 + nxy * z0;
+  if (sg == 0) {
+    if (threadIdx.x == 0) p.tstat[tile] = 0;
+    return;
+  }
+  if (sg == sc) {  // every cell is gas: one component rooted at the first cell
+    if (threadIdx.x == 0) {
+      p.tstat[tile] = 1;
+      p.troot[tile] = (int)root0;
+    }
+    for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
+      const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
+      if (x < p.nx && y < p.ny && z < p.nz) {
+        const long long n = x + nx * y + nxy * z;
+        p.parent[n] = (int)root0;
+        p.lsize[n] = t == 0 ? sg : 0;
+      }
+    }
+    return;
+  }
   bool ok = true;
   for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
     if (lp[t] < 0) continue;
@@ -116,53 +203,143 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_local(Params p) {
   }
   if (!ok) atomicOr(p.err, ERR_NOTCONV);
   __syncthreads();
+  __shared__ int nroot, rfirst;
+  if (threadIdx.x == 0) {
+    nroot = 0;
+    rfirst = TN;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < TN; t += TILE_THREADS)
+    if (lp[t] >= 0) {
+      const int r = sm_find(lp, t);
+      atomicAdd(&lsz[r], 1);
+      if (r == t) {
+        atomicAdd(&nroot, 1);
+        atomicMin(&rfirst, t);
+      }
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    p.tstat[tile] = nroot == 1 ? 1 : 2;
+    const int r = rfirst;
+    p.troot[tile] = (int)(x0 + r % TX + nx * (y0 + (r / TX) % TY) + nxy * (z0 + r / (TX * TY)));
+  }
   for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
-    if (lp[t] < 0) continue;
-    const int r = sm_find(lp, t);
     const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
+    if (lp[t] < 0 || x >= p.nx || y >= p.ny || z >= p.nz) continue;
+    const int r = sm_find(lp, t);
     const int rx = x0 + r % TX, ry = y0 + (r / TX) % TY, rz = z0 + r / (TX * TY);
-    p.parent[x + nx * y + nxy * z] = (int)(rx + nx * ry + nxy * rz);
+    const long long n = x + nx * y + nxy * z;
+    p.parent[n] = (int)(rx + nx * ry + nxy * rz);
+    p.lsize[n] = r == t ? lsz[t] : 0;
   }
 }
 
-// gas cells join their gas neighbours in other tiles (or across the
-// periodic boundary)
+// one block per tile: join gas components across tile faces (and the
+// periodic boundary).  Two all-gas tiles are joined by one union of their
+// roots; otherwise every crossing link of a gas cell is joined.
 template <int D>
-__global__ void k_uf_merge(Params p) {
-  Cell c;
-  if (!grid_cell(p, c)) return;
-  const long long n = c.n;
-  if (ftype(p.flags_out[n]) != T_GAS) return;
-  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
-  const int lx = c.x % TX, ly = c.y % TY, lz = c.z % TZ;
+__global__ void __launch_bounds__(TILE_THREADS) k_uf_merge(Params p) {
+  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ;
+  const TileGrid<D> tgd(p);
+  const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const int own = p.tstat[tile];
+  if (own == 0) return;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  const long long nx = p.nx, nxy = (long long)p.nx * p.ny;
+  // statuses of the 3^d neighbouring tiles (periodic)
+  __shared__ int nst[27];
+  if (threadIdx.x < 27) {
+    const int ox = threadIdx.x % 3 - 1, oy = (threadIdx.x / 3) % 3 - 1, oz = threadIdx.x / 9 - 1;
+    nst[threadIdx.x] = (D == 2 && oz != 0) ? 0 : p.tstat[tgd.id(blockIdx.x + ox, blockIdx.y + oy, blockIdx.z + oz)];
+  }
+  __syncthreads();
   bool ok = true;
+  // one gas link suffices between two single-component tiles: the first
+  // thread that meets one claims the neighbour offset
+  __shared__ int claimed[27];
+  if (threadIdx.x < 27) claimed[threadIdx.x] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
+    const int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
+    const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+    if (x >= p.nx || y >= p.ny || z >= p.nz) continue;
+    const bool onface = lx == 0 || lx == TX - 1 || x == p.nx - 1 || ly == 0 || ly == TY - 1 || y == p.ny - 1 ||
+                        (D == 3 && (lz == 0 || lz == TZ - 1 || z == p.nz - 1));
+    if (!onface) continue;
+    const long long n = x + nx * y + nxy * z;
+    if (ftype(p.flags[n]) != T_GAS) continue;
 #pragma unroll
-  for (int i = 1; i < Lat<D>::Q; i += 2) {
-    const int dx = Lat<D>::cx(i), dy = Lat<D>::cy(i), dz = Lat<D>::cz(i);
-    const int ax = c.x + dx, ay = c.y + dy, az = c.z + dz;
-    const bool wraps = ax < 0 || ax >= p.nx || ay < 0 || ay >= p.ny || az < 0 || az >= p.nz;
-    const bool crosses = wraps || lx + dx < 0 || lx + dx >= TX || ly + dy < 0 || ly + dy >= TY ||
-                         lz + dz < 0 || lz + dz >= TZ;
-    if (!crosses) continue;
-    const long long m = nb<D>(p, c, i);
-    if (ftype(p.flags_out[m]) == T_GAS) ok &= uf_union(p.parent, (int)n, (int)m);
+    for (int i = 1; i < Lat<D>::Q; i += 2) {
+      const int dx = Lat<D>::cx(i), dy = Lat<D>::cy(i), dz = Lat<D>::cz(i);
+      const int ax = x + dx, ay = y + dy, az = z + dz;
+      const bool wraps = ax < 0 || ax >= p.nx || ay < 0 || ay >= p.ny || az < 0 || az >= p.nz;
+      // tile offset of the link's far end
+      const int ox = (lx + dx < 0) ? -1 : ((lx + dx >= TX || ax >= p.nx) ? 1 : 0);
+      const int oy = (ly + dy < 0) ? -1 : ((ly + dy >= TY || ay >= p.ny) ? 1 : 0);
+      const int oz = (lz + dz < 0) ? -1 : ((lz + dz >= TZ || az >= p.nz) ? 1 : 0);
+      if (!wraps && ox == 0 && oy == 0 && oz == 0) continue;  // joined by the local pass
+      const int oi = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
+      const int ns = nst[oi];
+      if (ns == 0) continue;
+      if (own == 1 && ns == 1 && claimed[oi]) continue;
+      const long long m = at_far(p, ax, ay, az);
+      if (ftype(p.flags[m]) != T_GAS) continue;
+      if (own == 1 && ns == 1 && atomicExch(&claimed[oi], 1)) continue;
+      ok &= uf_union(p.parent, (int)n, (int)m);
+    }
   }
   if (!ok) atomicOr(p.err, ERR_NOTCONV);
 }
 
-static __global__ void k_uf_compress(Params p) {
-  Cell c;
-  if (!grid_cell(p, c)) return;
-  const long long n = c.n;
-  if (ftype(p.flags_out[n]) != T_GAS) return;
-  const int r = uf_find(p.parent, (int)n);
-  p.parent[n] = r;
-  if (r == (int)n) {
-    const int k = atomicAdd(p.nroots, 1);
-    if (k < p.cap)
-      p.roots[k] = r;
-    else
-      atomicOr(p.err, ERR_CAPACITY);
+// one block per tile: every gas cell points at its component's root; roots
+// are registered
+template <int D>
+__global__ void __launch_bounds__(TILE_THREADS) k_uf_compress(Params p) {
+  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ;
+  const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const int own = p.tstat[tile];
+  if (own == 0) return;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  const long long nx = p.nx, nxy = (long long)p.nx * p.ny;
+  __shared__ int sroot;
+  if (own == 1) {
+    const int r0 = p.troot[tile];
+    if (threadIdx.x == 0) {
+      sroot = uf_find(p.parent, r0);
+      if (sroot == r0) {
+        const int k = atomicAdd(p.nroots, 1);
+        if (k < p.cap)
+          p.roots[k] = r0;
+        else
+          atomicOr(p.err, ERR_CAPACITY);
+      }
+    }
+    __syncthreads();
+    const int r = sroot;
+    for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
+      const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
+      if (x < p.nx && y < p.ny && z < p.nz) {
+        const long long n = x + nx * y + nxy * z;
+        if (ftype(p.flags[n]) == T_GAS) p.parent[n] = r;
+      }
+    }
+    return;
+  }
+  for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
+    const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
+    if (x >= p.nx || y >= p.ny || z >= p.nz) continue;
+    const long long n = x + nx * y + nxy * z;
+    if (ftype(p.flags[n]) != T_GAS) continue;
+    const int r = uf_find(p.parent, (int)n);
+    p.parent[n] = r;
+    if (r == (int)n) {
+      const int k = atomicAdd(p.nroots, 1);
+      if (k < p.cap)
+        p.roots[k] = r;
+      else
+        atomicOr(p.err, ERR_CAPACITY);
+    }
   }
 }
 
@@ -214,7 +391,11 @@ __device__ __forceinline__ void hash_insert(const Params &p, unsigned long long 
     if (cur == key) return;
     if (cur == HASH_EMPTY) {
       const unsigned long long prev = atomicCAS(p.hash + idx, HASH_EMPTY, key);
-      if (prev == HASH_EMPTY || prev == key) return;
+      if (prev == HASH_EMPTY) {
+        p.hlist[atomicAdd(p.hcount, 1)] = (int)idx;
+        return;
+      }
+      if (prev == key) return;
     }
     idx = (idx + 1) & (unsigned)(p.hash_size - 1);
   }
@@ -228,21 +409,19 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
   Cell c;
   const bool inr = grid_cell(p, c);
   const long long n = c.n;
-  const int t = inr ? ftype(p.flags_out[n]) : T_WALL;
+  const int t = inr ? ftype(p.flags[n]) : T_WALL;
   const int cnt = *p.tnew.count;
   int knew = -1;
   double v = 0.0;
   if (t == T_GAS) {
     knew = root_index(p.roots, cnt, p.parent[n]);
-    v = 1.0;
-    if (p.atmosphere && knew >= 0) {
-          if ((D == 2 ? c.y : c.z) == p.top_layer) p.tnew.atm[knew] = 1;
-    }
+    v = (double)p.lsize[n];  // non-zero only at tile-local roots
+    if (p.atmosphere && knew >= 0 && (D == 2 ? c.y : c.z) == p.top_layer && !p.tnew.atm[knew]) p.tnew.atm[knew] = 1;
   } else if (t == T_IFC) {
-  #pragma unroll
+#pragma unroll
     for (int i = 1; i < Lat<D>::Q; ++i) {
       const long long m = nb<D>(p, c, i);
-      if (ftype(p.flags_out[m]) == T_GAS) {
+      if (ftype(p.flags[m]) == T_GAS) {
         const int k = root_index(p.roots, cnt, p.parent[m]);
         if (k >= 0 && (knew < 0 || k < knew)) knew = k;
       }
@@ -250,7 +429,8 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
     if (knew >= 0) v = 1.0 - (double)((const R *)p.phi)[n];
   }
   if (inr) p.label_new[n] = knew;
-  if (__any_sync(0xffffffffu, knew >= 0)) agg_add(p.tnew.V, knew, v, wbuf + (threadIdx.x & ~31));
+  const bool contrib = knew >= 0 && v != 0.0;
+  if (__any_sync(0xffffffffu, contrib)) agg_add(p.tnew.V, contrib ? knew : -1, v, wbuf + (threadIdx.x & ~31));
   const int kold = inr ? p.label_old[n] : -1;
   const bool pair = kold >= 0 && knew >= 0;
   const unsigned long long key = pair ? (((unsigned long long)kold << 32) | (unsigned)knew) : HASH_EMPTY;
@@ -258,66 +438,77 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
   if (pair && (threadIdx.x & 31) == __ffs(peers) - 1) hash_insert(p, key);
 }
 
-// one block of 1024 threads: carry gas content from the old to the new table
+// one block of 1024 threads: carry gas content from the old to the new table.
+// Group bookkeeping lives in shared memory when there are at most
+// K10_SMEM old + new bubbles, in the global scratch arrays otherwise.
+constexpr int K10_SMEM = 512;
 static __global__ void __launch_bounds__(1024) k_bubble_update(Params p) {
   __shared__ int sfresh[1024];
   __shared__ int sbase;
+  __shared__ int s_par[K10_SMEM], s_nold[K10_SMEM], s_nnew[K10_SMEM], s_atm[K10_SMEM], s_minid[K10_SMEM],
+      s_heir[K10_SMEM];
+  __shared__ double s_mold[K10_SMEM], s_vnew[K10_SMEM];
+  __shared__ unsigned long long s_vmax[K10_SMEM];
   const int nold = *p.told.count, nnew = *p.tnew.count;
   const int T = nold + nnew;
+  const bool sm = T <= K10_SMEM;
+  int *gpar = sm ? s_par : p.gpar, *gnold = sm ? s_nold : p.gnold, *gnnew = sm ? s_nnew : p.gnnew;
+  int *gatm = sm ? s_atm : p.gatm, *gminid = sm ? s_minid : p.gminid, *gheir = sm ? s_heir : p.gheir;
+  double *gmold = sm ? s_mold : p.gmold, *gvnew = sm ? s_vnew : p.gvnew;
+  unsigned long long *gvmax = sm ? s_vmax : p.gvmax;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int nh = *p.hcount;
   for (int k = tid; k < T; k += nt) {
-    p.gpar[k] = k;
-    p.gnold[k] = 0;
-    p.gnnew[k] = 0;
-    p.gatm[k] = 0;
-    p.gminid[k] = 0x7fffffff;
-    p.gheir[k] = 0x7fffffff;
-    p.gmold[k] = 0.0;
-    p.gvnew[k] = 0.0;
-    p.gvmax[k] = 0ull;
+    gpar[k] = k;
+    gnold[k] = 0;
+    gnnew[k] = 0;
+    gatm[k] = 0;
+    gminid[k] = 0x7fffffff;
+    gmold[k] = 0.0;
+    gvnew[k] = 0.0;
+    gvmax[k] = 0ull;
   }
   for (int j = tid; j < nold; j += nt) p.told.m[j] += p.told.dm[j];
   __syncthreads();
   bool ok = true;
-  for (int h = tid; h < p.hash_size; h += nt) {
-    const unsigned long long key = p.hash[h];
-    if (key == HASH_EMPTY) continue;
+  for (int h = tid; h < nh; h += nt) {
+    const unsigned long long key = p.hash[p.hlist[h]];
     const int j = (int)(key >> 32), k = (int)(key & 0xffffffffu);
-    if (j < nold && k < nnew) ok &= uf_union(p.gpar, j, nold + k);
+    if (j < nold && k < nnew) ok &= uf_union_any(gpar, j, nold + k);
   }
   if (!ok) atomicOr(p.err, ERR_NOTCONV);
   __threadfence_block();
   __syncthreads();
   // group of every node (read-only finds into a separate array)
-  for (int k = tid; k < T; k += nt) p.gheir[k] = uf_find(p.gpar, k);
+  for (int k = tid; k < T; k += nt) gheir[k] = uf_find_any(gpar, k);
   __syncthreads();
-  for (int k = tid; k < T; k += nt) p.gpar[k] = p.gheir[k];
+  for (int k = tid; k < T; k += nt) gpar[k] = gheir[k];
   __syncthreads();
-  for (int k = tid; k < T; k += nt) p.gheir[k] = 0x7fffffff;
+  for (int k = tid; k < T; k += nt) gheir[k] = 0x7fffffff;
   __syncthreads();
-  const int *grp = p.gpar;
+  const int *grp = gpar;
   for (int j = tid; j < nold; j += nt) {
     const int g = grp[j];
-    atomicAdd(p.gmold + g, p.told.m[j]);
-    atomicAdd(p.gnold + g, 1);
-    atomicMin(p.gminid + g, p.told.id[j]);
+    atomicAdd(gmold + g, p.told.m[j]);
+    atomicAdd(gnold + g, 1);
+    atomicMin(gminid + g, p.told.id[j]);
   }
   for (int k = tid; k < nnew; k += nt) {
     const int g = grp[nold + k];
-    atomicAdd(p.gvnew + g, p.tnew.V[k]);
-    atomicAdd(p.gnnew + g, 1);
-    if (p.tnew.atm[k]) p.gatm[g] = 1;
-    atomicMax(p.gvmax + g, (unsigned long long)__double_as_longlong(p.tnew.V[k]));
+    atomicAdd(gvnew + g, p.tnew.V[k]);
+    atomicAdd(gnnew + g, 1);
+    if (p.tnew.atm[k]) gatm[g] = 1;
+    atomicMax(gvmax + g, (unsigned long long)__double_as_longlong(p.tnew.V[k]));
   }
   __syncthreads();
   for (int k = tid; k < nnew; k += nt) {
     const int g = grp[nold + k];
-    if ((unsigned long long)__double_as_longlong(p.tnew.V[k]) == p.gvmax[g]) atomicMin(p.gheir + g, k);
+    if ((unsigned long long)__double_as_longlong(p.tnew.V[k]) == gvmax[g]) atomicMin(gheir + g, k);
   }
   __syncthreads();
   for (int j = tid; j < nold; j += nt) {
     const int g = grp[j];
-    if (p.gnnew[g] == 0 || p.gatm[g]) atomicAdd(p.led + 5, p.told.m[j]);
+    if (gnnew[g] == 0 || gatm[g]) atomicAdd(p.led + 5, p.told.m[j]);
   }
   // new rows; fresh ids are numbered in bubble order
   const int chunk = (nnew + nt - 1) / nt;
@@ -327,24 +518,24 @@ static __global__ void __launch_bounds__(1024) k_bubble_update(Params p) {
     const int g = grp[nold + k];
     const double V = p.tnew.V[k];
     double m, pr;
-    if (p.gatm[g]) {
+    if (gatm[g]) {
       pr = p.p0;
       m = p.p0 * V / p.RT;
       atomicAdd(p.led + 5, -m);
-    } else if (p.gnold[g] == 0) {
+    } else if (gnold[g] == 0) {
       const double Req = p.dim == 3 ? cbrt(3.0 * V / (4.0 * 3.14159265358979323846)) : sqrt(V / 3.14159265358979323846);
       pr = p.p0 + (p.dim - 1) * p.sigma / Req;
       m = pr * V / p.RT;
       atomicAdd(p.led + 5, -m);
     } else {
-      m = p.gmold[g] * V / p.gvnew[g];
+      m = gmold[g] * V / gvnew[g];
       pr = m * p.RT / V;
     }
     p.tnew.m[k] = m;
     p.tnew.p[k] = pr;
     p.tnew.dm[k] = 0.0;
     p.tnew.root[k] = p.roots[k];
-    myfresh += !(p.gnold[g] > 0 && p.gheir[g] == k);
+    myfresh += !(gnold[g] > 0 && gheir[g] == k);
   }
   sfresh[tid] = myfresh;
   __syncthreads();
@@ -359,14 +550,15 @@ static __global__ void __launch_bounds__(1024) k_bubble_update(Params p) {
   int fid = sbase + sfresh[tid] - myfresh;
   for (int k = k0; k < k1; ++k) {
     const int g = grp[nold + k];
-    if (p.gnold[g] > 0 && p.gheir[g] == k)
-      p.tnew.id[k] = p.gminid[g];
+    if (gnold[g] > 0 && gheir[g] == k)
+      p.tnew.id[k] = gminid[g];
     else
       p.tnew.id[k] = fid++;
   }
   __syncthreads();
   if (tid == nt - 1) *p.next_id = sbase + sfresh[nt - 1];
-  for (int h = tid; h < p.hash_size; h += nt) p.hash[h] = HASH_EMPTY;
+  for (int h = tid; h < nh; h += nt) p.hash[p.hlist[h]] = HASH_EMPTY;
+  if (tid == 0) *p.hcount = 0;
 }
 
 }  // namespace lbf

@@ -18,6 +18,7 @@ struct Ops {
   virtual void nucleate(const Params &p, int par, const double *c, double R, cudaStream_t s) = 0;
   // step pieces (par = parity of the populations when the step starts)
   virtual void exchange(const Params &p, int par, cudaStream_t s) = 0;
+  virtual void build_ilist(const Params &p, cudaStream_t s) = 0;
   virtual void stream_collide(const Params &p, int par, cudaStream_t s) = 0;
   virtual void convert(const Params &p, int par, cudaStream_t s) = 0;
   virtual void label(const Params &p, cudaStream_t s) = 0;

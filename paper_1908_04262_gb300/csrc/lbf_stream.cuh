@@ -42,21 +42,54 @@ template <class R> __device__ __forceinline__ R tau_model(const Params &p, R gd,
 }
 
 // Sec. 2.3: tau solves tau = tau_model(A / tau) (shear rate A / tau from the
-// non-equilibrium stress); safeguarded Newton on [tau_min, tau_max].
+// non-equilibrium stress), clamped to [tau_min, tau_max].
+// Power law: with g = A / tau the equation reads g/2 + 3 k g^n = A; its root
+// lies in [min(A, (A/6k)^(1/n)), min(2A, (A/3k)^(1/n))] (each term is below A
+// at the lower end and at most A at the upper end), a bracket within a
+// factor 2^(1/n); Newton inside it (monotone from the left for n < 1, from
+// the right for n > 1).  Carreau-Yasuda: safeguarded Newton on tau.
 template <class R> __device__ __forceinline__ R solve_tau(const Params &p, R A) {
-  R lo = (R)p.tau_min, hi = (R)p.tau_max, d;
-  if (!(hi - tau_model<R>(p, A / hi, d) > (R)0)) return hi;
-  if (!(lo - tau_model<R>(p, A / lo, d) < (R)0)) return lo;
+  const R lo = (R)p.tau_min, hi = (R)p.tau_max;
+  if (p.rheo == 1) {
+    const R n = (R)p.rn, k3 = (R)3 * (R)p.rk;
+    if (!(A > (R)0)) return n < (R)1 ? hi : lo;
+    if (n == (R)1) {
+      const R t = (R)0.5 + k3;
+      return t < lo ? lo : (t > hi ? hi : t);
+    }
+    const R inv = (R)1 / n;
+    R gl = fmin(A, pow(A / ((R)2 * k3), inv));
+    R gu = fmin((R)2 * A, pow(A / k3, inv));
+    if (!(gl > (R)0)) return n < (R)1 ? hi : lo;  // shear rate below range
+    R g = n < (R)1 ? gl : gu;
+    for (int it = 0; it < Prec<R>::iters; ++it) {
+      const R gp = pow(g, n - (R)1);  // g^(n-1)
+      const R fval = (R)0.5 * g + k3 * gp * g - A;
+      const R fder = (R)0.5 + n * k3 * gp;
+      R gn = g - fval / fder;
+      if (!(gn >= gl && gn <= gu)) gn = (R)0.5 * (gl + gu);
+      if (fval < (R)0) gl = g; else gu = g;
+      const R step = gn - g;
+      g = gn;
+      if (fabs(step) <= Prec<R>::tol * g) break;
+    }
+    const R t = A / g;
+    return t < lo ? lo : (t > hi ? hi : t);
+  }
+  R d;
+  R l = lo, h = hi;
+  if (!(h - tau_model<R>(p, A / h, d) > (R)0)) return h;
+  if (!(l - tau_model<R>(p, A / l, d) < (R)0)) return l;
   // Newton from the upper end of the bracket, falling back to bisection
   // whenever a step leaves the bracket; h(t) = t - tau_model(A / t)
-  R t = hi;
+  R t = h;
   for (int it = 0; it < Prec<R>::iters; ++it) {
     R dm;
-    const R h = t - tau_model<R>(p, A / t, dm);
-    if (h > (R)0) hi = t; else lo = t;
+    const R hv = t - tau_model<R>(p, A / t, dm);
+    if (hv > (R)0) h = t; else l = t;
     const R deriv = (R)1 + dm * A / (t * t);
-    R tn = t - h / deriv;
-    if (!(tn > lo && tn < hi)) tn = (R)0.5 * (lo + hi);
+    R tn = t - hv / deriv;
+    if (!(tn > l && tn < h)) tn = (R)0.5 * (l + h);
     const R step = tn - t;
     t = tn;
     if (fabs(step) <= Prec<R>::tol * t) break;
@@ -68,10 +101,10 @@ template <int D, class S, int PAR>
 __global__ void __launch_bounds__(128) k_exchange(Params p) {
   using R = typename ST<S>::R;
   constexpr int Q = Lat<D>::Q;
-  Cell c;
-  if (!grid_cell(p, c)) return;
-  const long long n = c.n;
-  if (ftype(p.flags[n]) != T_IFC) return;
+  const int cnt = *p.icount;
+  FOR_LIST(k, cnt) {
+  const long long n = p.ilist[k];
+  const Cell c = make_cell(p, n);
   const S *f = (const S *)p.f;
   R *M = (R *)p.M;
   const R *phi = (const R *)p.phi;
@@ -106,11 +139,134 @@ __global__ void __launch_bounds__(128) k_exchange(Params p) {
     }
   }
   M[n] = Mn;
+  }
 }
 
 template <class R> struct SweepOcc;
 template <> struct SweepOcc<double> { static constexpr int blocks = 3; };
 template <> struct SweepOcc<float> { static constexpr int blocks = 6; };
+
+// Sec. 2.3: local relaxation time.  The non-equilibrium stress is the raw
+// second moment minus its equilibrium value rho (u u + cs^2 I) (identical
+// to sum e e (f - f_eq) for the second-order equilibrium).
+template <int D, class R>
+__device__ __forceinline__ R local_tau(const Params &p, const R *fi, R rho, R ux, R uy, R uz) {
+  if (p.rheo == 0) return (R)p.tau;
+  R mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
+#pragma unroll
+  for (int i = 1; i < Lat<D>::Q; ++i) {
+    const int ex = Lat<D>::cx(i), ey = Lat<D>::cy(i), ez = Lat<D>::cz(i);
+    if (ex) mxx += fi[i];
+    if (ey) myy += fi[i];
+    if (ez) mzz += fi[i];
+    if (ex * ey > 0) mxy += fi[i];
+    if (ex * ey < 0) mxy -= fi[i];
+    if (ex * ez > 0) mxz += fi[i];
+    if (ex * ez < 0) mxz -= fi[i];
+    if (ey * ez > 0) myz += fi[i];
+    if (ey * ez < 0) myz -= fi[i];
+  }
+  const R third = rho / (R)3;
+  const R pxx = mxx - rho * ux * ux - third, pyy = myy - rho * uy * uy - third;
+  const R pzz = D == 3 ? mzz - rho * uz * uz - third : (R)0;
+  const R pxy = mxy - rho * ux * uy, pxz = mxz - rho * ux * uz, pyz = myz - rho * uy * uz;
+  const R nrm2 = pxx * pxx + pyy * pyy + pzz * pzz + (R)2 * (pxy * pxy + pxz * pxz + pyz * pyz);
+  return solve_tau<R>(p, sqrt(nrm2) / ((R)1.4142135623730951 * rho / (R)3));
+}
+
+// BGK relaxation with Guo forcing of one cell, written to the outgoing slots
+template <int D, class S, int PAR>
+__device__ __forceinline__ void relax_store(const Params &p, const Cell &c, long long n, S *f, const typename ST<S>::R *fi,
+                                            typename ST<S>::R rho, typename ST<S>::R ux, typename ST<S>::R uy,
+                                            typename ST<S>::R uz, typename ST<S>::R tau) {
+  using R = typename ST<S>::R;
+  constexpr int Q = Lat<D>::Q;
+  const R om = (R)1 / tau;
+  const R base = (R)1 - (ux * ux + uy * uy + uz * uz) * (R)1.5;
+  if (p.has_force) {
+    const R ff = (R)1 - (R)0.5 * om;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const R ex = (R)Lat<D>::cx(i), ey = (R)Lat<D>::cy(i), ez = (R)Lat<D>::cz(i);
+      const R eu = ex * ux + ey * uy + ez * uz;
+      const R fe = (R)Lat<D>::w(i) * rho * (base + eu * ((R)3 + eu * (R)4.5));
+      const R F = ((ex - ux) * (R)3 + eu * ex * (R)9) * rho * (R)p.ax +
+                  ((ey - uy) * (R)3 + eu * ey * (R)9) * rho * (R)p.ay +
+                  ((ez - uz) * (R)3 + eu * ez * (R)9) * rho * (R)p.az;
+      st(f, slot_out<D>(p, c, n, i, 1 - PAR), fi[i] - (fi[i] - fe) * om + ff * (R)Lat<D>::w(i) * F,
+         fshift<S, D>(p, i));
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const R eu = (R)Lat<D>::cx(i) * ux + (R)Lat<D>::cy(i) * uy + (R)Lat<D>::cz(i) * uz;
+      const R fe = (R)Lat<D>::w(i) * rho * (base + eu * ((R)3 + eu * (R)4.5));
+      st(f, slot_out<D>(p, c, n, i, 1 - PAR), fi[i] - (fi[i] - fe) * om, fshift<S, D>(p, i));
+    }
+  }
+}
+
+// a liquid cell: its lattice neighbours are liquid, interface or walls
+// (liquid never touches gas); walls bounce back by reading the cell's own
+// outgoing population from the wall cell's slot
+template <int D, class S, int PAR>
+__device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long long n, uint8_t fl) {
+  using R = typename ST<S>::R;
+  constexpr int Q = Lat<D>::Q, QA = Lat<D>::QA;
+  S *f = (S *)p.f;
+  S *g = (S *)p.g;
+  unsigned wallm = 0;
+  if (fl & NEARWALL) {
+#pragma unroll
+    for (int i = 1; i < Q; ++i) wallm |= (ftype(p.flags[src<D>(p, c, i)]) == T_WALL ? 1u : 0u) << i;
+  }
+  R fi[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const bool w = (wallm >> i) & 1u;
+    fi[i] = ld(f, w ? slot_out<D>(p, c, n, opp(i), PAR) : slot_in<D>(p, c, n, i, PAR),
+               w ? fshift<S, D>(p, opp(i)) : fshift<S, D>(p, i));
+  }
+  R gi[QA];
+#pragma unroll
+  for (int i = 0; i < QA; ++i) {
+    const bool w = (wallm >> i) & 1u;
+    gi[i] = ld(g, w ? slot_out<D>(p, c, n, opp(i), PAR) : slot_in<D>(p, c, n, i, PAR),
+               w ? gshift<S, D>(p, opp(i)) : gshift<S, D>(p, i));
+  }
+  if (wallm && (p.walls & 8)) {
+    // moving walls of the +y face
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const bool top = Lat<D>::cy(i) > 0 ? c.y == 0 : (Lat<D>::cy(i) < 0 ? c.y == p.ny - 2 : c.y == p.ny - 1);
+      if (((wallm >> i) & 1u) && top) {
+        const R eu = (R)Lat<D>::cx(i) * (R)p.uwx + (R)Lat<D>::cy(i) * (R)p.uwy + (R)Lat<D>::cz(i) * (R)p.uwz;
+        fi[i] += (R)2 * (R)Lat<D>::w(i) * (R)p.rho0 * eu * (R)3;
+      }
+    }
+  }
+  R rho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    rho += fi[i];
+    if (Lat<D>::cx(i)) jx += Lat<D>::cx(i) > 0 ? fi[i] : -fi[i];
+    if (Lat<D>::cy(i)) jy += Lat<D>::cy(i) > 0 ? fi[i] : -fi[i];
+    if (Lat<D>::cz(i)) jz += Lat<D>::cz(i) > 0 ? fi[i] : -fi[i];
+  }
+  const R ux = (jx + (R)0.5 * rho * (R)p.ax) / rho;
+  const R uy = (jy + (R)0.5 * rho * (R)p.ay) / rho;
+  const R uz = (jz + (R)0.5 * rho * (R)p.az) / rho;
+  relax_store<D, S, PAR>(p, c, n, f, fi, rho, ux, uy, uz, local_tau<D, R>(p, fi, rho, ux, uy, uz));
+  R cg = 0;
+#pragma unroll
+  for (int i = 0; i < QA; ++i) cg += gi[i];
+  const R omg = (R)1 / (R)p.taug;
+#pragma unroll
+  for (int i = 0; i < QA; ++i) {
+    const R v = gi[i] + (geq<R, D>(i, cg, ux, uy, uz) - gi[i]) * omg + (R)Lat<D>::wa(i) * (R)p.q;
+    st(g, slot_out<D>(p, c, n, i, 1 - PAR), v, gshift<S, D>(p, i));
+  }
+}
 
 template <int D, class S, int PAR>
 __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_stream_collide(Params p) {
@@ -126,10 +282,19 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
   const bool isI = active && type == T_IFC;
   double flux = 0.0;
   int lab = -1;
+  const bool simple = active && type == T_LIQ && !(fl & NEARWALL);
+  if (__all_sync(0xffffffffu, !isI)) {
+    // warp without interface cells: the liquid path, nothing to aggregate
+    if (active) liquid_cell<D, S, PAR>(p, c, n, fl);
+    if (p.q != 0.0) {
+      const unsigned b = __ballot_sync(0xffffffffu, active);
+      if ((threadIdx.x & 31) == 0 && b) atomicAdd(p.fluid_updates, (unsigned long long)__popc(b));
+    }
+    return;
+  }
   if (active) {
     S *f = (S *)p.f;
     S *g = (S *)p.g;
-    const bool simple = type == T_LIQ && !(fl & NEARWALL);
     // kinds of the source cells: bit i set when x - e_i is gas / a wall
     unsigned gasm = 0, wallm = 0;
     if (!simple) {
@@ -189,43 +354,7 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
     const R ux = (jx + (R)0.5 * rho * (R)p.ax) / rho;
     const R uy = (jy + (R)0.5 * rho * (R)p.ay) / rho;
     const R uz = (jz + (R)0.5 * rho * (R)p.az) / rho;
-    R tau = (R)p.tau;
-    if (p.rheo != 0) {
-      R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const R fn = fi[i] - feq<R, D>(i, rho, ux, uy, uz);
-        const R ex = (R)Lat<D>::cx(i), ey = (R)Lat<D>::cy(i), ez = (R)Lat<D>::cz(i);
-        pxx += ex * ex * fn;
-        pyy += ey * ey * fn;
-        pzz += ez * ez * fn;
-        pxy += ex * ey * fn;
-        pxz += ex * ez * fn;
-        pyz += ey * ez * fn;
-      }
-      const R nrm2 = pxx * pxx + pyy * pyy + pzz * pzz + (R)2 * (pxy * pxy + pxz * pxz + pyz * pyz);
-      tau = solve_tau<R>(p, sqrt(nrm2) / ((R)1.4142135623730951 * rho / (R)3));
-    }
-    const R om = (R)1 / tau;
-    if (p.has_force) {
-      const R ff = (R)1 - (R)0.5 * om;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const R ex = (R)Lat<D>::cx(i), ey = (R)Lat<D>::cy(i), ez = (R)Lat<D>::cz(i);
-        const R eu = ex * ux + ey * uy + ez * uz;
-        const R F = ((ex - ux) * (R)3 + eu * ex * (R)9) * rho * (R)p.ax +
-                    ((ey - uy) * (R)3 + eu * ey * (R)9) * rho * (R)p.ay +
-                    ((ez - uz) * (R)3 + eu * ez * (R)9) * rho * (R)p.az;
-        const R v = fi[i] - (fi[i] - feq<R, D>(i, rho, ux, uy, uz)) * om + ff * (R)Lat<D>::w(i) * F;
-        st(f, slot_out<D>(p, c, n, i, 1 - PAR), v, fshift<S, D>(p, i));
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const R v = fi[i] - (fi[i] - feq<R, D>(i, rho, ux, uy, uz)) * om;
-        st(f, slot_out<D>(p, c, n, i, 1 - PAR), v, fshift<S, D>(p, i));
-      }
-    }
+    relax_store<D, S, PAR>(p, c, n, f, fi, rho, ux, uy, uz, local_tau<D, R>(p, fi, rho, ux, uy, uz));
 
     R phin = 0, pho = 0;
     if (isI) {
