@@ -172,6 +172,34 @@ long long lbf_step_count(const lbf_sim *s);
 
 const char *lbf_last_error(void);
 
+/* Bubble labels of a cell-type field without allocating any memory.
+ * The paper has no counterpart: this is a service for callers that cannot
+ * call cudaMalloc (a framework whose caching allocator has reserved the
+ * device, or a real-time loop where an allocation may stall).
+ * type: device, N = nx*ny*nz bytes, cell types 0 gas, 1 liquid,
+ * 2 interface, 3 wall (cells indexed as everywhere in this header; every
+ * face periodic).  label: device, N int32 outputs -- gas cells get the
+ * index of their bubble (bubbles = gas regions connected over D2Q9/D3Q19
+ * links, numbered by their smallest cell index), interface cells the
+ * smallest index among their gas neighbours, other cells -1; identical to
+ * lbf_fields(LBF_F_LABEL) after lbf_set_cells with the same types.
+ * count: device, one int32: the number of bubbles, or -1 if there were more
+ * than 4096 of them or the union-find hit its iteration cap.
+ * Work is queued on `stream` (a cudaStream_t) and the call returns without
+ * waiting.  Scratch: one static device array per GPU, held from the first
+ * call on that GPU until the process exits, for at most 1,048,576 cells
+ * (and 65,536 tiles of 32x8x4 / 32x32 cells); larger lattices return
+ * LBF_EINVAL.  The first call on a device looks the array's address up with
+ * that device current; make that first call before any stream capture.
+ * Every call on a device shares the array: calls that overlap on the GPU
+ * (other streams, other threads) race and must be serialised by the caller;
+ * each call clears the counters it needs.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.
+ * Errors: LBF_EINVAL (NULL buffers, bad extents, lattice too large),
+ * LBF_ECUDA. */
+int lbf_label_gas_noalloc(const uint8_t *type, int nx, int ny, int nz, int32_t *label, int32_t *count,
+                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,7 @@ UNITS = {
     "k_f16.cu": [],
     "k_bf16.cu": [],
     "lbf_abi.cu": [],
+    "lbf_noalloc.cu": [],
 }
 
 

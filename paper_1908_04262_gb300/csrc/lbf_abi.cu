@@ -296,6 +296,10 @@ int validate(const lbf_config *c) {
 
 }  // namespace
 
+namespace lbf {
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace lbf
+
 extern "C" {
 
 const char *lbf_last_error(void) { return g_err.c_str(); }

@@ -30,6 +30,9 @@ struct Ops {
   virtual void ledger(const Params &p, int par, double *acc, unsigned long long *counts, cudaStream_t s) = 0;
 };
 
+// message returned by lbf_last_error() on the calling thread
+void set_last_error(const char *msg);
+
 // defined in one translation unit per storage type
 Ops *make_ops_f64(int dim);
 Ops *make_ops_f32(int dim);

@@ -59,7 +59,8 @@ class Bubble(ctypes.Structure):
 
 EXPORTS = ("lbf_create", "lbf_destroy", "lbf_nucleate", "lbf_set_cells", "lbf_step",
            "lbf_bubbles", "lbf_fields", "lbf_ledger", "lbf_timing_enable", "lbf_timing_read",
-           "lbf_timing_name", "lbf_cell_counts", "lbf_step_count", "lbf_last_error")
+           "lbf_timing_name", "lbf_cell_counts", "lbf_step_count", "lbf_last_error",
+           "lbf_label_gas_noalloc")
 
 _lib = None
 
@@ -91,6 +92,7 @@ def load(path: str = LIB_PATH):
     lib.lbf_step_count.argtypes = [P]
     lib.lbf_step_count.restype = ctypes.c_longlong
     lib.lbf_last_error.restype = ctypes.c_char_p
+    lib.lbf_label_gas_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P]
     _lib = lib
     return lib
 
@@ -108,6 +110,16 @@ def make_config(d: dict, stream: int | None = None) -> Config:
         elif name in d:
             setattr(c, name, d[name])
     return c
+
+
+def label_gas_noalloc(types, nx: int, ny: int, nz: int, labels, count, stream: int | None = None):
+    """Bubble labels of a device cell-type field without any allocation
+    (``lbf_label_gas_noalloc``): ``types`` uint8, ``labels`` int32 (N) and
+    ``count`` int32 (1) are caller-owned device tensors."""
+    lib = load()
+    rc = lib.lbf_label_gas_noalloc(types.data_ptr(), nx, ny, nz, labels.data_ptr(), count.data_ptr(), stream)
+    if rc != 0:
+        raise LbfError(rc, lib.lbf_last_error().decode(errors="replace"))
 
 
 def _p(a: np.ndarray):
