@@ -55,7 +55,7 @@ struct lbf_sim {
   void *f = nullptr, *g = nullptr;
   uint8_t *flags = nullptr;
   int *ilist[2] = {nullptr, nullptr}, *icount[2] = {nullptr, nullptr}, *nlist = nullptr, *ncount = nullptr;
-  int list_blocks = 0;
+  int list_blocks = 0, warp_blocks = 0;
   void *M = nullptr, *phi = nullptr, *uI = nullptr, *kappa = nullptr, *Pi = nullptr, *nrm = nullptr,
        *dst = nullptr, *ex = nullptr;
   int *label[2] = {nullptr, nullptr}, *parent = nullptr, *roots = nullptr, *nroots = nullptr;
@@ -76,6 +76,9 @@ struct lbf_sim {
   double *acc = nullptr;
   unsigned long long *counts = nullptr;
   void *staging = nullptr;
+  float *tau_tab = nullptr;
+  int tab_n = 0;
+  float tab_lnA0 = 0.f, tab_inv_dlnA = 0.f;
   long long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t tgraph[2] = {nullptr, nullptr};  // with event records
@@ -120,6 +123,7 @@ Params make_params(lbf_sim *s, long long step) {
   p.nlist = s->nlist;
   p.ncount = s->ncount;
   p.list_blocks = s->list_blocks;
+  p.warp_blocks = s->warp_blocks;
   p.M = s->M; p.phi = s->phi; p.uI = s->uI; p.kappa = s->kappa; p.Pi = s->Pi; p.nrm = s->nrm;
   p.dst = s->dst; p.ex = s->ex;
   p.label_old = s->label[par];
@@ -134,6 +138,7 @@ Params make_params(lbf_sim *s, long long step) {
   p.gpar = s->gpar; p.gnold = s->gnold; p.gnnew = s->gnnew; p.gatm = s->gatm; p.gminid = s->gminid;
   p.gheir = s->gheir; p.gmold = s->gmold; p.gvnew = s->gvnew; p.gvmax = s->gvmax;
   p.next_id = s->next_id; p.led = s->led; p.fluid_updates = s->fluid_updates; p.err = s->err;
+  p.tau_tab = s->tau_tab; p.tab_n = s->tab_n; p.tab_lnA0 = s->tab_lnA0; p.tab_inv_dlnA = s->tab_inv_dlnA;
   p.tau = c.tau; p.rho0 = c.rho0; p.ax = c.accel[0]; p.ay = c.accel[1]; p.az = c.accel[2];
   p.has_force = (c.accel[0] != 0.0 || c.accel[1] != 0.0 || c.accel[2] != 0.0);
   p.rheo = c.rheo; p.rn = c.rheo_n; p.rk = c.rheo_k; p.rlam = c.rheo_lambda; p.ra = c.rheo_a;
@@ -156,6 +161,8 @@ int relabel_in_place(lbf_sim *s) {
   const int par = (int)(s->step & 1);
   Params p = make_params(s, s->step);
   s->ops->build_ilist(p, s->st);
+  CK(cudaMemsetAsync(p.inext_count, 0, sizeof(int), s->st));
+  s->ops->label_prep(p, s->st);
   s->ops->label(p, s->st);
   s->ops->bubble_update(p, s->st);
   const size_t cap = (size_t)s->cap;
@@ -172,6 +179,8 @@ int relabel_in_place(lbf_sim *s) {
   p.label_new = s->label[par];
   s->ops->geometry(p, s->st);
   s->ops->disjoining(p, s->st);
+  // the next step accumulates into table [1-par] and counts roots afresh
+  s->ops->label_prep(p, s->st);
   CK(cudaGetLastError());
   return 0;
 }
@@ -277,6 +286,41 @@ int check_device_error(lbf_sim *s) {
   return 0;
 }
 
+// Sec. 2.3 on the host: tau of the rheology model at shear rate gd, and the
+// relaxation time solving tau = tau_model(A / tau), clamped to
+// [tau_min, tau_max] (bisection; used to tabulate tau(A))
+double host_tau_model(const lbf_config &c, double gd) {
+  if (c.rheo == 1) return 0.5 + 3.0 * c.rheo_k * std::pow(gd, c.rheo_n - 1.0);
+  return c.tau_inf + (c.tau0 - c.tau_inf) * std::pow(1.0 + std::pow(c.rheo_lambda * gd, c.rheo_a), (c.rheo_n - 1.0) / c.rheo_a);
+}
+double host_solve_tau(const lbf_config &c, double A) {
+  double lo = c.tau_min, hi = c.tau_max;
+  if (!(hi - host_tau_model(c, A / hi) > 0.0)) return hi;
+  if (!(lo - host_tau_model(c, A / lo) < 0.0)) return lo;
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid - host_tau_model(c, A / mid) > 0.0) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+int build_tau_table(lbf_sim *s) {
+  const lbf_config &c = s->cfg;
+  if (c.rheo == 0 || c.storage == LBF_FP64) return 0;
+  const int n = 8192;
+  const double lnA0 = std::log(1e-14), lnA1 = std::log(1e2);
+  const double dl = (lnA1 - lnA0) / (n - 1);
+  std::vector<float> tab(n);
+  for (int k = 0; k < n; ++k) tab[k] = (float)host_solve_tau(c, std::exp(lnA0 + k * dl));
+  int rc = dalloc(s, &s->tau_tab, (size_t)n);
+  if (rc) return rc;
+  CK(cudaMemcpy(s->tau_tab, tab.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+  s->tab_n = n;
+  s->tab_lnA0 = (float)lnA0;
+  s->tab_inv_dlnA = (float)(1.0 / dl);
+  return 0;
+}
+
 int validate(const lbf_config *c) {
   if (!c) return fail(LBF_EINVAL, "cfg is NULL");
   if (c->nx <= 0 || c->ny <= 0 || c->nz <= 0) return fail(LBF_EINVAL, "lattice sizes must be positive");
@@ -357,6 +401,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     s->list_blocks = 4 * (sms > 0 ? sms : 132);
+    s->warp_blocks = 16 * (sms > 0 ? sms : 132);
   }
   s->cap = cfg->bubble_capacity;
   int hs = 1024;
@@ -458,6 +503,12 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   if (e != cudaSuccess) {
     lbf_destroy(s);
     return fail(LBF_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  }
+  rc = build_tau_table(s);
+  if (rc) {
+    std::string msg = g_err;
+    lbf_destroy(s);
+    return fail(rc, msg);
   }
   Params p = make_params(s, 0);
   s->ops->init_fill(p, 0, cfg->fill_height, s->st);

@@ -99,7 +99,8 @@ struct Params {
   int *ilist, *icount;   // interface cells at the start of the step
   int *inext, *inext_count;  // interface cells after the conversion
   int *nlist, *ncount;   // gas/liquid cells turning interface this step
-  int list_blocks;       // persistent grid size of the list kernels
+  int list_blocks;       // persistent grid size of the thread-per-cell list kernels
+  int warp_blocks;       // ... of the warp-per-cell list kernels (full occupancy)
   void *M, *phi;         // liquid mass, fill level (arithmetic type)
   void *uI;              // 3N: velocity of interface cells from the last step
   void *kappa, *Pi, *nrm, *dst, *ex;
@@ -120,6 +121,11 @@ struct Params {
   double *led;                   // 8 ledger accumulators
   unsigned long long *fluid_updates;
   int *err;
+  // tabulated relaxation time tau(A) of the non-Newtonian models for the
+  // single-precision forms: tau_tab[k] at ln A = tab_lnA0 + k * tab_dlnA
+  const float *tau_tab;
+  int tab_n;
+  float tab_lnA0, tab_inv_dlnA;
   // physics
   double tau, rho0, ax, ay, az;
   int has_force, rheo;
@@ -165,11 +171,13 @@ __device__ __forceinline__ bool grid_cell(const Params &p, Cell &c) {
 
 // cell from a linear index (rare paths only: uses division)
 __device__ __forceinline__ Cell make_cell(const Params &p, long long n) {
-  const long long nxy = (long long)p.nx * p.ny;
-  const int z = (int)(n / nxy);
-  const long long r = n - (long long)z * nxy;
-  const int y = (int)(r / p.nx);
-  return cell_at(p, (int)(r - (long long)y * p.nx), y, z);
+  // lattices hold fewer than 2^31 cells: 32-bit division suffices
+  const unsigned nxy = (unsigned)p.nx * (unsigned)p.ny;
+  const unsigned u = (unsigned)n;
+  const unsigned z = u / nxy;
+  const unsigned r = u - z * nxy;
+  const unsigned y = r / (unsigned)p.nx;
+  return cell_at(p, (int)(r - y * (unsigned)p.nx), (int)y, (int)z);
 }
 
 // cell at offset (dx,dy,dz) in {-1,0,1}^3

@@ -4,8 +4,8 @@
 //
 // Conversion (after the sweep has marked interface cells whose fill level
 // left [-eps, 1+eps]):
-//   k_conv_unmark     an emptying cell next to a filling cell stays interface
-//   k_conv_neighbours gas next to a filling cell and liquid next to an
+//   k_conv_mark       an emptying cell next to a filling cell stays interface;
+//                     gas next to a filling cell and liquid next to an
 //                     emptying cell become interface (liquid never meets gas)
 //   k_conv_compute    excess mass of converting cells, split equally over the
 //                     neighbours that are interface afterwards; new interface
@@ -13,7 +13,8 @@
 //                     interface neighbours; dissolved gas moves between the
 //                     liquid and the cell's bubble
 //   k_conv_apply      interface cells collect the excess and refresh alpha
-//   k_conv_finalize   new types replace the marks; the next interface list
+// (the relabelling pass then writes the new types and lists the interface
+// cells of the next step)
 #pragma once
 #include "lbf_common.cuh"
 
@@ -70,27 +71,6 @@ __device__ __forceinline__ void write_equilibrium(const Params &p, const Cell &c
 // that can fill or empty) and the list of cells they turn into interface;
 // persistent grids, one thread per listed cell
 
-template <int D>
-__global__ void k_conv_unmark(Params p) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *p.inext_count = 0;
-    *p.ncount = 0;
-  }
-  const int cnt = *p.icount;
-  FOR_LIST(k, cnt) {
-    const long long n = p.ilist[k];
-    const uint8_t fl = p.flags[n];
-    if (fmark(fl) != MK_EMPTY) continue;
-    const Cell c = make_cell(p, n);
-#pragma unroll
-    for (int i = 1; i < Lat<D>::Q; ++i)
-      if (fmark(p.flags[nb<D>(p, c, i)]) == MK_FILL) {
-        p.flags[n] = (uint8_t)(fl & ~(7 << 2));
-        break;
-      }
-  }
-}
-
 // set a conversion mark on a neighbour's flag byte; true for the first writer
 __device__ __forceinline__ bool mark_byte(uint8_t *flags, long long m, int mk) {
   const uintptr_t a = (uintptr_t)(flags + m);
@@ -100,10 +80,13 @@ __device__ __forceinline__ bool mark_byte(uint8_t *flags, long long m, int mk) {
   return ((old >> sh) & (7u << 2)) == 0;
 }
 
-// gas next to a filling cell and liquid next to an emptying cell become
-// interface (liquid never meets gas); the first marker lists the cell
+// An emptying cell next to a filling cell stays interface (filling wins);
+// gas next to a filling cell and liquid next to a (still) emptying cell
+// become interface, so that liquid never meets gas.  The first marker lists
+// the new interface cell.  Filling marks are final when this runs, so an
+// emptying cell decides its own fate without waiting for other threads.
 template <int D>
-__global__ void k_conv_neighbours(Params p) {
+__global__ void k_conv_mark(Params p) {
   const int cnt = *p.icount;
   for (int base = blockIdx.x * blockDim.x; base < cnt; base += gridDim.x * blockDim.x) {
     const int k = base + threadIdx.x;
@@ -115,15 +98,26 @@ __global__ void k_conv_neighbours(Params p) {
     }
     if (mk == MK_FILL || mk == MK_EMPTY) {
       const Cell c = make_cell(p, n);
-      const int want = mk == MK_FILL ? T_GAS : T_LIQ;
-      const int put = mk == MK_FILL ? MK_GI : MK_LI;
+      bool stay = false;
+      if (mk == MK_EMPTY) {
 #pragma unroll
-      for (int i = 1; i < Lat<D>::Q; ++i) {
-        const long long m = nb<D>(p, c, i);
-        const bool first = ftype(p.flags[m]) == want && mark_byte(p.flags, m, put);
-        if (first) {
-          const int pos = atomicAdd(p.ncount, 1);
-          p.nlist[pos] = (int)m;
+        for (int i = 1; i < Lat<D>::Q; ++i) stay |= fmark(p.flags[nb<D>(p, c, i)]) == MK_FILL;
+      }
+      if (stay) {
+        // clear the emptying mark (mark bits only; other threads read the
+        // type bits of this byte)
+        const uintptr_t a = (uintptr_t)(p.flags + n);
+        atomicAnd((unsigned *)(a & ~(uintptr_t)3), ~((7u << 2) << ((int)(a & 3) * 8)));
+      } else {
+        const int want = mk == MK_FILL ? T_GAS : T_LIQ;
+        const int put = mk == MK_FILL ? MK_GI : MK_LI;
+#pragma unroll
+        for (int i = 1; i < Lat<D>::Q; ++i) {
+          const long long m = nb<D>(p, c, i);
+          if (ftype(p.flags[m]) == want && mark_byte(p.flags, m, put)) {
+            const int pos = atomicAdd(p.ncount, 1);
+            p.nlist[pos] = (int)m;
+          }
         }
       }
     }
@@ -249,24 +243,6 @@ __global__ void k_conv_apply(Params p, int par) {
       ((R *)p.phi)[n] = 0;
       ((R *)p.M)[n] = 0;
     }
-  }
-}
-
-// new types replace the marks; the interface cells of the next step are listed
-static __global__ void k_conv_finalize(Params p) {
-  const int ni = *p.icount, total = ni + *p.ncount;
-  for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
-    const int k = base + threadIdx.x;
-    bool take = false;
-    long long n = 0;
-    if (k < total) {
-      n = list_cell(p, k, ni);
-      const uint8_t fl = p.flags[n];
-      const int pt = post_type(fl);
-      p.flags[n] = (uint8_t)(pt | (fl & NEARWALL));
-      take = pt == T_IFC;
-    }
-    list_append(p.inext, p.inext_count, take, (int)n);
   }
 }
 

@@ -96,70 +96,81 @@ __device__ __forceinline__ R plic_a3(R m1, R m2, R m3, R V) {
   return m3 * V + (R)0.5 * m12;
 }
 
-// offset s of the plane n.p = s (n unit) leaving liquid fraction alpha on
-// the +n side of the cell [-1/2, 1/2]^d
+// PLIC inversion for one normal: the normalised, sorted components are
+// computed once and reused for every fill level cut with that normal
+template <int D, class R> struct Plic {
+  R sum, m1, m2, m3;
+  __device__ __forceinline__ Plic(R nx, R ny, R nz) {
+    R a1 = fabs(nx), a2 = fabs(ny), a3 = D == 3 ? fabs(nz) : (R)0;
+    sum = a1 + a2 + a3;
+    const R inv = sum > (R)0 ? (R)1 / sum : (R)0;
+    a1 *= inv;
+    a2 *= inv;
+    a3 *= inv;
+    R t;
+    if (a1 > a2) { t = a1; a1 = a2; a2 = t; }
+    if (a2 > a3) { t = a2; a2 = a3; a3 = t; }
+    if (a1 > a2) { t = a1; a1 = a2; a2 = t; }
+    m1 = a1;
+    m2 = a2;
+    m3 = a3;
+  }
+  // offset s of the plane n.p = s leaving liquid fraction alpha on the +n
+  // side of the cell [-1/2, 1/2]^d (out of line: called once per stencil
+  // neighbour)
+  __device__ __noinline__ R offset(R alpha) const {
+    if (!(sum > (R)0)) return (R)0;
+    if (alpha >= (R)1) return (R)-0.5 * sum;
+    if (alpha <= (R)0) return (R)0.5 * sum;
+    R V = (R)1 - alpha;
+    const bool flip = V > (R)0.5;
+    if (flip) V = (R)1 - V;
+    R a = plic_a3<R>(m1, m2, m3, V);
+    if (flip) a = (R)1 - a;
+    return a * sum - (R)0.5 * sum;
+  }
+};
+
 template <int D, class R>
 __device__ __forceinline__ R plic_offset(R nx, R ny, R nz, R alpha) {
-  R a1 = fabs(nx), a2 = fabs(ny), a3 = D == 3 ? fabs(nz) : (R)0;
-  const R sum = a1 + a2 + a3;
-  if (!(sum > (R)0)) return (R)0;
-  if (alpha >= (R)1) return (R)-0.5 * sum;
-  if (alpha <= (R)0) return (R)0.5 * sum;
-  a1 /= sum;
-  a2 /= sum;
-  a3 /= sum;
-  // sort ascending
-  R t;
-  if (a1 > a2) { t = a1; a1 = a2; a2 = t; }
-  if (a2 > a3) { t = a2; a2 = a3; a3 = t; }
-  if (a1 > a2) { t = a1; a1 = a2; a2 = t; }
-  R V = (R)1 - alpha;
-  const bool flip = V > (R)0.5;
-  if (flip) V = (R)1 - V;
-  R a = plic_a3<R>(a1, a2, a3, V);
-  if (flip) a = (R)1 - a;
-  return a * sum - (R)0.5 * sum;
+  return Plic<D, R>(nx, ny, nz).offset(alpha);
 }
 
-// k x k Gaussian elimination with partial pivoting (A, b destroyed)
+// Cholesky solve of the k x k symmetric positive definite system A x = b
+// (the ridge keeps the least-squares normal matrix definite)
 template <class R, int K>
-__device__ __forceinline__ bool solve_small(R (&A)[K][K], R (&b)[K], R (&x)[K]) {
+__device__ __forceinline__ bool chol_solve(R (&A)[K][K], R (&b)[K], R (&x)[K]) {
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    R d = A[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+    if (!(d > (R)1e-9)) return false;
+    const R l = sqrt(d);
+    A[j][j] = l;
+    const R il = (R)1 / l;
+#pragma unroll
+    for (int i = j + 1; i < K; ++i) {
+      R v = A[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) v -= A[i][k] * A[j][k];
+      A[i][j] = v * il;
+    }
+  }
+  R y[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    int piv = i;
-    R best = fabs(A[i][i]);
+    R v = b[i];
 #pragma unroll
-    for (int r = i + 1; r < K; ++r)
-      if (fabs(A[r][i]) > best) {
-        best = fabs(A[r][i]);
-        piv = r;
-      }
-    if (best < (R)1e-9) return false;
-    if (piv != i) {
-#pragma unroll
-      for (int j = 0; j < K; ++j) {
-        const R tt = A[i][j];
-        A[i][j] = A[piv][j];
-        A[piv][j] = tt;
-      }
-      const R tt = b[i];
-      b[i] = b[piv];
-      b[piv] = tt;
-    }
-#pragma unroll
-    for (int r = i + 1; r < K; ++r) {
-      const R f = A[r][i] / A[i][i];
-#pragma unroll
-      for (int j = i; j < K; ++j) A[r][j] -= f * A[i][j];
-      b[r] -= f * b[i];
-    }
+    for (int k = 0; k < i; ++k) v -= A[i][k] * y[k];
+    y[i] = v / A[i][i];
   }
 #pragma unroll
   for (int i = K - 1; i >= 0; --i) {
-    R acc = b[i];
+    R v = y[i];
 #pragma unroll
-    for (int j = i + 1; j < K; ++j) acc -= A[i][j] * x[j];
-    x[i] = acc / A[i][i];
+    for (int k = i + 1; k < K; ++k) v -= A[k][i] * x[k];
+    x[i] = v / A[i][i];
   }
   return true;
 }
@@ -169,129 +180,134 @@ __device__ __forceinline__ bool solve_small(R (&A)[K][K], R (&b)[K], R (&x)[K]) 
 // axis-aligned planes) then give a smooth, bounded curvature
 constexpr double kLsqRidge = 1e-3;
 
+template <class R> __device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// one warp per interface cell, one lane per stencil cell (27 in 3D, 9 in 2D)
 template <int D, class R>
 __global__ void __launch_bounds__(128) k_geometry(Params p) {
+  constexpr int K = D == 3 ? 5 : 2;
+  constexpr int NS = D == 3 ? 27 : 9;
+  constexpr int CTR = D == 3 ? 13 : 4;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int cnt = *p.icount;
-  FOR_LIST(kk, cnt) {
-  const long long n = p.ilist[kk];
-  const Cell c = make_cell(p, n);
   const R *phi = (const R *)p.phi;
   R *kap = (R *)p.kappa, *nr = (R *)p.nrm, *ds = (R *)p.dst;
-  constexpr int ZR = D == 3 ? 1 : 0;
-  R A[3][3][3];
-  unsigned act = 0;
-  const R ac = phi[n] < (R)0 ? (R)0 : (phi[n] > (R)1 ? (R)1 : phi[n]);
-  for (int dz = -ZR; dz <= ZR; ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const long long m = at(p, c, dx, dy, dz);
-        const int tm = ftype(p.flags[m]);
-        R a;
-        if (tm == T_LIQ) a = 1;
-        else if (tm == T_GAS) a = 0;
-        else if (tm == T_WALL) a = ac;
-        else {
-          a = phi[m];
-          a = a < (R)0 ? (R)0 : (a > (R)1 ? (R)1 : a);
-        }
-        A[dz + 1][dy + 1][dx + 1] = a;
-        if (tm == T_IFC && a > (R)0 && a < (R)1) act |= 1u << ((dz + 1) * 9 + (dy + 1) * 3 + dx + 1);
+  const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = D == 3 ? lane / 9 - 1 : 0;
+  const bool mine = lane < NS;
+  for (int k = warp; k < cnt; k += nwarps) {
+    const long long n = p.ilist[k];
+    const Cell c = make_cell(p, n);
+    int tm = T_LIQ;
+    R a = 0;
+    if (mine) {
+      const long long m = at(p, c, dx, dy, dz);
+      tm = ftype(p.flags[m]);
+      if (tm == T_LIQ) a = 1;
+      else if (tm == T_IFC) {
+        a = phi[m];
+        a = a < (R)0 ? (R)0 : (a > (R)1 ? (R)1 : a);
       }
-  R gx = 0, gy = 0, gz = 0;
-  for (int dz = -ZR; dz <= ZR; ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const R v = A[dz + 1][dy + 1][dx + 1];
-        const R wx = (dy == 0 ? (R)2 : (R)1) * (D == 3 ? (dz == 0 ? (R)2 : (R)1) : (R)1);
-        const R wy = (dx == 0 ? (R)2 : (R)1) * (D == 3 ? (dz == 0 ? (R)2 : (R)1) : (R)1);
-        const R wz = (dx == 0 ? (R)2 : (R)1) * (dy == 0 ? (R)2 : (R)1);
-        gx += (R)dx * wx * v;
-        gy += (R)dy * wy * v;
-        if (D == 3) gz += (R)dz * wz * v;
-      }
-  const R gn = sqrt(gx * gx + gy * gy + gz * gz);
-  if (!(gn > (R)1e-12)) {
-    kap[n] = 0;
-    ds[n] = 0;
-    nr[n] = 0;
-    nr[p.N + n] = 0;
-    nr[2 * p.N + n] = 0;
-    continue;
-  }
-  const R mx = gx / gn, my = gy / gn, mz = gz / gn;
-  const R s0 = plic_offset<D, R>(mx, my, mz, ac);
-  nr[n] = mx;
-  nr[p.N + n] = my;
-  nr[2 * p.N + n] = mz;
-  ds[n] = s0;
-  // local frame
-  R t1x, t1y, t1z, t2x = 0, t2y = 0, t2z = 0;
-  if (D == 2) {
-    t1x = -my; t1y = mx; t1z = 0;
-  } else {
-    const R ax = fabs(mx), ay = fabs(my), az = fabs(mz);
-    const int kmin = ax <= ay ? (ax <= az ? 0 : 2) : (ay <= az ? 1 : 2);
-    const R mk = kmin == 0 ? mx : (kmin == 1 ? my : mz);
-    t1x = (kmin == 0 ? (R)1 : (R)0) - mk * mx;
-    t1y = (kmin == 1 ? (R)1 : (R)0) - mk * my;
-    t1z = (kmin == 2 ? (R)1 : (R)0) - mk * mz;
-    const R l = sqrt(t1x * t1x + t1y * t1y + t1z * t1z);
-    t1x /= l; t1y /= l; t1z /= l;
-    t2x = my * t1z - mz * t1y;
-    t2y = mz * t1x - mx * t1z;
-    t2z = mx * t1y - my * t1x;
-  }
-  // normal equations of the least-squares fit
-  constexpr int K = D == 3 ? 5 : 2;
-  R NA[K][K], Nb[K], N1 = 0, b1 = 0;
-  for (int i = 0; i < K; ++i) {
-    Nb[i] = 0;
-    for (int j = 0; j < K; ++j) NA[i][j] = 0;
-  }
-  int np = 0;
-  for (int dz = -ZR; dz <= ZR; ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        if (dx == 0 && dy == 0 && dz == 0) continue;
-        if (!(act & (1u << ((dz + 1) * 9 + (dy + 1) * 3 + dx + 1)))) continue;
-        const R sj = plic_offset<D, R>(mx, my, mz, A[dz + 1][dy + 1][dx + 1]);
-        const R x = (R)dx * t1x + (R)dy * t1y + (R)dz * t1z;
-        const R y = (R)dx * t2x + (R)dy * t2y + (R)dz * t2z;
-        const R z = (R)dx * mx + (R)dy * my + (R)dz * mz + sj - s0;
-        R ph[K];
-        if constexpr (D == 3) {
-          ph[0] = x * x; ph[1] = y * y; ph[2] = x * y; ph[3] = x; ph[4] = y;
-        } else {
-          ph[0] = x * x; ph[1] = x;
-        }
-#pragma unroll
-        for (int i = 0; i < K; ++i) {
-#pragma unroll
-          for (int j = 0; j < K; ++j) NA[i][j] += ph[i] * ph[j];
-          Nb[i] += ph[i] * z;
-        }
-        const R r2 = x * x + y * y;
-        N1 += r2 * r2;
-        b1 += r2 * z;
-        ++np;
-      }
-  R kv = 0;
-  R beta[K];
-#pragma unroll
-  for (int i = 0; i < K; ++i) NA[i][i] += (R)kLsqRidge;
-  const bool full = np >= (D == 3 ? 5 : 2) && solve_small<R, K>(NA, Nb, beta);
-  if (full) {
-    if constexpr (D == 3) {
-      const R H = beta[3], I = beta[4];
-      kv = -(((R)1 + I * I) * beta[0] - H * I * beta[2] + ((R)1 + H * H) * beta[1]) /
-           pow((R)1 + H * H + I * I, (R)1.5);
-    } else {
-      kv = -beta[0] / pow((R)1 + beta[1] * beta[1], (R)1.5);
     }
-  } else if (np >= 1) {
-    kv = (D == 3 ? (R)-2 : (R)-1) * (b1 / (N1 + (R)kLsqRidge));
-  }
-  kap[n] = kv < (R)-1 ? (R)-1 : (kv > (R)1 ? (R)1 : kv);
+    const R ac = __shfl_sync(0xffffffffu, a, CTR);
+    if (tm == T_WALL) a = ac;  // walls repeat the centre value
+    const bool act = mine && lane != CTR && tm == T_IFC && a > (R)0 && a < (R)1;
+    // Parker-Youngs weighted centred differences
+    const R wz = D == 3 ? (dz == 0 ? (R)2 : (R)1) : (R)1;
+    const R gx = warp_sum<R>(mine ? (R)dx * (dy == 0 ? (R)2 : (R)1) * wz * a : (R)0);
+    const R gy = warp_sum<R>(mine ? (R)dy * (dx == 0 ? (R)2 : (R)1) * wz * a : (R)0);
+    const R gz = D == 3 ? warp_sum<R>(mine ? (R)dz * (dx == 0 ? (R)2 : (R)1) * (dy == 0 ? (R)2 : (R)1) * a : (R)0)
+                        : (R)0;
+    const R gn = sqrt(gx * gx + gy * gy + gz * gz);
+    if (!(gn > (R)1e-12)) {
+      if (lane == 0) {
+        kap[n] = 0;
+        ds[n] = 0;
+        nr[n] = 0;
+        nr[p.N + n] = 0;
+        nr[2 * p.N + n] = 0;
+      }
+      continue;
+    }
+    const R mx = gx / gn, my = gy / gn, mz = gz / gn;
+    const Plic<D, R> plic(mx, my, mz);
+    // every lane cuts its own cell (the centre lane cuts the centre)
+    const R sj = (act || lane == CTR) ? plic.offset(lane == CTR ? ac : a) : (R)0;
+    const R s0 = __shfl_sync(0xffffffffu, sj, CTR);
+    // local frame (t1, t2, m)
+    R t1x, t1y, t1z, t2x = 0, t2y = 0, t2z = 0;
+    if (D == 2) {
+      t1x = -my; t1y = mx; t1z = 0;
+    } else {
+      const R ax = fabs(mx), ay = fabs(my), az = fabs(mz);
+      const int kmin = ax <= ay ? (ax <= az ? 0 : 2) : (ay <= az ? 1 : 2);
+      const R mk = kmin == 0 ? mx : (kmin == 1 ? my : mz);
+      t1x = (kmin == 0 ? (R)1 : (R)0) - mk * mx;
+      t1y = (kmin == 1 ? (R)1 : (R)0) - mk * my;
+      t1z = (kmin == 2 ? (R)1 : (R)0) - mk * mz;
+      const R l = (R)1 / sqrt(t1x * t1x + t1y * t1y + t1z * t1z);
+      t1x *= l; t1y *= l; t1z *= l;
+      t2x = my * t1z - mz * t1y;
+      t2y = mz * t1x - mx * t1z;
+      t2z = mx * t1y - my * t1x;
+    }
+    R ph[K], z = 0, r2 = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) ph[i] = 0;
+    if (act) {
+      const R x = (R)dx * t1x + (R)dy * t1y + (R)dz * t1z;
+      const R y = (R)dx * t2x + (R)dy * t2y + (R)dz * t2z;
+      z = (R)dx * mx + (R)dy * my + (R)dz * mz + sj - s0;
+      if constexpr (D == 3) {
+        ph[0] = x * x; ph[1] = y * y; ph[2] = x * y; ph[3] = x; ph[4] = y;
+      } else {
+        ph[0] = x * x; ph[1] = x;
+      }
+      r2 = x * x + y * y;
+    }
+    // normal equations of the least-squares paraboloid, summed over lanes
+    R NA[K][K], Nb[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+#pragma unroll
+      for (int j = 0; j <= i; ++j) NA[i][j] = warp_sum<R>(ph[i] * ph[j]);
+      Nb[i] = warp_sum<R>(ph[i] * z);
+    }
+    const R N1 = warp_sum<R>(r2 * r2), b1 = warp_sum<R>(r2 * z);
+    const int np = __popc(__ballot_sync(0xffffffffu, act));
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        NA[i][i] += (R)kLsqRidge;
+#pragma unroll
+        for (int j = i + 1; j < K; ++j) NA[i][j] = NA[j][i];
+      }
+      R kv = 0;
+      R beta[K];
+      const bool full = np >= (D == 3 ? 5 : 2) && chol_solve<R, K>(NA, Nb, beta);
+      if (full) {
+        if constexpr (D == 3) {
+          const R H = beta[3], I = beta[4];
+          const R q2 = (R)1 + H * H + I * I;
+          kv = -(((R)1 + I * I) * beta[0] - H * I * beta[2] + ((R)1 + H * H) * beta[1]) / (q2 * sqrt(q2));
+        } else {
+          const R q2 = (R)1 + beta[1] * beta[1];
+          kv = -beta[0] / (q2 * sqrt(q2));
+        }
+      } else if (np >= 1) {
+        kv = (D == 3 ? (R)-2 : (R)-1) * (b1 / (N1 + (R)kLsqRidge));
+      }
+      kap[n] = kv < (R)-1 ? (R)-1 : (kv > (R)1 ? (R)1 : kv);
+      nr[n] = mx;
+      nr[p.N + n] = my;
+      nr[2 * p.N + n] = mz;
+      ds[n] = s0;
+    }
   }
 }
 

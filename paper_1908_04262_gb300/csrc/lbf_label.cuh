@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_local(Params p) {
     bool gas = false;
     if (x < p.nx && y < p.ny && z < p.nz) {
       ++ncell;
-      gas = ftype(p.flags[x + nx * y + nxy * z]) == T_GAS;
+      gas = post_type(p.flags[x + nx * y + nxy * z]) == T_GAS;
     }
     ngas += gas;
     lp[t] = gas ? t : -1;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_merge(Params p) {
                         (D == 3 && (lz == 0 || lz == TZ - 1 || z == p.nz - 1));
     if (!onface) continue;
     const long long n = x + nx * y + nxy * z;
-    if (ftype(p.flags[n]) != T_GAS) continue;
+    if (post_type(p.flags[n]) != T_GAS) continue;
 #pragma unroll
     for (int i = 1; i < Lat<D>::Q; i += 2) {
       const int dx = Lat<D>::cx(i), dy = Lat<D>::cy(i), dz = Lat<D>::cz(i);
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_merge(Params p) {
       if (ns == 0) continue;
       if (own == 1 && ns == 1 && claimed[oi]) continue;
       const long long m = at_far(p, ax, ay, az);
-      if (ftype(p.flags[m]) != T_GAS) continue;
+      if (post_type(p.flags[m]) != T_GAS) continue;
       if (own == 1 && ns == 1 && atomicExch(&claimed[oi], 1)) continue;
       ok &= uf_union(p.parent, (int)n, (int)m);
     }
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_compress(Params p) {
       const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
       if (x < p.nx && y < p.ny && z < p.nz) {
         const long long n = x + nx * y + nxy * z;
-        if (ftype(p.flags[n]) == T_GAS) p.parent[n] = r;
+        if (post_type(p.flags[n]) == T_GAS) p.parent[n] = r;
       }
     }
     return;
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_compress(Params p) {
     const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
     if (x >= p.nx || y >= p.ny || z >= p.nz) continue;
     const long long n = x + nx * y + nxy * z;
-    if (ftype(p.flags[n]) != T_GAS) continue;
+    if (post_type(p.flags[n]) != T_GAS) continue;
     const int r = uf_find(p.parent, (int)n);
     p.parent[n] = r;
     if (r == (int)n) {
@@ -409,7 +409,10 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
   Cell c;
   const bool inr = grid_cell(p, c);
   const long long n = c.n;
-  const int t = inr ? ftype(p.flags[n]) : T_WALL;
+  const uint8_t fl = inr ? p.flags[n] : (uint8_t)T_WALL;
+  const int t = post_type(fl);
+  // the conversion's new types replace the marks
+  if (inr && fmark(fl)) p.flags[n] = (uint8_t)(t | (fl & NEARWALL));
   const int cnt = *p.tnew.count;
   int knew = -1;
   double v = 0.0;
@@ -421,7 +424,7 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
 #pragma unroll
     for (int i = 1; i < Lat<D>::Q; ++i) {
       const long long m = nb<D>(p, c, i);
-      if (ftype(p.flags[m]) == T_GAS) {
+      if (post_type(p.flags[m]) == T_GAS) {
         const int k = root_index(p.roots, cnt, p.parent[m]);
         if (k >= 0 && (knew < 0 || k < knew)) knew = k;
       }
@@ -429,6 +432,7 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
     if (knew >= 0) v = 1.0 - (double)((const R *)p.phi)[n];
   }
   if (inr) p.label_new[n] = knew;
+  list_append(p.inext, p.inext_count, inr && t == T_IFC, (int)n);
   const bool contrib = knew >= 0 && v != 0.0;
   if (__any_sync(0xffffffffu, contrib)) agg_add(p.tnew.V, contrib ? knew : -1, v, wbuf + (threadIdx.x & ~31));
   const int kold = inr ? p.label_old[n] : -1;
@@ -558,7 +562,15 @@ static __global__ void __launch_bounds__(1024) k_bubble_update(Params p) {
   __syncthreads();
   if (tid == nt - 1) *p.next_id = sbase + sfresh[nt - 1];
   for (int h = tid; h < nh; h += nt) p.hash[p.hlist[h]] = HASH_EMPTY;
-  if (tid == 0) *p.hcount = 0;
+  if (tid == 0) {
+    *p.hcount = 0;
+    *p.nroots = 0;
+  }
+  // the old table is the next step's new table: clear its accumulators
+  for (int k = tid; k < p.cap; k += nt) {
+    p.told.V[k] = 0.0;
+    p.told.atm[k] = 0;
+  }
 }
 
 }  // namespace lbf

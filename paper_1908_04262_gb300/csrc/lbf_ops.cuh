@@ -49,9 +49,9 @@ struct OpsImpl final : Ops {
   }
   void exchange(const Params &p, int par, cudaStream_t s) override {
     if (par)
-      k_exchange<D, S, 1><<<p.list_blocks, 128, 0, s>>>(p);
+      k_exchange<D, S, 1><<<p.warp_blocks, 128, 0, s>>>(p);
     else
-      k_exchange<D, S, 0><<<p.list_blocks, 128, 0, s>>>(p);
+      k_exchange<D, S, 0><<<p.warp_blocks, 128, 0, s>>>(p);
   }
   void build_ilist(const Params &p, cudaStream_t s) override {
     cudaMemsetAsync(p.icount, 0, sizeof(int), s);
@@ -65,14 +65,14 @@ struct OpsImpl final : Ops {
   }
   void convert(const Params &p, int par, cudaStream_t s) override {
     const int post = 1 - par;
-    k_conv_unmark<D><<<p.list_blocks, 128, 0, s>>>(p);
-    k_conv_neighbours<D><<<p.list_blocks, 128, 0, s>>>(p);
+    k_conv_mark<D><<<p.list_blocks, 128, 0, s>>>(p);
     k_conv_compute<D, S><<<p.list_blocks, 128, 0, s>>>(p, post);
     k_conv_apply<D, S><<<p.list_blocks, 128, 0, s>>>(p, post);
-    k_conv_finalize<<<p.list_blocks, 128, 0, s>>>(p);
+  }
+  void label_prep(const Params &p, cudaStream_t s) override {
+    k_label_prep<<<blocks_for(p.cap, B), B, 0, s>>>(p);
   }
   void label(const Params &p, cudaStream_t s) override {
-    k_label_prep<<<blocks_for(p.cap, B), B, 0, s>>>(p);
     const dim3 tg((unsigned)((p.nx + Tile<D>::TX - 1) / Tile<D>::TX), (unsigned)((p.ny + Tile<D>::TY - 1) / Tile<D>::TY),
                   (unsigned)((p.nz + Tile<D>::TZ - 1) / Tile<D>::TZ));
     k_uf_local<D><<<tg, TILE_THREADS, 0, s>>>(p);
@@ -85,7 +85,7 @@ struct OpsImpl final : Ops {
   }
   void bubble_update(const Params &p, cudaStream_t s) override { k_bubble_update<<<1, 1024, 0, s>>>(p); }
   void geometry(const Params &p, cudaStream_t s) override {
-    k_geometry<D, R><<<p.list_blocks, 128, 0, s>>>(p);
+    k_geometry<D, R><<<p.warp_blocks, 128, 0, s>>>(p);
   }
   void disjoining(const Params &p, cudaStream_t s) override {
     k_disjoining<D, R><<<p.list_blocks, 128, 0, s>>>(p);

@@ -22,6 +22,7 @@ struct Ops {
   virtual void stream_collide(const Params &p, int par, cudaStream_t s) = 0;
   virtual void convert(const Params &p, int par, cudaStream_t s) = 0;
   virtual void label(const Params &p, cudaStream_t s) = 0;
+  virtual void label_prep(const Params &p, cudaStream_t s) = 0;
   virtual void bubble_update(const Params &p, cudaStream_t s) = 0;
   virtual void geometry(const Params &p, cudaStream_t s) = 0;
   virtual void disjoining(const Params &p, cudaStream_t s) = 0;

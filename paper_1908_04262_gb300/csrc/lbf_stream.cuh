@@ -23,6 +23,12 @@
 
 namespace lbf {
 
+template <class R> __device__ __forceinline__ R warp_sum_r(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 template <class R> struct Prec;
 template <> struct Prec<double> { static constexpr double tol = 1e-13; static constexpr int iters = 60; };
 template <> struct Prec<float> { static constexpr float tol = 2e-6f; static constexpr int iters = 24; };
@@ -97,54 +103,71 @@ template <class R> __device__ __forceinline__ R solve_tau(const Params &p, R A) 
   return t;
 }
 
+// one warp per interface cell, one lane per lattice direction
 template <int D, class S, int PAR>
 __global__ void __launch_bounds__(128) k_exchange(Params p) {
   using R = typename ST<S>::R;
   constexpr int Q = Lat<D>::Q;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int cnt = *p.icount;
-  FOR_LIST(k, cnt) {
-  const long long n = p.ilist[k];
-  const Cell c = make_cell(p, n);
   const S *f = (const S *)p.f;
   R *M = (R *)p.M;
   const R *phi = (const R *)p.phi;
-  R fo[Q];
-  R rho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    fo[i] = ld(f, slot_out<D>(p, c, n, i, PAR), fshift<S, D>(p, i));
-    rho += fo[i];
-    jx += fo[i] * (R)Lat<D>::cx(i);
-    jy += fo[i] * (R)Lat<D>::cy(i);
-    jz += fo[i] * (R)Lat<D>::cz(i);
-  }
-  R *uI = (R *)p.uI;
-  uI[n] = (jx - (R)0.5 * rho * (R)p.ax) / rho;
-  uI[p.N + n] = (jy - (R)0.5 * rho * (R)p.ay) / rho;
-  uI[2 * p.N + n] = (jz - (R)0.5 * rho * (R)p.az) / rho;
-  R Mn = M[n];
-  const R ph = phi[n];
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const long long m = nb<D>(p, c, i);
-    const int tn = ftype(p.flags[m]);
-    if (tn == T_LIQ || tn == T_IFC) {
-      // arriving along opp(i) from m: the slot holding m's outgoing f_opp(i)
-      const R fin = ld(f, slot_in<D>(p, c, n, opp(i), PAR), fshift<S, D>(p, opp(i)));
-      const R dm = fin - fo[i];
-      if (tn == T_LIQ)
-        Mn += dm;
-      else
-        Mn += (R)0.5 * (ph + phi[m]) * dm;
+  for (int k = warp; k < cnt; k += nwarps) {
+    const long long n = p.ilist[k];
+    const Cell c = make_cell(p, n);
+    R fo = 0, dm = 0, ex = 0, ey = 0, ez = 0;
+    if (lane < Q) {
+      const int i = lane;  // the lane's lattice direction
+      fo = ld(f, slot_out<D>(p, c, n, i, PAR), fshift<S, D>(p, i));
+      ex = (R)Lat<D>::cx(i);
+      ey = (R)Lat<D>::cy(i);
+      ez = (R)Lat<D>::cz(i);
+      if (i > 0) {
+        const long long m = nb<D>(p, c, i);
+        const int tn = ftype(p.flags[m]);
+        if (tn == T_LIQ || tn == T_IFC) {
+          // arriving along opp(i) from m: the slot holding m's outgoing f_opp(i)
+          const R fin = ld(f, slot_in<D>(p, c, n, opp(i), PAR), fshift<S, D>(p, opp(i)));
+          dm = tn == T_LIQ ? fin - fo : (R)0.5 * (phi[n] + phi[m]) * (fin - fo);
+        }
+      }
     }
-  }
-  M[n] = Mn;
+    const R rho = warp_sum_r<R>(fo), jx = warp_sum_r<R>(fo * ex), jy = warp_sum_r<R>(fo * ey),
+            jz = warp_sum_r<R>(fo * ez), dM = warp_sum_r<R>(dm);
+    if (lane == 0) {
+      R *uI = (R *)p.uI;
+      uI[n] = (jx - (R)0.5 * rho * (R)p.ax) / rho;
+      uI[p.N + n] = (jy - (R)0.5 * rho * (R)p.ay) / rho;
+      uI[2 * p.N + n] = (jz - (R)0.5 * rho * (R)p.az) / rho;
+      M[n] = M[n] + dM;
+    }
   }
 }
 
 template <class R> struct SweepOcc;
 template <> struct SweepOcc<double> { static constexpr int blocks = 3; };
 template <> struct SweepOcc<float> { static constexpr int blocks = 6; };
+
+// tau(A) of the single-precision forms: linear interpolation in ln A of a
+// table built on the host by bisection (constant beyond its ends)
+__device__ __forceinline__ float tau_lookup(const Params &p, float A) {
+  const float x = (__logf(fmaxf(A, 1e-30f)) - p.tab_lnA0) * p.tab_inv_dlnA;
+  if (!(x > 0.f)) return __ldg(p.tau_tab);
+  if (x >= (float)(p.tab_n - 1)) return __ldg(p.tau_tab + p.tab_n - 1);
+  const int k = (int)x;
+  const float fr = x - (float)k;
+  const float a = __ldg(p.tau_tab + k), b = __ldg(p.tau_tab + k + 1);
+  return a + fr * (b - a);
+}
+template <class R> __device__ __forceinline__ R model_tau(const Params &p, R A) {
+  if constexpr (sizeof(R) == 4)
+    return tau_lookup(p, A);
+  else
+    return solve_tau<R>(p, A);
+}
 
 // Sec. 2.3: local relaxation time.  The non-equilibrium stress is the raw
 // second moment minus its equilibrium value rho (u u + cs^2 I) (identical
@@ -171,7 +194,7 @@ __device__ __forceinline__ R local_tau(const Params &p, const R *fi, R rho, R ux
   const R pzz = D == 3 ? mzz - rho * uz * uz - third : (R)0;
   const R pxy = mxy - rho * ux * uy, pxz = mxz - rho * ux * uz, pyz = myz - rho * uy * uz;
   const R nrm2 = pxx * pxx + pyy * pyy + pzz * pzz + (R)2 * (pxy * pxy + pxz * pxz + pyz * pyz);
-  return solve_tau<R>(p, sqrt(nrm2) / ((R)1.4142135623730951 * rho / (R)3));
+  return model_tau<R>(p, sqrt(nrm2) / ((R)1.4142135623730951 * rho / (R)3));
 }
 
 // BGK relaxation with Guo forcing of one cell, written to the outgoing slots
@@ -276,6 +299,11 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
   Cell c;
   const bool inr = grid_cell(p, c);
   const long long n = c.n;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
+    // counters of the lists the conversion and the relabelling fill
+    *p.ncount = 0;
+    *p.inext_count = 0;
+  }
   const uint8_t fl = inr ? p.flags[n] : (uint8_t)T_GAS;
   const int type = ftype(fl);
   const bool active = inr && (type == T_LIQ || type == T_IFC);
