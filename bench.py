@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS (D3Q19 FSLBM + D3Q7 ADE) and % HBM roofline; FP16+learned-κ vs FP32 plain"
 WORKLOAD = "3D D3Q19 FSLBM + D3Q7 ADE, 128^3, FP32 storage, 8 bubbles (R 4-6), power-law n=0.6, disjoining on"
-KERNELS_PER_STEP = 14  # exchange 1, sweep 1, conversion 4, labelling 5, bubble update 1, geometry 1, disjoining 1
+KERNELS_PER_STEP = 13  # exchange 1, sweep 1, conversion 3, labelling 5, bubble update 1, geometry 1, disjoining 1
 
 
 def parse():
@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP16S + learned-curvature comparison")
     return ap.parse_args()
 
 
@@ -114,6 +115,84 @@ def algorithmic_bytes_sweep(counts, storage_bytes, arith_bytes, Q=19, QA=7):
     N = gas + liq + ifc + wall
     fluid = liq + ifc
     return fluid * 2 * (Q + QA) * storage_bytes + N * 1 + ifc * (8 * arith_bytes + 1)
+
+
+def bubble_volume(b: dict) -> float:
+    """Total volume of the bubbles (the atmosphere excluded)."""
+    return float(sum(v for v, a in zip(b["volume"], b["atm"]) if not a))
+
+
+def timed_steps(sim, stream, steps: int) -> float:
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def static_bubble_laplace(lbf, theta, storage: str, R: float = 5.0, steps: int = 1500, sigma: float = 0.01):
+    """Relative error of the Laplace jump of a static bubble (48^3, periodic)
+    against 2 sigma / R_eq after `steps` steps, mean of the last 4 samples."""
+    import numpy as np
+
+    from paper_1908_04262_gb300 import curvature
+
+    n = 48
+    sim = lbf.Sim(curvature.static_bubble_config(R, storage, sigma=sigma, n=n))
+    c = [n / 2 + 0.31, n / 2 - 0.17, n / 2 + 0.23]
+    sim.nucleate([c], [R])
+    if theta is not None:
+        sim.mlp_attach(theta)
+    idx = np.arange(n ** 3)
+    d = np.sqrt((idx % n - c[0]) ** 2 + ((idx // n) % n - c[1]) ** 2 + (idx // (n * n) - c[2]) ** 2)
+    rel = []
+    for _ in range(steps // 250):
+        sim.step(250)
+        b = sim.bubbles()
+        f = sim.fields(["rho", "flags"])
+        pl = f["rho"][((f["flags"] & 3) == 1) & (d > R + 4)].mean() / 3
+        rel.append((b["pressure"][0] - pl) / (2 * sigma / np.cbrt(3 * b["volume"][0] / (4 * np.pi))) - 1)
+    sim.close()
+    return float(np.mean(rel[-4:]))
+
+
+def forms_comparison(args, lbf, cfg, pts, rad, stream, fp32_line):
+    """The same workload in shifted-FP16 storage with the learned curvature
+    (and the two halves of that change alone) against FP32 with least
+    squares; the network is trained first by the package's recipe."""
+    import torch
+
+    from paper_1908_04262_gb300 import curvature
+
+    t0 = time.perf_counter()
+    theta, info = curvature.train(seed=1, rounds=3, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    out = {"fp32_plain": fp32_line, "mlp_training_s": t_train, "mlp_training": info}
+    N = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    for name, storage, use in (("fp16s_mlp", "fp16s", True), ("fp16s_plain", "fp16s", False),
+                               ("fp32_mlp", "fp32", True)):
+        sim = lbf.Sim(dict(cfg, storage=storage), stream=stream.cuda_stream)
+        sim.nucleate(pts, rad)
+        if use:
+            sim.mlp_attach(theta)
+        sim.step(args.warmup)
+        ms = timed_steps(sim, stream, args.steps)
+        V = bubble_volume(sim.bubbles())
+        out[name] = {"mlups": N * args.steps / (ms / 1e3) / 1e6, "ms_per_step": ms / args.steps,
+                     "bubble_volume_rel_diff_vs_fp32_plain": V / fp32_line["bubble_volume"] - 1}
+        sim.close()
+    out["laplace_rel_err_static_bubble_R5"] = {
+        "fp32_plain": static_bubble_laplace(lbf, None, "fp32"),
+        "fp16s_mlp": static_bubble_laplace(lbf, theta, "fp16s")}
+    out["note"] = ("same workload, steps and warm-up as the headline; bubble volume = total over the "
+                   "bubbles after warm-up + timed steps; Laplace error of a static R=5 bubble, 48^3")
+    return out
 
 
 def reduce_max(x: float, world: int) -> float:
@@ -225,6 +304,7 @@ def run_ours(args):
     clocks = stop_clocks(*clk)
     ms = reduce_max(e0.elapsed_time(e1), world)
     counts1 = sim.cell_counts()
+    fp32_volume = bubble_volume(sim.bubbles())
     value = N * args.steps * world / (ms / 1e3) / 1e6
 
     # --- kernel timing (CUDA events around every kernel group) -----------
@@ -285,6 +365,10 @@ def run_ours(args):
             "roofline": roofline, "kernel_ms": kernel_ms,
             "fluid_mlups": (counts0[1] + counts0[2]) * args.steps * world / (ms / 1e3) / 1e6,
             "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clocks, "e2e": e2e}
+    if world == 1 and not args.no_forms:
+        line["forms"] = forms_comparison(args, lbf, cfg, pts, rad, stream,
+                                         {"mlups": value, "ms_per_step": ms / args.steps,
+                                          "bubble_volume": fp32_volume})
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(cfg, pts, rad)
     if rank == 0:

@@ -172,6 +172,71 @@ long long lbf_step_count(const lbf_sim *s);
 
 const char *lbf_last_error(void);
 
+/* ------------------------------------------------------------------------
+ * Learned interface curvature (not in the paper; replaces the least-squares
+ * kappa of Sec. 2.2 Eq. rhob where it is inside its training range).
+ * Network: canonical 3x3x3 fill-level stencil (27 values in [0,1], index
+ * (dz+1)*9 + (dy+1)*3 + (dx+1); axes reflected so the interface normal is
+ * non-negative, then ordered by increasing normal component) -> 64 -> 64 -> 1
+ * with SiLU; output y = 4 kappa.  BF16 weights and activations, FP32
+ * accumulation, tensor cores.  Parameters theta: 6017 FP32 values, W1 (64x27
+ * row-major), b1 (64), W2 (64x64), b2 (64), W3 (64), b3 (1).
+ */
+typedef struct {
+  unsigned long long seed; /* counter-based generator seed                   */
+  int n_samples;           /* synthetic stencils generated on the device     */
+  int epochs, batch;       /* Adam epochs over the samples, mini-batch size  */
+  double lr;               /* Adam learning rate (x0.1 for the last quarter) */
+  double rmin, rmax;       /* radii, log-uniform; spheres and ellipsoids     */
+  double noise;            /* augmentation: fill levels strictly inside (0,1)
+                              get uniform noise of this half-width, clamped  */
+  const float *x_extra;    /* device, n_extra x 27: further canonical stencils
+                              (e.g. harvested by lbf_mlp_harvest), or NULL   */
+  const float *y_extra;    /* device, n_extra targets y = 4 kappa            */
+  int n_extra;
+  void *stream;            /* cudaStream_t                                   */
+} lbf_mlp_train_cfg;
+
+/* y[i] for n canonical stencils x (device, n x 27 FP32); theta and y are
+ * device pointers.  Asynchronous on `stream`.  Errors: LBF_EINVAL. */
+int lbf_mlp_forward(const float *theta, const float *x, int n, float *y, void *stream);
+/* Loss 0.5 mean((y - t)^2) of n stencils x with targets t (all device) and
+ * its gradient: grad (device, 6017 FP32) and *loss (device, one double) are
+ * overwritten.  Asynchronous.  Errors: LBF_EINVAL. */
+int lbf_mlp_loss_grad(const float *theta, const float *x, const float *t, int n, float *grad, double *loss,
+                      void *stream);
+/* n synthetic training pairs (canonical stencil, y = 4 kappa) into device
+ * buffers x (n x 27) and y (n): voxelised spheres and ellipsoids (axes
+ * 0.75-1.25 R, random rotation and sub-cell offset, 3/4 gas inside), R
+ * log-uniform in [rmin, rmax], fill level = fraction of 6^3 sub-points in
+ * the liquid, kappa = analytic mean curvature at the surface point nearest
+ * the cell centre (positive for convex gas).  Errors: LBF_EINVAL, LBF_ECUDA. */
+int lbf_mlp_generate(unsigned long long seed, int n, double rmin, double rmax, float *x, float *y, void *stream);
+/* The same from explicit shape parameters (host, n x 20 doubles: centre[3],
+ * axes[3], rotation[9] row-major, gas_inside, cell[3], unused); synchronises. */
+int lbf_mlp_stencils_from_params(const double *params, int n, float *x, float *y, void *stream);
+/* Train the network on the device (generation, forward/backward on the
+ * tensor cores, Adam); theta_io (host, 6017) holds the start point and
+ * receives the result; loss_curve (host, epochs floats, may be NULL)
+ * receives the mean training loss of every epoch.  Synchronises. */
+int lbf_mlp_train(const lbf_mlp_train_cfg *cfg, float *theta_io, float *loss_curve);
+/* Training pairs from the current state of s (3D): the canonical stencil of
+ * every interface cell (x: device, cap x 27 FP32) and the target
+ * y = 4 / R_eq of the cell's bubble (y: device, cap FP32), R_eq =
+ * (3 V / 4 pi)^(1/3) from the bubble's volume -- the curvature of a
+ * relaxed, nearly spherical bubble.  Skipped: cells with a wall in the
+ * stencil, a zero normal, no bubble or the atmosphere.  cells (device,
+ * cap int32, may be NULL) receives each pair's linear cell index; the
+ * order of the pairs is unspecified.  *count (host)
+ * receives the number written (<= cap).  Synchronises.
+ * Errors: LBF_EINVAL, LBF_ECUDA. */
+int lbf_mlp_harvest(lbf_sim *s, float *x, float *y, int *cells, int cap, int *count);
+/* Use the network for kappa in every following step of s (3D only): theta
+ * host, copied; NULL returns to the least-squares curvature.  The network's
+ * kappa replaces the least-squares value where |kappa_LSQ| lies in
+ * [0.02, 0.55] and no wall is in the stencil.  Errors: LBF_EINVAL. */
+int lbf_mlp_attach(lbf_sim *s, const float *theta);
+
 /* Bubble labels of a cell-type field without allocating any memory.
  * The paper has no counterpart: this is a service for callers that cannot
  * call cudaMalloc (a framework whose caching allocator has reserved the

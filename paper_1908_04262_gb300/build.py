@@ -26,6 +26,7 @@ UNITS = {
     "k_bf16.cu": [],
     "lbf_abi.cu": [],
     "lbf_noalloc.cu": [],
+    "lbf_mlp.cu": [],
 }
 
 

@@ -77,6 +77,9 @@ struct lbf_sim {
   unsigned long long *counts = nullptr;
   void *staging = nullptr;
   float *tau_tab = nullptr;
+  float *mlp_theta = nullptr;  // learned curvature parameters, when attached
+  float *mlp_buf = nullptr;    // owned copy of the parameters
+  int *mlp_count = nullptr;    // harvest counter
   int tab_n = 0;
   float tab_lnA0 = 0.f, tab_inv_dlnA = 0.f;
   long long step = 0;
@@ -178,6 +181,7 @@ int relabel_in_place(lbf_sim *s) {
   CK(cudaMemcpyAsync(a.count, b.count, sizeof(int), cudaMemcpyDeviceToDevice, s->st));
   p.label_new = s->label[par];
   s->ops->geometry(p, s->st);
+  if (s->mlp_theta) s->ops->mlp_kappa(p, s->mlp_theta, s->st);
   s->ops->disjoining(p, s->st);
   // the next step accumulates into table [1-par] and counts roots afresh
   s->ops->label_prep(p, s->st);
@@ -211,7 +215,10 @@ void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
   Params pn = p;
   pn.ilist = p.inext;
   pn.icount = p.inext_count;
-  group(G_GEOMETRY, [&] { s->ops->geometry(pn, s->st); });
+  group(G_GEOMETRY, [&] {
+    s->ops->geometry(pn, s->st);
+    if (s->mlp_theta) s->ops->mlp_kappa(pn, s->mlp_theta, s->st);
+  });
   group(G_DISJOIN, [&] { s->ops->disjoining(pn, s->st); });
 }
 
@@ -586,6 +593,47 @@ int lbf_step(lbf_sim *s, int nsteps) {
 }
 
 long long lbf_step_count(const lbf_sim *s) { return s ? s->step : -1; }
+
+int lbf_mlp_harvest(lbf_sim *s, float *x, float *y, int *cells, int cap, int *count) {
+  if (!s || !x || !y || cap < 0 || !count) return fail(LBF_EINVAL, "bad arguments");
+  if (s->dim != 3) return fail(LBF_EINVAL, "the learned curvature is three-dimensional");
+  if (!s->mlp_count) {
+    int rc = dalloc(s, &s->mlp_count, 1);
+    if (rc) return rc;
+  }
+  Params p = make_params(s, s->step);
+  CK(cudaMemsetAsync(s->mlp_count, 0, sizeof(int), s->st));
+  s->ops->mlp_harvest(p, x, y, cells, cap, s->mlp_count, s->st);
+  CK(cudaGetLastError());
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, s->mlp_count, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  *count = h < cap ? h : cap;
+  return 0;
+}
+
+int lbf_mlp_attach(lbf_sim *s, const float *theta) {
+  if (!s) return fail(LBF_EINVAL, "NULL sim");
+  if (theta && s->dim != 3) return fail(LBF_EINVAL, "the learned curvature is three-dimensional");
+  if (theta) {
+    if (!s->mlp_buf) {
+      int rc = dalloc(s, &s->mlp_buf, 6017);
+      if (rc) return rc;
+    }
+    CK(cudaMemcpyAsync(s->mlp_buf, theta, sizeof(float) * 6017, cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    s->mlp_theta = s->mlp_buf;
+  } else {
+    s->mlp_theta = nullptr;  // the buffer stays owned by the sim until destroy
+  }
+  // the step graphs change shape
+  for (int k = 0; k < 2; ++k) {
+    if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
+    if (s->tgraph[k]) cudaGraphExecDestroy(s->tgraph[k]);
+    s->graph[k] = s->tgraph[k] = nullptr;
+  }
+  return 0;
+}
 
 int lbf_bubbles(lbf_sim *s, lbf_bubble *out, int capacity, int *count) {
   if (!s || !count || capacity < 0 || (capacity > 0 && !out)) return fail(LBF_EINVAL, "bad arguments");

@@ -8,6 +8,7 @@
 #include "lbf_convert.cuh"
 #include "lbf_geom.cuh"
 #include "lbf_label.cuh"
+#include "lbf_mlp_kappa.cuh"
 #include "lbf_stream.cuh"
 
 namespace lbf {
@@ -86,6 +87,12 @@ struct OpsImpl final : Ops {
   void bubble_update(const Params &p, cudaStream_t s) override { k_bubble_update<<<1, 1024, 0, s>>>(p); }
   void geometry(const Params &p, cudaStream_t s) override {
     k_geometry<D, R><<<p.warp_blocks, 128, 0, s>>>(p);
+  }
+  void mlp_kappa(const Params &p, const float *theta, cudaStream_t s) override {
+    if (D == 3) k_mlp_kappa<D, R><<<p.list_blocks, 128, 0, s>>>(p, theta);
+  }
+  void mlp_harvest(const Params &p, float *x, float *y, int *cells, int cap, int *count, cudaStream_t s) override {
+    if (D == 3) k_mlp_harvest<D, R><<<p.warp_blocks, 128, 0, s>>>(p, x, y, cells, cap, count);
   }
   void disjoining(const Params &p, cudaStream_t s) override {
     k_disjoining<D, R><<<p.list_blocks, 128, 0, s>>>(p);

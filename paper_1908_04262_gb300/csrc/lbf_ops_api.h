@@ -26,6 +26,8 @@ struct Ops {
   virtual void bubble_update(const Params &p, cudaStream_t s) = 0;
   virtual void geometry(const Params &p, cudaStream_t s) = 0;
   virtual void disjoining(const Params &p, cudaStream_t s) = 0;
+  virtual void mlp_kappa(const Params &p, const float *theta, cudaStream_t s) = 0;
+  virtual void mlp_harvest(const Params &p, float *x, float *y, int *cells, int cap, int *count, cudaStream_t s) = 0;
   // export
   virtual void field(const Params &p, int par, int which, void *out, int dtype, cudaStream_t s) = 0;
   virtual void ledger(const Params &p, int par, double *acc, unsigned long long *counts, cudaStream_t s) = 0;

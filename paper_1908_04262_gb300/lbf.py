@@ -57,10 +57,20 @@ class Bubble(ctypes.Structure):
                 ("pressure", ctypes.c_double)]
 
 
+class MlpTrainCfg(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_ulonglong), ("n_samples", ctypes.c_int), ("epochs", ctypes.c_int),
+                ("batch", ctypes.c_int), ("lr", ctypes.c_double), ("rmin", ctypes.c_double),
+                ("rmax", ctypes.c_double), ("noise", ctypes.c_double), ("x_extra", ctypes.c_void_p),
+                ("y_extra", ctypes.c_void_p), ("n_extra", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
 EXPORTS = ("lbf_create", "lbf_destroy", "lbf_nucleate", "lbf_set_cells", "lbf_step",
            "lbf_bubbles", "lbf_fields", "lbf_ledger", "lbf_timing_enable", "lbf_timing_read",
            "lbf_timing_name", "lbf_cell_counts", "lbf_step_count", "lbf_last_error",
-           "lbf_label_gas_noalloc")
+           "lbf_label_gas_noalloc", "lbf_mlp_forward", "lbf_mlp_loss_grad", "lbf_mlp_generate",
+           "lbf_mlp_stencils_from_params", "lbf_mlp_train", "lbf_mlp_harvest", "lbf_mlp_attach")
+
+MLP_NPARAM = 6017
 
 _lib = None
 
@@ -93,6 +103,13 @@ def load(path: str = LIB_PATH):
     lib.lbf_step_count.restype = ctypes.c_longlong
     lib.lbf_last_error.restype = ctypes.c_char_p
     lib.lbf_label_gas_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P]
+    lib.lbf_mlp_forward.argtypes = [P, P, ctypes.c_int, P, P]
+    lib.lbf_mlp_loss_grad.argtypes = [P, P, P, ctypes.c_int, P, P, P]
+    lib.lbf_mlp_generate.argtypes = [ctypes.c_ulonglong, ctypes.c_int, ctypes.c_double, ctypes.c_double, P, P, P]
+    lib.lbf_mlp_stencils_from_params.argtypes = [P, ctypes.c_int, P, P, P]
+    lib.lbf_mlp_train.argtypes = [ctypes.POINTER(MlpTrainCfg), P, P]
+    lib.lbf_mlp_attach.argtypes = [P, P]
+    lib.lbf_mlp_harvest.argtypes = [P, P, P, P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     _lib = lib
     return lib
 
@@ -120,6 +137,53 @@ def label_gas_noalloc(types, nx: int, ny: int, nz: int, labels, count, stream: i
     rc = lib.lbf_label_gas_noalloc(types.data_ptr(), nx, ny, nz, labels.data_ptr(), count.data_ptr(), stream)
     if rc != 0:
         raise LbfError(rc, lib.lbf_last_error().decode(errors="replace"))
+
+
+def _raise(rc: int):
+    if rc != 0:
+        raise LbfError(rc, load().lbf_last_error().decode(errors="replace"))
+
+
+# --- learned curvature (device tensors in, device tensors out) -------------
+
+
+def mlp_forward(theta, x, y, stream: int | None = None):
+    """y (n) = network(x (n x 27)); float32 device tensors."""
+    _raise(load().lbf_mlp_forward(theta.data_ptr(), x.data_ptr(), x.shape[0], y.data_ptr(), stream))
+
+
+def mlp_loss_grad(theta, x, t, grad, loss, stream: int | None = None):
+    """grad (6017 float32) and loss (1 float64) of 0.5 mean((y - t)^2)."""
+    _raise(load().lbf_mlp_loss_grad(theta.data_ptr(), x.data_ptr(), t.data_ptr(), x.shape[0],
+                                    grad.data_ptr(), loss.data_ptr(), stream))
+
+
+def mlp_generate(seed: int, x, y, rmin: float = 2.0, rmax: float = 40.0, stream: int | None = None):
+    """Synthetic canonical stencils x (n x 27) and targets y = 4 kappa (n)."""
+    _raise(load().lbf_mlp_generate(int(seed), x.shape[0], rmin, rmax, x.data_ptr(), y.data_ptr(), stream))
+
+
+def mlp_stencils_from_params(params, x, y, stream: int | None = None):
+    """Stencils of explicit shapes: params host (n x 20) float64."""
+    p = np.ascontiguousarray(np.asarray(params, np.float64).reshape(-1, 20))
+    _raise(load().lbf_mlp_stencils_from_params(_p(p), p.shape[0], x.data_ptr(), y.data_ptr(), stream))
+
+
+def mlp_train(theta0, n_samples: int = 1 << 22, epochs: int = 20, batch: int = 2048, lr: float = 3e-3,
+              rmin: float = 2.0, rmax: float = 40.0, seed: int = 1, noise: float = 0.0,
+              x_extra=None, y_extra=None, stream: int | None = None):
+    """Train on the device from theta0 (host, 6017) on ``n_samples``
+    generated stencils plus optional extra device tensors (n x 27, n);
+    returns (theta, mean loss per epoch)."""
+    th = np.ascontiguousarray(np.asarray(theta0, np.float32).reshape(-1).copy())
+    assert th.size == MLP_NPARAM
+    curve = np.zeros(epochs, np.float32)
+    ne = 0 if x_extra is None else int(x_extra.shape[0])
+    c = MlpTrainCfg(int(seed), int(n_samples), int(epochs), int(batch), float(lr), float(rmin),
+                    float(rmax), float(noise), None if ne == 0 else x_extra.data_ptr(),
+                    None if ne == 0 else y_extra.data_ptr(), ne, stream)
+    _raise(load().lbf_mlp_train(ctypes.byref(c), _p(th), _p(curve)))
+    return th, curve
 
 
 def _p(a: np.ndarray):
@@ -229,6 +293,25 @@ class Sim:
         out = np.zeros(4, np.int64)
         self._check(self.lib.lbf_cell_counts(self.h, _p(out)))
         return out
+
+    def mlp_attach(self, theta=None):
+        """Learned curvature from the next step on (3D); None detaches."""
+        if theta is None:
+            self._check(self.lib.lbf_mlp_attach(self.h, None))
+            return
+        th = np.ascontiguousarray(np.asarray(theta, np.float32).reshape(-1))
+        assert th.size == MLP_NPARAM
+        self._check(self.lib.lbf_mlp_attach(self.h, _p(th)))
+
+    def mlp_harvest(self, x, y, cells=None) -> int:
+        """Training pairs of the current interface cells into the device
+        tensors x (cap x 27) and y (cap), float32, and optionally their cell
+        indices (cap int32); returns how many."""
+        cnt = ctypes.c_int()
+        self._check(self.lib.lbf_mlp_harvest(self.h, x.data_ptr(), y.data_ptr(),
+                                             None if cells is None else cells.data_ptr(),
+                                             int(x.shape[0]), ctypes.byref(cnt)))
+        return cnt.value
 
     def timing_enable(self, on: bool = True):
         self._check(self.lib.lbf_timing_enable(self.h, 1 if on else 0))

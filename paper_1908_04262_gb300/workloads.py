@@ -190,3 +190,38 @@ def random_flow_state(cfg: dict, seed: int, du: float = 0.02, drho: float = 0.01
         u[:, 2] = 0.0
     conc = cfg["c0"] + 0.1 * rng.random(N)
     return rho, u, conc
+
+
+# ---------------------------------------------------------------------------
+# voxelised spheres (fill levels by sub-sampling)
+
+
+def voxel_spheres(shape, centres, radii, sub: int = 4, gas_inside: bool = True):
+    """Cell types (0 gas, 1 liquid, 2 interface) and fill levels of spheres
+    drawn on a periodic lattice of ``shape`` (nx, ny, nz): the fill level of
+    a cell is the fraction of its sub^3 regularly spaced sample points that
+    lie in the liquid.  Arrays are flat, ``n = x + nx*(y + ny*z)``."""
+    nx, ny, nz = shape
+    g = (np.arange(sub) + 0.5) / sub - 0.5
+    liquid = np.zeros((nz, ny, nx))
+    for c, r in zip(np.asarray(centres, float), np.asarray(radii, float)):
+        lo = np.floor(c - r - 1).astype(int)
+        hi = np.ceil(c + r + 1).astype(int)
+        ix = np.arange(lo[0], hi[0] + 1) % nx
+        iy = np.arange(lo[1], hi[1] + 1) % ny
+        iz = np.arange(lo[2], hi[2] + 1) % nz
+        frac = np.zeros((iz.size, iy.size, ix.size))
+        cx = np.arange(lo[0], hi[0] + 1)[None, None, :]
+        cy = np.arange(lo[1], hi[1] + 1)[None, :, None]
+        cz = np.arange(lo[2], hi[2] + 1)[:, None, None]
+        for sz in g:
+            for sy in g:
+                for sx in g:
+                    d2 = (cx + sx - c[0]) ** 2 + (cy + sy - c[1]) ** 2 + (cz + sz - c[2]) ** 2
+                    frac += d2 < r * r
+        frac /= sub ** 3
+        liquid[np.ix_(iz, iy, ix)] += frac
+    inside = np.clip(liquid, 0.0, 1.0).reshape(-1)
+    alpha = 1.0 - inside if gas_inside else inside
+    types = np.where(alpha <= 0.0, 0, np.where(alpha >= 1.0, 1, 2)).astype(np.uint8)
+    return types, alpha

@@ -1,0 +1,386 @@
+"""GPU parity of the learned curvature (the network of oracle/mlp.py on the
+tensor cores) and what it gains over the least-squares curvature of
+Sec. 2.2 Eq. rhob.
+
+Tolerances, from the arithmetic: the kernels round x, W1, W2 and both
+hidden activations to BF16 and accumulate in FP32.  Against the FP64
+network with the same BF16 roundings (``mlp.forward_bf16``) only the FP32
+accumulation order (~1e-7) and the fast exponential remain, except where a
+pre-activation lies within that distance of a BF16 rounding boundary and the
+two sides round it to neighbouring BF16 values: such a one-ulp flip (2^-8
+relative) of an output-layer activation h2_j moves y by at most
+2^-8 |W3_j h2_j|, of a first-layer activation by less.  So 99 % of the
+outputs agree to 1e-5 (1 + |y|) and every output to
+2^-8 sum_j |W3_j h2_j|.  Against the unrounded FP64 network the BF16 unit
+roundoff 2^-9 of every operand enters: the relative RMS of y, and of each
+gradient block, stays below 2e-2.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_1908_04262_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("the GPU tests need a CUDA device")
+    from paper_1908_04262_gb300 import build as B
+    from paper_1908_04262_gb300 import lbf as L
+
+    B.build()
+    return L, torch
+
+
+def _dev(torch, a, dt=None):
+    return torch.tensor(np.asarray(a), dtype=dt or torch.float32, device="cuda")
+
+
+def _theta(seed, noise=0.05):
+    rng = np.random.default_rng(seed)
+    th = mlp.init_params(seed) + noise * rng.normal(size=mlp.NPARAM)
+    return th.astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("n", [1, 16, 1000, 40003])
+def test_forward_matches_oracle(env, n):
+    L, torch = env
+    rng = np.random.default_rng(n)
+    th = _theta(3)
+    x = rng.random((n, 27)).astype(np.float32).astype(np.float64)
+    y = torch.zeros(n, device="cuda")
+    L.mlp_forward(_dev(torch, th), _dev(torch, x), y)
+    torch.cuda.synchronize()
+    y = y.cpu().numpy().astype(np.float64)
+    yb = mlp.forward_bf16(th, x)
+    d = np.abs(y - yb)
+    assert np.mean(d <= 1e-5 * (1 + np.abs(yb))) >= 0.99
+    W1, b1, W2, b2, W3, b3 = mlp.split(th)
+    h2 = mlp.silu(mlp.silu(x @ W1.T + b1) @ W2.T + b2)
+    assert np.all(d <= 2.0 ** -8 * (np.abs(h2) @ np.abs(W3)) + 1e-5)
+    y64 = mlp.forward(th, x)
+    assert np.sqrt(np.mean((y - y64) ** 2) / np.mean(y64 ** 2)) < 2e-2
+
+
+def test_gradient_matches_oracle(env):
+    L, torch = env
+    rng = np.random.default_rng(5)
+    th = _theta(7, 0.02)
+    n = 4099  # ragged: 256 full tiles of 16 and a tail of 3
+    x = rng.random((n, 27)).astype(np.float32).astype(np.float64)
+    t = rng.normal(size=n).astype(np.float32).astype(np.float64)
+    grad = torch.zeros(mlp.NPARAM, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    L.mlp_loss_grad(_dev(torch, th), _dev(torch, x), _dev(torch, t), grad, loss)
+    torch.cuda.synchronize()
+    g = grad.cpu().numpy().astype(np.float64)
+    L64, g64 = mlp.loss_and_grad(th, x, t)
+    Lb = 0.5 * np.mean((mlp.forward_bf16(th, x) - t) ** 2)
+    assert abs(loss.item() - Lb) < 1e-4 * Lb
+    assert abs(loss.item() - L64) < 2e-2 * L64
+    k = 0
+    for s in mlp.SIZES:
+        m = int(np.prod(s))
+        a, b = g[k:k + m], g64[k:k + m]
+        assert np.linalg.norm(a - b) < 2e-2 * np.linalg.norm(b), (s, np.linalg.norm(a - b) / np.linalg.norm(b))
+        k += m
+    assert g @ g64 / (np.linalg.norm(g) * np.linalg.norm(g64)) > 0.9995
+
+
+def _random_rotation(rng):
+    q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def _shape_params(rng, n, rmin=2.0, rmax=40.0):
+    P = np.zeros((n, 20))
+    for i in range(n):
+        R = np.exp(rng.uniform(np.log(rmin), np.log(rmax)))
+        axes = R * (rng.uniform(0.75, 1.25, 3) if i % 2 else np.ones(3))
+        rot = _random_rotation(rng)
+        c = rng.random(3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        A = rot @ np.diag(1 / axes ** 2) @ rot.T
+        tt = 1 / np.sqrt(d @ A @ d)
+        P[i, 0:3], P[i, 3:6], P[i, 6:15] = c, axes, rot.ravel()
+        P[i, 15] = 1.0 if i % 4 else 0.0
+        P[i, 16:19] = np.floor(c + tt * d + 0.5)
+    return P
+
+
+def _orientations(n, tol):
+    """Source maps of every canonical orientation consistent with normal n
+    up to ties within tol (several are correct when components tie)."""
+    an = np.abs(n)
+    out = []
+    for perm in itertools.permutations(range(3)):
+        if any(an[perm[j]] > an[perm[j + 1]] + tol for j in range(2)):
+            continue
+        for signs in itertools.product((-1, 1), repeat=3):
+            if any(signs[d] * n[d] < -tol for d in range(3)):
+                continue
+            src = np.zeros(27, np.int64)
+            for q in range(27):
+                old = np.zeros(3, np.int64)
+                for j in range(3):
+                    old[perm[j]] = signs[perm[j]] * mlp.OFFS[q][j]
+                src[q] = (old[2] + 1) * 9 + (old[1] + 1) * 3 + (old[0] + 1)
+            out.append(src)
+    return out
+
+
+def test_stencil_generator_matches_oracle(env):
+    L, torch = env
+    rng = np.random.default_rng(21)
+    P = _shape_params(rng, 300)
+    x = torch.zeros((300, 27), device="cuda")
+    y = torch.zeros(300, device="cuda")
+    L.mlp_stencils_from_params(P, x, y)
+    x, y = x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64)
+    exact = 0
+    for i in range(300):
+        rot = P[i, 6:15].reshape(3, 3)
+        a, kap = mlp.ellipsoid_stencil(P[i, 0:3], P[i, 3:6], rot, P[i, 15] > 0.5, P[i, 16:19])
+        assert abs(y[i] - mlp.Y_SCALE * kap) <= 1e-6 * max(1.0, abs(mlp.Y_SCALE * kap))
+        ref = a[mlp.canonical_map(mlp.py_normal(a))]
+        if np.max(np.abs(x[i] - ref)) <= 1e-7:  # fill levels k/216 stored as FP32
+            exact += 1
+            continue
+        # a sub-point on the surface or a near-tie of normal components:
+        # the stencil must still be a valid canonical form of the same cells
+        cands = [a[s] for s in _orientations(mlp.py_normal(a), 1e-5)]
+        assert any(np.max(np.abs(x[i] - c)) <= 1 / 216 + 1e-7 for c in cands), i
+    assert exact >= 294
+
+
+def test_generator_properties(env):
+    L, torch = env
+    n = 100003
+    x = torch.zeros((n, 27), device="cuda")
+    y = torch.zeros(n, device="cuda")
+    L.mlp_generate(99, x, y, 2.0, 40.0)
+    x2 = torch.zeros((n, 27), device="cuda")
+    y2 = torch.zeros(n, device="cuda")
+    L.mlp_generate(99, x2, y2, 2.0, 40.0)
+    assert torch.equal(x, x2) and torch.equal(y, y2)  # counter-based: reproducible
+    X, Y = x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64)
+    assert X.min() >= 0 and X.max() <= 1
+    assert np.all(np.abs(X * 216 - np.round(X * 216)) < 1e-4)
+    dx, dy, dz = mlp.OFFS.T
+    w = np.stack([dx * np.where(dy == 0, 2, 1) * np.where(dz == 0, 2, 1),
+                  dy * np.where(dx == 0, 2, 1) * np.where(dz == 0, 2, 1),
+                  dz * np.where(dx == 0, 2, 1) * np.where(dy == 0, 2, 1)], 1)
+    nrm = X @ w
+    assert np.all(nrm >= -1e-4)
+    assert np.all(nrm[:, 0] <= nrm[:, 1] + 1e-4) and np.all(nrm[:, 1] <= nrm[:, 2] + 1e-4)
+    k = Y / mlp.Y_SCALE
+    assert np.all(np.abs(k) <= 1.25 / 0.75 ** 2 / 2.0 + 1e-6)
+    assert np.all(np.abs(k) >= 0.75 / 1.25 ** 2 / 40.0 - 1e-6)
+    assert abs(np.mean(k > 0) - 0.75) < 0.01
+
+
+@pytest.fixture(scope="module")
+def trained(env):
+    L, torch = env
+    th, curve = L.mlp_train(mlp.init_params(0), n_samples=1 << 21, epochs=8, batch=1024, lr=2e-3, seed=11)
+    return th.astype(np.float64), curve
+
+
+def test_training_reduces_loss(env, trained):
+    L, torch = env
+    th, curve = trained
+    assert np.all(np.isfinite(curve))
+    assert curve[-1] < 0.2 * curve[0]
+    # held-out stencils (another seed): the network's kappa error
+    n = 65536
+    x = torch.zeros((n, 27), device="cuda")
+    y = torch.zeros(n, device="cuda")
+    L.mlp_generate(12345, x, y, 2.0, 40.0)
+    p = torch.zeros(n, device="cuda")
+    L.mlp_forward(_dev(torch, th), x, p)
+    err = (p - y).cpu().numpy() / mlp.Y_SCALE
+    print("held-out kappa RMS error %.4g (targets RMS %.4g); loss per epoch %s"
+          % (np.sqrt(np.mean(err ** 2)), np.sqrt(np.mean((y.cpu().numpy() / 4) ** 2)), curve))
+    assert np.sqrt(np.mean(err ** 2)) < 0.35 * np.sqrt(np.mean((y.cpu().numpy() / 4) ** 2))
+
+
+SPHERES = dict(centres=[[12.3, 11.8, 12.6], [12.1, 12.4, 32.7], [12.6, 34.2, 20.3], [34.4, 12.3, 22.2],
+                        [33.2, 33.6, 30.9]],
+               radii=[2.6, 3.7, 5.2, 7.3, 10.1])
+
+
+def _sphere_case(storage="fp32"):
+    cfg = W.config(nx=48, ny=48, nz=48, storage=storage, walls=0, atmosphere=0, tau=0.8)
+    t, a = W.voxel_spheres((48, 48, 48), SPHERES["centres"], SPHERES["radii"])
+    n = t.size
+    return cfg, t, np.ones(n), np.zeros(3 * n), a, np.zeros(n)
+
+
+def _true_kappa(cells, shape):
+    nx, ny, nz = shape
+    x, y, z = cells % nx, (cells // nx) % ny, cells // (nx * ny)
+    best, kap = np.full(cells.size, np.inf), np.zeros(cells.size)
+    for c, r in zip(SPHERES["centres"], SPHERES["radii"]):
+        d = np.abs(np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2) - r)
+        m = d < best
+        best[m], kap[m] = d[m], 1.0 / r
+    return kap
+
+
+@pytest.mark.parametrize("storage,ktol", [("fp64", 1e-9), ("fp32", 1e-3)])
+def test_in_loop_kappa_matches_oracle_and_beats_least_squares(env, oracle_mod, trained, storage, ktol):
+    """The learned kappa inside the simulation (after the least-squares
+    geometry pass) against the oracle's stencils through the BF16-operand
+    network, with the least-squares fallback; ktol is the tolerance of the
+    least-squares kappa of this storage form against the FP64 oracle."""
+    L, torch = env
+    th, _ = trained
+    cfg, t, rho, u, a, c = _sphere_case(storage)
+    ora = oracle_mod.OracleSim(cfg)
+    ora.set_cells(t, rho, u, a, c)
+    ot, oa, ok = ora.types(), ora.get("alpha"), ora.get("kappa")
+    sim = L.Sim(cfg)
+    sim.set_cells(t, rho, u, a, c)
+    f0 = sim.fields(["kappa", "flags"])
+    assert np.array_equal(f0["flags"] & 3, ot)
+    sim.mlp_attach(th.astype(np.float32))
+    sim.set_cells(t, rho, u, a, c)
+    f1 = sim.fields(["kappa", "flags"])
+    ifc = np.nonzero(ot == 2)[0]
+    # oracle side: stencil of every interface cell, canonical orientation(s),
+    # the BF16-operand network, fallback to the least-squares kappa
+    nx, ny, nz = 48, 48, 48
+    xs, ys, zs = ifc % nx, (ifc // nx) % ny, ifc // (nx * ny)
+    st = np.zeros((ifc.size, 27))
+    for q in range(27):
+        dx, dy, dz = mlp.OFFS[q]
+        m = (xs + dx) % nx + nx * ((ys + dy) % ny + ny * ((zs + dz) % nz))
+        st[:, q] = np.where(ot[m] == 1, 1.0, np.where(ot[m] == 2, np.clip(oa[m], 0, 1), 0.0))
+    mism = 0
+    used = np.zeros(ifc.size, bool)
+    for i in range(ifc.size):
+        n = mlp.py_normal(st[i])
+        kl = ok[ifc[i]]
+        inwin = 0.02 <= abs(kl) <= 0.55 and np.any(n != 0)
+        edge = min(abs(abs(kl) - 0.02), abs(abs(kl) - 0.55)) < 1e-3
+        cands = []
+        if inwin or edge:
+            srcs = _orientations(n, 1e-4 * np.linalg.norm(n))
+            cands += list(mlp.forward_bf16(th, np.array([st[i][s] for s in srcs])) / mlp.Y_SCALE)
+        g = f1["kappa"][ifc[i]]
+        ok_net = any(abs(g - cc) <= 5e-4 + 1e-3 * abs(cc) for cc in cands)
+        ok_fb = (not inwin or edge) and abs(g - kl) <= ktol * max(1.0, abs(kl))
+        if not (ok_net or ok_fb):
+            mism += 1
+        if not inwin and not edge:
+            assert g == f0["kappa"][ifc[i]]  # the fallback leaves the value untouched
+        used[i] = inwin
+    assert mism == 0
+    # gain: error against the analytic curvature 1/R of the nearest sphere
+    kt = _true_kappa(ifc, (nx, ny, nz))
+    e_lsq = np.sqrt(np.mean(((f0["kappa"][ifc] - kt) / kt)[used] ** 2))
+    e_mlp = np.sqrt(np.mean(((f1["kappa"][ifc] - kt) / kt)[used] ** 2))
+    print("interface cells %d (network on %d): relative RMS kappa error LSQ %.4f, MLP %.4f"
+          % (ifc.size, used.sum(), e_lsq, e_mlp))
+    assert e_mlp < 0.7 * e_lsq
+
+
+def test_harvest_matches_oracle(env, oracle_mod):
+    """Training pairs harvested from a run (FP64 storage, right after
+    nucleation) against the oracle's state: the same interface cells, their
+    canonical stencils, and y = 4 / R_eq of the cell's bubble."""
+    L, torch = env
+    from paper_1908_04262_gb300 import curvature
+
+    cfg = curvature.static_bubble_config(5.3, "fp64", n=30)
+    sim, ora = L.Sim(cfg), oracle_mod.OracleSim(cfg)
+    for s in (sim, ora):
+        s.nucleate([[15.2, 14.7, 15.4]], [5.3])
+    cap = 4000
+    x = torch.zeros((cap, 27), device="cuda")
+    y = torch.zeros(cap, device="cuda")
+    cells = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+    k = sim.mlp_harvest(x, y, cells)
+    x, y, cells = x[:k].cpu().numpy(), y[:k].cpu().numpy(), cells[:k].cpu().numpy()
+    ot, oa, ol = ora.types(), ora.get("alpha"), ora.labels()
+    ob = ora.bubbles()
+    n = cfg["nx"]
+
+    def stencil(c):
+        cx, cy, cz = c % n, (c // n) % n, c // (n * n)
+        st = np.zeros(27)
+        for q in range(27):
+            dx, dy, dz = mlp.OFFS[q]
+            m = (cx + dx) % n + n * ((cy + dy) % n + n * ((cz + dz) % n))
+            st[q] = 1.0 if ot[m] == 1 else (np.clip(oa[m], 0, 1) if ot[m] == 2 else 0.0)
+        return st
+
+    expect = [c for c in np.nonzero(ot == 2)[0]
+              if ol[c] >= 0 and not ob["atm"][ol[c]] and np.any(mlp.py_normal(stencil(c)) != 0)]
+    assert sorted(cells.tolist()) == sorted(int(c) for c in expect)
+    for i in range(k):
+        st = stencil(cells[i])
+        cands = [st[s] for s in _orientations(mlp.py_normal(st), 1e-9 * np.linalg.norm(mlp.py_normal(st)))]
+        assert any(np.max(np.abs(x[i] - cc)) <= 1e-6 for cc in cands), i
+        V = ob["volume"][ol[cells[i]]]
+        assert abs(y[i] - 4.0 / np.cbrt(3 * V / (4 * np.pi))) <= 1e-6 * abs(y[i])
+
+
+def _laplace(L, theta, storage, R, steps=2000, sigma=0.01, n=48):
+    """Static bubble: relative error of the measured jump p_b - p_l against
+    2 sigma / R_eq (mean over the last four samples), relative volume
+    change, largest |u|."""
+    from paper_1908_04262_gb300 import curvature
+
+    cfg = curvature.static_bubble_config(R, storage, sigma=sigma, n=n)
+    sim = L.Sim(cfg)
+    c = [n / 2 + 0.31, n / 2 - 0.17, n / 2 + 0.23]
+    sim.nucleate([c], [R])
+    if theta is not None:
+        sim.mlp_attach(theta)
+    V0 = sim.bubbles()["volume"][0]
+    idx = np.arange(n ** 3)
+    d = np.sqrt((idx % n - c[0]) ** 2 + ((idx // n) % n - c[1]) ** 2 + (idx // (n * n) - c[2]) ** 2)
+    rel, umax = [], 0.0
+    for _ in range(steps // 250):
+        sim.step(250)
+        b = sim.bubbles()
+        f = sim.fields(["rho", "flags", "u"])
+        pl = f["rho"][((f["flags"] & 3) == 1) & (d > R + 4)].mean() / 3
+        Req = np.cbrt(3 * b["volume"][0] / (4 * np.pi))
+        rel.append((b["pressure"][0] - pl) / (2 * sigma / Req) - 1)
+        umax = max(umax, float(np.abs(f["u"]).max()))
+    return float(np.mean(rel[-4:])), float(b["volume"][0] / V0 - 1), umax
+
+
+def test_learned_kappa_static_bubble_laplace(env):
+    """The training recipe (synthetic + harvested + dataset aggregation),
+    then static bubbles driven by the network against the least-squares
+    curvature: Laplace jump error, volume change and spurious currents of
+    both are printed; the network must keep the jump within 5 % and the
+    currents below 1e-2 (without dataset aggregation they reach 2e-2 - 6e-2
+    and the jump is off by up to 300 %)."""
+    L, torch = env
+    from paper_1908_04262_gb300 import curvature
+
+    th, info = curvature.train(seed=1, rounds=3)
+    print("recipe:", info)
+    for storage in ("fp32", "fp16s"):
+        for R in (4.0, 6.0):
+            e0, v0, u0 = _laplace(L, None, storage, R)
+            e1, v1, u1 = _laplace(L, th, storage, R)
+            print("%s R=%g: Laplace rel. error LSQ %+.4f MLP %+.4f; volume change LSQ %+.4f MLP %+.4f; "
+                  "max|u| LSQ %.1e MLP %.1e" % (storage, R, e0, e1, v0, v1, u0, u1))
+            assert abs(e1) < 0.05 and u1 < 1e-2 and abs(v1) < 0.02
+            assert abs(e0) < 0.05
