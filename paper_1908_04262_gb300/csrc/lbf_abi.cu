@@ -73,12 +73,14 @@ struct lbf_sim {
   double *led = nullptr;
   unsigned long long *fluid_updates = nullptr;
   int *err = nullptr;
+  int *gas_dirty = nullptr;
   double *acc = nullptr;
   unsigned long long *counts = nullptr;
   void *staging = nullptr;
   float *tau_tab = nullptr;
-  float *mlp_theta = nullptr;  // learned curvature parameters, when attached
+  void *mlp_theta = nullptr;   // packed network image when attached, else NULL
   float *mlp_buf = nullptr;    // owned copy of the parameters
+  void *mlp_img = nullptr;     // owned packed image
   int *mlp_count = nullptr;    // harvest counter
   int tab_n = 0;
   float tab_lnA0 = 0.f, tab_inv_dlnA = 0.f;
@@ -141,6 +143,7 @@ Params make_params(lbf_sim *s, long long step) {
   p.gpar = s->gpar; p.gnold = s->gnold; p.gnnew = s->gnnew; p.gatm = s->gatm; p.gminid = s->gminid;
   p.gheir = s->gheir; p.gmold = s->gmold; p.gvnew = s->gvnew; p.gvmax = s->gvmax;
   p.next_id = s->next_id; p.led = s->led; p.fluid_updates = s->fluid_updates; p.err = s->err;
+  p.gas_dirty = s->gas_dirty;
   p.tau_tab = s->tau_tab; p.tab_n = s->tab_n; p.tab_lnA0 = s->tab_lnA0; p.tab_inv_dlnA = s->tab_inv_dlnA;
   p.tau = c.tau; p.rho0 = c.rho0; p.ax = c.accel[0]; p.ay = c.accel[1]; p.az = c.accel[2];
   p.has_force = (c.accel[0] != 0.0 || c.accel[1] != 0.0 || c.accel[2] != 0.0);
@@ -155,6 +158,10 @@ Params make_params(lbf_sim *s, long long step) {
   const int n_up = up == 1 ? c.ny : c.nz;
   p.top_layer = n_up - 1 - ((c.walls >> (2 * up + 1)) & 1);
   p.ray_steps = (int)std::ceil(c.d_max) + 1;
+  p.pf = {(float)p.tau, (float)p.rho0, (float)p.ax, (float)p.ay, (float)p.az, (float)p.rn, (float)p.rk,
+          (float)p.rlam, (float)p.ra, (float)p.tau0, (float)p.tau_inf, (float)p.tau_min, (float)p.tau_max,
+          (float)p.sigma, (float)p.k_pi, (float)p.d_max, (float)p.taug, (float)p.kH, (float)p.RT, (float)p.c0,
+          (float)p.q, (float)p.p0, (float)p.eps, (float)p.uwx, (float)p.uwy, (float)p.uwz};
   return p;
 }
 
@@ -166,6 +173,8 @@ int relabel_in_place(lbf_sim *s) {
   s->ops->build_ilist(p, s->st);
   CK(cudaMemsetAsync(p.inext_count, 0, sizeof(int), s->st));
   s->ops->label_prep(p, s->st);
+  // the state was set from outside: label from scratch
+  CK(cudaMemsetAsync(s->gas_dirty, 1, sizeof(int), s->st));
   s->ops->label(p, s->st);
   s->ops->bubble_update(p, s->st);
   const size_t cap = (size_t)s->cap;
@@ -480,6 +489,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   AL(dalloc(s, &s->led, 8));
   AL(dalloc(s, &s->fluid_updates, 1));
   AL(dalloc(s, &s->err, 1));
+  AL(dalloc(s, &s->gas_dirty, 1));
   AL(dalloc(s, &s->acc, 4));
   AL(dalloc(s, &s->counts, 4));
 #undef AL
@@ -507,6 +517,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   e = e ? e : zero(s->led, 8 * sizeof(double));
   e = e ? e : zero(s->fluid_updates, sizeof(unsigned long long));
   e = e ? e : zero(s->err, sizeof(int));
+  e = e ? e : zero(s->gas_dirty, sizeof(int));
   if (e != cudaSuccess) {
     lbf_destroy(s);
     return fail(LBF_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
@@ -620,9 +631,15 @@ int lbf_mlp_attach(lbf_sim *s, const float *theta) {
       int rc = dalloc(s, &s->mlp_buf, 6017);
       if (rc) return rc;
     }
+    if (!s->mlp_img) {
+      int rc = dev_alloc(s, &s->mlp_img, lbf::mlp::image_bytes());
+      if (rc) return rc;
+    }
     CK(cudaMemcpyAsync(s->mlp_buf, theta, sizeof(float) * 6017, cudaMemcpyHostToDevice, s->st));
+    lbf::mlp::pack_launch(s->mlp_buf, s->mlp_img, s->st);
+    CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->st));
-    s->mlp_theta = s->mlp_buf;
+    s->mlp_theta = s->mlp_img;
   } else {
     s->mlp_theta = nullptr;  // the buffer stays owned by the sim until destroy
   }

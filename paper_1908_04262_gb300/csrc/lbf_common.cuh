@@ -80,6 +80,14 @@ __device__ __forceinline__ void st(double *p, size_t k, double v, double) { p[k]
 __device__ __forceinline__ void st(float *p, size_t k, float v, float) { p[k] = v; }
 __device__ __forceinline__ void st(__half *p, size_t k, float v, float sh) { p[k] = __float2half_rn(v - sh); }
 __device__ __forceinline__ void st(__nv_bfloat16 *p, size_t k, float v, float sh) { p[k] = __float2bfloat16_rn(v - sh); }
+__device__ __forceinline__ double ld(const double *p, int k, double) { return p[k]; }
+__device__ __forceinline__ float ld(const float *p, int k, float) { return p[k]; }
+__device__ __forceinline__ float ld(const __half *p, int k, float sh) { return __half2float(p[k]) + sh; }
+__device__ __forceinline__ float ld(const __nv_bfloat16 *p, int k, float sh) { return __bfloat162float(p[k]) + sh; }
+__device__ __forceinline__ void st(double *p, int k, double v, double) { p[k] = v; }
+__device__ __forceinline__ void st(float *p, int k, float v, float) { p[k] = v; }
+__device__ __forceinline__ void st(__half *p, int k, float v, float sh) { p[k] = __float2half_rn(v - sh); }
+__device__ __forceinline__ void st(__nv_bfloat16 *p, int k, float v, float sh) { p[k] = __float2bfloat16_rn(v - sh); }
 
 // ---------------------------------------------------------------------------
 // bubble table (one of two, swapped every step)
@@ -121,12 +129,22 @@ struct Params {
   double *led;                   // 8 ledger accumulators
   unsigned long long *fluid_updates;
   int *err;
+  // non-zero when the conversion of this step added or removed gas cells
+  // (or the state was set from outside): the union-find passes run only
+  // then, otherwise the forest of the last labelling is still exact.  NULL
+  // means always.
+  int *gas_dirty;
   // tabulated relaxation time tau(A) of the non-Newtonian models for the
   // single-precision forms: tau_tab[k] at ln A = tab_lnA0 + k * tab_dlnA
   const float *tau_tab;
   int tab_n;
   float tab_lnA0, tab_inv_dlnA;
-  // physics
+  // physics, in double and as float copies (the single-precision kernels
+  // must not touch the FP64 pipe)
+  struct PF {
+    float tau, rho0, ax, ay, az, rn, rk, rlam, ra, tau0, tau_inf, tau_min, tau_max;
+    float sigma, k_pi, d_max, taug, kH, RT, c0, q, p0, eps, uwx, uwy, uwz;
+  } pf;
   double tau, rho0, ax, ay, az;
   int has_force, rheo;
   double rn, rk, rlam, ra, tau0, tau_inf, tau_min, tau_max;
@@ -135,30 +153,42 @@ struct Params {
   int walls, atmosphere, top_layer, ray_steps;
 };
 
+// a physics parameter in the arithmetic type R
+template <class R> __device__ __forceinline__ R pv(double d, float f) {
+  if constexpr (sizeof(R) == 4)
+    return f;
+  else
+    return d;
+}
+#define PV(R, name) pv<R>(p.name, p.pf.name)
+
 // ---------------------------------------------------------------------------
 // indexing.  Full-lattice kernels run on a (ceil(nx/B), ny, nz) grid of
 // B-thread blocks along x, so a thread finds its cell without division; the
 // six periodic neighbour offsets are kept as index deltas.
 
+// Lattices hold fewer than 2^31 cells (checked at creation), so cell
+// indices and offsets are 32-bit; only plane offsets (direction x N) are
+// 64-bit.
 struct Cell {
   int x, y, z;
-  long long n;
-  int dxm, dxp;          // -1 / +1 along x, wrapped
-  long long dym, dyp;    // -nx / +nx along y, wrapped
-  long long dzm, dzp;    // -nx*ny / +nx*ny along z, wrapped
+  int n;
+  int dxm, dxp;  // -1 / +1 along x, wrapped
+  int dym, dyp;  // -nx / +nx along y, wrapped
+  int dzm, dzp;  // -nx*ny / +nx*ny along z, wrapped
 };
 
 __device__ __forceinline__ Cell cell_at(const Params &p, int x, int y, int z) {
   Cell c;
   c.x = x; c.y = y; c.z = z;
-  const long long nx = p.nx, nxy = (long long)p.nx * p.ny;
-  c.n = x + nx * (y + (long long)p.ny * z);
+  const int nx = p.nx, nxy = p.nx * p.ny;
+  c.n = x + nx * y + nxy * z;
   c.dxm = x == 0 ? p.nx - 1 : -1;
   c.dxp = x == p.nx - 1 ? 1 - p.nx : 1;
-  c.dym = y == 0 ? (long long)(p.ny - 1) * nx : -nx;
-  c.dyp = y == p.ny - 1 ? -(long long)(p.ny - 1) * nx : nx;
-  c.dzm = z == 0 ? (long long)(p.nz - 1) * nxy : -nxy;
-  c.dzp = z == p.nz - 1 ? -(long long)(p.nz - 1) * nxy : nxy;
+  c.dym = y == 0 ? (p.ny - 1) * nx : -nx;
+  c.dyp = y == p.ny - 1 ? -(p.ny - 1) * nx : nx;
+  c.dzm = z == 0 ? (p.nz - 1) * nxy : -nxy;
+  c.dzp = z == p.nz - 1 ? -(p.nz - 1) * nxy : nxy;
   return c;
 }
 
@@ -181,7 +211,7 @@ __device__ __forceinline__ Cell make_cell(const Params &p, long long n) {
 }
 
 // cell at offset (dx,dy,dz) in {-1,0,1}^3
-__device__ __forceinline__ long long at(const Params &, const Cell &c, int dx, int dy, int dz) {
+__device__ __forceinline__ int at(const Params &, const Cell &c, int dx, int dy, int dz) {
   return c.n + (dx < 0 ? c.dxm : (dx > 0 ? c.dxp : 0)) + (dy < 0 ? c.dym : (dy > 0 ? c.dyp : 0)) +
          (dz < 0 ? c.dzm : (dz > 0 ? c.dzp : 0));
 }
@@ -194,10 +224,10 @@ __device__ __forceinline__ long long at_far(const Params &p, int x, int y, int z
   return x + (long long)p.nx * (y + (long long)p.ny * z);
 }
 
-template <int D> __device__ __forceinline__ long long nb(const Params &p, const Cell &c, int i) {
+template <int D> __device__ __forceinline__ int nb(const Params &p, const Cell &c, int i) {
   return at(p, c, Lat<D>::cx(i), Lat<D>::cy(i), Lat<D>::cz(i));
 }
-template <int D> __device__ __forceinline__ long long src(const Params &p, const Cell &c, int i) {
+template <int D> __device__ __forceinline__ int src(const Params &p, const Cell &c, int i) {
   return at(p, c, -Lat<D>::cx(i), -Lat<D>::cy(i), -Lat<D>::cz(i));
 }
 
@@ -208,6 +238,20 @@ template <int D> __device__ __forceinline__ size_t slot_out(const Params &p, con
 }
 template <int D> __device__ __forceinline__ size_t slot_in(const Params &p, const Cell &c, long long n, int i, int par) {
   return par == 0 ? (size_t)i * p.N + n : (size_t)opp(i) * p.N + src<D>(p, c, i);
+}
+
+// the same slots as (plane, cell): the plane pointer is uniform across the
+// warp, so an access costs one 32-bit index and one wide multiply-add
+template <class T> __device__ __forceinline__ T *plane(T *f, const Params &p, int dir) {
+  return f + (size_t)dir * (size_t)p.N;
+}
+template <int D> __device__ __forceinline__ int dir_out(int i, int par) { return par == 0 ? i : opp(i); }
+template <int D> __device__ __forceinline__ int cell_out(const Params &p, const Cell &c, int i, int par) {
+  return par == 0 ? nb<D>(p, c, i) : c.n;
+}
+template <int D> __device__ __forceinline__ int dir_in(int i, int par) { return par == 0 ? i : opp(i); }
+template <int D> __device__ __forceinline__ int cell_in(const Params &p, const Cell &c, int i, int par) {
+  return par == 0 ? c.n : src<D>(p, c, i);
 }
 
 template <class R, int D> __device__ __forceinline__ R feq(int i, R rho, R ux, R uy, R uz) {
@@ -222,10 +266,12 @@ template <class R, int D> __device__ __forceinline__ R geq(int i, R c, R ux, R u
 }
 
 template <class S, int D> __device__ __forceinline__ typename ST<S>::R fshift(const Params &p, int i) {
-  return (typename ST<S>::R)(Lat<D>::w(i) * p.rho0);
+  using R = typename ST<S>::R;
+  return (R)Lat<D>::w(i) * PV(R, rho0);
 }
 template <class S, int D> __device__ __forceinline__ typename ST<S>::R gshift(const Params &p, int i) {
-  return (typename ST<S>::R)(Lat<D>::wa(i) * p.c0);
+  using R = typename ST<S>::R;
+  return (R)Lat<D>::wa(i) * PV(R, c0);
 }
 
 // lists of cells: grid-stride loop over n entries
@@ -244,6 +290,8 @@ __device__ __forceinline__ void list_append(int *list, int *count, bool take, in
 }
 
 // post-conversion type from a flag byte carrying marks
+__device__ __forceinline__ bool gas_unchanged(const Params &p) { return p.gas_dirty && *p.gas_dirty == 0; }
+
 __device__ __forceinline__ int post_type(uint8_t f) {
   const int m = fmark(f);
   if (m == MK_FILL) return T_LIQ;

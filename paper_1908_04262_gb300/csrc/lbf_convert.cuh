@@ -35,9 +35,9 @@ __device__ __forceinline__ typename ST<S>::R sum_out_f(const Params &p, const Ce
     jz += v * (R)Lat<D>::cz(i);
   }
   if (u) {
-    u[0] = (jx - (R)0.5 * rho * (R)p.ax) / rho;
-    u[1] = (jy - (R)0.5 * rho * (R)p.ay) / rho;
-    u[2] = (jz - (R)0.5 * rho * (R)p.az) / rho;
+    u[0] = (jx - (R)0.5 * rho * PV(R, ax)) / rho;
+    u[1] = (jy - (R)0.5 * rho * PV(R, ay)) / rho;
+    u[2] = (jz - (R)0.5 * rho * PV(R, az)) / rho;
   }
   return rho;
 }
@@ -111,14 +111,17 @@ __global__ void k_conv_mark(Params p) {
       } else {
         const int want = mk == MK_FILL ? T_GAS : T_LIQ;
         const int put = mk == MK_FILL ? MK_GI : MK_LI;
+        bool gas_change = mk == MK_EMPTY;  // this cell turns gas
 #pragma unroll
         for (int i = 1; i < Lat<D>::Q; ++i) {
           const long long m = nb<D>(p, c, i);
           if (ftype(p.flags[m]) == want && mark_byte(p.flags, m, put)) {
             const int pos = atomicAdd(p.ncount, 1);
             p.nlist[pos] = (int)m;
+            gas_change |= put == MK_GI;  // a gas cell turns interface
           }
         }
+        if (gas_change && p.gas_dirty) *p.gas_dirty = 1;
       }
     }
   }
@@ -291,8 +294,8 @@ __global__ void k_init_fill(Params p, int par, double fill_height) {
   M[n] = 0;
   if (t != T_GAS) {
     const R u[3] = {0, 0, 0};
-    write_equilibrium<D, S>(p, c, n, par, (R)p.rho0, u, (R)p.c0);
-    if (t == T_IFC) M[n] = (R)a * (R)p.rho0;
+    write_equilibrium<D, S>(p, c, n, par, PV(R, rho0), u, PV(R, c0));
+    if (t == T_IFC) M[n] = (R)a * PV(R, rho0);
   }
 }
 

@@ -320,7 +320,7 @@ __global__ void k_disjoining(Params p) {
   const int b = p.label_new[n];
   const R *nr = (const R *)p.nrm, *ds = (const R *)p.dst;
   const R dir[3] = {nr[n], nr[p.N + n], nr[2 * p.N + n]};
-  if (p.k_pi == 0.0 || b < 0 || (dir[0] == (R)0 && dir[1] == (R)0 && dir[2] == (R)0)) {
+  if (p.pf.k_pi == 0.f || b < 0 || (dir[0] == (R)0 && dir[1] == (R)0 && dir[2] == (R)0)) {
     Pi[n] = 0;
     continue;
   }
@@ -359,7 +359,7 @@ __global__ void k_disjoining(Params p) {
       break;
     }
   }
-  Pi[n] = (dist >= (R)0 && dist < (R)p.d_max) ? (R)p.k_pi * ((R)p.d_max - dist) : (R)0;
+  Pi[n] = (dist >= (R)0 && dist < PV(R, d_max)) ? PV(R, k_pi) * (PV(R, d_max) - dist) : (R)0;
   }
 }
 

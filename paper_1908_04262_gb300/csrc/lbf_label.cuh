@@ -143,6 +143,7 @@ template <int D> struct TileGrid {
 template <int D>
 __global__ void __launch_bounds__(TILE_THREADS) k_uf_local(Params p) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ;
+  if (gas_unchanged(p)) return;
   __shared__ int lp[TN];
   __shared__ int lsz[TN];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
@@ -241,6 +242,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_local(Params p) {
 template <int D>
 __global__ void __launch_bounds__(TILE_THREADS) k_uf_merge(Params p) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ;
+  if (gas_unchanged(p)) return;
   const TileGrid<D> tgd(p);
   const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   const int own = p.tstat[tile];
@@ -297,6 +299,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_merge(Params p) {
 template <int D>
 __global__ void __launch_bounds__(TILE_THREADS) k_uf_compress(Params p) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ;
+  if (gas_unchanged(p)) return;
   const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   const int own = p.tstat[tile];
   if (own == 0) return;
@@ -346,6 +349,10 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_compress(Params p) {
 // one block: sort the roots (bitonic, in shared memory) and publish the count
 static __global__ void k_sort_roots(Params p) {
   extern __shared__ int sr[];
+  if (gas_unchanged(p)) {  // the sorted roots of the last labelling stand
+    if (threadIdx.x == 0) *p.tnew.count = *p.told.count;
+    return;
+  }
   const int total = *p.nroots;
   const int cnt = total < p.cap ? total : p.cap;
   int P = 1;
@@ -565,6 +572,7 @@ static __global__ void __launch_bounds__(1024) k_bubble_update(Params p) {
   if (tid == 0) {
     *p.hcount = 0;
     *p.nroots = 0;
+    if (p.gas_dirty) *p.gas_dirty = 0;
   }
   // the old table is the next step's new table: clear its accumulators
   for (int k = tid; k < p.cap; k += nt) {

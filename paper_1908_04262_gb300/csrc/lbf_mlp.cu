@@ -30,9 +30,9 @@ constexpr int WARPS = 4;  // warps per block of the network kernels
 
 // inference: canonical stencils (n x 27 fp32) -> y = 4 kappa
 __global__ void __launch_bounds__(32 * WARPS) k_forward(const float *theta, const float *x, int n, float *y) {
-  __shared__ Smem s;
+  __shared__ NetF s;
   __shared__ __nv_bfloat16 xs[WARPS][16 * 32];
-  load_net(s, theta);
+  load_netf(s, theta);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2;
   const int tiles = (n + 15) / 16;
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_grad(const float *theta, const f
     }
     __syncwarp();
     Fwd F;
-    forward16(s, S.x, F);
+    forward16(s.f, S.x, F);
     const int r0 = tile * 16 + g, r1 = r0 + 8;
     auto tg = [&](int row) {
       return tgt[(bt.a * (unsigned long long)(bt.start + row) + bt.b) % (unsigned long long)bt.ntot];
@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_grad(const float *theta, const f
         const float h20 = __bfloat162float(__float2bfloat16_rn(silu(F.z2[j][c])));
         const float h21 = __bfloat162float(__float2bfloat16_rn(silu(F.z2[j][2 + c])));
         float gw3 = d30 * h20 + d31 * h21;
-        const float dd0 = d30 * s.w3[col] * dsilu(F.z2[j][c]);
-        const float dd1 = d31 * s.w3[col] * dsilu(F.z2[j][2 + c]);
+        const float dd0 = d30 * s.f.w3[col] * dsilu(F.z2[j][c]);
+        const float dd1 = d31 * s.f.w3[col] * dsilu(F.z2[j][2 + c]);
         float gb2 = dd0 + dd1;
         S.d2[g * 64 + col] = __float2bfloat16_rn(dd0);
         S.d2[(g + 8) * 64 + col] = __float2bfloat16_rn(dd1);
@@ -408,8 +408,16 @@ int grad_launch(const float *theta, const float *x, const float *t, int n, const
 
 }  // namespace
 
+namespace {
+__global__ void k_pack_net(const float *theta, NetF *img) { load_netf(*img, theta); }
+}  // namespace
+
 namespace lbf {
 namespace mlp {
+size_t image_bytes() { return sizeof(NetF); }
+void pack_launch(const float *theta, void *img, cudaStream_t st) {
+  k_pack_net<<<1, 256, 0, st>>>(theta, (NetF *)img);
+}
 // in-loop use by the simulation (declared in lbf_ops_api.h)
 void forward_launch(const float *theta, const float *x, int n, float *y, cudaStream_t st) {
   const int tiles = (n + 15) / 16;

@@ -23,14 +23,20 @@ constexpr float Y_SCALE = 4.f;
 constexpr int W1_LD = 40;  // 32 inputs (27 used) + pad, bf16
 constexpr int W2_LD = 72;  // 64 + pad, bf16
 
+// the network as the forward pass reads it (a 16-byte multiple, so a packed
+// image in global memory copies into shared memory with vector loads)
+struct __align__(16) NetF {
+  __nv_bfloat16 w1[64 * W1_LD];  // w1[n][k] = W1[n][k]
+  __nv_bfloat16 w2[64 * W2_LD];  // w2[n][k] = W2[n][k]
+  float b1[64], b2[64], w3[64], b3, pad[3];
+};
+// training adds the transpose of W2 for the backward pass
 struct Smem {
-  __nv_bfloat16 w1[64 * W1_LD];   // w1[n][k] = W1[n][k]
-  __nv_bfloat16 w2[64 * W2_LD];   // w2[n][k] = W2[n][k]
+  NetF f;
   __nv_bfloat16 w2t[64 * W2_LD];  // w2t[k][n] = W2[n][k]
-  float b1[64], b2[64], w3[64], b3;
 };
 
-__device__ __forceinline__ void load_net(Smem &s, const float *theta) {
+__device__ __forceinline__ void load_netf(NetF &s, const float *theta) {
   for (int i = threadIdx.x; i < 64 * W1_LD; i += blockDim.x) {
     const int n = i / W1_LD, k = i % W1_LD;
     s.w1[i] = __float2bfloat16_rn(k < 27 ? theta[OFF_W1 + n * 27 + k] : 0.f);
@@ -38,14 +44,31 @@ __device__ __forceinline__ void load_net(Smem &s, const float *theta) {
   for (int i = threadIdx.x; i < 64 * W2_LD; i += blockDim.x) {
     const int r = i / W2_LD, k = i % W2_LD;
     s.w2[i] = __float2bfloat16_rn(k < 64 ? theta[OFF_W2 + r * 64 + k] : 0.f);
-    s.w2t[i] = __float2bfloat16_rn(k < 64 ? theta[OFF_W2 + k * 64 + r] : 0.f);
   }
   for (int i = threadIdx.x; i < 64; i += blockDim.x) {
     s.b1[i] = theta[OFF_B1 + i];
     s.b2[i] = theta[OFF_B2 + i];
     s.w3[i] = theta[OFF_W3 + i];
   }
-  if (threadIdx.x == 0) s.b3 = theta[OFF_B3];
+  if (threadIdx.x == 0) {
+    s.b3 = theta[OFF_B3];
+    s.pad[0] = s.pad[1] = s.pad[2] = 0.f;
+  }
+}
+
+__device__ __forceinline__ void load_net(Smem &s, const float *theta) {
+  load_netf(s.f, theta);
+  for (int i = threadIdx.x; i < 64 * W2_LD; i += blockDim.x) {
+    const int r = i / W2_LD, k = i % W2_LD;
+    s.w2t[i] = __float2bfloat16_rn(k < 64 ? theta[OFF_W2 + k * 64 + r] : 0.f);
+  }
+}
+
+// copy a packed image (global, 16-byte aligned) into shared memory
+__device__ __forceinline__ void copy_netf(NetF &s, const NetF *img) {
+  const uint4 *src = reinterpret_cast<const uint4 *>(img);
+  uint4 *dst = reinterpret_cast<uint4 *>(&s);
+  for (int i = threadIdx.x; i < (int)(sizeof(NetF) / 16); i += blockDim.x) dst[i] = src[i];
 }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
@@ -79,7 +102,7 @@ struct Fwd {
   float y0, y1;
 };
 
-__device__ __forceinline__ void forward16(const Smem &s, const __nv_bfloat16 *xs, Fwd &F) {
+__device__ __forceinline__ void forward16(const NetF &s, const __nv_bfloat16 *xs, Fwd &F) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   // layer 1: 16x32 * 32x64
   uint32_t a[2][4];

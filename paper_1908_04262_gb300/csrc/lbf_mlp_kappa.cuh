@@ -9,62 +9,65 @@ namespace lbf {
 
 // In-loop learned curvature (3D): one warp per 16 interface cells of the
 // list; every cell's stencil is gathered, turned into the canonical
-// orientation of its geometry normal and fed to the network.  The
-// least-squares curvature stays where the network is outside its training
-// range (|kappa| outside [0.02, 0.55], i.e. radii beyond [1.8, 50] cells) or
-// the stencil touches a wall.
+// orientation of its geometry normal and fed to the network (img: the
+// packed BF16 image of the parameters).  The least-squares curvature stays
+// where the network is outside its training range (|kappa| outside
+// [0.02, 0.55], i.e. radii beyond [1.8, 50] cells) or the stencil touches a
+// wall.
+constexpr int MLP_WARPS = 8;
 template <int D, class R>
-__global__ void __launch_bounds__(128) k_mlp_kappa(Params p, const float *theta) {
+__global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp_kappa(Params p, const mlp::NetF *img) {
   if constexpr (D == 3) {
-    __shared__ mlp::Smem s;
-    __shared__ __nv_bfloat16 xs[4][16 * 32];
-    __shared__ long long cn[4][16];
-    __shared__ int ord[4][16][3], sgn[4][16][3], use[4][16];
-    mlp::load_net(s, theta);
+    __shared__ mlp::NetF s;
+    __shared__ __nv_bfloat16 xs[MLP_WARPS][16 * 32];
+    __shared__ Cell cs[MLP_WARPS][16];
+    __shared__ int ord[MLP_WARPS][16][3], sgn[MLP_WARPS][16][3], use[MLP_WARPS][16];
+    mlp::copy_netf(s, img);
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
     const int cnt = *p.icount;
     const int tiles = (cnt + 15) / 16;
     const R *phi = (const R *)p.phi, *nr = (const R *)p.nrm;
     R *kap = (R *)p.kappa;
-    for (int tile = blockIdx.x * 4 + w; tile < tiles; tile += gridDim.x * 4) {
+    for (int tile = blockIdx.x * MLP_WARPS + w; tile < tiles; tile += gridDim.x * MLP_WARPS) {
       if (lane < 16) {
         const int k = tile * 16 + lane;
-        long long n = -1;
         int ok = 0;
+        Cell c;
+        c.n = -1;
         if (k < cnt) {
-          n = p.ilist[k];
-          const float mx = (float)nr[n], my = (float)nr[p.N + n], mz = (float)nr[2 * p.N + n];
-          const float ka = fabsf((float)kap[n]);
+          c = make_cell(p, p.ilist[k]);
+          const float mx = (float)nr[c.n], my = (float)nr[p.N + c.n], mz = (float)nr[2 * p.N + c.n];
+          const float ka = fabsf((float)kap[c.n]);
           ok = (mx != 0.f || my != 0.f || mz != 0.f) && ka >= 0.02f && ka <= 0.55f;
           mlp::canonical_order(mx, my, mz, ord[w][lane], sgn[w][lane]);
         }
-        cn[w][lane] = n;
+        cs[w][lane] = c;
         use[w][lane] = ok;
       }
       __syncwarp();
-      for (int e = lane; e < 16 * 32; e += 32) {
-        const int r = e >> 5, q = e & 31;
-        const long long n = cn[w][r];
+      // lane q gathers stencil position q of the 16 cells
+#pragma unroll 4
+      for (int r = 0; r < 16; ++r) {
         float a = 0.f;
-        if (n >= 0 && q < 27) {
-          const int src = mlp::canonical_src(q, ord[w][r], sgn[w][r]);
-          const Cell c = make_cell(p, n);
-          const long long m = at(p, c, src % 3 - 1, (src / 3) % 3 - 1, src / 9 - 1);
+        const Cell &c = cs[w][r];
+        if (c.n >= 0 && lane < 27 && use[w][r]) {
+          const int src = mlp::canonical_src(lane, ord[w][r], sgn[w][r]);
+          const int m = at(p, c, src % 3 - 1, (src / 3) % 3 - 1, src / 9 - 1);
           const int tm = ftype(p.flags[m]);
           if (tm == T_LIQ) a = 1.f;
           else if (tm == T_IFC) a = fminf(fmaxf((float)phi[m], 0.f), 1.f);
           else if (tm == T_WALL) use[w][r] = 0;
         }
-        xs[w][e] = __float2bfloat16_rn(a);
+        xs[w][r * 32 + lane] = __float2bfloat16_rn(a);
       }
       __syncwarp();
       mlp::Fwd F;
       mlp::forward16(s, xs[w], F);
       if (t == 0) {
-        const long long n0 = cn[w][g], n1 = cn[w][g + 8];
-        if (n0 >= 0 && use[w][g]) kap[n0] = (R)(F.y0 / mlp::Y_SCALE);
-        if (n1 >= 0 && use[w][g + 8]) kap[n1] = (R)(F.y1 / mlp::Y_SCALE);
+        const int n0 = cs[w][g].n, n1 = cs[w][g + 8].n;
+        if (n0 >= 0 && use[w][g]) kap[n0] = (R)fminf(fmaxf(F.y0 / mlp::Y_SCALE, -1.f), 1.f);
+        if (n1 >= 0 && use[w][g + 8]) kap[n1] = (R)fminf(fmaxf(F.y1 / mlp::Y_SCALE, -1.f), 1.f);
       }
       __syncwarp();
     }

@@ -88,8 +88,9 @@ struct OpsImpl final : Ops {
   void geometry(const Params &p, cudaStream_t s) override {
     k_geometry<D, R><<<p.warp_blocks, 128, 0, s>>>(p);
   }
-  void mlp_kappa(const Params &p, const float *theta, cudaStream_t s) override {
-    if (D == 3) k_mlp_kappa<D, R><<<p.list_blocks, 128, 0, s>>>(p, theta);
+  void mlp_kappa(const Params &p, const void *img, cudaStream_t s) override {
+    // one block of MLP_WARPS warps per SM (list_blocks holds 4 per SM)
+    if (D == 3) k_mlp_kappa<D, R><<<p.list_blocks / 4, 32 * MLP_WARPS, 0, s>>>(p, (const mlp::NetF *)img);
   }
   void mlp_harvest(const Params &p, float *x, float *y, int *cells, int cap, int *count, cudaStream_t s) override {
     if (D == 3) k_mlp_harvest<D, R><<<p.warp_blocks, 128, 0, s>>>(p, x, y, cells, cap, count);

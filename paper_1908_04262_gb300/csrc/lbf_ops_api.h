@@ -26,7 +26,7 @@ struct Ops {
   virtual void bubble_update(const Params &p, cudaStream_t s) = 0;
   virtual void geometry(const Params &p, cudaStream_t s) = 0;
   virtual void disjoining(const Params &p, cudaStream_t s) = 0;
-  virtual void mlp_kappa(const Params &p, const float *theta, cudaStream_t s) = 0;
+  virtual void mlp_kappa(const Params &p, const void *img, cudaStream_t s) = 0;
   virtual void mlp_harvest(const Params &p, float *x, float *y, int *cells, int cap, int *count, cudaStream_t s) = 0;
   // export
   virtual void field(const Params &p, int par, int which, void *out, int dtype, cudaStream_t s) = 0;
@@ -35,6 +35,13 @@ struct Ops {
 
 // message returned by lbf_last_error() on the calling thread
 void set_last_error(const char *msg);
+
+namespace mlp {
+// bytes of the packed BF16 image of the network parameters, and the launch
+// that builds it from the 6017 FP32 parameters (both device pointers)
+size_t image_bytes();
+void pack_launch(const float *theta, void *img, cudaStream_t st);
+}  // namespace mlp
 
 // defined in one translation unit per storage type
 Ops *make_ops_f64(int dim);

@@ -36,15 +36,15 @@ template <> struct Prec<float> { static constexpr float tol = 2e-6f; static cons
 // tau of the rheology model at shear rate gd, and d tau / d gd
 template <class R> __device__ __forceinline__ R tau_model(const Params &p, R gd, R &dtau) {
   if (p.rheo == 1) {
-    const R t = (R)3 * (R)p.rk * pow(gd, (R)p.rn - (R)1);
-    dtau = t * ((R)p.rn - (R)1) / gd;
+    const R t = (R)3 * PV(R, rk) * pow(gd, PV(R, rn) - (R)1);
+    dtau = t * (PV(R, rn) - (R)1) / gd;
     return (R)0.5 + t;
   }
-  const R lg = pow((R)p.rlam * gd, (R)p.ra);
+  const R lg = pow(PV(R, rlam) * gd, PV(R, ra));
   const R base = (R)1 + lg;
-  const R fac = pow(base, ((R)p.rn - (R)1) / (R)p.ra);
-  dtau = (R)(p.tau0 - p.tau_inf) * fac * ((R)p.rn - (R)1) / base * lg / gd;
-  return (R)p.tau_inf + (R)(p.tau0 - p.tau_inf) * fac;
+  const R fac = pow(base, (PV(R, rn) - (R)1) / PV(R, ra));
+  dtau = (R)(p.tau0 - p.tau_inf) * fac * (PV(R, rn) - (R)1) / base * lg / gd;
+  return PV(R, tau_inf) + (R)(p.tau0 - p.tau_inf) * fac;
 }
 
 // Sec. 2.3: tau solves tau = tau_model(A / tau) (shear rate A / tau from the
@@ -55,9 +55,9 @@ template <class R> __device__ __forceinline__ R tau_model(const Params &p, R gd,
 // factor 2^(1/n); Newton inside it (monotone from the left for n < 1, from
 // the right for n > 1).  Carreau-Yasuda: safeguarded Newton on tau.
 template <class R> __device__ __forceinline__ R solve_tau(const Params &p, R A) {
-  const R lo = (R)p.tau_min, hi = (R)p.tau_max;
+  const R lo = PV(R, tau_min), hi = PV(R, tau_max);
   if (p.rheo == 1) {
-    const R n = (R)p.rn, k3 = (R)3 * (R)p.rk;
+    const R n = PV(R, rn), k3 = (R)3 * PV(R, rk);
     if (!(A > (R)0)) return n < (R)1 ? hi : lo;
     if (n == (R)1) {
       const R t = (R)0.5 + k3;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(128) k_exchange(Params p) {
     R fo = 0, dm = 0, ex = 0, ey = 0, ez = 0;
     if (lane < Q) {
       const int i = lane;  // the lane's lattice direction
-      fo = ld(f, slot_out<D>(p, c, n, i, PAR), fshift<S, D>(p, i));
+      fo = ld(plane(f, p, dir_out<D>(i, PAR)), cell_out<D>(p, c, i, PAR), fshift<S, D>(p, i));
       ex = (R)Lat<D>::cx(i);
       ey = (R)Lat<D>::cy(i);
       ez = (R)Lat<D>::cz(i);
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(128) k_exchange(Params p) {
         const int tn = ftype(p.flags[m]);
         if (tn == T_LIQ || tn == T_IFC) {
           // arriving along opp(i) from m: the slot holding m's outgoing f_opp(i)
-          const R fin = ld(f, slot_in<D>(p, c, n, opp(i), PAR), fshift<S, D>(p, opp(i)));
+          const R fin = ld(plane(f, p, dir_in<D>(opp(i), PAR)), cell_in<D>(p, c, opp(i), PAR), fshift<S, D>(p, opp(i)));
           dm = tn == T_LIQ ? fin - fo : (R)0.5 * (phi[n] + phi[m]) * (fin - fo);
         }
       }
@@ -139,9 +139,9 @@ __global__ void __launch_bounds__(128) k_exchange(Params p) {
             jz = warp_sum_r<R>(fo * ez), dM = warp_sum_r<R>(dm);
     if (lane == 0) {
       R *uI = (R *)p.uI;
-      uI[n] = (jx - (R)0.5 * rho * (R)p.ax) / rho;
-      uI[p.N + n] = (jy - (R)0.5 * rho * (R)p.ay) / rho;
-      uI[2 * p.N + n] = (jz - (R)0.5 * rho * (R)p.az) / rho;
+      uI[n] = (jx - (R)0.5 * rho * PV(R, ax)) / rho;
+      uI[p.N + n] = (jy - (R)0.5 * rho * PV(R, ay)) / rho;
+      uI[2 * p.N + n] = (jz - (R)0.5 * rho * PV(R, az)) / rho;
       M[n] = M[n] + dM;
     }
   }
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(128) k_exchange(Params p) {
 
 template <class R> struct SweepOcc;
 template <> struct SweepOcc<double> { static constexpr int blocks = 3; };
-template <> struct SweepOcc<float> { static constexpr int blocks = 6; };
+template <> struct SweepOcc<float> { static constexpr int blocks = 8; };
 
 // tau(A) of the single-precision forms: linear interpolation in ln A of a
 // table built on the host by bisection (constant beyond its ends)
@@ -174,7 +174,7 @@ template <class R> __device__ __forceinline__ R model_tau(const Params &p, R A) 
 // to sum e e (f - f_eq) for the second-order equilibrium).
 template <int D, class R>
 __device__ __forceinline__ R local_tau(const Params &p, const R *fi, R rho, R ux, R uy, R uz) {
-  if (p.rheo == 0) return (R)p.tau;
+  if (p.rheo == 0) return PV(R, tau);
   R mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
 #pragma unroll
   for (int i = 1; i < Lat<D>::Q; ++i) {
@@ -207,24 +207,26 @@ __device__ __forceinline__ void relax_store(const Params &p, const Cell &c, long
   const R om = (R)1 / tau;
   const R base = (R)1 - (ux * ux + uy * uy + uz * uz) * (R)1.5;
   if (p.has_force) {
-    const R ff = (R)1 - (R)0.5 * om;
+    // Guo forcing: F_i = w_i rho [3 (e_i - u).a + 9 (e_i.u)(e_i.a)]
+    const R ax = PV(R, ax), ay = PV(R, ay), az = PV(R, az);
+    const R ua = ux * ax + uy * ay + uz * az;
+    const R fr = ((R)1 - (R)0.5 * om) * rho;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const R ex = (R)Lat<D>::cx(i), ey = (R)Lat<D>::cy(i), ez = (R)Lat<D>::cz(i);
       const R eu = ex * ux + ey * uy + ez * uz;
+      const R ea = ex * ax + ey * ay + ez * az;
       const R fe = (R)Lat<D>::w(i) * rho * (base + eu * ((R)3 + eu * (R)4.5));
-      const R F = ((ex - ux) * (R)3 + eu * ex * (R)9) * rho * (R)p.ax +
-                  ((ey - uy) * (R)3 + eu * ey * (R)9) * rho * (R)p.ay +
-                  ((ez - uz) * (R)3 + eu * ez * (R)9) * rho * (R)p.az;
-      st(f, slot_out<D>(p, c, n, i, 1 - PAR), fi[i] - (fi[i] - fe) * om + ff * (R)Lat<D>::w(i) * F,
-         fshift<S, D>(p, i));
+      const R F = (R)3 * (ea - ua) + (R)9 * eu * ea;
+      st(plane(f, p, dir_out<D>(i, 1 - PAR)), cell_out<D>(p, c, i, 1 - PAR),
+         fi[i] - (fi[i] - fe) * om + (R)Lat<D>::w(i) * fr * F, fshift<S, D>(p, i));
     }
   } else {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const R eu = (R)Lat<D>::cx(i) * ux + (R)Lat<D>::cy(i) * uy + (R)Lat<D>::cz(i) * uz;
       const R fe = (R)Lat<D>::w(i) * rho * (base + eu * ((R)3 + eu * (R)4.5));
-      st(f, slot_out<D>(p, c, n, i, 1 - PAR), fi[i] - (fi[i] - fe) * om, fshift<S, D>(p, i));
+      st(plane(f, p, dir_out<D>(i, 1 - PAR)), cell_out<D>(p, c, i, 1 - PAR), fi[i] - (fi[i] - fe) * om, fshift<S, D>(p, i));
     }
   }
 }
@@ -247,15 +249,15 @@ __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const bool w = (wallm >> i) & 1u;
-    fi[i] = ld(f, w ? slot_out<D>(p, c, n, opp(i), PAR) : slot_in<D>(p, c, n, i, PAR),
-               w ? fshift<S, D>(p, opp(i)) : fshift<S, D>(p, i));
+    fi[i] = w ? ld(plane(f, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), fshift<S, D>(p, opp(i)))
+              : ld(plane(f, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), fshift<S, D>(p, i));
   }
   R gi[QA];
 #pragma unroll
   for (int i = 0; i < QA; ++i) {
     const bool w = (wallm >> i) & 1u;
-    gi[i] = ld(g, w ? slot_out<D>(p, c, n, opp(i), PAR) : slot_in<D>(p, c, n, i, PAR),
-               w ? gshift<S, D>(p, opp(i)) : gshift<S, D>(p, i));
+    gi[i] = w ? ld(plane(g, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), gshift<S, D>(p, opp(i)))
+              : ld(plane(g, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), gshift<S, D>(p, i));
   }
   if (wallm && (p.walls & 8)) {
     // moving walls of the +y face
@@ -263,8 +265,8 @@ __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long
     for (int i = 1; i < Q; ++i) {
       const bool top = Lat<D>::cy(i) > 0 ? c.y == 0 : (Lat<D>::cy(i) < 0 ? c.y == p.ny - 2 : c.y == p.ny - 1);
       if (((wallm >> i) & 1u) && top) {
-        const R eu = (R)Lat<D>::cx(i) * (R)p.uwx + (R)Lat<D>::cy(i) * (R)p.uwy + (R)Lat<D>::cz(i) * (R)p.uwz;
-        fi[i] += (R)2 * (R)Lat<D>::w(i) * (R)p.rho0 * eu * (R)3;
+        const R eu = (R)Lat<D>::cx(i) * PV(R, uwx) + (R)Lat<D>::cy(i) * PV(R, uwy) + (R)Lat<D>::cz(i) * PV(R, uwz);
+        fi[i] += (R)2 * (R)Lat<D>::w(i) * PV(R, rho0) * eu * (R)3;
       }
     }
   }
@@ -276,18 +278,18 @@ __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long
     if (Lat<D>::cy(i)) jy += Lat<D>::cy(i) > 0 ? fi[i] : -fi[i];
     if (Lat<D>::cz(i)) jz += Lat<D>::cz(i) > 0 ? fi[i] : -fi[i];
   }
-  const R ux = (jx + (R)0.5 * rho * (R)p.ax) / rho;
-  const R uy = (jy + (R)0.5 * rho * (R)p.ay) / rho;
-  const R uz = (jz + (R)0.5 * rho * (R)p.az) / rho;
+  const R ux = (jx + (R)0.5 * rho * PV(R, ax)) / rho;
+  const R uy = (jy + (R)0.5 * rho * PV(R, ay)) / rho;
+  const R uz = (jz + (R)0.5 * rho * PV(R, az)) / rho;
   relax_store<D, S, PAR>(p, c, n, f, fi, rho, ux, uy, uz, local_tau<D, R>(p, fi, rho, ux, uy, uz));
   R cg = 0;
 #pragma unroll
   for (int i = 0; i < QA; ++i) cg += gi[i];
-  const R omg = (R)1 / (R)p.taug;
+  const R omg = (R)1 / PV(R, taug);
 #pragma unroll
   for (int i = 0; i < QA; ++i) {
-    const R v = gi[i] + (geq<R, D>(i, cg, ux, uy, uz) - gi[i]) * omg + (R)Lat<D>::wa(i) * (R)p.q;
-    st(g, slot_out<D>(p, c, n, i, 1 - PAR), v, gshift<S, D>(p, i));
+    const R v = gi[i] + (geq<R, D>(i, cg, ux, uy, uz) - gi[i]) * omg + (R)Lat<D>::wa(i) * PV(R, q);
+    st(plane(g, p, dir_out<D>(i, 1 - PAR)), cell_out<D>(p, c, i, 1 - PAR), v, gshift<S, D>(p, i));
   }
 }
 
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
   if (__all_sync(0xffffffffu, !isI)) {
     // warp without interface cells: the liquid path, nothing to aggregate
     if (active) liquid_cell<D, S, PAR>(p, c, n, fl);
-    if (p.q != 0.0) {
+    if (p.pf.q != 0.f) {
       const unsigned b = __ballot_sync(0xffffffffu, active);
       if ((threadIdx.x & 31) == 0 && b) atomicAdd(p.fluid_updates, (unsigned long long)__popc(b));
     }
@@ -336,7 +338,7 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
     R fi[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      if (i == 0 || !((gasm | wallm) >> i & 1u)) fi[i] = ld(f, slot_in<D>(p, c, n, i, PAR), fshift<S, D>(p, i));
+      if (i == 0 || !((gasm | wallm) >> i & 1u)) fi[i] = ld(plane(f, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), fshift<S, D>(p, i));
     }
     if (gasm | wallm) {
       R uIx = 0, uIy = 0, uIz = 0, kap = 0, pi = 0;
@@ -353,19 +355,19 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
         if (wallm >> i & 1u) {
           // half-way bounce-back: the cell's own outgoing population towards
           // the wall, reflected (the slot belongs to the wall cell)
-          R v = ld(f, slot_out<D>(p, c, n, opp(i), PAR), fshift<S, D>(p, opp(i)));
+          R v = ld(plane(f, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), fshift<S, D>(p, opp(i)));
           const bool top = Lat<D>::cy(i) > 0 ? c.y == 0 : (Lat<D>::cy(i) < 0 ? c.y == p.ny - 2 : c.y == p.ny - 1);
           if ((p.walls & 8) && top) {
-            const R eu = (R)Lat<D>::cx(i) * (R)p.uwx + (R)Lat<D>::cy(i) * (R)p.uwy + (R)Lat<D>::cz(i) * (R)p.uwz;
-            v += (R)2 * (R)Lat<D>::w(i) * (R)p.rho0 * eu * (R)3;
+            const R eu = (R)Lat<D>::cx(i) * PV(R, uwx) + (R)Lat<D>::cy(i) * PV(R, uwy) + (R)Lat<D>::cz(i) * PV(R, uwz);
+            v += (R)2 * (R)Lat<D>::w(i) * PV(R, rho0) * eu * (R)3;
           }
           fi[i] = v;
         } else if (gasm >> i & 1u) {
           // Sec. 2.2 Eq. reconstruct with rho_g of Eq. rhob / rhobplusdisjoining
           const int b = p.label_old[src<D>(p, c, i)];
-          const R pg = b >= 0 ? (R)p.told.p[b] : (R)p.p0;
-          const R rg = (pg - (R)2 * (R)p.sigma * kap - pi) * (R)3;
-          const R fo = ld(f, slot_out<D>(p, c, n, opp(i), PAR), fshift<S, D>(p, opp(i)));
+          const R pg = b >= 0 ? (R)p.told.p[b] : PV(R, p0);
+          const R rg = (pg - (R)2 * PV(R, sigma) * kap - pi) * (R)3;
+          const R fo = ld(plane(f, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), fshift<S, D>(p, opp(i)));
           fi[i] = feq<R, D>(i, rg, uIx, uIy, uIz) + feq<R, D>(opp(i), rg, uIx, uIy, uIz) - fo;
         }
       }
@@ -379,9 +381,9 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
       jy += fi[i] * (R)Lat<D>::cy(i);
       jz += fi[i] * (R)Lat<D>::cz(i);
     }
-    const R ux = (jx + (R)0.5 * rho * (R)p.ax) / rho;
-    const R uy = (jy + (R)0.5 * rho * (R)p.ay) / rho;
-    const R uz = (jz + (R)0.5 * rho * (R)p.az) / rho;
+    const R ux = (jx + (R)0.5 * rho * PV(R, ax)) / rho;
+    const R uy = (jy + (R)0.5 * rho * PV(R, ay)) / rho;
+    const R uz = (jz + (R)0.5 * rho * PV(R, az)) / rho;
     relax_store<D, S, PAR>(p, c, n, f, fi, rho, ux, uy, uz, local_tau<D, R>(p, fi, rho, ux, uy, uz));
 
     R phin = 0, pho = 0;
@@ -392,9 +394,9 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
       phin = Mn / rho;
       phi[n] = phin;
       int mk = MK_NONE;
-      if (Mn > ((R)1 + (R)p.eps) * rho)
+      if (Mn > ((R)1 + PV(R, eps)) * rho)
         mk = MK_FILL;
-      else if (Mn < -(R)p.eps * rho)
+      else if (Mn < -PV(R, eps) * rho)
         mk = MK_EMPTY;
       if (mk) p.flags[n] = (uint8_t)(fl | (mk << 2));
     }
@@ -405,23 +407,23 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
 #pragma unroll
     for (int i = 0; i < QA; ++i) {
       if (i > 0 && (wallm >> i & 1u)) {
-        gi[i] = ld(g, slot_out<D>(p, c, n, opp(i), PAR), gshift<S, D>(p, opp(i)));
+        gi[i] = ld(plane(g, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), gshift<S, D>(p, opp(i)));
       } else if (i > 0 && (gasm >> i & 1u)) {
         const int b = p.label_old[src<D>(p, c, i)];
-        const R cH = (R)p.kH * (b >= 0 ? (R)p.told.p[b] : (R)p.p0);
-        const R go = ld(g, slot_out<D>(p, c, n, opp(i), PAR), gshift<S, D>(p, opp(i)));
+        const R cH = PV(R, kH) * (b >= 0 ? (R)p.told.p[b] : PV(R, p0));
+        const R go = ld(plane(g, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), gshift<S, D>(p, opp(i)));
         gi[i] = (R)2 * (R)Lat<D>::wa(i) * cH - go;
         fl_gas += go - gi[i];
       } else {
-        gi[i] = ld(g, slot_in<D>(p, c, n, i, PAR), gshift<S, D>(p, i));
+        gi[i] = ld(plane(g, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), gshift<S, D>(p, i));
       }
       cgas += gi[i];
     }
-    const R omg = (R)1 / (R)p.taug;
+    const R omg = (R)1 / PV(R, taug);
 #pragma unroll
     for (int i = 0; i < QA; ++i) {
-      const R v = gi[i] + (geq<R, D>(i, cgas, ux, uy, uz) - gi[i]) * omg + (R)Lat<D>::wa(i) * (R)p.q;
-      st(g, slot_out<D>(p, c, n, i, 1 - PAR), v, gshift<S, D>(p, i));
+      const R v = gi[i] + (geq<R, D>(i, cgas, ux, uy, uz) - gi[i]) * omg + (R)Lat<D>::wa(i) * PV(R, q);
+      st(plane(g, p, dir_out<D>(i, 1 - PAR)), cell_out<D>(p, c, i, 1 - PAR), v, gshift<S, D>(p, i));
     }
     if (isI) {
       flux = (double)(fl_gas - cgas * (phin - pho));
@@ -429,7 +431,7 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
       if (lab < 0) atomicAdd(p.led + 5, flux);
     }
   }
-  if (p.q != 0.0) {
+  if (p.pf.q != 0.f) {
     const unsigned b = __ballot_sync(0xffffffffu, active);
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(p.fluid_updates, (unsigned long long)__popc(b));
   }
