@@ -74,6 +74,7 @@ struct lbf_sim {
   unsigned long long *fluid_updates = nullptr;
   int *err = nullptr;
   int *gas_dirty = nullptr;
+  int *rlabel = nullptr;
   double *acc = nullptr;
   unsigned long long *counts = nullptr;
   void *staging = nullptr;
@@ -144,6 +145,7 @@ Params make_params(lbf_sim *s, long long step) {
   p.gheir = s->gheir; p.gmold = s->gmold; p.gvnew = s->gvnew; p.gvmax = s->gvmax;
   p.next_id = s->next_id; p.led = s->led; p.fluid_updates = s->fluid_updates; p.err = s->err;
   p.gas_dirty = s->gas_dirty;
+  p.rlabel = s->rlabel;
   p.tau_tab = s->tau_tab; p.tab_n = s->tab_n; p.tab_lnA0 = s->tab_lnA0; p.tab_inv_dlnA = s->tab_inv_dlnA;
   p.tau = c.tau; p.rho0 = c.rho0; p.ax = c.accel[0]; p.ay = c.accel[1]; p.az = c.accel[2];
   p.has_force = (c.accel[0] != 0.0 || c.accel[1] != 0.0 || c.accel[2] != 0.0);
@@ -490,6 +492,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   AL(dalloc(s, &s->fluid_updates, 1));
   AL(dalloc(s, &s->err, 1));
   AL(dalloc(s, &s->gas_dirty, 1));
+  AL(dalloc(s, &s->rlabel, N));
   AL(dalloc(s, &s->acc, 4));
   AL(dalloc(s, &s->counts, 4));
 #undef AL

@@ -134,6 +134,9 @@ struct Params {
   // then, otherwise the forest of the last labelling is still exact.  NULL
   // means always.
   int *gas_dirty;
+  // label of each current root cell (rank among the sorted roots, -1 past
+  // the bubble capacity); read only at cells that are roots
+  int *rlabel;
   // tabulated relaxation time tau(A) of the non-Newtonian models for the
   // single-precision forms: tau_tab[k] at ln A = tab_lnA0 + k * tab_dlnA
   const float *tau_tab;

@@ -138,36 +138,65 @@ template <int D> struct TileGrid {
   }
 };
 
-// one block per tile: status, local union-find in shared memory, parents
-// and local component sizes
+// the row-to-row links of the tile-local pass: one of each opposite pair of
+// the lattice vectors that leave the x-row (x-links join runs directly);
+// (dx, dy, dz)
+template <int D> struct RowLinks;
+template <> struct RowLinks<3> {
+  static constexpr int n = 8;
+  __device__ static constexpr int dx(int k) { return k == 2 ? -1 : k == 3 ? 1 : k == 4 ? -1 : k == 5 ? 1 : 0; }
+  __device__ static constexpr int dy(int k) { return k == 0 ? -1 : k == 2 || k == 3 ? -1 : k == 6 ? -1 : k == 7 ? 1 : 0; }
+  __device__ static constexpr int dz(int k) { return k == 1 || k == 4 || k == 5 || k == 6 || k == 7 ? -1 : 0; }
+};
+template <> struct RowLinks<2> {
+  static constexpr int n = 3;
+  __device__ static constexpr int dx(int k) { return k == 1 ? -1 : k == 2 ? 1 : 0; }
+  __device__ static constexpr int dy(int) { return -1; }
+  __device__ static constexpr int dz(int) { return 0; }
+};
+
+// One block per tile: status, local union-find in shared memory, parents
+// and local component sizes.  A tile is 32 rows of 32 cells along x; a
+// warp's ballot gives each row's gas mask, every gas cell starts out
+// pointing at the first cell of its x-run, and two rows are joined once per
+// overlapping segment of their runs (at the segment's first cell), so the
+// number of unions grows with the number of runs rather than of cells.
+// Roots are the smallest local index of each component, which orders cells
+// like their global index.
 template <int D>
 __global__ void __launch_bounds__(TILE_THREADS) k_uf_local(Params p) {
-  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ;
+  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ, NR = TY * TZ;
+  static_assert(TX == 32 && NR == 32, "a tile is 32 rows of 32 cells");
   if (gas_unchanged(p)) return;
   __shared__ int lp[TN];
   __shared__ int lsz[TN];
+  __shared__ unsigned rowm[NR];
+  __shared__ int sg, sc, nroot, rfirst;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
   const long long nx = p.nx, nxy = (long long)p.nx * p.ny;
-  __shared__ int sg, sc;
   if (threadIdx.x == 0) {
     sg = 0;
     sc = 0;
+    nroot = 0;
+    rfirst = TN;
   }
   __syncthreads();
-  int ngas = 0, ncell = 0;
-  for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
-    const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
-    bool gas = false;
-    if (x < p.nx && y < p.ny && z < p.nz) {
-      ++ncell;
-      gas = post_type(p.flags[x + nx * y + nxy * z]) == T_GAS;
+  // row masks, runs
+  for (int r = warp; r < NR; r += TILE_THREADS / 32) {
+    const int x = x0 + lane, y = y0 + r % TY, z = z0 + r / TY;
+    const bool inside = x < p.nx && y < p.ny && z < p.nz;
+    const bool gas = inside && post_type(p.flags[x + nx * y + nxy * z]) == T_GAS;
+    const unsigned m = __ballot_sync(0xffffffffu, gas), in = __ballot_sync(0xffffffffu, inside);
+    if (lane == 0) {
+      rowm[r] = m;
+      if (m) atomicAdd(&sg, __popc(m));
+      atomicAdd(&sc, __popc(in));
     }
-    ngas += gas;
-    lp[t] = gas ? t : -1;
-    lsz[t] = 0;
+    const unsigned starts = m & ~(m << 1);
+    lp[r * TX + lane] = gas ? r * TX + (31 - __clz(starts & (0xffffffffu >> (31 - lane)))) : -1;
+    lsz[r * TX + lane] = 0;
   }
-  atomicAdd(&sg, ngas);
-  atomicAdd(&sc, ncell);
   __syncthreads();
   const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   const long long root0 = x0 + nx * y0 + nxy * z0;
@@ -190,35 +219,44 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_local(Params p) {
     }
     return;
   }
+  // rows joined at the first cell of each overlapping segment
   bool ok = true;
-  for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
-    if (lp[t] < 0) continue;
-    const int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
+  for (int r = warp; r < NR; r += TILE_THREADS / 32) {
+    const unsigned a = rowm[r];
+    if (!a) continue;
+    const int ly = r % TY, lz = r / TY;
 #pragma unroll
-    for (int i = 1; i < Lat<D>::Q; i += 2) {  // one vector of each opposite pair
-      const int ax = lx + Lat<D>::cx(i), ay = ly + Lat<D>::cy(i), az = lz + Lat<D>::cz(i);
-      if (ax < 0 || ax >= TX || ay < 0 || ay >= TY || az < 0 || az >= TZ) continue;
-      const int u = ax + TX * (ay + TY * az);
-      if (lp[u] >= 0) ok &= sm_union(lp, t, u);
+    for (int k = 0; k < RowLinks<D>::n; ++k) {
+      const int dx = RowLinks<D>::dx(k), ry = ly + RowLinks<D>::dy(k), rz = lz + RowLinks<D>::dz(k);
+      if (ry < 0 || ry >= TY || rz < 0 || rz >= TZ) continue;  // across the tile face: the merge pass
+      const int rr = ry + TY * rz;
+      const unsigned b = rowm[rr];
+      const unsigned bs = dx > 0 ? (b >> 1) : (dx < 0 ? (b << 1) : b);  // bit x: gas at x + dx in row rr
+      const unsigned ov = a & bs;
+      const unsigned seg = ov & ~(ov << 1);
+      if ((seg >> lane) & 1u) ok &= sm_union(lp, r * TX + lane, rr * TX + lane + dx);
     }
   }
   if (!ok) atomicOr(p.err, ERR_NOTCONV);
   __syncthreads();
-  __shared__ int nroot, rfirst;
-  if (threadIdx.x == 0) {
-    nroot = 0;
-    rfirst = TN;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < TN; t += TILE_THREADS)
-    if (lp[t] >= 0) {
-      const int r = sm_find(lp, t);
-      atomicAdd(&lsz[r], 1);
-      if (r == t) {
-        atomicAdd(&nroot, 1);
-        atomicMin(&rfirst, t);
-      }
+  // flatten, count roots, sizes per run
+  for (int r = warp; r < NR; r += TILE_THREADS / 32) {
+    const unsigned m = rowm[r];
+    const int t = r * TX + lane;
+    int root = -1;
+    if ((m >> lane) & 1u) root = sm_find(lp, t);
+    __syncwarp();
+    if (root >= 0) lp[t] = root;
+    const unsigned starts = m & ~(m << 1);
+    if ((starts >> lane) & 1u) {
+      const int len = __ffs(~(m >> lane)) - 1;
+      atomicAdd(&lsz[root], len > 0 ? len : 32 - lane);
     }
+    if (root == t) {
+      atomicAdd(&nroot, 1);
+      atomicMin(&rfirst, t);
+    }
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     p.tstat[tile] = nroot == 1 ? 1 : 2;
@@ -228,7 +266,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_local(Params p) {
   for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
     const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
     if (lp[t] < 0 || x >= p.nx || y >= p.ny || z >= p.nz) continue;
-    const int r = sm_find(lp, t);
+    const int r = lp[t];
     const int rx = x0 + r % TX, ry = y0 + (r / TX) % TY, rz = z0 + r / (TX * TY);
     const long long n = x + nx * y + nxy * z;
     p.parent[n] = (int)(rx + nx * ry + nxy * rz);
@@ -260,7 +298,13 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_merge(Params p) {
   // one gas link suffices between two single-component tiles: the first
   // thread that meets one claims the neighbour offset
   __shared__ int claimed[27];
-  if (threadIdx.x < 27) claimed[threadIdx.x] = 0;
+  // per neighbouring tile, the last pair of representatives joined: links
+  // between the same two local components need one union only
+  __shared__ unsigned long long lastpair[27];
+  if (threadIdx.x < 27) {
+    claimed[threadIdx.x] = 0;
+    lastpair[threadIdx.x] = ~0ull;
+  }
   __syncthreads();
   for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
     const int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
@@ -288,7 +332,13 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_merge(Params p) {
       const long long m = at_far(p, ax, ay, az);
       if (post_type(p.flags[m]) != T_GAS) continue;
       if (own == 1 && ns == 1 && atomicExch(&claimed[oi], 1)) continue;
-      ok &= uf_union(p.parent, (int)n, (int)m);
+      // representatives: the parents the local pass left (any ancestor
+      // stands for the same component)
+      const int ra = __ldcg(p.parent + n), rb = __ldcg(p.parent + m);
+      const unsigned long long key = ((unsigned long long)(unsigned)ra << 32) | (unsigned)rb;
+      if (lastpair[oi] == key) continue;
+      lastpair[oi] = key;
+      ok &= uf_union(p.parent, ra, rb);
     }
   }
   if (!ok) atomicOr(p.err, ERR_NOTCONV);
@@ -312,10 +362,12 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_compress(Params p) {
       sroot = uf_find(p.parent, r0);
       if (sroot == r0) {
         const int k = atomicAdd(p.nroots, 1);
-        if (k < p.cap)
+        if (k < p.cap) {
           p.roots[k] = r0;
-        else
+        } else {
           atomicOr(p.err, ERR_CAPACITY);
+          if (p.rlabel) p.rlabel[r0] = -1;
+        }
       }
     }
     __syncthreads();
@@ -338,10 +390,12 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_compress(Params p) {
     p.parent[n] = r;
     if (r == (int)n) {
       const int k = atomicAdd(p.nroots, 1);
-      if (k < p.cap)
+      if (k < p.cap) {
         p.roots[k] = r;
-      else
+      } else {
         atomicOr(p.err, ERR_CAPACITY);
+        if (p.rlabel) p.rlabel[r] = -1;
+      }
     }
   }
 }
@@ -374,7 +428,10 @@ static __global__ void k_sort_roots(Params p) {
       }
       __syncthreads();
     }
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) p.roots[k] = sr[k];
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    p.roots[k] = sr[k];
+    if (p.rlabel) p.rlabel[sr[k]] = k;
+  }
   if (threadIdx.x == 0) *p.tnew.count = cnt;
 }
 
@@ -424,7 +481,7 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
   int knew = -1;
   double v = 0.0;
   if (t == T_GAS) {
-    knew = root_index(p.roots, cnt, p.parent[n]);
+    knew = p.rlabel[p.parent[n]];
     v = (double)p.lsize[n];  // non-zero only at tile-local roots
     if (p.atmosphere && knew >= 0 && (D == 2 ? c.y : c.z) == p.top_layer && !p.tnew.atm[knew]) p.tnew.atm[knew] = 1;
   } else if (t == T_IFC) {
@@ -432,7 +489,7 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
     for (int i = 1; i < Lat<D>::Q; ++i) {
       const long long m = nb<D>(p, c, i);
       if (post_type(p.flags[m]) == T_GAS) {
-        const int k = root_index(p.roots, cnt, p.parent[m]);
+        const int k = p.rlabel[p.parent[m]];
         if (k >= 0 && (knew < 0 || k < knew)) knew = k;
       }
     }
