@@ -49,6 +49,8 @@ struct lbf_sim {
   size_t ssz = 0, rsz = 0;
   cudaStream_t st = nullptr;
   bool own_stream = false;
+  cudaStream_t st2 = nullptr;        // second branch of the step graph
+  cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr};
   Ops *ops = nullptr;
   std::vector<void *> allocs;
   // device state
@@ -219,18 +221,37 @@ void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
   group(G_EXCHANGE, [&] { s->ops->exchange(p, par, s->st); });
   group(G_STREAM, [&] { s->ops->stream_collide(p, par, s->st); });
   group(G_CONVERT, [&] { s->ops->convert(p, par, s->st); });
-  group(G_LABEL, [&] { s->ops->label(p, s->st); });
-  group(G_BUBBLE, [&] { s->ops->bubble_update(p, s->st); });
-  // the geometry of the next step works on the interface list the
-  // conversion produced
+  // the geometry of the next step works on the interface list and the final
+  // flags the conversion produced; it needs no labels
   Params pn = p;
   pn.ilist = p.inext;
   pn.icount = p.inext_count;
-  group(G_GEOMETRY, [&] {
-    s->ops->geometry(pn, s->st);
-    if (s->mlp_theta) s->ops->mlp_kappa(pn, s->mlp_theta, s->st);
-  });
-  group(G_DISJOIN, [&] { s->ops->disjoining(pn, s->st); });
+  auto geometry = [&](cudaStream_t st) {
+    s->ops->geometry(pn, st);
+    if (s->mlp_theta) s->ops->mlp_kappa(pn, s->mlp_theta, st);
+  };
+  if (ev) {
+    // timing: every group on the one stream, in order
+    group(G_LABEL, [&] { s->ops->label(p, s->st); });
+    group(G_BUBBLE, [&] { s->ops->bubble_update(p, s->st); });
+    group(G_GEOMETRY, [&] { geometry(s->st); });
+    group(G_DISJOIN, [&] { s->ops->disjoining(pn, s->st); });
+    return;
+  }
+  // geometry beside the labelling, the bubble update beside the disjoining
+  // pressure (which needs both the labels and the geometry)
+  cudaEventRecord(s->fork[0], s->st);
+  cudaStreamWaitEvent(s->st2, s->fork[0], 0);
+  geometry(s->st2);
+  cudaEventRecord(s->join[0], s->st2);
+  s->ops->label(p, s->st);
+  cudaEventRecord(s->fork[1], s->st);
+  cudaStreamWaitEvent(s->st2, s->fork[1], 0);
+  s->ops->bubble_update(p, s->st2);
+  cudaEventRecord(s->join[1], s->st2);
+  cudaStreamWaitEvent(s->st, s->join[0], 0);
+  s->ops->disjoining(pn, s->st);
+  cudaStreamWaitEvent(s->st, s->join[1], 0);
 }
 
 int capture(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev, cudaGraphExec_t *out) {
@@ -377,6 +398,11 @@ void lbf_destroy(lbf_sim *s) {
     for (int k = 0; k < 2; ++k)
       for (int j = 0; j < 2 * G_COUNT; ++j) cudaEventDestroy(s->tev[k][j]);
   for (void *p : s->allocs) cudaFree(p);
+  for (int k = 0; k < 2; ++k) {
+    if (s->fork[k]) cudaEventDestroy(s->fork[k]);
+    if (s->join[k]) cudaEventDestroy(s->join[k]);
+  }
+  if (s->st2) cudaStreamDestroy(s->st2);
   if (s->own_stream && s->st) cudaStreamDestroy(s->st);
   delete s->ops;
   delete s;
@@ -412,6 +438,17 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
       return fail(LBF_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
     }
     s->own_stream = true;
+  }
+  {
+    cudaError_t e = cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&s->fork[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+      lbf_destroy(s);
+      return fail(LBF_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
   }
   const size_t N = (size_t)s->N;
   {

@@ -249,6 +249,29 @@ __global__ void k_conv_apply(Params p, int par) {
   }
 }
 
+// the conversion's new types replace the marks, and the interface cells of
+// the next step are listed (every marked cell is on the interface list or on
+// the new-interface list, and so is every interface cell after the
+// conversion); a separate pass because k_conv_apply reads the marks of
+// neighbouring cells
+template <int D>
+__global__ void k_conv_finalize(Params p) {
+  const int ni = *p.icount, total = ni + *p.ncount;
+  for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+    const int k = base + threadIdx.x;
+    bool take = false;
+    int n = 0;
+    if (k < total) {
+      n = (int)list_cell(p, k, ni);
+      const uint8_t fl = p.flags[n];
+      const int t = post_type(fl);
+      if (fmark(fl)) p.flags[n] = (uint8_t)(t | (fl & NEARWALL));
+      take = t == T_IFC;
+    }
+    list_append(p.inext, p.inext_count, take, n);
+  }
+}
+
 // list every interface cell (initialisation paths)
 static __global__ void k_build_ilist(Params p) {
   Cell c;

@@ -475,9 +475,6 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
   const long long n = c.n;
   const uint8_t fl = inr ? p.flags[n] : (uint8_t)T_WALL;
   const int t = post_type(fl);
-  // the conversion's new types replace the marks
-  if (inr && fmark(fl)) p.flags[n] = (uint8_t)(t | (fl & NEARWALL));
-  const int cnt = *p.tnew.count;
   int knew = -1;
   double v = 0.0;
   if (t == T_GAS) {
@@ -496,7 +493,6 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
     if (knew >= 0) v = 1.0 - (double)((const R *)p.phi)[n];
   }
   if (inr) p.label_new[n] = knew;
-  list_append(p.inext, p.inext_count, inr && t == T_IFC, (int)n);
   const bool contrib = knew >= 0 && v != 0.0;
   if (__any_sync(0xffffffffu, contrib)) agg_add(p.tnew.V, contrib ? knew : -1, v, wbuf + (threadIdx.x & ~31));
   const int kold = inr ? p.label_old[n] : -1;

@@ -69,6 +69,7 @@ struct OpsImpl final : Ops {
     k_conv_mark<D><<<p.list_blocks, 128, 0, s>>>(p);
     k_conv_compute<D, S><<<p.list_blocks, 128, 0, s>>>(p, post);
     k_conv_apply<D, S><<<p.list_blocks, 128, 0, s>>>(p, post);
+    k_conv_finalize<D><<<p.list_blocks, 128, 0, s>>>(p);
   }
   void label_prep(const Params &p, cudaStream_t s) override {
     k_label_prep<<<blocks_for(p.cap, B), B, 0, s>>>(p);
