@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS (D3Q19 FSLBM + D3Q7 ADE) and % HBM roofline; FP16+learned-κ vs FP32 plain"
 WORKLOAD = "3D D3Q19 FSLBM + D3Q7 ADE, 128^3, FP32 storage, 8 bubbles (R 4-6), power-law n=0.6, disjoining on"
-KERNELS_PER_STEP = 13  # exchange 1, sweep 1, conversion 3, labelling 5, bubble update 1, geometry 1, disjoining 1
+KERNELS_PER_STEP = 14  # exchange 1, sweep 1, conversion 4, labelling 5, bubble update 1, geometry 1, disjoining 1
 
 
 def parse():
@@ -105,6 +105,24 @@ def stop_clocks(proc, path):
 
 
 # ---------------------------------------------------------------------------
+
+# DRAM bytes (read + write) per launch of the FP32 sweep on this workload,
+# mean of the two parities, from profiles/k_stream_collide_128cube_fp32.md,
+# valid while the sweep's sources are the ones that were profiled
+SWEEP_TRAFFIC_BYTES = 267.0e6
+SWEEP_SOURCES = ("paper_1908_04262_gb300/csrc/lbf_stream.cuh", "paper_1908_04262_gb300/csrc/lbf_common.cuh")
+SWEEP_SOURCES_SHA256_16 = "a8fceef7b4661706"
+
+
+def sweep_traffic():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return SWEEP_TRAFFIC_BYTES if h.hexdigest()[:16] == SWEEP_SOURCES_SHA256_16 else None
+
 
 def algorithmic_bytes_sweep(counts, storage_bytes, arith_bytes, Q=19, QA=7):
     """Bytes the fused sweep must move in one launch: every liquid or
@@ -230,13 +248,14 @@ def cpu_baseline_oracle(cfg, pts, rad, steps=1):
 
 def reference_sample_cfg():
     """Bounded sample of the workload for the oracle: the same physics on a
-    64^3 lattice with one bubble (same seed)."""
+    48^3 lattice with one bubble (same seed); about 0.15 s per step on one
+    core, so that a default run stays near a minute."""
     from paper_1908_04262_gb300 import workloads as W
 
     cfg, c, r = W.c2_crop_3d_32()
-    n = 64
+    n = 48
     cfg.update(nx=n, ny=n, nz=n, fill_height=0.75 * n)
-    return cfg, [[32.0 + c[0][0] - 16.0, 32.0 + c[0][1] - 16.0, 24.0 + c[0][2] - 12.0]], list(r)
+    return cfg, [[24.0 + c[0][0] - 16.0, 24.0 + c[0][1] - 16.0, 18.0 + c[0][2] - 12.0]], list(r)
 
 
 def run_reference(args):
@@ -254,7 +273,7 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     N = cfg["nx"] * cfg["ny"] * cfg["nz"]
     v = N * args.steps / dt / 1e6
-    sample = "each step: one oracle step of the workload's physics on a 64^3 lattice with one bubble"
+    sample = "each step: one oracle step of the workload's physics on a 48^3 lattice with one bubble"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -322,7 +341,9 @@ def run_ours(args):
     peak, peak_kind = peaks()
     total_ms = sum(v[0] for v in groups.values())
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": sweep_traffic(),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
+                                  "profiles/k_stream_collide_128cube_fp32.md",
                 "kernel": "k_stream_collide<3,float> (fused sweep)",
                 "bytes_per_launch": bytes_sweep, "launch_ms": sweep_ms / sweep_n,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,

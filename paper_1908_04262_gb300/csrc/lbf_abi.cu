@@ -49,8 +49,8 @@ struct lbf_sim {
   size_t ssz = 0, rsz = 0;
   cudaStream_t st = nullptr;
   bool own_stream = false;
-  cudaStream_t st2 = nullptr;        // second branch of the step graph
-  cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr};
+  cudaStream_t st2 = nullptr, st3 = nullptr;  // further branches of the step graphs
+  cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr}, joinx = nullptr;
   Ops *ops = nullptr;
   std::vector<void *> allocs;
   // device state
@@ -90,6 +90,7 @@ struct lbf_sim {
   long long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t tgraph[2] = {nullptr, nullptr};  // with event records
+  cudaGraphExec_t graph2[2] = {nullptr, nullptr};  // two steps from parity k
   cudaEvent_t tev[2][2 * G_COUNT];
   bool tev_made = false;
   std::vector<Nucleus> queue;
@@ -210,8 +211,48 @@ int separate_and_relabel(lbf_sim *s) {
   return relabel_in_place(s);
 }
 
-// the launch sequence of one step; with `ev` every kernel group is
-// bracketed by event records (captured into the timing graph)
+// the geometry of the next step works on the interface list and the final
+// flags the conversion produced; it needs no labels
+Params next_geometry_params(const Params &p) {
+  Params pn = p;
+  pn.ilist = p.inext;
+  pn.icount = p.inext_count;
+  return pn;
+}
+
+void enqueue_geometry(lbf_sim *s, const Params &pn, cudaStream_t st) {
+  s->ops->geometry(pn, st);
+  if (s->mlp_theta) s->ops->mlp_kappa(pn, s->mlp_theta, st);
+}
+
+// after the conversion: the geometry beside the labelling, the bubble update
+// beside the disjoining pressure (which needs both the labels and the
+// geometry); with `pnext`, the next step's mass exchange (which needs only
+// what the conversion left) runs on a third branch beside all of them
+void enqueue_tail(lbf_sim *s, const Params &p, const Params *pnext, int parnext) {
+  const Params pn = next_geometry_params(p);
+  cudaEventRecord(s->fork[0], s->st);
+  cudaStreamWaitEvent(s->st2, s->fork[0], 0);
+  enqueue_geometry(s, pn, s->st2);
+  cudaEventRecord(s->join[0], s->st2);
+  if (pnext) {
+    cudaStreamWaitEvent(s->st3, s->fork[0], 0);
+    s->ops->exchange(*pnext, parnext, s->st3);
+    cudaEventRecord(s->joinx, s->st3);
+  }
+  s->ops->label(p, s->st);
+  cudaEventRecord(s->fork[1], s->st);
+  cudaStreamWaitEvent(s->st2, s->fork[1], 0);
+  s->ops->bubble_update(p, s->st2);
+  cudaEventRecord(s->join[1], s->st2);
+  cudaStreamWaitEvent(s->st, s->join[0], 0);
+  s->ops->disjoining(pn, s->st);
+  cudaStreamWaitEvent(s->st, s->join[1], 0);
+  if (pnext) cudaStreamWaitEvent(s->st, s->joinx, 0);
+}
+
+// the launch sequence of one step; with `ev` every kernel group runs in
+// order on the one stream, bracketed by event records (the timing graph)
 void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
   auto group = [&](int gidx, auto &&fn) {
     if (ev) cudaEventRecordWithFlags(ev[2 * gidx], s->st, cudaEventRecordExternal);
@@ -221,37 +262,38 @@ void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
   group(G_EXCHANGE, [&] { s->ops->exchange(p, par, s->st); });
   group(G_STREAM, [&] { s->ops->stream_collide(p, par, s->st); });
   group(G_CONVERT, [&] { s->ops->convert(p, par, s->st); });
-  // the geometry of the next step works on the interface list and the final
-  // flags the conversion produced; it needs no labels
-  Params pn = p;
-  pn.ilist = p.inext;
-  pn.icount = p.inext_count;
-  auto geometry = [&](cudaStream_t st) {
-    s->ops->geometry(pn, st);
-    if (s->mlp_theta) s->ops->mlp_kappa(pn, s->mlp_theta, st);
-  };
   if (ev) {
-    // timing: every group on the one stream, in order
+    const Params pn = next_geometry_params(p);
     group(G_LABEL, [&] { s->ops->label(p, s->st); });
     group(G_BUBBLE, [&] { s->ops->bubble_update(p, s->st); });
-    group(G_GEOMETRY, [&] { geometry(s->st); });
+    group(G_GEOMETRY, [&] { enqueue_geometry(s, pn, s->st); });
     group(G_DISJOIN, [&] { s->ops->disjoining(pn, s->st); });
     return;
   }
-  // geometry beside the labelling, the bubble update beside the disjoining
-  // pressure (which needs both the labels and the geometry)
-  cudaEventRecord(s->fork[0], s->st);
-  cudaStreamWaitEvent(s->st2, s->fork[0], 0);
-  geometry(s->st2);
-  cudaEventRecord(s->join[0], s->st2);
-  s->ops->label(p, s->st);
-  cudaEventRecord(s->fork[1], s->st);
-  cudaStreamWaitEvent(s->st2, s->fork[1], 0);
-  s->ops->bubble_update(p, s->st2);
-  cudaEventRecord(s->join[1], s->st2);
-  cudaStreamWaitEvent(s->st, s->join[0], 0);
-  s->ops->disjoining(pn, s->st);
-  cudaStreamWaitEvent(s->st, s->join[1], 0);
+  enqueue_tail(s, p, nullptr, 0);
+}
+
+// two consecutive steps in one graph (parities par, 1 - par): the second
+// step's mass exchange overlaps the first step's labelling
+void enqueue_two(lbf_sim *s, const Params &pa, int par, const Params &pb) {
+  s->ops->exchange(pa, par, s->st);
+  s->ops->stream_collide(pa, par, s->st);
+  s->ops->convert(pa, par, s->st);
+  enqueue_tail(s, pa, &pb, 1 - par);
+  s->ops->stream_collide(pb, 1 - par, s->st);
+  s->ops->convert(pb, 1 - par, s->st);
+  enqueue_tail(s, pb, nullptr, 0);
+}
+
+int capture_two(lbf_sim *s, const Params &pa, int par, const Params &pb, cudaGraphExec_t *out) {
+  cudaGraph_t gr;
+  CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+  enqueue_two(s, pa, par, pb);
+  CK(cudaStreamEndCapture(s->st, &gr));
+  cudaError_t e = cudaGraphInstantiate(out, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return fail(LBF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  return 0;
 }
 
 int capture(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev, cudaGraphExec_t *out) {
@@ -294,6 +336,23 @@ int run_one_step(lbf_sim *s) {
   }
   CK(cudaGraphLaunch(s->graph[par], s->st));
   return 0;
+}
+
+int run_two_steps(lbf_sim *s) {
+  const int par = (int)(s->step & 1);
+  if (!s->graph2[par]) {
+    const Params pa = make_params(s, s->step), pb = make_params(s, s->step + 1);
+    int rc = capture_two(s, pa, par, pb, &s->graph2[par]);
+    if (rc) return rc;
+  }
+  CK(cudaGraphLaunch(s->graph2[par], s->st));
+  return 0;
+}
+
+bool nucleus_due(const lbf_sim *s, long long step) {
+  for (const auto &nu : s->queue)
+    if (nu.step <= step) return true;
+  return false;
 }
 
 int carve_due_nuclei(lbf_sim *s) {
@@ -393,6 +452,7 @@ void lbf_destroy(lbf_sim *s) {
   for (int k = 0; k < 2; ++k) {
     if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
     if (s->tgraph[k]) cudaGraphExecDestroy(s->tgraph[k]);
+    if (s->graph2[k]) cudaGraphExecDestroy(s->graph2[k]);
   }
   if (s->tev_made)
     for (int k = 0; k < 2; ++k)
@@ -402,7 +462,9 @@ void lbf_destroy(lbf_sim *s) {
     if (s->fork[k]) cudaEventDestroy(s->fork[k]);
     if (s->join[k]) cudaEventDestroy(s->join[k]);
   }
+  if (s->joinx) cudaEventDestroy(s->joinx);
   if (s->st2) cudaStreamDestroy(s->st2);
+  if (s->st3) cudaStreamDestroy(s->st3);
   if (s->own_stream && s->st) cudaStreamDestroy(s->st);
   delete s->ops;
   delete s;
@@ -441,6 +503,8 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   }
   {
     cudaError_t e = cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st3, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joinx, cudaEventDisableTiming);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
       e = cudaEventCreateWithFlags(&s->fork[k], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join[k], cudaEventDisableTiming);
@@ -633,12 +697,20 @@ int lbf_set_cells(lbf_sim *s, const uint8_t *type, const double *rho, const doub
 
 int lbf_step(lbf_sim *s, int nsteps) {
   if (!s || nsteps < 0) return fail(LBF_EINVAL, "bad arguments");
-  for (int k = 0; k < nsteps; ++k) {
+  for (int k = 0; k < nsteps;) {
     int rc = carve_due_nuclei(s);
     if (rc) return rc;
-    rc = run_one_step(s);
-    if (rc) return rc;
-    ++s->step;
+    if (!s->timing && k + 1 < nsteps && !nucleus_due(s, s->step + 1)) {
+      rc = run_two_steps(s);
+      if (rc) return rc;
+      s->step += 2;
+      k += 2;
+    } else {
+      rc = run_one_step(s);
+      if (rc) return rc;
+      ++s->step;
+      ++k;
+    }
   }
   return check_device_error(s);
 }
@@ -687,7 +759,8 @@ int lbf_mlp_attach(lbf_sim *s, const float *theta) {
   for (int k = 0; k < 2; ++k) {
     if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
     if (s->tgraph[k]) cudaGraphExecDestroy(s->tgraph[k]);
-    s->graph[k] = s->tgraph[k] = nullptr;
+    if (s->graph2[k]) cudaGraphExecDestroy(s->graph2[k]);
+    s->graph[k] = s->tgraph[k] = s->graph2[k] = nullptr;
   }
   return 0;
 }
