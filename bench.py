@@ -371,9 +371,10 @@ def run_ours(args):
     t_e2e = reduce_max(time.perf_counter() - t0, world)
     e2e = {"value": N * args.steps * world / t_e2e / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": h2d / args.steps,
-           "d2h_bytes_per_step": 40 * nb_rows + N * (8 + 8 + 4) / args.steps,
-           "note": "lbf_set_cells from pinned host arrays, then per step lbf_step(1) + lbf_bubbles, "
-                   "then lbf_fields(rho, alpha, flags) to host"}
+           "d2h_bytes_per_step": 16 + 40 * max(64, nb_rows) + N * (8 + 8 + 4) / args.steps,
+           "note": "lbf_set_cells from pinned host arrays, then per step lbf_step(1) + lbf_bubbles "
+                   "(one packed copy of the header and the first 64 rows; %d live rows), then lbf_fields(rho, alpha, flags) to host"
+                   % nb_rows}
     del out
 
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,

@@ -77,6 +77,11 @@ struct lbf_sim {
   int *err = nullptr;
   int *gas_dirty = nullptr;
   int *rlabel = nullptr;
+  unsigned char *bub_dev = nullptr;   // packed bubble rows: count (16 bytes), then lbf_bubble records
+  unsigned char *bub_host = nullptr;  // pinned staging copy
+  int *err_host = nullptr;            // pinned copy of the sticky error bits
+  void *pin[2] = {nullptr, nullptr};  // pinned chunks for host copies of fields
+  cudaEvent_t pin_ev[2] = {nullptr, nullptr};
   double *acc = nullptr;
   unsigned long long *counts = nullptr;
   void *staging = nullptr;
@@ -374,10 +379,43 @@ int carve_due_nuclei(lbf_sim *s) {
   return separate_and_relabel(s);
 }
 
+// device -> caller's (possibly pageable) host memory through two pinned
+// chunks: the copy of one chunk overlaps the host copy of the other
+int copy_to_host(lbf_sim *s, void *dst, const void *src, size_t bytes) {
+  constexpr size_t kChunk = size_t(4) << 20;
+  if (!s->pin[0]) {
+    for (int b = 0; b < 2; ++b) {
+      CK(cudaMallocHost(&s->pin[b], kChunk));
+      CK(cudaEventCreateWithFlags(&s->pin_ev[b], cudaEventDisableTiming));
+    }
+  }
+  const unsigned char *sp = (const unsigned char *)src;
+  unsigned char *dp = (unsigned char *)dst;
+  size_t prev_off = 0, prev_len = 0;
+  int b = 0;
+  for (size_t off = 0; off < bytes; off += kChunk, b ^= 1) {
+    const size_t len = std::min(kChunk, bytes - off);
+    CK(cudaMemcpyAsync(s->pin[b], sp + off, len, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaEventRecord(s->pin_ev[b], s->st));
+    if (prev_len) {
+      CK(cudaEventSynchronize(s->pin_ev[b ^ 1]));
+      std::memcpy(dp + prev_off, s->pin[b ^ 1], prev_len);
+    }
+    prev_off = off;
+    prev_len = len;
+  }
+  if (prev_len) {
+    CK(cudaEventSynchronize(s->pin_ev[b ^ 1]));
+    std::memcpy(dp + prev_off, s->pin[b ^ 1], prev_len);
+  }
+  return 0;
+}
+
 int check_device_error(lbf_sim *s) {
-  int e = 0;
-  CK(cudaMemcpyAsync(&e, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  if (!s->err_host) CK(cudaMallocHost((void **)&s->err_host, sizeof(int)));
+  CK(cudaMemcpyAsync(s->err_host, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->st));
   CK(cudaStreamSynchronize(s->st));
+  const int e = *s->err_host;
   if (e & ERR_CAPACITY) return fail(LBF_ECAPACITY, "more bubbles than bubble_capacity");
   if (e & ERR_NOTCONV) return fail(LBF_ENOTCONV, "union-find iteration cap reached");
   if (e & ERR_HASH) return fail(LBF_ECAPACITY, "bubble overlap table full");
@@ -440,6 +478,28 @@ int validate(const lbf_config *c) {
 
 namespace lbf {
 void set_last_error(const char *msg) { g_err = msg; }
+
+// the bubble table as lbf_bubble rows after a 16-byte header holding the
+// row count
+__global__ void k_pack_bubbles(Table t, unsigned char *out, int rows) {
+  const int nb = *t.count;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *reinterpret_cast<int *>(out) = nb;
+  lbf_bubble *r = reinterpret_cast<lbf_bubble *>(out + 16);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows && i < nb; i += gridDim.x * blockDim.x) {
+    lbf_bubble b;
+    b.id = t.id[i];
+    b.atm = t.atm[i];
+    b.label = t.root[i];
+    b.volume = t.V[i];
+    b.gas_mass = t.m[i];
+    b.pressure = t.p[i];
+    r[i] = b;
+  }
+}
+void pack_bubbles_launch(const Table &t, unsigned char *out, int rows, cudaStream_t st) {
+  const int blocks = rows > 0 ? (rows + 255) / 256 : 1;
+  k_pack_bubbles<<<blocks, 256, 0, st>>>(t, out, rows);
+}
 }  // namespace lbf
 
 extern "C" {
@@ -461,6 +521,12 @@ void lbf_destroy(lbf_sim *s) {
   for (int k = 0; k < 2; ++k) {
     if (s->fork[k]) cudaEventDestroy(s->fork[k]);
     if (s->join[k]) cudaEventDestroy(s->join[k]);
+  }
+  if (s->bub_host) cudaFreeHost(s->bub_host);
+  if (s->err_host) cudaFreeHost(s->err_host);
+  for (int b = 0; b < 2; ++b) {
+    if (s->pin[b]) cudaFreeHost(s->pin[b]);
+    if (s->pin_ev[b]) cudaEventDestroy(s->pin_ev[b]);
   }
   if (s->joinx) cudaEventDestroy(s->joinx);
   if (s->st2) cudaStreamDestroy(s->st2);
@@ -767,31 +833,32 @@ int lbf_mlp_attach(lbf_sim *s, const float *theta) {
 
 int lbf_bubbles(lbf_sim *s, lbf_bubble *out, int capacity, int *count) {
   if (!s || !count || capacity < 0 || (capacity > 0 && !out)) return fail(LBF_EINVAL, "bad arguments");
-  const Table &t = s->tab[s->step & 1];
-  int nb = 0;
-  CK(cudaMemcpyAsync(&nb, t.count, sizeof(int), cudaMemcpyDeviceToHost, s->st));
-  CK(cudaStreamSynchronize(s->st));
-  *count = nb;
-  const int k = std::min(nb, capacity);
-  if (k > 0) {
-    std::vector<double> m(k), p(k), V(k);
-    std::vector<int> id(k), atm(k), root(k);
-    CK(cudaMemcpyAsync(m.data(), t.m, sizeof(double) * k, cudaMemcpyDeviceToHost, s->st));
-    CK(cudaMemcpyAsync(p.data(), t.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s->st));
-    CK(cudaMemcpyAsync(V.data(), t.V, sizeof(double) * k, cudaMemcpyDeviceToHost, s->st));
-    CK(cudaMemcpyAsync(id.data(), t.id, sizeof(int) * k, cudaMemcpyDeviceToHost, s->st));
-    CK(cudaMemcpyAsync(atm.data(), t.atm, sizeof(int) * k, cudaMemcpyDeviceToHost, s->st));
-    CK(cudaMemcpyAsync(root.data(), t.root, sizeof(int) * k, cudaMemcpyDeviceToHost, s->st));
-    CK(cudaStreamSynchronize(s->st));
-    for (int i = 0; i < k; ++i) {
-      out[i].id = id[i];
-      out[i].atm = atm[i];
-      out[i].label = root[i];
-      out[i].volume = V[i];
-      out[i].gas_mass = m[i];
-      out[i].pressure = p[i];
-    }
+  // rows packed on the device, then one copy into pinned staging memory
+  const int rows = std::min(capacity, s->cap);
+  const size_t bytes = 16 + sizeof(lbf_bubble) * (size_t)rows;
+  if (!s->bub_dev) {
+    int rc = dev_alloc(s, (void **)&s->bub_dev, 16 + sizeof(lbf_bubble) * (size_t)s->cap);
+    if (rc) return rc;
+    CK(cudaMallocHost((void **)&s->bub_host, 16 + sizeof(lbf_bubble) * (size_t)s->cap));
   }
+  lbf::pack_bubbles_launch(s->tab[s->step & 1], s->bub_dev, rows, s->st);
+  CK(cudaGetLastError());
+  // the header and the first rows in one copy; the rest only when present
+  constexpr int kFirst = 64;
+  const size_t first = std::min(bytes, 16 + sizeof(lbf_bubble) * (size_t)kFirst);
+  CK(cudaMemcpyAsync(s->bub_host, s->bub_dev, first, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  int nb = 0;
+  std::memcpy(&nb, s->bub_host, sizeof(int));
+  *count = nb;
+  const int k = std::min(nb, rows);
+  if (k > kFirst) {
+    const size_t off = 16 + sizeof(lbf_bubble) * (size_t)kFirst;
+    CK(cudaMemcpyAsync(s->bub_host + off, s->bub_dev + off, sizeof(lbf_bubble) * (size_t)(k - kFirst),
+                       cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+  }
+  if (k > 0) std::memcpy(out, s->bub_host + 16, sizeof(lbf_bubble) * (size_t)k);
   return 0;
 }
 
@@ -820,8 +887,8 @@ int lbf_fields(lbf_sim *s, unsigned mask, void *const *dst, int dst_is_device, i
       }
       s->ops->field(p, par, bit, s->staging, dtype, s->st);
       CK(cudaGetLastError());
-      CK(cudaMemcpyAsync(out, s->staging, bytes, cudaMemcpyDeviceToHost, s->st));
-      CK(cudaStreamSynchronize(s->st));
+      int rc = copy_to_host(s, out, s->staging, bytes);
+      if (rc) return rc;
     }
   }
   return 0;

@@ -240,12 +240,14 @@ class Sim:
         return int(self.lib.lbf_step_count(self.h))
 
     def bubbles(self) -> dict:
+        """The bubble table (one library call: rows up to the capacity)."""
+        if getattr(self, "_bub", None) is None:
+            self._bub = (Bubble * max(int(self.cfg.get("bubble_capacity", 4096)), 1))()
         cnt = ctypes.c_int()
-        self._check(self.lib.lbf_bubbles(self.h, None, 0, ctypes.byref(cnt)))
-        n = cnt.value
-        arr = (Bubble * max(n, 1))()
-        self._check(self.lib.lbf_bubbles(self.h, ctypes.cast(arr, ctypes.c_void_p), n, ctypes.byref(cnt)))
-        rows = arr[:n]
+        self._check(self.lib.lbf_bubbles(self.h, ctypes.cast(self._bub, ctypes.c_void_p), len(self._bub),
+                                         ctypes.byref(cnt)))
+        n = min(cnt.value, len(self._bub))
+        rows = self._bub[:n]
         return dict(id=np.array([b.id for b in rows], np.int32),
                     atm=np.array([b.atm for b in rows], np.int32),
                     root=np.array([b.label for b in rows], np.int64),
