@@ -157,10 +157,27 @@ def test_mass_ledger_gpu(lbf):
         assert L[7] == 0
 
 
-@pytest.mark.parametrize("storage,tol", [("fp32", 1e-4), ("fp16s", 2e-2), ("bf16s", 1e-1)])
-def test_reduced_precision_crop(lbf, oracle_mod, storage, tol):
+# Per-field bounds (norm-relative, max |gpu - oracle| / max |oracle| over
+# cells liquid or interface in both) after 20 steps of the 32^3 crop.  FP32:
+# the 1e-4 of the task for every field.  Shifted 16-bit storage keeps f - w_i
+# (g - w_i c0) with unit roundoff 2^-11 (FP16) or 2^-8 (BF16): density, fill
+# level, mass and bubble volume integrate many rounded populations with
+# alternating signs and stay near the FP32 error; velocity (a small
+# difference of populations, max |u| ~ 1e-2) and concentration (which
+# departs from c0 by up to ~0.8 at the Henry interface, so the shifted g are
+# O(w_i)) carry the storage roundoff itself.
+REDUCED_TOL = {
+    "fp32": dict(rho=1e-4, u=1e-4, alpha=1e-4, mass=1e-4, conc=1e-4, volume=1e-4),
+    "fp16s": dict(rho=1e-4, u=2e-3, alpha=1e-4, mass=1e-4, conc=2e-3, volume=1e-4),
+    "bf16s": dict(rho=1e-3, u=2e-2, alpha=2e-2, mass=2e-2, conc=2e-2, volume=1e-4),
+}
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16s", "bf16s"])
+def test_reduced_precision_crop(lbf, oracle_mod, storage):
     """32^3 crop in FP32 / shifted FP16 / shifted BF16 storage against the
-    FP64 oracle after 20 steps; the errors are printed for the record."""
+    FP64 oracle after 20 steps; every field's error is printed and bounded
+    (REDUCED_TOL); flags must agree exactly."""
     cfg, c, r = W.c2_crop_3d_32(storage=storage)
     sim, ora = _pair(lbf, oracle_mod, cfg)
     for s in (sim, ora):
@@ -169,7 +186,8 @@ def test_reduced_precision_crop(lbf, oracle_mod, storage, tol):
     ora.step(20)
     errs, nflag = compare_state(sim, ora)
     bg, bo = sim.bubbles(), ora.bubbles()
-    verr = rel_err(bg["volume"], bo["volume"])
-    print("\n%s: field errors %s, flag mismatches %d, volume error %.3g" % (storage, errs, nflag, verr))
-    assert errs["rho"] < tol and errs["alpha"] < 10 * tol
-    assert verr < 10 * tol
+    errs["volume"] = rel_err(bg["volume"], bo["volume"])
+    print("\n%s: errors against the FP64 oracle %s, flag mismatches %d" % (storage, errs, nflag))
+    assert nflag == 0
+    for k, bound in REDUCED_TOL[storage].items():
+        assert errs[k] < bound, (storage, k, errs[k], bound)
