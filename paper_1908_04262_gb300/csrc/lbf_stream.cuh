@@ -235,7 +235,7 @@ __device__ __forceinline__ void relax_store(const Params &p, const Cell &c, long
 // (liquid never touches gas); walls bounce back by reading the cell's own
 // outgoing population from the wall cell's slot
 template <int D, class S, int PAR>
-__device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long long n, uint8_t fl) {
+__device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long long n, uint8_t fl, bool wallwarp) {
   using R = typename ST<S>::R;
   constexpr int Q = Lat<D>::Q, QA = Lat<D>::QA;
   S *f = (S *)p.f;
@@ -245,19 +245,35 @@ __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long
 #pragma unroll
     for (int i = 1; i < Q; ++i) wallm |= (ftype(p.flags[src<D>(p, c, i)]) == T_WALL ? 1u : 0u) << i;
   }
+  // wallwarp: some active lane of this warp is a near-wall cell (decided by
+  // the caller with all lanes present).
+  // Plain streaming loads; in a warp with near-wall cells every lane loads
+  // plainly too (a wall direction's slot belongs to the wall cell: an
+  // in-bounds read of a value this thread itself rewrites later) and the
+  // near-wall lanes then replace their wall directions by bounce-back.  A
+  // warp-uniform choice keeps the common path free of per-direction selects.
   R fi[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const bool w = (wallm >> i) & 1u;
-    fi[i] = w ? ld(plane(f, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), fshift<S, D>(p, opp(i)))
-              : ld(plane(f, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), fshift<S, D>(p, i));
-  }
   R gi[QA];
+  if (!wallwarp) {
 #pragma unroll
-  for (int i = 0; i < QA; ++i) {
-    const bool w = (wallm >> i) & 1u;
-    gi[i] = w ? ld(plane(g, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), gshift<S, D>(p, opp(i)))
-              : ld(plane(g, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), gshift<S, D>(p, i));
+    for (int i = 0; i < Q; ++i) fi[i] = ld(plane(f, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), fshift<S, D>(p, i));
+#pragma unroll
+    for (int i = 0; i < QA; ++i) gi[i] = ld(plane(g, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), gshift<S, D>(p, i));
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fi[i] = ld(plane(f, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), fshift<S, D>(p, i));
+#pragma unroll
+    for (int i = 0; i < QA; ++i) gi[i] = ld(plane(g, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), gshift<S, D>(p, i));
+    if (wallm) {
+#pragma unroll
+      for (int i = 1; i < Q; ++i)
+        if ((wallm >> i) & 1u)
+          fi[i] = ld(plane(f, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), fshift<S, D>(p, opp(i)));
+#pragma unroll
+      for (int i = 1; i < QA; ++i)
+        if ((wallm >> i) & 1u)
+          gi[i] = ld(plane(g, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), gshift<S, D>(p, opp(i)));
+    }
   }
   if (wallm && (p.walls & 8)) {
     // moving walls of the +y face
@@ -315,7 +331,8 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
   const bool simple = active && type == T_LIQ && !(fl & NEARWALL);
   if (__all_sync(0xffffffffu, !isI)) {
     // warp without interface cells: the liquid path, nothing to aggregate
-    if (active) liquid_cell<D, S, PAR>(p, c, n, fl);
+    const bool wallwarp = __any_sync(0xffffffffu, active && (fl & NEARWALL));
+    if (active) liquid_cell<D, S, PAR>(p, c, n, fl, wallwarp);
     if (p.pf.q != 0.f) {
       const unsigned b = __ballot_sync(0xffffffffu, active);
       if ((threadIdx.x & 31) == 0 && b) atomicAdd(p.fluid_updates, (unsigned long long)__popc(b));
