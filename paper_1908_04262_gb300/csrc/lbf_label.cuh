@@ -601,17 +601,30 @@ static __global__ void __launch_bounds__(1024) k_bubble_update(Params p) {
     p.tnew.root[k] = p.roots[k];
     myfresh += !(gnold[g] > 0 && gheir[g] == k);
   }
-  sfresh[tid] = myfresh;
-  __syncthreads();
-  for (int off = 1; off < nt; off <<= 1) {  // inclusive scan
-    const int v = tid >= off ? sfresh[tid - off] : 0;
-    __syncthreads();
-    sfresh[tid] += v;
-    __syncthreads();
+  // inclusive scan of myfresh over the block: within each warp by shuffles,
+  // then over the warp totals by the first warp
+  const int lane = tid & 31, wid = tid >> 5;
+  int incl = myfresh;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += v;
   }
+  if (lane == 31) sfresh[wid] = incl;
   if (tid == 0) sbase = *p.next_id;
   __syncthreads();
-  int fid = sbase + sfresh[tid] - myfresh;
+  if (wid == 0) {
+    int w = lane < (nt >> 5) ? sfresh[lane] : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += v;
+    }
+    sfresh[32 + lane] = w;  // inclusive totals of warps 0..lane
+  }
+  __syncthreads();
+  const int before = (wid > 0 ? sfresh[32 + wid - 1] : 0) + incl - myfresh;
+  int fid = sbase + before;
   for (int k = k0; k < k1; ++k) {
     const int g = grp[nold + k];
     if (gnold[g] > 0 && gheir[g] == k)
@@ -620,7 +633,7 @@ static __global__ void __launch_bounds__(1024) k_bubble_update(Params p) {
       p.tnew.id[k] = fid++;
   }
   __syncthreads();
-  if (tid == nt - 1) *p.next_id = sbase + sfresh[nt - 1];
+  if (tid == nt - 1) *p.next_id = sbase + sfresh[32 + (nt >> 5) - 1];
   for (int h = tid; h < nh; h += nt) p.hash[p.hlist[h]] = HASH_EMPTY;
   if (tid == 0) {
     *p.hcount = 0;
