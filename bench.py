@@ -213,6 +213,17 @@ def forms_comparison(args, lbf, cfg, pts, rad, stream, fp32_line):
     return out
 
 
+def algorithmic_bytes_step(counts, storage_bytes, Q=19, QA=7):
+    """Bytes one whole step must move by the per-step model: every liquid or
+    interface cell reads and writes its populations once and its flag byte
+    (base = 2 (Q + QA) s + 2); an interface cell adds its mass, velocity,
+    curvature, disjoining pressure, normal and its own outgoing populations
+    for the exchange (~120 B in the FP32 form); a gas cell adds its flag and
+    label (9 B) for the labelling."""
+    gas, liq, ifc, wall = [float(x) for x in counts]
+    return (liq + ifc) * (2 * (Q + QA) * storage_bytes + 2) + ifc * 120.0 + gas * 9.0
+
+
 def reduce_max(x: float, world: int) -> float:
     if world == 1:
         return x
@@ -349,6 +360,12 @@ def run_ours(args):
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "sweep_share_of_step": sweep_ms / total_ms if total_ms > 0 else None}
     kernel_ms = {k: v[0] / max(v[1], 1) for k, v in groups.items()}
+    step_bytes = algorithmic_bytes_step(np.asarray(counts1, float), 4)
+    step_achieved = step_bytes / (ms / args.steps / 1e3) / 1e9 * world
+    step_roofline = {"bound": "hbm", "achieved": step_achieved, "peak": peak, "unit": "GB/s",
+                     "frac": step_achieved / (peak * world), "bytes_per_step": step_bytes,
+                     "note": "whole step (all 14 kernels) against the per-step byte model; "
+                             "the step is latency- and instruction-bound outside the sweep"}
 
     # --- end to end through the public API with host buffers -------------
     f = sim.fields(["flags", "rho", "u", "alpha", "conc"])
@@ -385,6 +402,7 @@ def run_ours(args):
                        "parallelism": "replicas x%d" % world,
                        "cells_gas_liquid_interface_wall": [int(x) for x in counts1]},
             "roofline": roofline, "kernel_ms": kernel_ms,
+            "step_roofline": step_roofline,
             "fluid_mlups": (counts0[1] + counts0[2]) * args.steps * world / (ms / 1e3) / 1e6,
             "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clocks, "e2e": e2e}
     if world == 1 and not args.no_forms:
