@@ -76,6 +76,7 @@ struct lbf_sim {
   unsigned long long *fluid_updates = nullptr;
   int *err = nullptr;
   int *gas_dirty = nullptr;
+  unsigned *wmask = nullptr;
   int *rlabel = nullptr;
   unsigned char *bub_dev = nullptr;   // packed bubble rows: count (16 bytes), then lbf_bubble records
   unsigned char *bub_host = nullptr;  // pinned staging copy
@@ -130,6 +131,7 @@ Params make_params(lbf_sim *s, long long step) {
   p.nx = c.nx; p.ny = c.ny; p.nz = c.nz; p.dim = s->dim; p.N = s->N;
   p.f = s->f; p.g = s->g;
   p.flags = s->flags;
+  p.wmask = s->wmask;
   p.ilist = s->ilist[par];
   p.icount = s->icount[par];
   p.inext = s->ilist[1 - par];
@@ -659,6 +661,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   AL(dalloc(s, &s->fluid_updates, 1));
   AL(dalloc(s, &s->err, 1));
   AL(dalloc(s, &s->gas_dirty, 1));
+  AL(dalloc(s, &s->wmask, N));
   AL(dalloc(s, &s->rlabel, N));
   AL(dalloc(s, &s->acc, 4));
   AL(dalloc(s, &s->counts, 4));

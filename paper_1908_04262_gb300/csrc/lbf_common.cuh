@@ -104,6 +104,7 @@ struct Params {
   long long N;
   void *f, *g;           // populations (storage type)
   uint8_t *flags;        // cell flags (conversion marks written in place)
+  unsigned *wmask;       // per cell: bit i set when x - e_i is a wall (walls never move)
   int *ilist, *icount;   // interface cells at the start of the step
   int *inext, *inext_count;  // interface cells after the conversion
   int *nlist, *ncount;   // gas/liquid cells turning interface this step

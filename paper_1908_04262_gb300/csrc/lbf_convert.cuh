@@ -376,11 +376,13 @@ __global__ void k_nearwall(Params p) {
   Cell c;
   if (!grid_cell(p, c)) return;
   const long long n = c.n;
-  bool w = false;
+  // bit i of the wall mask: the source x - e_i of direction i is a wall
+  unsigned wm = 0;
 #pragma unroll
-  for (int i = 1; i < Lat<D>::Q; ++i) w |= ftype(p.flags[nb<D>(p, c, i)]) == T_WALL;
+  for (int i = 1; i < Lat<D>::Q; ++i) wm |= (ftype(p.flags[src<D>(p, c, i)]) == T_WALL ? 1u : 0u) << i;
   const uint8_t fl = p.flags[n];
-  p.flags[n] = (uint8_t)(w ? (fl | NEARWALL) : (fl & ~NEARWALL));
+  p.flags[n] = (uint8_t)(wm ? (fl | NEARWALL) : (fl & ~NEARWALL));
+  p.wmask[n] = wm;
 }
 
 // Sec. 3.4: carve one nucleus (sphere or disk of radius R at (cx,cy,cz))

@@ -240,11 +240,7 @@ __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long
   constexpr int Q = Lat<D>::Q, QA = Lat<D>::QA;
   S *f = (S *)p.f;
   S *g = (S *)p.g;
-  unsigned wallm = 0;
-  if (fl & NEARWALL) {
-#pragma unroll
-    for (int i = 1; i < Q; ++i) wallm |= (ftype(p.flags[src<D>(p, c, i)]) == T_WALL ? 1u : 0u) << i;
-  }
+  const unsigned wallm = (fl & NEARWALL) ? p.wmask[n] : 0u;
   // wallwarp: some active lane of this warp is a near-wall cell (decided by
   // the caller with all lanes present).
   // Plain streaming loads; in a warp with near-wall cells every lane loads
