@@ -76,6 +76,8 @@ struct lbf_sim {
   unsigned long long *fluid_updates = nullptr;
   int *err = nullptr;
   int *gas_dirty = nullptr;
+  uint8_t *tdirty = nullptr;
+  size_t ntiles_alloc = 0;
   unsigned *wmask = nullptr;
   int *rlabel = nullptr;
   unsigned char *bub_dev = nullptr;   // packed bubble rows: count (16 bytes), then lbf_bubble records
@@ -155,6 +157,7 @@ Params make_params(lbf_sim *s, long long step) {
   p.gheir = s->gheir; p.gmold = s->gmold; p.gvnew = s->gvnew; p.gvmax = s->gvmax;
   p.next_id = s->next_id; p.led = s->led; p.fluid_updates = s->fluid_updates; p.err = s->err;
   p.gas_dirty = s->gas_dirty;
+  p.tdirty = s->tdirty;
   p.rlabel = s->rlabel;
   p.tau_tab = s->tau_tab; p.tab_n = s->tab_n; p.tab_lnA0 = s->tab_lnA0; p.tab_inv_dlnA = s->tab_inv_dlnA;
   p.tau = c.tau; p.rho0 = c.rho0; p.ax = c.accel[0]; p.ay = c.accel[1]; p.az = c.accel[2];
@@ -186,7 +189,7 @@ int relabel_in_place(lbf_sim *s) {
   CK(cudaMemsetAsync(p.inext_count, 0, sizeof(int), s->st));
   s->ops->label_prep(p, s->st);
   // the state was set from outside: label from scratch
-  CK(cudaMemsetAsync(s->gas_dirty, 1, sizeof(int), s->st));
+  CK(cudaMemsetAsync(s->gas_dirty, 0xff, sizeof(int), s->st));
   s->ops->label(p, s->st);
   s->ops->bubble_update(p, s->st);
   const size_t cap = (size_t)s->cap;
@@ -629,6 +632,8 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
                  tz = s->dim == 3 ? (cfg->nz + 3) / 4 : 1;
     AL(dalloc(s, &s->tstat, tx * ty * tz));
     AL(dalloc(s, &s->troot, tx * ty * tz));
+    AL(dalloc(s, &s->tdirty, tx * ty * tz));
+    s->ntiles_alloc = tx * ty * tz;
   }
   AL(dalloc(s, &s->roots, (size_t)s->cap));
   AL(dalloc(s, &s->nroots, 1));
@@ -691,6 +696,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   e = e ? e : zero(s->fluid_updates, sizeof(unsigned long long));
   e = e ? e : zero(s->err, sizeof(int));
   e = e ? e : zero(s->gas_dirty, sizeof(int));
+  e = e ? e : zero(s->tdirty, s->ntiles_alloc);
   if (e != cudaSuccess) {
     lbf_destroy(s);
     return fail(LBF_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));

@@ -130,11 +130,13 @@ struct Params {
   double *led;                   // 8 ledger accumulators
   unsigned long long *fluid_updates;
   int *err;
-  // non-zero when the conversion of this step added or removed gas cells
-  // (or the state was set from outside): the union-find passes run only
-  // then, otherwise the forest of the last labelling is still exact.  NULL
-  // means always.
+  // what the conversion of this step did to the gas cells: 0 nothing (the
+  // forest of the last labelling is still exact), 1 added some only (the
+  // components can only grow or merge: the touched tiles, marked in
+  // tdirty, are redone), anything else removed some or the state was set
+  // from outside (full labelling).  NULL means always full.
   int *gas_dirty;
+  uint8_t *tdirty;  // per union-find tile: touched by added gas cells this step
   // label of each current root cell (rank among the sorted roots, -1 past
   // the bubble capacity); read only at cells that are roots
   int *rlabel;
@@ -294,7 +296,22 @@ __device__ __forceinline__ void list_append(int *list, int *count, bool take, in
 }
 
 // post-conversion type from a flag byte carrying marks
+enum : int { LABEL_SKIP = 0, LABEL_ADDED = 1, LABEL_FULL = 2 };
+__device__ __forceinline__ int label_mode(const Params &p) {
+  if (!p.gas_dirty || !p.tdirty) return LABEL_FULL;
+  const int d = *p.gas_dirty;
+  return d == 0 ? LABEL_SKIP : (d == 1 ? LABEL_ADDED : LABEL_FULL);
+}
 __device__ __forceinline__ bool gas_unchanged(const Params &p) { return p.gas_dirty && *p.gas_dirty == 0; }
+
+// union-find tiles: 32 x-rows of 32 cells
+template <int D> struct Tile;
+template <> struct Tile<3> { static constexpr int TX = 32, TY = 8, TZ = 4; };
+template <> struct Tile<2> { static constexpr int TX = 32, TY = 32, TZ = 1; };
+template <int D> __device__ __forceinline__ int tile_of(const Params &p, const Cell &c) {
+  const int ntx = (p.nx + Tile<D>::TX - 1) / Tile<D>::TX, nty = (p.ny + Tile<D>::TY - 1) / Tile<D>::TY;
+  return c.x / Tile<D>::TX + ntx * (c.y / Tile<D>::TY + nty * (c.z / Tile<D>::TZ));
+}
 
 __device__ __forceinline__ int post_type(uint8_t f) {
   const int m = fmark(f);

@@ -111,17 +111,24 @@ __global__ void k_conv_mark(Params p) {
       } else {
         const int want = mk == MK_FILL ? T_GAS : T_LIQ;
         const int put = mk == MK_FILL ? MK_GI : MK_LI;
-        bool gas_change = mk == MK_EMPTY;  // this cell turns gas
+        const bool added = mk == MK_EMPTY;  // this cell turns gas
+        bool removed = false;
 #pragma unroll
         for (int i = 1; i < Lat<D>::Q; ++i) {
           const long long m = nb<D>(p, c, i);
           if (ftype(p.flags[m]) == want && mark_byte(p.flags, m, put)) {
             const int pos = atomicAdd(p.ncount, 1);
             p.nlist[pos] = (int)m;
-            gas_change |= put == MK_GI;  // a gas cell turns interface
+            removed |= put == MK_GI;  // a gas cell turns interface
           }
         }
-        if (gas_change && p.gas_dirty) *p.gas_dirty = 1;
+        if (p.gas_dirty) {
+          if (added) {
+            atomicOr(p.gas_dirty, 1);
+            if (p.tdirty) p.tdirty[tile_of<D>(p, c)] = 1;
+          }
+          if (removed) atomicOr(p.gas_dirty, 2);
+        }
       }
     }
   }

@@ -91,9 +91,6 @@ static __global__ void k_label_prep(Params p) {
 
 // union-find tiles: the local pass joins gas cells of one tile in shared
 // memory, the merge pass joins tiles across their faces in global memory
-template <int D> struct Tile;
-template <> struct Tile<3> { static constexpr int TX = 32, TY = 8, TZ = 4; };
-template <> struct Tile<2> { static constexpr int TX = 32, TY = 32, TZ = 1; };
 constexpr int TILE_THREADS = 256;
 
 // parents only ever point to smaller indices, so a chain has at most TN
@@ -167,7 +164,10 @@ template <int D>
 __global__ void __launch_bounds__(TILE_THREADS) k_uf_local(Params p) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ, NR = TY * TZ;
   static_assert(TX == 32 && NR == 32, "a tile is 32 rows of 32 cells");
-  if (gas_unchanged(p)) return;
+  const int mode = label_mode(p);
+  if (mode == LABEL_SKIP) return;
+  // a step that only added gas cells redoes the tiles it touched only
+  if (mode == LABEL_ADDED && !p.tdirty[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)]) return;
   __shared__ int lp[TN];
   __shared__ int lsz[TN];
   __shared__ unsigned rowm[NR];
@@ -280,20 +280,29 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_local(Params p) {
 template <int D>
 __global__ void __launch_bounds__(TILE_THREADS) k_uf_merge(Params p) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ;
-  if (gas_unchanged(p)) return;
+  const int mode = label_mode(p);
+  if (mode == LABEL_SKIP) return;
   const TileGrid<D> tgd(p);
   const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   const int own = p.tstat[tile];
   if (own == 0) return;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
   const long long nx = p.nx, nxy = (long long)p.nx * p.ny;
-  // statuses of the 3^d neighbouring tiles (periodic)
+  // statuses of the 3^d neighbouring tiles (periodic); after a step that
+  // only added gas cells, only links near a touched tile can be new
   __shared__ int nst[27];
+  __shared__ int near_dirty;
+  if (threadIdx.x == 0) near_dirty = 0;
+  __syncthreads();
   if (threadIdx.x < 27) {
     const int ox = threadIdx.x % 3 - 1, oy = (threadIdx.x / 3) % 3 - 1, oz = threadIdx.x / 9 - 1;
-    nst[threadIdx.x] = (D == 2 && oz != 0) ? 0 : p.tstat[tgd.id(blockIdx.x + ox, blockIdx.y + oy, blockIdx.z + oz)];
+    const bool in = !(D == 2 && oz != 0);
+    const int nt = tgd.id(blockIdx.x + ox, blockIdx.y + oy, blockIdx.z + oz);
+    nst[threadIdx.x] = in ? p.tstat[nt] : 0;
+    if (mode == LABEL_ADDED && in && p.tdirty[nt]) near_dirty = 1;
   }
   __syncthreads();
+  if (mode == LABEL_ADDED && !near_dirty) return;
   bool ok = true;
   // one gas link suffices between two single-component tiles: the first
   // thread that meets one claims the neighbour offset
@@ -351,6 +360,8 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_compress(Params p) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ;
   if (gas_unchanged(p)) return;
   const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  // the merge pass has read the touched-tile marks: clear them for the next step
+  if (threadIdx.x == 0 && p.tdirty) p.tdirty[tile] = 0;
   const int own = p.tstat[tile];
   if (own == 0) return;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
