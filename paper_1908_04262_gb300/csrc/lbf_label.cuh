@@ -91,7 +91,7 @@ static __global__ void k_label_prep(Params p) {
 
 // union-find tiles: the local pass joins gas cells of one tile in shared
 // memory, the merge pass joins tiles across their faces in global memory
-constexpr int TILE_THREADS = 256;
+constexpr int TILE_THREADS = 1024;  // one thread per cell of a tile, one x-row per warp
 
 // parents only ever point to smaller indices, so a chain has at most TN
 // links; the caps below are never reached by a consistent forest
