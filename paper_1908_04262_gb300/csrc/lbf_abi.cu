@@ -99,6 +99,7 @@ struct lbf_sim {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t tgraph[2] = {nullptr, nullptr};  // with event records
   cudaGraphExec_t graph2[2] = {nullptr, nullptr};  // two steps from parity k
+  cudaGraphExec_t graph4[2] = {nullptr, nullptr};  // four steps from parity k
   cudaEvent_t tev[2][2 * G_COUNT];
   bool tev_made = false;
   std::vector<Nucleus> queue;
@@ -283,22 +284,23 @@ void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
   enqueue_tail(s, p, nullptr, 0);
 }
 
-// two consecutive steps in one graph (parities par, 1 - par): the second
-// step's mass exchange overlaps the first step's labelling
-void enqueue_two(lbf_sim *s, const Params &pa, int par, const Params &pb) {
-  s->ops->exchange(pa, par, s->st);
-  s->ops->stream_collide(pa, par, s->st);
-  s->ops->convert(pa, par, s->st);
-  enqueue_tail(s, pa, &pb, 1 - par);
-  s->ops->stream_collide(pb, 1 - par, s->st);
-  s->ops->convert(pb, 1 - par, s->st);
-  enqueue_tail(s, pb, nullptr, 0);
+// k consecutive steps in one graph (parities alternating from par): every
+// step after the first has its mass exchange overlap the previous step's
+// labelling
+void enqueue_chain(lbf_sim *s, const Params *ps, int par, int k) {
+  s->ops->exchange(ps[0], par, s->st);
+  for (int i = 0; i < k; ++i) {
+    const int pi = (par + i) & 1;
+    s->ops->stream_collide(ps[i], pi, s->st);
+    s->ops->convert(ps[i], pi, s->st);
+    enqueue_tail(s, ps[i], i + 1 < k ? &ps[i + 1] : nullptr, 1 - pi);
+  }
 }
 
-int capture_two(lbf_sim *s, const Params &pa, int par, const Params &pb, cudaGraphExec_t *out) {
+int capture_chain(lbf_sim *s, const Params *ps, int par, int k, cudaGraphExec_t *out) {
   cudaGraph_t gr;
   CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
-  enqueue_two(s, pa, par, pb);
+  enqueue_chain(s, ps, par, k);
   CK(cudaStreamEndCapture(s->st, &gr));
   cudaError_t e = cudaGraphInstantiate(out, gr, 0);
   cudaGraphDestroy(gr);
@@ -348,14 +350,17 @@ int run_one_step(lbf_sim *s) {
   return 0;
 }
 
-int run_two_steps(lbf_sim *s) {
+// k = 2 or 4 steps as one graph (graphs[k / 4][parity])
+int run_steps(lbf_sim *s, int k) {
   const int par = (int)(s->step & 1);
-  if (!s->graph2[par]) {
-    const Params pa = make_params(s, s->step), pb = make_params(s, s->step + 1);
-    int rc = capture_two(s, pa, par, pb, &s->graph2[par]);
+  cudaGraphExec_t &g = k == 4 ? s->graph4[par] : s->graph2[par];
+  if (!g) {
+    Params ps[4];
+    for (int i = 0; i < k; ++i) ps[i] = make_params(s, s->step + i);
+    int rc = capture_chain(s, ps, par, k, &g);
     if (rc) return rc;
   }
-  CK(cudaGraphLaunch(s->graph2[par], s->st));
+  CK(cudaGraphLaunch(g, s->st));
   return 0;
 }
 
@@ -518,6 +523,7 @@ void lbf_destroy(lbf_sim *s) {
     if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
     if (s->tgraph[k]) cudaGraphExecDestroy(s->tgraph[k]);
     if (s->graph2[k]) cudaGraphExecDestroy(s->graph2[k]);
+    if (s->graph4[k]) cudaGraphExecDestroy(s->graph4[k]);
   }
   if (s->tev_made)
     for (int k = 0; k < 2; ++k)
@@ -775,11 +781,16 @@ int lbf_step(lbf_sim *s, int nsteps) {
   for (int k = 0; k < nsteps;) {
     int rc = carve_due_nuclei(s);
     if (rc) return rc;
-    if (!s->timing && k + 1 < nsteps && !nucleus_due(s, s->step + 1)) {
-      rc = run_two_steps(s);
+    int chain = 1;
+    if (!s->timing && k + 3 < nsteps && !nucleus_due(s, s->step + 3))
+      chain = 4;
+    else if (!s->timing && k + 1 < nsteps && !nucleus_due(s, s->step + 1))
+      chain = 2;
+    if (chain > 1) {
+      rc = run_steps(s, chain);
       if (rc) return rc;
-      s->step += 2;
-      k += 2;
+      s->step += chain;
+      k += chain;
     } else {
       rc = run_one_step(s);
       if (rc) return rc;
@@ -835,7 +846,8 @@ int lbf_mlp_attach(lbf_sim *s, const float *theta) {
     if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
     if (s->tgraph[k]) cudaGraphExecDestroy(s->tgraph[k]);
     if (s->graph2[k]) cudaGraphExecDestroy(s->graph2[k]);
-    s->graph[k] = s->tgraph[k] = s->graph2[k] = nullptr;
+    if (s->graph4[k]) cudaGraphExecDestroy(s->graph4[k]);
+    s->graph[k] = s->tgraph[k] = s->graph2[k] = s->graph4[k] = nullptr;
   }
   return 0;
 }
