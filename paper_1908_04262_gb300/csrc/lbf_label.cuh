@@ -506,8 +506,11 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
   if (inr) p.label_new[n] = knew;
   const bool contrib = knew >= 0 && v != 0.0;
   if (__any_sync(0xffffffffu, contrib)) agg_add(p.tnew.V, contrib ? knew : -1, v, wbuf + (threadIdx.x & ~31));
-  const int kold = inr ? p.label_old[n] : -1;
+  // old -> new overlap pairs (cells without a new label have none: no
+  // old label read, and warps without any pair skip the match)
+  const int kold = (inr && knew >= 0) ? p.label_old[n] : -1;
   const bool pair = kold >= 0 && knew >= 0;
+  if (!__any_sync(0xffffffffu, pair)) return;
   const unsigned long long key = pair ? (((unsigned long long)kold << 32) | (unsigned)knew) : HASH_EMPTY;
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   if (pair && (threadIdx.x & 31) == __ffs(peers) - 1) hash_insert(p, key);
