@@ -109,9 +109,9 @@ def stop_clocks(proc, path):
 # DRAM bytes (read + write) per launch of the FP32 sweep on this workload,
 # mean of the two parities, from profiles/k_stream_collide_128cube_fp32.md,
 # valid while the sweep's sources are the ones that were profiled
-SWEEP_TRAFFIC_BYTES = 267.2e6
+SWEEP_TRAFFIC_BYTES = 270.5e6
 SWEEP_SOURCES = ("paper_1908_04262_gb300/csrc/lbf_stream.cuh", "paper_1908_04262_gb300/csrc/lbf_common.cuh")
-SWEEP_SOURCES_SHA256_16 = "c83d6cc69a2cf1fd"
+SWEEP_SOURCES_SHA256_16 = "59be5eb9cae83f11"
 
 
 def sweep_traffic():
