@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS (D3Q19 FSLBM + D3Q7 ADE) and % HBM roofline; FP16+learned-κ vs FP32 plain"
 WORKLOAD = "3D D3Q19 FSLBM + D3Q7 ADE, 128^3, FP32 storage, 8 bubbles (R 4-6), power-law n=0.6, disjoining on"
-KERNELS_PER_STEP = 14  # exchange 1, sweep 1, conversion 4, labelling 5, bubble update 1, geometry 1, disjoining 1
+KERNELS_PER_STEP = 15  # exchange 1, sweep 2, conversion 4, labelling 5, bubble update 1, geometry 1, disjoining 1
 
 
 def parse():
@@ -106,12 +106,13 @@ def stop_clocks(proc, path):
 
 # ---------------------------------------------------------------------------
 
-# DRAM bytes (read + write) per launch of the FP32 sweep on this workload,
-# mean of the two parities, from profiles/k_stream_collide_128cube_fp32.md,
-# valid while the sweep's sources are the ones that were profiled
-SWEEP_TRAFFIC_BYTES = 270.5e6
+# DRAM bytes (read + write) per launch of the FP32 liquid sweep on this
+# workload, mean of the two parities, from profiles/k_stream_liquid_128cube_fp32.md,
+# valid while the sweep's sources are the ones that were profiled (None: not
+# yet profiled)
+SWEEP_TRAFFIC_BYTES = None
 SWEEP_SOURCES = ("paper_1908_04262_gb300/csrc/lbf_stream.cuh", "paper_1908_04262_gb300/csrc/lbf_common.cuh")
-SWEEP_SOURCES_SHA256_16 = "59be5eb9cae83f11"
+SWEEP_SOURCES_SHA256_16 = ""
 
 
 def sweep_traffic():
@@ -124,15 +125,13 @@ def sweep_traffic():
     return SWEEP_TRAFFIC_BYTES if h.hexdigest()[:16] == SWEEP_SOURCES_SHA256_16 else None
 
 
-def algorithmic_bytes_sweep(counts, storage_bytes, arith_bytes, Q=19, QA=7):
-    """Bytes the fused sweep must move in one launch: every liquid or
-    interface cell reads and writes its Q + QA populations once; every cell's
-    flag byte is read; interface cells also read u_I (3), kappa, Pi, M, alpha
-    and write alpha and their flag byte."""
+def algorithmic_bytes_sweep(counts, storage_bytes, Q=19, QA=7):
+    """Bytes the liquid sweep must move in one launch: every liquid cell
+    reads and writes its Q + QA populations once; every cell's flag byte is
+    read."""
     gas, liq, ifc, wall = [float(x) for x in counts]
     N = gas + liq + ifc + wall
-    fluid = liq + ifc
-    return fluid * 2 * (Q + QA) * storage_bytes + N * 1 + ifc * (8 * arith_bytes + 1)
+    return liq * 2 * (Q + QA) * storage_bytes + N * 1
 
 
 def bubble_volume(b: dict) -> float:
@@ -345,17 +344,17 @@ def run_ours(args):
     groups = sim.timing_read()
     cb = sim.cell_counts()
     sim.timing_enable(False)
-    sweep_ms, sweep_n = groups["stream_collide"]
+    sweep_ms, sweep_n = groups["stream_liquid"]
     avg_counts = (np.asarray(ca, float) + np.asarray(cb, float)) / 2
-    bytes_sweep = algorithmic_bytes_sweep(avg_counts, 4, 4)
+    bytes_sweep = algorithmic_bytes_sweep(avg_counts, 4)
     achieved = bytes_sweep / (sweep_ms / sweep_n / 1e3) / 1e9
     peak, peak_kind = peaks()
     total_ms = sum(v[0] for v in groups.values())
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": sweep_traffic(),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
-                                  "profiles/k_stream_collide_128cube_fp32.md",
-                "kernel": "k_stream_collide<3,float> (fused sweep)",
+                                  "profiles/k_stream_liquid_128cube_fp32.md",
+                "kernel": "k_stream_liquid<3,float> (liquid cells of the sweep)",
                 "bytes_per_launch": bytes_sweep, "launch_ms": sweep_ms / sweep_n,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "sweep_share_of_step": sweep_ms / total_ms if total_ms > 0 else None}
@@ -364,7 +363,7 @@ def run_ours(args):
     step_achieved = step_bytes / (ms / args.steps / 1e3) / 1e9 * world
     step_roofline = {"bound": "hbm", "achieved": step_achieved, "peak": peak, "unit": "GB/s",
                      "frac": step_achieved / (peak * world), "bytes_per_step": step_bytes,
-                     "note": "whole step (all 14 kernels) against the per-step byte model; "
+                     "note": "whole step (all 15 kernels) against the per-step byte model; "
                              "the step is latency- and instruction-bound outside the sweep"}
 
     # --- end to end through the public API with host buffers -------------

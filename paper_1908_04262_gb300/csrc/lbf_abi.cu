@@ -31,9 +31,9 @@ int fail(int code, const std::string &msg) {
   } while (0)
 
 // kernel groups of one step, in launch order
-enum { G_EXCHANGE = 0, G_STREAM, G_CONVERT, G_LABEL, G_BUBBLE, G_GEOMETRY, G_DISJOIN, G_COUNT };
-const char *kGroupNames[G_COUNT] = {"exchange",      "stream_collide", "convert",   "label",
-                                    "bubble_update", "geometry",       "disjoining"};
+enum { G_EXCHANGE = 0, G_LIQUID, G_IFACE, G_CONVERT, G_LABEL, G_BUBBLE, G_GEOMETRY, G_DISJOIN, G_COUNT };
+const char *kGroupNames[G_COUNT] = {"exchange", "stream_liquid", "stream_interface", "convert",   "label",
+                                    "bubble_update", "geometry", "disjoining"};
 
 struct Nucleus {
   long long step;
@@ -50,6 +50,8 @@ struct lbf_sim {
   cudaStream_t st = nullptr;
   bool own_stream = false;
   cudaStream_t st2 = nullptr, st3 = nullptr;  // further branches of the step graphs
+  int prio_least = 0, prio_greatest = 0;      // stream priority range of the device
+  std::vector<cudaGraphNode_t> low_nodes;      // liquid sweeps captured on the third branch
   cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr}, joinx = nullptr;
   Ops *ops = nullptr;
   std::vector<void *> allocs;
@@ -57,6 +59,8 @@ struct lbf_sim {
   void *f = nullptr, *g = nullptr;
   uint8_t *flags = nullptr;
   int *ilist[2] = {nullptr, nullptr}, *icount[2] = {nullptr, nullptr}, *nlist = nullptr, *ncount = nullptr;
+  int *seglist[2] = {nullptr, nullptr}, *segcount[2] = {nullptr, nullptr}, *segflag = nullptr;
+  size_t nseg = 0;  // 32-cell segments along x: ceil(nx / 32) per row
   int list_blocks = 0, warp_blocks = 0;
   void *M = nullptr, *phi = nullptr, *uI = nullptr, *kappa = nullptr, *Pi = nullptr, *nrm = nullptr,
        *dst = nullptr, *ex = nullptr;
@@ -139,6 +143,11 @@ Params make_params(lbf_sim *s, long long step) {
   p.icount = s->icount[par];
   p.inext = s->ilist[1 - par];
   p.inext_count = s->icount[1 - par];
+  p.seglist = s->seglist[par];
+  p.segcount = s->segcount[par];
+  p.segnext = s->seglist[1 - par];
+  p.segnext_count = s->segcount[1 - par];
+  p.segflag = s->segflag;
   p.nlist = s->nlist;
   p.ncount = s->ncount;
   p.list_blocks = s->list_blocks;
@@ -186,8 +195,10 @@ Params make_params(lbf_sim *s, long long step) {
 int relabel_in_place(lbf_sim *s) {
   const int par = (int)(s->step & 1);
   Params p = make_params(s, s->step);
+  CK(cudaMemsetAsync(s->segflag, 0, sizeof(int) * s->nseg, s->st));
   s->ops->build_ilist(p, s->st);
   CK(cudaMemsetAsync(p.inext_count, 0, sizeof(int), s->st));
+  CK(cudaMemsetAsync(p.segnext_count, 0, sizeof(int), s->st));
   s->ops->label_prep(p, s->st);
   // the state was set from outside: label from scratch
   CK(cudaMemsetAsync(s->gas_dirty, 0xff, sizeof(int), s->st));
@@ -238,8 +249,9 @@ void enqueue_geometry(lbf_sim *s, const Params &pn, cudaStream_t st) {
 
 // after the conversion: the geometry beside the labelling, the bubble update
 // beside the disjoining pressure (which needs both the labels and the
-// geometry); with `pnext`, the next step's mass exchange (which needs only
-// what the conversion left) runs on a third branch beside all of them
+// geometry); with `pnext`, the next step's mass exchange and then its liquid
+// sweep (which need only what the conversion left) run on a third branch
+// beside all of them, signalled by `joinx`
 void enqueue_tail(lbf_sim *s, const Params &p, const Params *pnext, int parnext) {
   const Params pn = next_geometry_params(p);
   cudaEventRecord(s->fork[0], s->st);
@@ -249,6 +261,15 @@ void enqueue_tail(lbf_sim *s, const Params &p, const Params *pnext, int parnext)
   if (pnext) {
     cudaStreamWaitEvent(s->st3, s->fork[0], 0);
     s->ops->exchange(*pnext, parnext, s->st3);
+    s->ops->stream_liquid(*pnext, parnext, s->st3);
+    // the liquid sweep is the branch's last node: remembered so that it can
+    // take the lowest priority (the labelling's blocks go first)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(s->st3, &cs, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess &&
+        cs == cudaStreamCaptureStatusActive)
+      s->low_nodes.insert(s->low_nodes.end(), deps, deps + nd);
     cudaEventRecord(s->joinx, s->st3);
   }
   s->ops->label(p, s->st);
@@ -259,7 +280,6 @@ void enqueue_tail(lbf_sim *s, const Params &p, const Params *pnext, int parnext)
   cudaStreamWaitEvent(s->st, s->join[0], 0);
   s->ops->disjoining(pn, s->st);
   cudaStreamWaitEvent(s->st, s->join[1], 0);
-  if (pnext) cudaStreamWaitEvent(s->st, s->joinx, 0);
 }
 
 // the launch sequence of one step; with `ev` every kernel group runs in
@@ -271,7 +291,8 @@ void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
     if (ev) cudaEventRecordWithFlags(ev[2 * gidx + 1], s->st, cudaEventRecordExternal);
   };
   group(G_EXCHANGE, [&] { s->ops->exchange(p, par, s->st); });
-  group(G_STREAM, [&] { s->ops->stream_collide(p, par, s->st); });
+  group(G_LIQUID, [&] { s->ops->stream_liquid(p, par, s->st); });
+  group(G_IFACE, [&] { s->ops->stream_interface(p, par, s->st); });
   group(G_CONVERT, [&] { s->ops->convert(p, par, s->st); });
   if (ev) {
     const Params pn = next_geometry_params(p);
@@ -285,24 +306,55 @@ void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
 }
 
 // k consecutive steps in one graph (parities alternating from par): every
-// step after the first has its mass exchange overlap the previous step's
-// labelling
+// step after the first has its mass exchange and its liquid sweep overlap the
+// previous step's labelling, geometry, bubble update and disjoining pressure;
+// its interface sweep waits for those, its conversion for both sweeps
 void enqueue_chain(lbf_sim *s, const Params *ps, int par, int k) {
   s->ops->exchange(ps[0], par, s->st);
+  s->ops->stream_liquid(ps[0], par, s->st);
   for (int i = 0; i < k; ++i) {
     const int pi = (par + i) & 1;
-    s->ops->stream_collide(ps[i], pi, s->st);
+    s->ops->stream_interface(ps[i], pi, s->st);
+    if (i > 0) cudaStreamWaitEvent(s->st, s->joinx, 0);
     s->ops->convert(ps[i], pi, s->st);
     enqueue_tail(s, ps[i], i + 1 < k ? &ps[i + 1] : nullptr, 1 - pi);
   }
 }
 
+// kernel node priorities of a captured chain: the overlapped liquid sweeps
+// the least, every other kernel the greatest (the graph is instantiated to
+// honour them)
+int set_node_priorities(lbf_sim *s, cudaGraph_t gr) {
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(gr, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  CK(cudaGraphGetNodes(gr, nodes.data(), &nn));
+  for (size_t j = 0; j < nn; ++j) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nodes[j], &t));
+    if (t != cudaGraphNodeTypeKernel) continue;
+    const bool low = std::find(s->low_nodes.begin(), s->low_nodes.end(), nodes[j]) != s->low_nodes.end();
+    cudaLaunchAttributeValue v;
+    std::memset(&v, 0, sizeof(v));
+    v.priority = low ? s->prio_least : s->prio_greatest;
+    CK(cudaGraphKernelNodeSetAttribute(nodes[j], cudaLaunchAttributePriority, &v));
+  }
+  return 0;
+}
+
 int capture_chain(lbf_sim *s, const Params *ps, int par, int k, cudaGraphExec_t *out) {
   cudaGraph_t gr;
+  s->low_nodes.clear();
   CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
   enqueue_chain(s, ps, par, k);
   CK(cudaStreamEndCapture(s->st, &gr));
-  cudaError_t e = cudaGraphInstantiate(out, gr, 0);
+  int rc = set_node_priorities(s, gr);
+  s->low_nodes.clear();
+  if (rc) {
+    cudaGraphDestroy(gr);
+    return rc;
+  }
+  cudaError_t e = cudaGraphInstantiate(out, gr, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(gr);
   if (e != cudaSuccess) return fail(LBF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
   return 0;
@@ -579,8 +631,9 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     s->own_stream = true;
   }
   {
-    cudaError_t e = cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st3, cudaStreamNonBlocking);
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&s->prio_least, &s->prio_greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->st2, cudaStreamNonBlocking, s->prio_greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->st3, cudaStreamNonBlocking, s->prio_least);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joinx, cudaEventDisableTiming);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
       e = cudaEventCreateWithFlags(&s->fork[k], cudaEventDisableTiming);
@@ -619,6 +672,12 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   AL(dalloc(s, &s->icount[0], 1));
   AL(dalloc(s, &s->icount[1], 1));
   AL(dalloc(s, &s->nlist, N));
+  s->nseg = (size_t)cfg->ny * cfg->nz * ((cfg->nx + 31) / 32);
+  AL(dalloc(s, &s->seglist[0], s->nseg));
+  AL(dalloc(s, &s->seglist[1], s->nseg));
+  AL(dalloc(s, &s->segcount[0], 1));
+  AL(dalloc(s, &s->segcount[1], 1));
+  AL(dalloc(s, &s->segflag, s->nseg));
   AL(dalloc(s, &s->ncount, 1));
   AL(dev_alloc(s, &s->M, N * s->rsz));
   AL(dev_alloc(s, &s->phi, N * s->rsz));
@@ -697,6 +756,9 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   e = e ? e : zero(s->icount[0], sizeof(int));
   e = e ? e : zero(s->icount[1], sizeof(int));
   e = e ? e : zero(s->ncount, sizeof(int));
+  e = e ? e : zero(s->segcount[0], sizeof(int));
+  e = e ? e : zero(s->segcount[1], sizeof(int));
+  e = e ? e : zero(s->segflag, sizeof(int) * s->nseg);
   e = e ? e : zero(s->hcount, sizeof(int));
   e = e ? e : zero(s->led, 8 * sizeof(double));
   e = e ? e : zero(s->fluid_updates, sizeof(unsigned long long));

@@ -108,6 +108,11 @@ struct Params {
   int *ilist, *icount;   // interface cells at the start of the step
   int *inext, *inext_count;  // interface cells after the conversion
   int *nlist, *ncount;   // gas/liquid cells turning interface this step
+  // 32-cell segments along x that hold interface cells (the interface
+  // kernels run one warp per segment, one lane per cell)
+  int *seglist, *segcount;       // at the start of the step
+  int *segnext, *segnext_count;  // after the conversion
+  int *segflag;                  // per segment: 1 while listed in segnext (the interface sweep clears it)
   int list_blocks;       // persistent grid size of the thread-per-cell list kernels
   int warp_blocks;       // ... of the warp-per-cell list kernels (full occupancy)
   void *M, *phi;         // liquid mass, fill level (arithmetic type)
@@ -202,6 +207,21 @@ __device__ __forceinline__ Cell cell_at(const Params &p, int x, int y, int z) {
 __device__ __forceinline__ bool grid_cell(const Params &p, Cell &c) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   c = cell_at(p, x < p.nx ? x : p.nx - 1, blockIdx.y, blockIdx.z);
+  return x < p.nx;
+}
+
+// segments of 32 cells along x: ceil(nx / 32) per row of the lattice
+__device__ __forceinline__ int seg_of(const Params &p, int n) {
+  const int row = n / p.nx;
+  return row * ((p.nx + 31) >> 5) + ((n - row * p.nx) >> 5);
+}
+// the lane's cell of segment `seg`; false past the end of the row
+__device__ __forceinline__ bool seg_cell(const Params &p, int seg, int lane, Cell &c) {
+  const int nxb = (p.nx + 31) >> 5;
+  const int row = seg / nxb;
+  const int x = (seg - row * nxb) * 32 + lane;
+  const int z = row / p.ny;
+  c = cell_at(p, x < p.nx ? x : p.nx - 1, row - z * p.ny, z);
   return x < p.nx;
 }
 

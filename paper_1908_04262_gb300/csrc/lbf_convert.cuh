@@ -276,15 +276,25 @@ __global__ void k_conv_finalize(Params p) {
       take = t == T_IFC;
     }
     list_append(p.inext, p.inext_count, take, n);
+    // the segments of the listed cells, each once: one claim per distinct
+    // segment of the warp, then a flag that the interface sweep clears
+    const int seg = take ? seg_of(p, n) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, seg);
+    bool first = false;
+    if (take && (int)(threadIdx.x & 31) == __ffs(peers) - 1) first = atomicExch(p.segflag + seg, 1) == 0;
+    list_append(p.segnext, p.segnext_count, first, seg);
   }
 }
 
-// list every interface cell (initialisation paths)
+// list every interface cell and its segment (initialisation paths; blocks
+// are whole multiples of 32 cells along x, so a warp is one segment)
 static __global__ void k_build_ilist(Params p) {
   Cell c;
   const bool inr = grid_cell(p, c);
   const bool take = inr && ftype(p.flags[c.n]) == T_IFC;
   list_append(p.ilist, p.icount, take, (int)c.n);
+  const bool any = __any_sync(0xffffffffu, take);
+  list_append(p.seglist, p.segcount, any && (threadIdx.x & 31) == 0, seg_of(p, c.n));
 }
 
 // ---------------------------------------------------------------------------

@@ -56,13 +56,20 @@ struct OpsImpl final : Ops {
   }
   void build_ilist(const Params &p, cudaStream_t s) override {
     cudaMemsetAsync(p.icount, 0, sizeof(int), s);
+    cudaMemsetAsync(p.segcount, 0, sizeof(int), s);
     k_build_ilist<<<row_grid(p), row_block(p), 0, s>>>(p);
   }
-  void stream_collide(const Params &p, int par, cudaStream_t s) override {
+  void stream_liquid(const Params &p, int par, cudaStream_t s) override {
     if (par)
-      k_stream_collide<D, S, 1><<<row_grid(p), row_block(p), 0, s>>>(p);
+      k_stream_liquid<D, S, 1><<<row_grid(p), row_block(p), 0, s>>>(p);
     else
-      k_stream_collide<D, S, 0><<<row_grid(p), row_block(p), 0, s>>>(p);
+      k_stream_liquid<D, S, 0><<<row_grid(p), row_block(p), 0, s>>>(p);
+  }
+  void stream_interface(const Params &p, int par, cudaStream_t s) override {
+    if (par)
+      k_stream_interface<D, S, 1><<<p.list_blocks, 128, 0, s>>>(p);
+    else
+      k_stream_interface<D, S, 0><<<p.list_blocks, 128, 0, s>>>(p);
   }
   void convert(const Params &p, int par, cudaStream_t s) override {
     const int post = 1 - par;

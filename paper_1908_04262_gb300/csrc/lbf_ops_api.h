@@ -19,7 +19,9 @@ struct Ops {
   // step pieces (par = parity of the populations when the step starts)
   virtual void exchange(const Params &p, int par, cudaStream_t s) = 0;
   virtual void build_ilist(const Params &p, cudaStream_t s) = 0;
-  virtual void stream_collide(const Params &p, int par, cudaStream_t s) = 0;
+  // the sweep: liquid cells, then interface cells (the two commute)
+  virtual void stream_liquid(const Params &p, int par, cudaStream_t s) = 0;
+  virtual void stream_interface(const Params &p, int par, cudaStream_t s) = 0;
   virtual void convert(const Params &p, int par, cudaStream_t s) = 0;
   virtual void label(const Params &p, cudaStream_t s) = 0;
   virtual void label_prep(const Params &p, cudaStream_t s) = 0;

@@ -7,17 +7,26 @@
 // (alpha_x + alpha_nb)/2 towards interface, 0 towards gas and walls).  It
 // also keeps the cell's last velocity u_I for the reconstruction.
 //
-// k_stream_collide (every liquid and interface cell) then streams in place
-// (Sec. 2 Eq. streamingstep), bounces back at walls, rebuilds populations
-// arriving from gas cells (Sec. 2.2 Eq. reconstruct with the gas density of
-// Eq. rhob / rhobplusdisjoining), relaxes with BGK plus Guo forcing
-// (Sec. 2 Eq. collision/equilibrium) at a per-cell tau from the local shear
-// rate (Sec. 2.3 Eq. tau/carreauTau), updates the fill level
-// (Sec. 2.1 Eq. alpha) and marks interface cells that fill or empty.  The
-// same thread advances the dissolved gas on D2Q5/D3Q7 (Sec. 3.1
-// Eq. diffusion) with Henry's law at gas links (Sec. 3.2 Eq. henryslaw /
-// reconstructdiffusion) and adds the cell's gas current (Sec. 3.1
-// Eq. gascurrent) to its bubble.
+// The sweep then streams in place (Sec. 2 Eq. streamingstep), bounces back
+// at walls, relaxes with BGK plus Guo forcing (Sec. 2 Eq.
+// collision/equilibrium) at a per-cell tau from the local shear rate
+// (Sec. 2.3 Eq. tau/carreauTau) and advances the dissolved gas on D2Q5/D3Q7
+// (Sec. 3.1 Eq. diffusion), in two kernels over disjoint sets of cells:
+//   k_stream_liquid     every liquid cell (row grid); it needs nothing that
+//                       the labelling, the bubble update, the geometry or
+//                       the disjoining pressure of the last step produce
+//   k_stream_interface  every interface cell of the step's list: it also
+//                       rebuilds populations arriving from gas cells
+//                       (Sec. 2.2 Eq. reconstruct with the gas density of
+//                       Eq. rhob / rhobplusdisjoining), updates the fill
+//                       level (Sec. 2.1 Eq. alpha), marks cells that fill or
+//                       empty, applies Henry's law at gas links (Sec. 3.2
+//                       Eq. henryslaw / reconstructdiffusion) and adds the
+//                       cell's gas current (Sec. 3.1 Eq. gascurrent) to its
+//                       bubble.
+// In the AA pattern every cell reads and writes only its own set of slots,
+// so the two kernels commute; the liquid one may run as soon as the mass
+// exchange of its step has read the slots it rewrites.
 #pragma once
 #include "lbf_common.cuh"
 
@@ -103,7 +112,8 @@ template <class R> __device__ __forceinline__ R solve_tau(const Params &p, R A) 
   return t;
 }
 
-// one warp per interface cell, one lane per lattice direction
+// one warp per segment of interface cells, one lane per cell (loads along x
+// coalesce like the lattice sweep's)
 template <int D, class S, int PAR>
 __global__ void __launch_bounds__(128) k_exchange(Params p) {
   using R = typename ST<S>::R;
@@ -111,39 +121,39 @@ __global__ void __launch_bounds__(128) k_exchange(Params p) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int cnt = *p.icount;
+  const int cnt = *p.segcount;
   const S *f = (const S *)p.f;
   R *M = (R *)p.M;
   const R *phi = (const R *)p.phi;
   for (int k = warp; k < cnt; k += nwarps) {
-    const long long n = p.ilist[k];
-    const Cell c = make_cell(p, n);
-    R fo = 0, dm = 0, ex = 0, ey = 0, ez = 0;
-    if (lane < Q) {
-      const int i = lane;  // the lane's lattice direction
-      fo = ld(plane(f, p, dir_out<D>(i, PAR)), cell_out<D>(p, c, i, PAR), fshift<S, D>(p, i));
-      ex = (R)Lat<D>::cx(i);
-      ey = (R)Lat<D>::cy(i);
-      ez = (R)Lat<D>::cz(i);
+    Cell c;
+    if (!seg_cell(p, p.seglist[k], lane, c)) continue;
+    const int n = c.n;
+    if (ftype(p.flags[n]) != T_IFC) continue;
+    const R phn = phi[n];
+    R rho = 0, jx = 0, jy = 0, jz = 0, dM = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const R fo = ld(plane(f, p, dir_out<D>(i, PAR)), cell_out<D>(p, c, i, PAR), fshift<S, D>(p, i));
+      rho += fo;
+      jx += fo * (R)Lat<D>::cx(i);
+      jy += fo * (R)Lat<D>::cy(i);
+      jz += fo * (R)Lat<D>::cz(i);
       if (i > 0) {
-        const long long m = nb<D>(p, c, i);
+        const int m = nb<D>(p, c, i);
         const int tn = ftype(p.flags[m]);
         if (tn == T_LIQ || tn == T_IFC) {
           // arriving along opp(i) from m: the slot holding m's outgoing f_opp(i)
           const R fin = ld(plane(f, p, dir_in<D>(opp(i), PAR)), cell_in<D>(p, c, opp(i), PAR), fshift<S, D>(p, opp(i)));
-          dm = tn == T_LIQ ? fin - fo : (R)0.5 * (phi[n] + phi[m]) * (fin - fo);
+          dM += tn == T_LIQ ? fin - fo : (R)0.5 * (phn + phi[m]) * (fin - fo);
         }
       }
     }
-    const R rho = warp_sum_r<R>(fo), jx = warp_sum_r<R>(fo * ex), jy = warp_sum_r<R>(fo * ey),
-            jz = warp_sum_r<R>(fo * ez), dM = warp_sum_r<R>(dm);
-    if (lane == 0) {
-      R *uI = (R *)p.uI;
-      uI[n] = (jx - (R)0.5 * rho * PV(R, ax)) / rho;
-      uI[p.N + n] = (jy - (R)0.5 * rho * PV(R, ay)) / rho;
-      uI[2 * p.N + n] = (jz - (R)0.5 * rho * PV(R, az)) / rho;
-      M[n] = M[n] + dM;
-    }
+    R *uI = (R *)p.uI;
+    uI[n] = (jx - (R)0.5 * rho * PV(R, ax)) / rho;
+    uI[p.N + n] = (jy - (R)0.5 * rho * PV(R, ay)) / rho;
+    uI[2 * p.N + n] = (jz - (R)0.5 * rho * PV(R, az)) / rho;
+    M[n] = M[n] + dM;
   }
 }
 
@@ -305,151 +315,154 @@ __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long
   }
 }
 
+// the liquid cells of the lattice, one thread per cell along x rows; every
+// warp takes the liquid path (interface cells are k_stream_interface's)
 template <int D, class S, int PAR>
-__global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_stream_collide(Params p) {
-  using R = typename ST<S>::R;
-  constexpr int Q = Lat<D>::Q, QA = Lat<D>::QA;
-  __shared__ double wbuf[128];
+__global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_stream_liquid(Params p) {
   Cell c;
   const bool inr = grid_cell(p, c);
   const long long n = c.n;
-  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
-    // counters of the lists the conversion and the relabelling fill
-    *p.ncount = 0;
-    *p.inext_count = 0;
-  }
   const uint8_t fl = inr ? p.flags[n] : (uint8_t)T_GAS;
-  const int type = ftype(fl);
-  const bool active = inr && (type == T_LIQ || type == T_IFC);
-  const bool isI = active && type == T_IFC;
-  double flux = 0.0;
-  int lab = -1;
-  const bool simple = active && type == T_LIQ && !(fl & NEARWALL);
-  if (__all_sync(0xffffffffu, !isI)) {
-    // warp without interface cells: the liquid path, nothing to aggregate
-    const bool wallwarp = __any_sync(0xffffffffu, active && (fl & NEARWALL));
-    if (active) liquid_cell<D, S, PAR>(p, c, n, fl, wallwarp);
-    if (p.pf.q != 0.f) {
-      const unsigned b = __ballot_sync(0xffffffffu, active);
-      if ((threadIdx.x & 31) == 0 && b) atomicAdd(p.fluid_updates, (unsigned long long)__popc(b));
-    }
-    return;
-  }
-  if (active) {
-    S *f = (S *)p.f;
-    S *g = (S *)p.g;
-    // kinds of the source cells: bit i set when x - e_i is gas / a wall
-    unsigned gasm = 0, wallm = 0;
-    if (!simple) {
-#pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int ts = ftype(p.flags[src<D>(p, c, i)]);
-        gasm |= (ts == T_GAS ? 1u : 0u) << i;
-        wallm |= (ts == T_WALL ? 1u : 0u) << i;
-      }
-    }
-    R fi[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if (i == 0 || !((gasm | wallm) >> i & 1u)) fi[i] = ld(plane(f, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), fshift<S, D>(p, i));
-    }
-    if (gasm | wallm) {
-      R uIx = 0, uIy = 0, uIz = 0, kap = 0, pi = 0;
-      if (isI) {
-        const R *uI = (const R *)p.uI;
-        uIx = uI[n];
-        uIy = uI[p.N + n];
-        uIz = uI[2 * p.N + n];
-        kap = ((const R *)p.kappa)[n];
-        pi = ((const R *)p.Pi)[n];
-      }
-#pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        if (wallm >> i & 1u) {
-          // half-way bounce-back: the cell's own outgoing population towards
-          // the wall, reflected (the slot belongs to the wall cell)
-          R v = ld(plane(f, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), fshift<S, D>(p, opp(i)));
-          const bool top = Lat<D>::cy(i) > 0 ? c.y == 0 : (Lat<D>::cy(i) < 0 ? c.y == p.ny - 2 : c.y == p.ny - 1);
-          if ((p.walls & 8) && top) {
-            const R eu = (R)Lat<D>::cx(i) * PV(R, uwx) + (R)Lat<D>::cy(i) * PV(R, uwy) + (R)Lat<D>::cz(i) * PV(R, uwz);
-            v += (R)2 * (R)Lat<D>::w(i) * PV(R, rho0) * eu * (R)3;
-          }
-          fi[i] = v;
-        } else if (gasm >> i & 1u) {
-          // Sec. 2.2 Eq. reconstruct with rho_g of Eq. rhob / rhobplusdisjoining
-          const int b = p.label_old[src<D>(p, c, i)];
-          const R pg = b >= 0 ? (R)p.told.p[b] : PV(R, p0);
-          const R rg = (pg - (R)2 * PV(R, sigma) * kap - pi) * (R)3;
-          const R fo = ld(plane(f, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), fshift<S, D>(p, opp(i)));
-          fi[i] = feq<R, D>(i, rg, uIx, uIy, uIz) + feq<R, D>(opp(i), rg, uIx, uIy, uIz) - fo;
-        }
-      }
-    }
-    // moments and Guo-shifted velocity
-    R rho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      rho += fi[i];
-      jx += fi[i] * (R)Lat<D>::cx(i);
-      jy += fi[i] * (R)Lat<D>::cy(i);
-      jz += fi[i] * (R)Lat<D>::cz(i);
-    }
-    const R ux = (jx + (R)0.5 * rho * PV(R, ax)) / rho;
-    const R uy = (jy + (R)0.5 * rho * PV(R, ay)) / rho;
-    const R uz = (jz + (R)0.5 * rho * PV(R, az)) / rho;
-    relax_store<D, S, PAR>(p, c, n, f, fi, rho, ux, uy, uz, local_tau<D, R>(p, fi, rho, ux, uy, uz));
-
-    R phin = 0, pho = 0;
-    if (isI) {
-      R *phi = (R *)p.phi;
-      const R Mn = ((const R *)p.M)[n];
-      pho = phi[n];
-      phin = Mn / rho;
-      phi[n] = phin;
-      int mk = MK_NONE;
-      if (Mn > ((R)1 + PV(R, eps)) * rho)
-        mk = MK_FILL;
-      else if (Mn < -PV(R, eps) * rho)
-        mk = MK_EMPTY;
-      if (mk) p.flags[n] = (uint8_t)(fl | (mk << 2));
-    }
-
-    // dissolved gas (Sec. 3.1-3.2)
-    R gi[QA];
-    R cgas = 0, fl_gas = 0;
-#pragma unroll
-    for (int i = 0; i < QA; ++i) {
-      if (i > 0 && (wallm >> i & 1u)) {
-        gi[i] = ld(plane(g, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), gshift<S, D>(p, opp(i)));
-      } else if (i > 0 && (gasm >> i & 1u)) {
-        const int b = p.label_old[src<D>(p, c, i)];
-        const R cH = PV(R, kH) * (b >= 0 ? (R)p.told.p[b] : PV(R, p0));
-        const R go = ld(plane(g, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), gshift<S, D>(p, opp(i)));
-        gi[i] = (R)2 * (R)Lat<D>::wa(i) * cH - go;
-        fl_gas += go - gi[i];
-      } else {
-        gi[i] = ld(plane(g, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), gshift<S, D>(p, i));
-      }
-      cgas += gi[i];
-    }
-    const R omg = (R)1 / PV(R, taug);
-#pragma unroll
-    for (int i = 0; i < QA; ++i) {
-      const R v = gi[i] + (geq<R, D>(i, cgas, ux, uy, uz) - gi[i]) * omg + (R)Lat<D>::wa(i) * PV(R, q);
-      st(plane(g, p, dir_out<D>(i, 1 - PAR)), cell_out<D>(p, c, i, 1 - PAR), v, gshift<S, D>(p, i));
-    }
-    if (isI) {
-      flux = (double)(fl_gas - cgas * (phin - pho));
-      lab = p.label_old[n];
-      if (lab < 0) atomicAdd(p.led + 5, flux);
-    }
-  }
+  const bool active = inr && ftype(fl) == T_LIQ;
+  const bool wallwarp = __any_sync(0xffffffffu, active && (fl & NEARWALL));
+  if (active) liquid_cell<D, S, PAR>(p, c, n, fl, wallwarp);
   if (p.pf.q != 0.f) {
     const unsigned b = __ballot_sync(0xffffffffu, active);
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(p.fluid_updates, (unsigned long long)__popc(b));
   }
-  if (__any_sync(0xffffffffu, isI && lab >= 0))
-    agg_add(p.told.dm, (isI && lab >= 0) ? lab : -1, flux, wbuf + (threadIdx.x & ~31));
+}
+
+// an interface cell: streaming, bounce-back, reconstruction from gas
+// neighbours, relaxation, fill level and marks, dissolved gas with Henry's
+// law at gas links; returns the cell's gas current and its bubble label
+template <int D, class S, int PAR>
+__device__ __forceinline__ void interface_cell(const Params &p, const Cell &c, long long n, uint8_t fl, double &flux,
+                                               int &lab) {
+  using R = typename ST<S>::R;
+  constexpr int Q = Lat<D>::Q, QA = Lat<D>::QA;
+  S *f = (S *)p.f;
+  S *g = (S *)p.g;
+  // kinds of the source cells: bit i set when x - e_i is gas / a wall
+  unsigned gasm = 0, wallm = 0;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int ts = ftype(p.flags[src<D>(p, c, i)]);
+    gasm |= (ts == T_GAS ? 1u : 0u) << i;
+    wallm |= (ts == T_WALL ? 1u : 0u) << i;
+  }
+  R fi[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (i == 0 || !((gasm | wallm) >> i & 1u)) fi[i] = ld(plane(f, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), fshift<S, D>(p, i));
+  }
+  if (gasm | wallm) {
+    const R *uI = (const R *)p.uI;
+    const R uIx = uI[n], uIy = uI[p.N + n], uIz = uI[2 * p.N + n];
+    const R kap = ((const R *)p.kappa)[n], pi = ((const R *)p.Pi)[n];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      if (wallm >> i & 1u) {
+        // half-way bounce-back: the cell's own outgoing population towards
+        // the wall, reflected (the slot belongs to the wall cell)
+        R v = ld(plane(f, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), fshift<S, D>(p, opp(i)));
+        const bool top = Lat<D>::cy(i) > 0 ? c.y == 0 : (Lat<D>::cy(i) < 0 ? c.y == p.ny - 2 : c.y == p.ny - 1);
+        if ((p.walls & 8) && top) {
+          const R eu = (R)Lat<D>::cx(i) * PV(R, uwx) + (R)Lat<D>::cy(i) * PV(R, uwy) + (R)Lat<D>::cz(i) * PV(R, uwz);
+          v += (R)2 * (R)Lat<D>::w(i) * PV(R, rho0) * eu * (R)3;
+        }
+        fi[i] = v;
+      } else if (gasm >> i & 1u) {
+        // Sec. 2.2 Eq. reconstruct with rho_g of Eq. rhob / rhobplusdisjoining
+        const int b = p.label_old[src<D>(p, c, i)];
+        const R pg = b >= 0 ? (R)p.told.p[b] : PV(R, p0);
+        const R rg = (pg - (R)2 * PV(R, sigma) * kap - pi) * (R)3;
+        const R fo = ld(plane(f, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), fshift<S, D>(p, opp(i)));
+        fi[i] = feq<R, D>(i, rg, uIx, uIy, uIz) + feq<R, D>(opp(i), rg, uIx, uIy, uIz) - fo;
+      }
+    }
+  }
+  // moments and Guo-shifted velocity
+  R rho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    rho += fi[i];
+    jx += fi[i] * (R)Lat<D>::cx(i);
+    jy += fi[i] * (R)Lat<D>::cy(i);
+    jz += fi[i] * (R)Lat<D>::cz(i);
+  }
+  const R ux = (jx + (R)0.5 * rho * PV(R, ax)) / rho;
+  const R uy = (jy + (R)0.5 * rho * PV(R, ay)) / rho;
+  const R uz = (jz + (R)0.5 * rho * PV(R, az)) / rho;
+  relax_store<D, S, PAR>(p, c, n, f, fi, rho, ux, uy, uz, local_tau<D, R>(p, fi, rho, ux, uy, uz));
+
+  R *phi = (R *)p.phi;
+  const R Mn = ((const R *)p.M)[n];
+  const R pho = phi[n];
+  const R phin = Mn / rho;
+  phi[n] = phin;
+  int mk = MK_NONE;
+  if (Mn > ((R)1 + PV(R, eps)) * rho)
+    mk = MK_FILL;
+  else if (Mn < -PV(R, eps) * rho)
+    mk = MK_EMPTY;
+  if (mk) p.flags[n] = (uint8_t)(fl | (mk << 2));
+
+  // dissolved gas (Sec. 3.1-3.2)
+  R gi[QA];
+  R cgas = 0, fl_gas = 0;
+#pragma unroll
+  for (int i = 0; i < QA; ++i) {
+    if (i > 0 && (wallm >> i & 1u)) {
+      gi[i] = ld(plane(g, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), gshift<S, D>(p, opp(i)));
+    } else if (i > 0 && (gasm >> i & 1u)) {
+      const int b = p.label_old[src<D>(p, c, i)];
+      const R cH = PV(R, kH) * (b >= 0 ? (R)p.told.p[b] : PV(R, p0));
+      const R go = ld(plane(g, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), gshift<S, D>(p, opp(i)));
+      gi[i] = (R)2 * (R)Lat<D>::wa(i) * cH - go;
+      fl_gas += go - gi[i];
+    } else {
+      gi[i] = ld(plane(g, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), gshift<S, D>(p, i));
+    }
+    cgas += gi[i];
+  }
+  const R omg = (R)1 / PV(R, taug);
+#pragma unroll
+  for (int i = 0; i < QA; ++i) {
+    const R v = gi[i] + (geq<R, D>(i, cgas, ux, uy, uz) - gi[i]) * omg + (R)Lat<D>::wa(i) * PV(R, q);
+    st(plane(g, p, dir_out<D>(i, 1 - PAR)), cell_out<D>(p, c, i, 1 - PAR), v, gshift<S, D>(p, i));
+  }
+  flux = (double)(fl_gas - cgas * (phin - pho));
+  lab = p.label_old[n];
+  if (lab < 0) atomicAdd(p.led + 5, flux);
+}
+
+// the interface cells of the step, one warp per segment of the segment list
+// and one lane per cell; block 0 also resets the counters of the lists that
+// the conversion fills
+template <int D, class S, int PAR>
+__global__ void __launch_bounds__(128) k_stream_interface(Params p) {
+  __shared__ double wbuf[128];
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int cnt = *p.segcount;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *p.ncount = 0;
+    *p.inext_count = 0;
+    *p.segnext_count = 0;
+    if (p.pf.q != 0.f) atomicAdd(p.fluid_updates, (unsigned long long)*p.icount);
+  }
+  for (int k = warp; k < cnt; k += nwarps) {
+    const int seg = p.seglist[k];
+    Cell c;
+    const bool inr = seg_cell(p, seg, lane, c);
+    const uint8_t fl = inr ? p.flags[c.n] : (uint8_t)T_GAS;
+    double flux = 0.0;
+    int lab = -1;
+    if (ftype(fl) == T_IFC) interface_cell<D, S, PAR>(p, c, c.n, fl, flux, lab);
+    if (lane == 0) p.segflag[seg] = 0;  // free for the conversion's next list
+    if (__any_sync(0xffffffffu, lab >= 0)) agg_add(p.told.dm, lab, flux, wbuf + (threadIdx.x & ~31));
+  }
 }
 
 }  // namespace lbf
