@@ -52,7 +52,7 @@ struct lbf_sim {
   cudaStream_t st2 = nullptr, st3 = nullptr;  // further branches of the step graphs
   int prio_least = 0, prio_greatest = 0;      // stream priority range of the device
   std::vector<cudaGraphNode_t> low_nodes;      // liquid sweeps captured on the third branch
-  cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr}, joinx = nullptr;
+  cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr}, joinx = nullptr, joinex = nullptr;
   Ops *ops = nullptr;
   std::vector<void *> allocs;
   // device state
@@ -60,6 +60,7 @@ struct lbf_sim {
   uint8_t *flags = nullptr;
   int *ilist[2] = {nullptr, nullptr}, *icount[2] = {nullptr, nullptr}, *nlist = nullptr, *ncount = nullptr;
   int *seglist[2] = {nullptr, nullptr}, *segcount[2] = {nullptr, nullptr}, *segflag = nullptr;
+  int *mlist = nullptr, *mcount = nullptr;
   size_t nseg = 0;  // 32-cell segments along x: ceil(nx / 32) per row
   int list_blocks = 0, warp_blocks = 0;
   void *M = nullptr, *phi = nullptr, *uI = nullptr, *kappa = nullptr, *Pi = nullptr, *nrm = nullptr,
@@ -148,6 +149,8 @@ Params make_params(lbf_sim *s, long long step) {
   p.segnext = s->seglist[1 - par];
   p.segnext_count = s->segcount[1 - par];
   p.segflag = s->segflag;
+  p.mlist = s->mlist;
+  p.mcount = s->mcount;
   p.nlist = s->nlist;
   p.ncount = s->ncount;
   p.list_blocks = s->list_blocks;
@@ -251,7 +254,7 @@ void enqueue_geometry(lbf_sim *s, const Params &pn, cudaStream_t st) {
 // beside the disjoining pressure (which needs both the labels and the
 // geometry); with `pnext`, the next step's mass exchange and then its liquid
 // sweep (which need only what the conversion left) run on a third branch
-// beside all of them, signalled by `joinx`
+// beside all of them, signalled by `joinex` and `joinx`
 void enqueue_tail(lbf_sim *s, const Params &p, const Params *pnext, int parnext) {
   const Params pn = next_geometry_params(p);
   cudaEventRecord(s->fork[0], s->st);
@@ -261,6 +264,7 @@ void enqueue_tail(lbf_sim *s, const Params &p, const Params *pnext, int parnext)
   if (pnext) {
     cudaStreamWaitEvent(s->st3, s->fork[0], 0);
     s->ops->exchange(*pnext, parnext, s->st3);
+    cudaEventRecord(s->joinex, s->st3);
     s->ops->stream_liquid(*pnext, parnext, s->st3);
     // the liquid sweep is the branch's last node: remembered so that it can
     // take the lowest priority (the labelling's blocks go first)
@@ -308,12 +312,14 @@ void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
 // k consecutive steps in one graph (parities alternating from par): every
 // step after the first has its mass exchange and its liquid sweep overlap the
 // previous step's labelling, geometry, bubble update and disjoining pressure;
-// its interface sweep waits for those, its conversion for both sweeps
+// its interface sweep waits for those and for its mass exchange, its
+// conversion for both sweeps
 void enqueue_chain(lbf_sim *s, const Params *ps, int par, int k) {
   s->ops->exchange(ps[0], par, s->st);
   s->ops->stream_liquid(ps[0], par, s->st);
   for (int i = 0; i < k; ++i) {
     const int pi = (par + i) & 1;
+    if (i > 0) cudaStreamWaitEvent(s->st, s->joinex, 0);
     s->ops->stream_interface(ps[i], pi, s->st);
     if (i > 0) cudaStreamWaitEvent(s->st, s->joinx, 0);
     s->ops->convert(ps[i], pi, s->st);
@@ -592,6 +598,7 @@ void lbf_destroy(lbf_sim *s) {
     if (s->pin_ev[b]) cudaEventDestroy(s->pin_ev[b]);
   }
   if (s->joinx) cudaEventDestroy(s->joinx);
+  if (s->joinex) cudaEventDestroy(s->joinex);
   if (s->st2) cudaStreamDestroy(s->st2);
   if (s->st3) cudaStreamDestroy(s->st3);
   if (s->own_stream && s->st) cudaStreamDestroy(s->st);
@@ -635,6 +642,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->st2, cudaStreamNonBlocking, s->prio_greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->st3, cudaStreamNonBlocking, s->prio_least);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joinx, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joinex, cudaEventDisableTiming);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
       e = cudaEventCreateWithFlags(&s->fork[k], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join[k], cudaEventDisableTiming);
@@ -678,6 +686,8 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   AL(dalloc(s, &s->segcount[0], 1));
   AL(dalloc(s, &s->segcount[1], 1));
   AL(dalloc(s, &s->segflag, s->nseg));
+  AL(dalloc(s, &s->mlist, N));
+  AL(dalloc(s, &s->mcount, 1));
   AL(dalloc(s, &s->ncount, 1));
   AL(dev_alloc(s, &s->M, N * s->rsz));
   AL(dev_alloc(s, &s->phi, N * s->rsz));
@@ -759,6 +769,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   e = e ? e : zero(s->segcount[0], sizeof(int));
   e = e ? e : zero(s->segcount[1], sizeof(int));
   e = e ? e : zero(s->segflag, sizeof(int) * s->nseg);
+  e = e ? e : zero(s->mcount, sizeof(int));
   e = e ? e : zero(s->hcount, sizeof(int));
   e = e ? e : zero(s->led, 8 * sizeof(double));
   e = e ? e : zero(s->fluid_updates, sizeof(unsigned long long));

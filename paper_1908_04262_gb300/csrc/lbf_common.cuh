@@ -108,6 +108,7 @@ struct Params {
   int *ilist, *icount;   // interface cells at the start of the step
   int *inext, *inext_count;  // interface cells after the conversion
   int *nlist, *ncount;   // gas/liquid cells turning interface this step
+  int *mlist, *mcount;   // interface cells the sweep marked to fill or empty this step
   // 32-cell segments along x that hold interface cells (the interface
   // kernels run one warp per segment, one lane per cell)
   int *seglist, *segcount;       // at the start of the step

@@ -3,7 +3,7 @@
 // the FP64 ledgers.  All kernels run one thread per cell.
 //
 // Conversion (after the sweep has marked interface cells whose fill level
-// left [-eps, 1+eps]):
+// left [-eps, 1+eps] and listed them):
 //   k_conv_mark       an emptying cell next to a filling cell stays interface;
 //                     gas next to a filling cell and liquid next to an
 //                     emptying cell become interface (liquid never meets gas)
@@ -12,9 +12,13 @@
 //                     cells from gas start at the mean equilibrium of their
 //                     interface neighbours; dissolved gas moves between the
 //                     liquid and the cell's bubble
-//   k_conv_apply      interface cells collect the excess and refresh alpha
-// (the relabelling pass then writes the new types and lists the interface
-// cells of the next step)
+//   k_conv_apply      interface cells collect the excess and refresh alpha;
+//                     the interface cells of the next step and their
+//                     segments are listed
+//   k_conv_finalize   the new types replace the marks
+// The first two and the last walk the marked cells and the new interface
+// cells only; k_conv_apply walks the step's interface cells and the new
+// interface cells.
 #pragma once
 #include "lbf_common.cuh"
 
@@ -71,6 +75,13 @@ __device__ __forceinline__ void write_equilibrium(const Params &p, const Cell &c
 // that can fill or empty) and the list of cells they turn into interface;
 // persistent grids, one thread per listed cell
 
+// passes over a short list: entry base + k sits on thread k / gridDim.x of
+// block k % gridDim.x, so that a few hundred entries occupy one thread in as
+// many blocks (and SMs) instead of whole warps of a few
+__device__ __forceinline__ int spread_index(int base) {
+  return base + (int)threadIdx.x * (int)gridDim.x + (int)blockIdx.x;
+}
+
 // set a conversion mark on a neighbour's flag byte; true for the first writer
 __device__ __forceinline__ bool mark_byte(uint8_t *flags, long long m, int mk) {
   const uintptr_t a = (uintptr_t)(flags + m);
@@ -85,23 +96,32 @@ __device__ __forceinline__ bool mark_byte(uint8_t *flags, long long m, int mk) {
 // become interface, so that liquid never meets gas.  The first marker lists
 // the new interface cell.  Filling marks are final when this runs, so an
 // emptying cell decides its own fate without waiting for other threads.
+// The neighbours' flags are loaded up front, the claims issued together and
+// the new interface cells of a warp appended with one atomic.
 template <int D>
-__global__ void k_conv_mark(Params p) {
-  const int cnt = *p.icount;
-  for (int base = blockIdx.x * blockDim.x; base < cnt; base += gridDim.x * blockDim.x) {
-    const int k = base + threadIdx.x;
+__global__ void __launch_bounds__(128) k_conv_mark(Params p) {
+  constexpr int Q = Lat<D>::Q;
+  const int lane = threadIdx.x & 31;
+  const int cnt = *p.mcount;
+  for (int base = 0; base < cnt; base += gridDim.x * blockDim.x) {
+    const int k = spread_index(base);
     int mk = MK_NONE;
-    long long n = 0;
+    int n = 0;
     if (k < cnt) {
-      n = p.ilist[k];
+      n = p.mlist[k];
       mk = fmark(p.flags[n]);
     }
+    unsigned claimed = 0;  // bit i: neighbour x + e_i turned interface by this cell
+    Cell c;
     if (mk == MK_FILL || mk == MK_EMPTY) {
-      const Cell c = make_cell(p, n);
+      c = make_cell(p, n);
+      uint8_t fn[Q];
+#pragma unroll
+      for (int i = 1; i < Q; ++i) fn[i] = p.flags[nb<D>(p, c, i)];
       bool stay = false;
       if (mk == MK_EMPTY) {
 #pragma unroll
-        for (int i = 1; i < Lat<D>::Q; ++i) stay |= fmark(p.flags[nb<D>(p, c, i)]) == MK_FILL;
+        for (int i = 1; i < Q; ++i) stay |= fmark(fn[i]) == MK_FILL;
       }
       if (stay) {
         // clear the emptying mark (mark bits only; other threads read the
@@ -111,32 +131,42 @@ __global__ void k_conv_mark(Params p) {
       } else {
         const int want = mk == MK_FILL ? T_GAS : T_LIQ;
         const int put = mk == MK_FILL ? MK_GI : MK_LI;
-        const bool added = mk == MK_EMPTY;  // this cell turns gas
-        bool removed = false;
 #pragma unroll
-        for (int i = 1; i < Lat<D>::Q; ++i) {
-          const long long m = nb<D>(p, c, i);
-          if (ftype(p.flags[m]) == want && mark_byte(p.flags, m, put)) {
-            const int pos = atomicAdd(p.ncount, 1);
-            p.nlist[pos] = (int)m;
-            removed |= put == MK_GI;  // a gas cell turns interface
-          }
-        }
+        for (int i = 1; i < Q; ++i)
+          if (ftype(fn[i]) == want && mark_byte(p.flags, nb<D>(p, c, i), put)) claimed |= 1u << i;
         if (p.gas_dirty) {
-          if (added) {
+          if (mk == MK_EMPTY) {  // this cell turns gas
             atomicOr(p.gas_dirty, 1);
             if (p.tdirty) p.tdirty[tile_of<D>(p, c)] = 1;
           }
-          if (removed) atomicOr(p.gas_dirty, 2);
+          if (put == MK_GI && claimed) atomicOr(p.gas_dirty, 2);  // gas cells turn interface
         }
       }
+    }
+    // warp-aggregated append of the claimed neighbours
+    const int mine = __popc(claimed);
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) continue;
+    int at = 0;
+    if (lane == 31) at = atomicAdd(p.ncount, total);
+    at = __shfl_sync(0xffffffffu, at, 31) + incl - mine;
+    while (claimed) {
+      const int i = __ffs(claimed) - 1;
+      claimed &= claimed - 1;
+      p.nlist[at++] = nb<D>(p, c, i);
     }
   }
 }
 
-// cell n of the interface list or of the new-interface list
-__device__ __forceinline__ long long list_cell(const Params &p, int k, int ni) {
-  return k < ni ? p.ilist[k] : p.nlist[k - ni];
+// cell k of the marked list followed by the new-interface list
+__device__ __forceinline__ long long list_cell(const Params &p, int k, int nm) {
+  return k < nm ? p.mlist[k] : p.nlist[k - nm];
 }
 
 // par: parity of the populations after the sweep
@@ -144,9 +174,9 @@ template <int D, class S>
 __global__ void __launch_bounds__(128) k_conv_compute(Params p, int par) {
   using R = typename ST<S>::R;
   __shared__ double wbuf[128];
-  const int ni = *p.icount, total = ni + *p.ncount;
-  for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
-    const int k = base + threadIdx.x;
+  const int ni = *p.mcount, total = ni + *p.ncount;
+  for (int base = 0; base < total; base += gridDim.x * blockDim.x) {
+    const int k = spread_index(base);
     double dmv = 0.0;
     int lab = -1;
     if (k < total) {
@@ -215,74 +245,87 @@ __global__ void __launch_bounds__(128) k_conv_compute(Params p, int par) {
   }
 }
 
-// interface cells after the conversion collect the excess of converting
-// neighbours and refresh their fill level
+// one cell of k_conv_apply: an interface cell after the conversion collects
+// the excess of its converting neighbours and refreshes its fill level
+// (new interface cells always do); filled and emptied cells take alpha 1 / 0.
+// True when the cell is interface after the conversion.
 template <int D, class S>
-__global__ void k_conv_apply(Params p, int par) {
+__device__ __forceinline__ bool apply_cell(const Params &p, const Cell &c, int n, uint8_t fl, int par) {
   using R = typename ST<S>::R;
-  const int ni = *p.icount, total = ni + *p.ncount;
-  FOR_LIST(k, total) {
-    const long long n = list_cell(p, k, ni);
-    const uint8_t fl = p.flags[n];
-    const int pt = post_type(fl);
-    const int mk = fmark(fl);
-    if (pt == T_IFC) {
-      const Cell c = make_cell(p, n);
-      const R *ex = (const R *)p.ex;
-      R *M = (R *)p.M;
-      R recv = 0;
-      bool has = false;
+  const int pt = post_type(fl);
+  const int mk = fmark(fl);
+  if (pt == T_IFC) {
+    const R *ex = (const R *)p.ex;
+    R *M = (R *)p.M;
+    R recv = 0;
+    bool has = false;
 #pragma unroll
-      for (int i = 1; i < Lat<D>::Q; ++i) {
-        const long long m = nb<D>(p, c, i);
-        const int fm = fmark(p.flags[m]);
-        if (fm == MK_FILL || fm == MK_EMPTY) {
-          recv += ex[m];
-          has = true;
-        }
+    for (int i = 1; i < Lat<D>::Q; ++i) {
+      const int m = nb<D>(p, c, i);
+      const int fm = fmark(p.flags[m]);
+      if (fm == MK_FILL || fm == MK_EMPTY) {
+        recv += ex[m];
+        has = true;
       }
-      if (has || mk == MK_GI || mk == MK_LI) {
-        const R Mv = M[n] + recv;
-        M[n] = Mv;
-        ((R *)p.phi)[n] = Mv / sum_out_f<D, S>(p, c, n, par, nullptr);
-      }
-    } else if (mk == MK_FILL) {
-      ((R *)p.phi)[n] = 1;
-      ((R *)p.M)[n] = 0;
-    } else if (mk == MK_EMPTY) {
-      ((R *)p.phi)[n] = 0;
-      ((R *)p.M)[n] = 0;
     }
+    if (has || mk == MK_GI || mk == MK_LI) {
+      const R Mv = M[n] + recv;
+      M[n] = Mv;
+      ((R *)p.phi)[n] = Mv / sum_out_f<D, S>(p, c, n, par, nullptr);
+    }
+  } else if (mk == MK_FILL) {
+    ((R *)p.phi)[n] = 1;
+    ((R *)p.M)[n] = 0;
+  } else if (mk == MK_EMPTY) {
+    ((R *)p.phi)[n] = 0;
+    ((R *)p.M)[n] = 0;
   }
+  return pt == T_IFC;
 }
 
-// the conversion's new types replace the marks, and the interface cells of
-// the next step are listed (every marked cell is on the interface list or on
-// the new-interface list, and so is every interface cell after the
-// conversion); a separate pass because k_conv_apply reads the marks of
-// neighbouring cells
-template <int D>
-__global__ void k_conv_finalize(Params p) {
+// list a segment of the next step once (the interface sweep clears the flag)
+__device__ __forceinline__ void claim_segment(const Params &p, bool take, int seg) {
+  bool first = false;
+  if (take) first = atomicExch(p.segflag + seg, 1) == 0;
+  list_append(p.segnext, p.segnext_count, first, seg);
+}
+
+// the excess collection over the step's interface cells and the new
+// interface cells (one thread each); lists the next step's interface cells
+// and their segments.  Marks stay in the flags until k_conv_finalize:
+// neighbours' marks are read here.
+template <int D, class S>
+__global__ void __launch_bounds__(128) k_conv_apply(Params p, int par) {
+  const int lane = threadIdx.x & 31;
   const int ni = *p.icount, total = ni + *p.ncount;
   for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
     const int k = base + threadIdx.x;
     bool take = false;
     int n = 0;
     if (k < total) {
-      n = (int)list_cell(p, k, ni);
-      const uint8_t fl = p.flags[n];
-      const int t = post_type(fl);
-      if (fmark(fl)) p.flags[n] = (uint8_t)(t | (fl & NEARWALL));
-      take = t == T_IFC;
+      n = k < ni ? p.ilist[k] : p.nlist[k - ni];
+      take = apply_cell<D, S>(p, make_cell(p, n), n, p.flags[n], par);
     }
     list_append(p.inext, p.inext_count, take, n);
-    // the segments of the listed cells, each once: one claim per distinct
-    // segment of the warp, then a flag that the interface sweep clears
+    // one claim per distinct segment of the warp
     const int seg = take ? seg_of(p, n) : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, seg);
-    bool first = false;
-    if (take && (int)(threadIdx.x & 31) == __ffs(peers) - 1) first = atomicExch(p.segflag + seg, 1) == 0;
-    list_append(p.segnext, p.segnext_count, first, seg);
+    claim_segment(p, take && lane == __ffs(peers) - 1, seg);
+  }
+}
+
+// the conversion's new types replace the marks (every marked cell is on the
+// marked list or on the new-interface list); a separate pass because
+// k_conv_apply reads the marks of neighbouring cells
+template <int D>
+__global__ void k_conv_finalize(Params p) {
+  const int nm = *p.mcount, total = nm + *p.ncount;
+  for (int base = 0; base < total; base += gridDim.x * blockDim.x) {
+    const int k = spread_index(base);
+    if (k >= total) continue;
+    const int n = (int)list_cell(p, k, nm);
+    const uint8_t fl = p.flags[n];
+    if (fmark(fl)) p.flags[n] = (uint8_t)(post_type(fl) | (fl & NEARWALL));
   }
 }
 

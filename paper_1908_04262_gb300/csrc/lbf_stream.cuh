@@ -125,6 +125,8 @@ __global__ void __launch_bounds__(128) k_exchange(Params p) {
   const S *f = (const S *)p.f;
   R *M = (R *)p.M;
   const R *phi = (const R *)p.phi;
+  // the step's first kernel: the interface sweep lists marked cells afresh
+  if (blockIdx.x == 0 && threadIdx.x == 0) *p.mcount = 0;
   for (int k = warp; k < cnt; k += nwarps) {
     Cell c;
     if (!seg_cell(p, p.seglist[k], lane, c)) continue;
@@ -334,10 +336,11 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
 
 // an interface cell: streaming, bounce-back, reconstruction from gas
 // neighbours, relaxation, fill level and marks, dissolved gas with Henry's
-// law at gas links; returns the cell's gas current and its bubble label
+// law at gas links; returns the cell's gas current and its bubble label, and
+// its conversion mark
 template <int D, class S, int PAR>
-__device__ __forceinline__ void interface_cell(const Params &p, const Cell &c, long long n, uint8_t fl, double &flux,
-                                               int &lab) {
+__device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, long long n, uint8_t fl, double &flux,
+                                              int &lab) {
   using R = typename ST<S>::R;
   constexpr int Q = Lat<D>::Q, QA = Lat<D>::QA;
   S *f = (S *)p.f;
@@ -434,11 +437,13 @@ __device__ __forceinline__ void interface_cell(const Params &p, const Cell &c, l
   flux = (double)(fl_gas - cgas * (phin - pho));
   lab = p.label_old[n];
   if (lab < 0) atomicAdd(p.led + 5, flux);
+  return mk;
 }
 
 // the interface cells of the step, one warp per segment of the segment list
-// and one lane per cell; block 0 also resets the counters of the lists that
-// the conversion fills
+// and one lane per cell; cells that fill or empty are listed for the
+// conversion.  Block 0 also resets the counters of the lists that the
+// conversion fills.
 template <int D, class S, int PAR>
 __global__ void __launch_bounds__(128) k_stream_interface(Params p) {
   __shared__ double wbuf[128];
@@ -458,9 +463,10 @@ __global__ void __launch_bounds__(128) k_stream_interface(Params p) {
     const bool inr = seg_cell(p, seg, lane, c);
     const uint8_t fl = inr ? p.flags[c.n] : (uint8_t)T_GAS;
     double flux = 0.0;
-    int lab = -1;
-    if (ftype(fl) == T_IFC) interface_cell<D, S, PAR>(p, c, c.n, fl, flux, lab);
+    int lab = -1, mk = MK_NONE;
+    if (ftype(fl) == T_IFC) mk = interface_cell<D, S, PAR>(p, c, c.n, fl, flux, lab);
     if (lane == 0) p.segflag[seg] = 0;  // free for the conversion's next list
+    list_append(p.mlist, p.mcount, mk != MK_NONE, c.n);
     if (__any_sync(0xffffffffu, lab >= 0)) agg_add(p.told.dm, lab, flux, wbuf + (threadIdx.x & ~31));
   }
 }

@@ -67,9 +67,13 @@ def harvest_static_bubbles(radii=HARVEST_RADII, snaps=(150, 300, 450, 600), thet
             done = st
             x = torch.empty((cap, 27), device="cuda")
             y = torch.empty(cap, device="cuda")
-            k = sim.mlp_harvest(x, y)
-            xs.append(x[:k])
-            ys.append(y[:k])
+            cells = torch.empty(cap, dtype=torch.int32, device="cuda")
+            k = sim.mlp_harvest(x, y, cells)
+            # pairs in cell order: the training set does not depend on the
+            # order in which the interface list was built
+            o = torch.argsort(cells[:k].long())
+            xs.append(x[:k][o])
+            ys.append(y[:k][o])
         sim.close()
     return torch.cat(xs), torch.cat(ys)
 
