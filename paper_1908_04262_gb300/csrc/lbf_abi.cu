@@ -52,7 +52,8 @@ struct lbf_sim {
   cudaStream_t st2 = nullptr, st3 = nullptr;  // further branches of the step graphs
   int prio_least = 0, prio_greatest = 0;      // stream priority range of the device
   std::vector<cudaGraphNode_t> low_nodes;      // liquid sweeps captured on the third branch
-  cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr}, joinx = nullptr, joinex = nullptr;
+  cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr}, joinx = nullptr, joinex = nullptr,
+              fin = nullptr;
   Ops *ops = nullptr;
   std::vector<void *> allocs;
   // device state
@@ -250,19 +251,23 @@ void enqueue_geometry(lbf_sim *s, const Params &pn, cudaStream_t st) {
   if (s->mlp_theta) s->ops->mlp_kappa(pn, s->mlp_theta, st);
 }
 
-// after the conversion: the geometry beside the labelling, the bubble update
-// beside the disjoining pressure (which needs both the labels and the
-// geometry); with `pnext`, the next step's mass exchange and then its liquid
-// sweep (which need only what the conversion left) run on a third branch
-// beside all of them, signalled by `joinex` and `joinx`
+// after the conversion's excess collection: the labelling (which reads
+// post-conversion types, marked or not) beside the pass that writes the new
+// types and then the geometry; the bubble update beside the disjoining
+// pressure (which needs both the labels and the geometry); with `pnext`, the
+// next step's mass exchange and then its liquid sweep (which need only what
+// the conversion left) run on a third branch beside all of them, signalled
+// by `joinex` and `joinx`
 void enqueue_tail(lbf_sim *s, const Params &p, const Params *pnext, int parnext) {
   const Params pn = next_geometry_params(p);
   cudaEventRecord(s->fork[0], s->st);
   cudaStreamWaitEvent(s->st2, s->fork[0], 0);
+  s->ops->convert_finalize(p, s->st2);
+  cudaEventRecord(s->fin, s->st2);
   enqueue_geometry(s, pn, s->st2);
   cudaEventRecord(s->join[0], s->st2);
   if (pnext) {
-    cudaStreamWaitEvent(s->st3, s->fork[0], 0);
+    cudaStreamWaitEvent(s->st3, s->fin, 0);
     s->ops->exchange(*pnext, parnext, s->st3);
     cudaEventRecord(s->joinex, s->st3);
     s->ops->stream_liquid(*pnext, parnext, s->st3);
@@ -297,8 +302,11 @@ void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
   group(G_EXCHANGE, [&] { s->ops->exchange(p, par, s->st); });
   group(G_LIQUID, [&] { s->ops->stream_liquid(p, par, s->st); });
   group(G_IFACE, [&] { s->ops->stream_interface(p, par, s->st); });
-  group(G_CONVERT, [&] { s->ops->convert(p, par, s->st); });
   if (ev) {
+    group(G_CONVERT, [&] {
+      s->ops->convert(p, par, s->st);
+      s->ops->convert_finalize(p, s->st);
+    });
     const Params pn = next_geometry_params(p);
     group(G_LABEL, [&] { s->ops->label(p, s->st); });
     group(G_BUBBLE, [&] { s->ops->bubble_update(p, s->st); });
@@ -306,6 +314,7 @@ void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
     group(G_DISJOIN, [&] { s->ops->disjoining(pn, s->st); });
     return;
   }
+  s->ops->convert(p, par, s->st);
   enqueue_tail(s, p, nullptr, 0);
 }
 
@@ -599,6 +608,7 @@ void lbf_destroy(lbf_sim *s) {
   }
   if (s->joinx) cudaEventDestroy(s->joinx);
   if (s->joinex) cudaEventDestroy(s->joinex);
+  if (s->fin) cudaEventDestroy(s->fin);
   if (s->st2) cudaStreamDestroy(s->st2);
   if (s->st3) cudaStreamDestroy(s->st3);
   if (s->own_stream && s->st) cudaStreamDestroy(s->st);
@@ -643,6 +653,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->st3, cudaStreamNonBlocking, s->prio_least);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joinx, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joinex, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fin, cudaEventDisableTiming);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
       e = cudaEventCreateWithFlags(&s->fork[k], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join[k], cudaEventDisableTiming);

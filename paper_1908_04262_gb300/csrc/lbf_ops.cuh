@@ -27,6 +27,9 @@ struct OpsImpl final : Ops {
   using R = typename ST<S>::R;
   static constexpr int B = 256;
 
+  // the root sort holds up to 16384 roots (64 KB) in shared memory
+  OpsImpl() { cudaFuncSetAttribute(k_sort_roots, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * (int)sizeof(int)); }
+
   void init_fill(const Params &p, int par, double h, cudaStream_t s) override {
     k_init_fill<D, S><<<row_grid(p), row_block(p), 0, s>>>(p, par, h);
   }
@@ -76,6 +79,8 @@ struct OpsImpl final : Ops {
     k_conv_mark<D><<<p.list_blocks, 128, 0, s>>>(p);
     k_conv_compute<D, S><<<p.list_blocks, 128, 0, s>>>(p, post);
     k_conv_apply<D, S><<<p.list_blocks, 128, 0, s>>>(p, post);
+  }
+  void convert_finalize(const Params &p, cudaStream_t s) override {
     k_conv_finalize<D><<<p.list_blocks, 128, 0, s>>>(p);
   }
   void label_prep(const Params &p, cudaStream_t s) override {

@@ -22,7 +22,10 @@ struct Ops {
   // the sweep: liquid cells, then interface cells (the two commute)
   virtual void stream_liquid(const Params &p, int par, cudaStream_t s) = 0;
   virtual void stream_interface(const Params &p, int par, cudaStream_t s) = 0;
+  // conversion: marks, excess, collection (convert) and the pass that
+  // writes the new types over the marks (convert_finalize)
   virtual void convert(const Params &p, int par, cudaStream_t s) = 0;
+  virtual void convert_finalize(const Params &p, cudaStream_t s) = 0;
   virtual void label(const Params &p, cudaStream_t s) = 0;
   virtual void label_prep(const Params &p, cudaStream_t s) = 0;
   virtual void bubble_update(const Params &p, cudaStream_t s) = 0;
