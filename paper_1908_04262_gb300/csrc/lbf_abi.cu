@@ -53,7 +53,7 @@ struct lbf_sim {
   int prio_least = 0, prio_greatest = 0;      // stream priority range of the device
   std::vector<cudaGraphNode_t> low_nodes;      // liquid sweeps captured on the third branch
   cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr}, joinx = nullptr, joinex = nullptr,
-              fin = nullptr;
+              fin = nullptr, applied = nullptr;
   Ops *ops = nullptr;
   std::vector<void *> allocs;
   // device state
@@ -251,17 +251,24 @@ void enqueue_geometry(lbf_sim *s, const Params &pn, cudaStream_t st) {
   if (s->mlp_theta) s->ops->mlp_kappa(pn, s->mlp_theta, st);
 }
 
-// after the conversion's excess collection: the labelling (which reads
-// post-conversion types, marked or not) beside the pass that writes the new
-// types and then the geometry; the bubble update beside the disjoining
-// pressure (which needs both the labels and the geometry); with `pnext`, the
-// next step's mass exchange and then its liquid sweep (which need only what
-// the conversion left) run on a third branch beside all of them, signalled
-// by `joinex` and `joinx`
-void enqueue_tail(lbf_sim *s, const Params &p, const Params *pnext, int parnext) {
+// everything of a step after its interface sweep.  The marking runs first;
+// then every cell's post-conversion type is known and the union-find passes
+// start, beside the excess pass (which with `waitx` also waits for the
+// step's liquid sweep on the third branch), the pass that writes the new
+// types and the geometry; the relabelling waits for the excess pass (it
+// reads the fill levels); the bubble update runs beside the disjoining
+// pressure (which needs both the labels and the geometry).  With `pnext`,
+// the next step's mass exchange and then its liquid sweep (which need only
+// what the conversion left) run on the third branch beside all of them,
+// signalled by `joinex` and `joinx`.
+void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const Params *pnext, int parnext) {
   const Params pn = next_geometry_params(p);
+  s->ops->convert_mark(p, s->st);
   cudaEventRecord(s->fork[0], s->st);
   cudaStreamWaitEvent(s->st2, s->fork[0], 0);
+  if (waitx) cudaStreamWaitEvent(s->st2, s->joinx, 0);
+  s->ops->convert_excess(p, par, s->st2);
+  cudaEventRecord(s->applied, s->st2);
   s->ops->convert_finalize(p, s->st2);
   cudaEventRecord(s->fin, s->st2);
   enqueue_geometry(s, pn, s->st2);
@@ -281,7 +288,9 @@ void enqueue_tail(lbf_sim *s, const Params &p, const Params *pnext, int parnext)
       s->low_nodes.insert(s->low_nodes.end(), deps, deps + nd);
     cudaEventRecord(s->joinx, s->st3);
   }
-  s->ops->label(p, s->st);
+  s->ops->label_forest(p, s->st);
+  cudaStreamWaitEvent(s->st, s->applied, 0);
+  s->ops->label_relabel(p, s->st);
   cudaEventRecord(s->fork[1], s->st);
   cudaStreamWaitEvent(s->st2, s->fork[1], 0);
   s->ops->bubble_update(p, s->st2);
@@ -314,15 +323,14 @@ void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
     group(G_DISJOIN, [&] { s->ops->disjoining(pn, s->st); });
     return;
   }
-  s->ops->convert(p, par, s->st);
-  enqueue_tail(s, p, nullptr, 0);
+  enqueue_after_sweep(s, p, par, false, nullptr, 0);
 }
 
 // k consecutive steps in one graph (parities alternating from par): every
 // step after the first has its mass exchange and its liquid sweep overlap the
 // previous step's labelling, geometry, bubble update and disjoining pressure;
 // its interface sweep waits for those and for its mass exchange, its
-// conversion for both sweeps
+// conversion's excess pass for both sweeps
 void enqueue_chain(lbf_sim *s, const Params *ps, int par, int k) {
   s->ops->exchange(ps[0], par, s->st);
   s->ops->stream_liquid(ps[0], par, s->st);
@@ -330,9 +338,7 @@ void enqueue_chain(lbf_sim *s, const Params *ps, int par, int k) {
     const int pi = (par + i) & 1;
     if (i > 0) cudaStreamWaitEvent(s->st, s->joinex, 0);
     s->ops->stream_interface(ps[i], pi, s->st);
-    if (i > 0) cudaStreamWaitEvent(s->st, s->joinx, 0);
-    s->ops->convert(ps[i], pi, s->st);
-    enqueue_tail(s, ps[i], i + 1 < k ? &ps[i + 1] : nullptr, 1 - pi);
+    enqueue_after_sweep(s, ps[i], pi, i > 0, i + 1 < k ? &ps[i + 1] : nullptr, 1 - pi);
   }
 }
 
@@ -609,6 +615,7 @@ void lbf_destroy(lbf_sim *s) {
   if (s->joinx) cudaEventDestroy(s->joinx);
   if (s->joinex) cudaEventDestroy(s->joinex);
   if (s->fin) cudaEventDestroy(s->fin);
+  if (s->applied) cudaEventDestroy(s->applied);
   if (s->st2) cudaStreamDestroy(s->st2);
   if (s->st3) cudaStreamDestroy(s->st3);
   if (s->own_stream && s->st) cudaStreamDestroy(s->st);
@@ -654,6 +661,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joinx, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joinex, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fin, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->applied, cudaEventDisableTiming);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
       e = cudaEventCreateWithFlags(&s->fork[k], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join[k], cudaEventDisableTiming);

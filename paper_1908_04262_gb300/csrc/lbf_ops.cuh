@@ -74,9 +74,9 @@ struct OpsImpl final : Ops {
     else
       k_stream_interface<D, S, 0><<<p.list_blocks, 128, 0, s>>>(p);
   }
-  void convert(const Params &p, int par, cudaStream_t s) override {
+  void convert_mark(const Params &p, cudaStream_t s) override { k_conv_mark<D><<<p.list_blocks, 128, 0, s>>>(p); }
+  void convert_excess(const Params &p, int par, cudaStream_t s) override {
     const int post = 1 - par;
-    k_conv_mark<D><<<p.list_blocks, 128, 0, s>>>(p);
     k_conv_compute<D, S><<<p.list_blocks, 128, 0, s>>>(p, post);
     k_conv_apply<D, S><<<p.list_blocks, 128, 0, s>>>(p, post);
   }
@@ -86,7 +86,7 @@ struct OpsImpl final : Ops {
   void label_prep(const Params &p, cudaStream_t s) override {
     k_label_prep<<<blocks_for(p.cap, B), B, 0, s>>>(p);
   }
-  void label(const Params &p, cudaStream_t s) override {
+  void label_forest(const Params &p, cudaStream_t s) override {
     const dim3 tg((unsigned)((p.nx + Tile<D>::TX - 1) / Tile<D>::TX), (unsigned)((p.ny + Tile<D>::TY - 1) / Tile<D>::TY),
                   (unsigned)((p.nz + Tile<D>::TZ - 1) / Tile<D>::TZ));
     k_uf_local<D><<<tg, TILE_THREADS, 0, s>>>(p);
@@ -95,6 +95,8 @@ struct OpsImpl final : Ops {
     int P = 1;
     while (P < p.cap) P <<= 1;
     k_sort_roots<<<1, 1024, P * sizeof(int), s>>>(p);
+  }
+  void label_relabel(const Params &p, cudaStream_t s) override {
     k_relabel<D, R><<<row_grid(p), row_block(p), 0, s>>>(p);
   }
   void bubble_update(const Params &p, cudaStream_t s) override { k_bubble_update<<<1, 1024, 0, s>>>(p); }

@@ -22,11 +22,24 @@ struct Ops {
   // the sweep: liquid cells, then interface cells (the two commute)
   virtual void stream_liquid(const Params &p, int par, cudaStream_t s) = 0;
   virtual void stream_interface(const Params &p, int par, cudaStream_t s) = 0;
-  // conversion: marks, excess, collection (convert) and the pass that
-  // writes the new types over the marks (convert_finalize)
-  virtual void convert(const Params &p, int par, cudaStream_t s) = 0;
+  // conversion: marks (after which every cell's post-conversion type is
+  // known), excess and its collection, and the pass that writes the new
+  // types over the marks
+  virtual void convert_mark(const Params &p, cudaStream_t s) = 0;
+  virtual void convert_excess(const Params &p, int par, cudaStream_t s) = 0;
   virtual void convert_finalize(const Params &p, cudaStream_t s) = 0;
-  virtual void label(const Params &p, cudaStream_t s) = 0;
+  void convert(const Params &p, int par, cudaStream_t s) {
+    convert_mark(p, s);
+    convert_excess(p, par, s);
+  }
+  // labelling: the union-find forest and sorted roots (post-conversion types
+  // only), then the relabelling (which also reads the fill levels)
+  virtual void label_forest(const Params &p, cudaStream_t s) = 0;
+  virtual void label_relabel(const Params &p, cudaStream_t s) = 0;
+  void label(const Params &p, cudaStream_t s) {
+    label_forest(p, s);
+    label_relabel(p, s);
+  }
   virtual void label_prep(const Params &p, cudaStream_t s) = 0;
   virtual void bubble_update(const Params &p, cudaStream_t s) = 0;
   virtual void geometry(const Params &p, cudaStream_t s) = 0;
