@@ -49,11 +49,11 @@ struct lbf_sim {
   size_t ssz = 0, rsz = 0;
   cudaStream_t st = nullptr;
   bool own_stream = false;
-  cudaStream_t st2 = nullptr, st3 = nullptr;  // further branches of the step graphs
+  cudaStream_t st2 = nullptr, st3 = nullptr, st4 = nullptr;  // further branches of the step graphs
   int prio_least = 0, prio_greatest = 0;      // stream priority range of the device
   std::vector<cudaGraphNode_t> low_nodes;      // liquid sweeps captured on the third branch
   cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr}, joinx = nullptr, joinex = nullptr,
-              fin = nullptr, applied = nullptr;
+              fin = nullptr, applied = nullptr, joink = nullptr;
   Ops *ops = nullptr;
   std::vector<void *> allocs;
   // device state
@@ -255,12 +255,13 @@ void enqueue_geometry(lbf_sim *s, const Params &pn, cudaStream_t st) {
 // then every cell's post-conversion type is known and the union-find passes
 // start, beside the excess pass (which with `waitx` also waits for the
 // step's liquid sweep on the third branch), the pass that writes the new
-// types and the geometry; the relabelling waits for the excess pass (it
-// reads the fill levels); the bubble update runs beside the disjoining
-// pressure (which needs both the labels and the geometry).  With `pnext`,
-// the next step's mass exchange and then its liquid sweep (which need only
-// what the conversion left) run on the third branch beside all of them,
-// signalled by `joinex` and `joinx`.
+// types and the geometry (second branch, the learned curvature after it);
+// the relabelling waits for the excess pass (it reads the fill levels) and
+// the bubble update follows it; the disjoining pressure (labels and the
+// geometry's normals, not the curvature) runs on a fourth branch.  With
+// `pnext`, the next step's mass exchange and then its liquid sweep (which
+// need only what the conversion left) run on the third branch beside all of
+// them, signalled by `joinex` and `joinx`.
 void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const Params *pnext, int parnext) {
   const Params pn = next_geometry_params(p);
   s->ops->convert_mark(p, s->st);
@@ -271,8 +272,10 @@ void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const
   cudaEventRecord(s->applied, s->st2);
   s->ops->convert_finalize(p, s->st2);
   cudaEventRecord(s->fin, s->st2);
-  enqueue_geometry(s, pn, s->st2);
+  s->ops->geometry(pn, s->st2);
   cudaEventRecord(s->join[0], s->st2);
+  if (s->mlp_theta) s->ops->mlp_kappa(pn, s->mlp_theta, s->st2);
+  cudaEventRecord(s->joink, s->st2);
   if (pnext) {
     cudaStreamWaitEvent(s->st3, s->fin, 0);
     s->ops->exchange(*pnext, parnext, s->st3);
@@ -292,12 +295,13 @@ void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const
   cudaStreamWaitEvent(s->st, s->applied, 0);
   s->ops->label_relabel(p, s->st);
   cudaEventRecord(s->fork[1], s->st);
-  cudaStreamWaitEvent(s->st2, s->fork[1], 0);
-  s->ops->bubble_update(p, s->st2);
-  cudaEventRecord(s->join[1], s->st2);
-  cudaStreamWaitEvent(s->st, s->join[0], 0);
-  s->ops->disjoining(pn, s->st);
+  s->ops->bubble_update(p, s->st);
+  cudaStreamWaitEvent(s->st4, s->fork[1], 0);
+  cudaStreamWaitEvent(s->st4, s->join[0], 0);
+  s->ops->disjoining(pn, s->st4);
+  cudaEventRecord(s->join[1], s->st4);
   cudaStreamWaitEvent(s->st, s->join[1], 0);
+  cudaStreamWaitEvent(s->st, s->joink, 0);
 }
 
 // the launch sequence of one step; with `ev` every kernel group runs in
@@ -616,8 +620,10 @@ void lbf_destroy(lbf_sim *s) {
   if (s->joinex) cudaEventDestroy(s->joinex);
   if (s->fin) cudaEventDestroy(s->fin);
   if (s->applied) cudaEventDestroy(s->applied);
+  if (s->joink) cudaEventDestroy(s->joink);
   if (s->st2) cudaStreamDestroy(s->st2);
   if (s->st3) cudaStreamDestroy(s->st3);
+  if (s->st4) cudaStreamDestroy(s->st4);
   if (s->own_stream && s->st) cudaStreamDestroy(s->st);
   delete s->ops;
   delete s;
@@ -658,10 +664,12 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&s->prio_least, &s->prio_greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->st2, cudaStreamNonBlocking, s->prio_greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->st3, cudaStreamNonBlocking, s->prio_least);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->st4, cudaStreamNonBlocking, s->prio_greatest);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joinx, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joinex, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fin, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->applied, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joink, cudaEventDisableTiming);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
       e = cudaEventCreateWithFlags(&s->fork[k], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join[k], cudaEventDisableTiming);

@@ -46,19 +46,29 @@ __global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp_kappa(Params p, const ml
         use[w][lane] = ok;
       }
       __syncwarp();
-      // lane q gathers stencil position q of the 16 cells
-#pragma unroll 4
+      // lane q gathers stencil position q of the 16 cells: every flag and
+      // fill level is loaded before any is used (one round trip, not 16)
+      uint8_t fr[16];
+      R pr[16];
+#pragma unroll
       for (int r = 0; r < 16; ++r) {
-        float a = 0.f;
         const Cell &c = cs[w][r];
+        fr[r] = (uint8_t)T_GAS;
+        pr[r] = (R)0;
         if (c.n >= 0 && lane < 27 && use[w][r]) {
           const int src = mlp::canonical_src(lane, ord[w][r], sgn[w][r]);
           const int m = at(p, c, src % 3 - 1, (src / 3) % 3 - 1, src / 9 - 1);
-          const int tm = ftype(p.flags[m]);
-          if (tm == T_LIQ) a = 1.f;
-          else if (tm == T_IFC) a = fminf(fmaxf((float)phi[m], 0.f), 1.f);
-          else if (tm == T_WALL) use[w][r] = 0;
+          fr[r] = p.flags[m];
+          pr[r] = phi[m];
         }
+      }
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        float a = 0.f;
+        const int tm = ftype(fr[r]);
+        if (tm == T_LIQ) a = 1.f;
+        else if (tm == T_IFC) a = fminf(fmaxf((float)pr[r], 0.f), 1.f);
+        else if (tm == T_WALL) use[w][r] = 0;
         xs[w][r * 32 + lane] = __float2bfloat16_rn(a);
       }
       __syncwarp();
