@@ -254,14 +254,21 @@ void enqueue_geometry(lbf_sim *s, const Params &pn, cudaStream_t st) {
 // everything of a step after its interface sweep.  The marking runs first;
 // then every cell's post-conversion type is known and the union-find passes
 // start, beside the excess pass (which with `waitx` also waits for the
-// step's liquid sweep on the third branch), the pass that writes the new
-// types and the geometry (second branch, the learned curvature after it);
-// the relabelling waits for the excess pass (it reads the fill levels) and
-// the bubble update follows it; the disjoining pressure (labels and the
-// geometry's normals, not the curvature) runs on a fourth branch.  With
-// `pnext`, the next step's mass exchange and then its liquid sweep (which
-// need only what the conversion left) run on the third branch beside all of
-// them, signalled by `joinex` and `joinx`.
+// step's liquid sweep on the third branch) and the geometry (second branch,
+// the learned curvature after it); the pass that writes the new types over
+// the marks runs before the geometry on the second branch, or, with the
+// learned curvature attached (a longer second branch), on the third branch
+// once the excess pass is done, so that the geometry starts at once (the
+// labelling, the geometry, the learned curvature and the disjoining
+// pressure read post-conversion types, marked or not; measured: the early
+// geometry pays with the learned curvature and costs ~4 % without it, as it
+// then only competes with the labelling); the relabelling
+// waits for the excess pass (it reads the fill levels) and the bubble update
+// follows it; the disjoining pressure (labels and the geometry's normals,
+// not the curvature) runs on a fourth branch.  With `pnext`, the next
+// step's mass exchange and then its liquid sweep (which need only what the
+// conversion left) follow on the third branch, signalled by `joinex` and
+// `joinx`.
 void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const Params *pnext, int parnext) {
   const Params pn = next_geometry_params(p);
   s->ops->convert_mark(p, s->st);
@@ -270,14 +277,22 @@ void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const
   if (waitx) cudaStreamWaitEvent(s->st2, s->joinx, 0);
   s->ops->convert_excess(p, par, s->st2);
   cudaEventRecord(s->applied, s->st2);
-  s->ops->convert_finalize(p, s->st2);
-  cudaEventRecord(s->fin, s->st2);
+  const bool early_geometry = s->mlp_theta != nullptr;
+  if (!early_geometry) {
+    s->ops->convert_finalize(p, s->st2);
+    cudaEventRecord(s->fin, s->st2);
+  }
   s->ops->geometry(pn, s->st2);
   cudaEventRecord(s->join[0], s->st2);
   if (s->mlp_theta) s->ops->mlp_kappa(pn, s->mlp_theta, s->st2);
   cudaEventRecord(s->joink, s->st2);
+  if (early_geometry) {
+    cudaStreamWaitEvent(s->st3, s->applied, 0);
+    s->ops->convert_finalize(p, s->st3);
+    cudaEventRecord(s->fin, s->st3);
+  }
   if (pnext) {
-    cudaStreamWaitEvent(s->st3, s->fin, 0);
+    if (!early_geometry) cudaStreamWaitEvent(s->st3, s->fin, 0);
     s->ops->exchange(*pnext, parnext, s->st3);
     cudaEventRecord(s->joinex, s->st3);
     s->ops->stream_liquid(*pnext, parnext, s->st3);
@@ -302,6 +317,7 @@ void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const
   cudaEventRecord(s->join[1], s->st4);
   cudaStreamWaitEvent(s->st, s->join[1], 0);
   cudaStreamWaitEvent(s->st, s->joink, 0);
+  cudaStreamWaitEvent(s->st, s->fin, 0);
 }
 
 // the launch sequence of one step; with `ev` every kernel group runs in

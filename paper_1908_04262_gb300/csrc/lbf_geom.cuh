@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(128) k_geometry(Params p) {
     R a = 0;
     if (mine) {
       const long long m = at(p, c, dx, dy, dz);
-      tm = ftype(p.flags[m]);
+      tm = post_type(p.flags[m]);  // may run while the conversion's marks are replaced
       if (tm == T_LIQ) a = 1;
       else if (tm == T_IFC) {
         a = phi[m];
@@ -344,7 +344,7 @@ __global__ void k_disjoining(Params p) {
     const long long y = at_far(p, c.x + off[0], c.y + off[1], c.z + off[2]);
     const int ly = p.label_new[y];
     if (ly == b) continue;
-    const int ty = ftype(p.flags[y]);
+    const int ty = post_type(p.flags[y]);
     if (ty == T_WALL) break;
     if ((ty == T_IFC || ty == T_GAS) && ly >= 0) {
       const R ny0 = nr[y], ny1 = nr[p.N + y], ny2 = nr[2 * p.N + y];

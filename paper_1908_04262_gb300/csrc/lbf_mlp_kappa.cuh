@@ -58,14 +58,14 @@ __global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp_kappa(Params p, const ml
         if (c.n >= 0 && lane < 27 && use[w][r]) {
           const int src = mlp::canonical_src(lane, ord[w][r], sgn[w][r]);
           const int m = at(p, c, src % 3 - 1, (src / 3) % 3 - 1, src / 9 - 1);
-          fr[r] = p.flags[m];
+          fr[r] = p.flags[m];  // read as post-conversion types below
           pr[r] = phi[m];
         }
       }
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
         float a = 0.f;
-        const int tm = ftype(fr[r]);
+        const int tm = post_type(fr[r]);
         if (tm == T_LIQ) a = 1.f;
         else if (tm == T_IFC) a = fminf(fmaxf((float)pr[r], 0.f), 1.f);
         else if (tm == T_WALL) use[w][r] = 0;
