@@ -1,5 +1,6 @@
 """The workloads at their full sizes, in the launch configuration the
-benchmark times (step graphs of two steps, the library's own stream).
+benchmark times (step graphs in which consecutive steps overlap; a graph of
+two steps for the 128^3 case, the library's own stream).
 
 * 2D 128^2 FP64 and 3D 128^3 FP32: element-wise against the FP64 oracle
   (the oracle runs the whole lattice: 200 steps in 2D, two steps in 3D).
