@@ -62,6 +62,7 @@ class _Config(ctypes.Structure):
         ("walls", ctypes.c_int), ("wall_u", ctypes.c_double * 3),
         ("atmosphere", ctypes.c_int), ("eps", ctypes.c_double),
         ("bubble_capacity", ctypes.c_int),
+        ("collision", ctypes.c_int), ("trt_magic", ctypes.c_double),
     ]
 
 

@@ -278,14 +278,40 @@ static void stream_collide(or_sim *s) {
       tau = s->c.tau;
     }
 
-    /* BGK collision with Guo forcing (Sec. 2 Eq. collision) */
-    for (i = 0; i < Q; ++i) {
-      double F = 0.0;
-      for (d = 0; d < 3; ++d)
-        F += ((s->e[i][d] - u[d]) / (1.0 / 3.0) + edot(s, i, u) * s->e[i][d] / (1.0 / 9.0)) *
-             rho * a[d];
-      F *= (1.0 - 0.5 / tau) * s->w[i];
-      fcn[n * Q + i] = f[i] - (f[i] - feq(s, i, rho, u)) / tau + F;
+    if (s->c.collision == 1) {
+      /* two relaxation times (the collision variant Sec. 2 names besides
+         BGK): the parts of f - f_eq even under e -> -e relax at 1/tau, the
+         odd parts at 1/tau_m with (tau - 1/2)(tau_m - 1/2) = trt_magic; the
+         Guo source splits the same way, each part scaled by
+         (1 - 1/(2 tau)) or (1 - 1/(2 tau_m)) */
+      const double tau_m = 0.5 + s->c.trt_magic / (tau - 0.5);
+      double fe[19], S[19];
+      for (i = 0; i < Q; ++i) {
+        fe[i] = feq(s, i, rho, u);
+        S[i] = 0.0;
+        for (d = 0; d < 3; ++d)
+          S[i] += ((s->e[i][d] - u[d]) / (1.0 / 3.0) + edot(s, i, u) * s->e[i][d] / (1.0 / 9.0)) *
+                  rho * a[d];
+        S[i] *= s->w[i];
+      }
+      for (i = 0; i < Q; ++i) {
+        const int k = s->opp[i];
+        const double fe_even = 0.5 * (fe[i] + fe[k]), fe_odd = 0.5 * (fe[i] - fe[k]);
+        const double f_even = 0.5 * (f[i] + f[k]), f_odd = 0.5 * (f[i] - f[k]);
+        const double S_even = 0.5 * (S[i] + S[k]), S_odd = 0.5 * (S[i] - S[k]);
+        fcn[n * Q + i] = f[i] - (f_even - fe_even) / tau - (f_odd - fe_odd) / tau_m +
+                         (1.0 - 0.5 / tau) * S_even + (1.0 - 0.5 / tau_m) * S_odd;
+      }
+    } else {
+      /* BGK collision with Guo forcing (Sec. 2 Eq. collision) */
+      for (i = 0; i < Q; ++i) {
+        double F = 0.0;
+        for (d = 0; d < 3; ++d)
+          F += ((s->e[i][d] - u[d]) / (1.0 / 3.0) + edot(s, i, u) * s->e[i][d] / (1.0 / 9.0)) *
+               rho * a[d];
+        F *= (1.0 - 0.5 / tau) * s->w[i];
+        fcn[n * Q + i] = f[i] - (f[i] - feq(s, i, rho, u)) / tau + F;
+      }
     }
 
     if (t == IFC) {

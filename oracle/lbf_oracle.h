@@ -37,6 +37,8 @@ typedef struct {
   int atmosphere;            /* 1: gas touching the top interior layer is at p0 */
   double eps;                /* conversion margin on alpha                      */
   int bubble_capacity;
+  int collision;             /* 0 BGK, 1 two relaxation times (TRT)             */
+  double trt_magic;          /* TRT: (tau - 1/2)(tau_minus - 1/2)               */
 } or_config;
 
 typedef struct or_sim or_sim;

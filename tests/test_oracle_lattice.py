@@ -167,3 +167,49 @@ def test_carreau_poiseuille_against_quadrature(oracle_mod):
     shear_thin = exact.max() / (g * (ny - 2) ** 2 / (8 * (t0 - 0.5) / 3))
     assert shear_thin > 1.2  # the rheology really acts in this case
     assert np.max(np.abs(u - exact)) < 0.02 * exact.max()
+
+
+# Two relaxation times (the collision variant Sec. 2 names besides BGK):
+# with the product (tau - 1/2)(tau_m - 1/2) = 3/16 the half-way bounce-back
+# wall sits exactly half-way for every tau, so body-force Poiseuille flow is
+# exact where BGK slips (the test above); with tau_m = tau it is BGK.
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_trt_poiseuille_exact_at_any_tau(oracle_mod, dim):
+    ny, g, tau = 18, 1e-6, 1.2
+    s = oracle_mod.OracleSim(_channel(dim, ny, tau=tau, accel=(g, 0.0, 0.0), collision=1,
+                                      trt_magic=3.0 / 16.0))
+    s.step(25000)
+    nu = (tau - 0.5) / 3.0
+    y = np.arange(1, ny - 1)
+    H = ny - 2
+    exact = g / (2 * nu) * (y - 0.5) * (H + 0.5 - y)
+    u = _poiseuille_profile(s, ny, dim)
+    assert np.max(np.abs(u - exact)) < 1e-9 * exact.max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_trt_with_equal_rates_is_bgk(oracle_mod, dim):
+    """tau_m = tau (trt_magic = (tau - 1/2)^2): the TRT path reproduces the
+    BGK path on a random periodic flow state with a body force to
+    round-off."""
+    rng = np.random.default_rng(7)
+    n = 8
+    nz = 1 if dim == 2 else n
+    base = W.config(nx=n, ny=n, nz=nz, storage="fp64", accel=(2e-5, -1e-5, 0.0), rheo=W.RHEO["newtonian"],
+                    tau=0.9, walls=0)
+    N = n * n * nz
+    t = np.ones(N, np.uint8)
+    rho = 1.0 + 0.005 * rng.standard_normal(N)
+    u = 0.02 * rng.uniform(-1, 1, (N, 3))
+    if dim == 2:
+        u[:, 2] = 0.0
+    runs = []
+    for coll in (0, 1):
+        cfg = dict(base, collision=coll, trt_magic=(0.9 - 0.5) ** 2)
+        s = oracle_mod.OracleSim(cfg)
+        s.set_cells(t, rho, u, np.ones(N), np.zeros(N))
+        s.step(50)
+        runs.append((s.get("rho"), s.get("u")))
+    assert np.max(np.abs(runs[0][0] - runs[1][0])) < 1e-13
+    assert np.max(np.abs(runs[0][1] - runs[1][1])) < 1e-14  # velocities O(1e-3)
