@@ -72,6 +72,14 @@ typedef struct {
                                empty when alpha < -eps (Sec. 2.1)               */
   int bubble_capacity;      /* maximum number of bubbles (<= 16384)             */
   void *stream;             /* cudaStream_t used by every call                  */
+  int collision;            /* 0 BGK (Sec. 2 Eq. collision); 1 two relaxation
+                               times, the variant Sec. 2 names: the parts of
+                               f - f_eq even under e -> -e relax at 1/tau, the
+                               odd parts at 1/tau_m (the dissolved gas stays
+                               BGK)                                             */
+  double trt_magic;         /* collision 1: (tau - 1/2)(tau_m - 1/2) > 0; 3/16
+                               puts half-way bounce-back walls exactly
+                               half-way for every tau                           */
 } lbf_config;
 
 /* one row of the bubble table */

@@ -155,10 +155,12 @@ struct Params {
   // must not touch the FP64 pipe)
   struct PF {
     float tau, rho0, ax, ay, az, rn, rk, rlam, ra, tau0, tau_inf, tau_min, tau_max;
-    float sigma, k_pi, d_max, taug, kH, RT, c0, q, p0, eps, uwx, uwy, uwz;
+    float sigma, k_pi, d_max, taug, kH, RT, c0, q, p0, eps, uwx, uwy, uwz, trt_magic;
   } pf;
   double tau, rho0, ax, ay, az;
   int has_force, rheo;
+  int trt;            // two relaxation times (else BGK)
+  double trt_magic;   // (tau - 1/2)(tau_m - 1/2)
   double rn, rk, rlam, ra, tau0, tau_inf, tau_min, tau_max;
   double sigma, k_pi, d_max, taug, kH, RT, c0, q, p0, eps;
   double uwx, uwy, uwz;

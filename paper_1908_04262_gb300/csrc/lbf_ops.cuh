@@ -62,17 +62,23 @@ struct OpsImpl final : Ops {
     cudaMemsetAsync(p.segcount, 0, sizeof(int), s);
     k_build_ilist<<<row_grid(p), row_block(p), 0, s>>>(p);
   }
+  // (the collision model is a template parameter: the BGK sweep keeps its
+  // registers)
   void stream_liquid(const Params &p, int par, cudaStream_t s) override {
-    if (par)
-      k_stream_liquid<D, S, 1><<<row_grid(p), row_block(p), 0, s>>>(p);
+    const dim3 g = row_grid(p);
+    const int b = row_block(p);
+    if (p.trt)
+      par ? k_stream_liquid<D, S, 1, true><<<g, b, 0, s>>>(p) : k_stream_liquid<D, S, 0, true><<<g, b, 0, s>>>(p);
     else
-      k_stream_liquid<D, S, 0><<<row_grid(p), row_block(p), 0, s>>>(p);
+      par ? k_stream_liquid<D, S, 1, false><<<g, b, 0, s>>>(p) : k_stream_liquid<D, S, 0, false><<<g, b, 0, s>>>(p);
   }
   void stream_interface(const Params &p, int par, cudaStream_t s) override {
-    if (par)
-      k_stream_interface<D, S, 1><<<p.list_blocks, 128, 0, s>>>(p);
+    const int g = p.list_blocks;
+    if (p.trt)
+      par ? k_stream_interface<D, S, 1, true><<<g, 128, 0, s>>>(p) : k_stream_interface<D, S, 0, true><<<g, 128, 0, s>>>(p);
     else
-      k_stream_interface<D, S, 0><<<p.list_blocks, 128, 0, s>>>(p);
+      par ? k_stream_interface<D, S, 1, false><<<g, 128, 0, s>>>(p)
+          : k_stream_interface<D, S, 0, false><<<g, 128, 0, s>>>(p);
   }
   void convert_mark(const Params &p, cudaStream_t s) override { k_conv_mark<D><<<p.list_blocks, 128, 0, s>>>(p); }
   void convert_excess(const Params &p, int par, cudaStream_t s) override {

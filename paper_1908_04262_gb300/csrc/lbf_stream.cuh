@@ -209,8 +209,9 @@ __device__ __forceinline__ R local_tau(const Params &p, const R *fi, R rho, R ux
   return model_tau<R>(p, sqrt(nrm2) / ((R)1.4142135623730951 * rho / (R)3));
 }
 
-// BGK relaxation with Guo forcing of one cell, written to the outgoing slots
-template <int D, class S, int PAR>
+// relaxation with Guo forcing of one cell (BGK, or with TRT two relaxation
+// times), written to the outgoing slots
+template <int D, class S, int PAR, bool TRT>
 __device__ __forceinline__ void relax_store(const Params &p, const Cell &c, long long n, S *f, const typename ST<S>::R *fi,
                                             typename ST<S>::R rho, typename ST<S>::R ux, typename ST<S>::R uy,
                                             typename ST<S>::R uz, typename ST<S>::R tau) {
@@ -218,6 +219,38 @@ __device__ __forceinline__ void relax_store(const Params &p, const Cell &c, long
   constexpr int Q = Lat<D>::Q;
   const R om = (R)1 / tau;
   const R base = (R)1 - (ux * ux + uy * uy + uz * uz) * (R)1.5;
+  if constexpr (TRT) {
+    // two relaxation times: per pair (i, opp(i) = i + 1) the even part of
+    // f - f_eq relaxes at om, the odd part at om_m with
+    // (tau - 1/2)(tau_m - 1/2) = trt_magic; the Guo source
+    // w_i rho [3 (e_i - u).a + 9 (e_i.u)(e_i.a)] splits alike (even part
+    // w_i rho (9 (e.u)(e.a) - 3 u.a), odd part 3 w_i rho e.a), each scaled by
+    // 1 - om/2 or 1 - om_m/2
+    const R om_m = (R)1 / ((R)0.5 + PV(R, trt_magic) / (tau - (R)0.5));
+    const R ax = p.has_force ? PV(R, ax) : (R)0, ay = p.has_force ? PV(R, ay) : (R)0,
+            az = p.has_force ? PV(R, az) : (R)0;
+    const R ua = ux * ax + uy * ay + uz * az;
+    const R ge = ((R)1 - (R)0.5 * om) * rho, go = ((R)1 - (R)0.5 * om_m) * rho;
+    {
+      const R fe = (R)Lat<D>::w(0) * rho * base;
+      const R v = fi[0] - (fi[0] - fe) * om - (R)Lat<D>::w(0) * ge * (R)3 * ua;
+      st(plane(f, p, dir_out<D>(0, 1 - PAR)), cell_out<D>(p, c, 0, 1 - PAR), v, fshift<S, D>(p, 0));
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+      const int k = i + 1;
+      const R w = (R)Lat<D>::w(i);
+      const R eu = (R)Lat<D>::cx(i) * ux + (R)Lat<D>::cy(i) * uy + (R)Lat<D>::cz(i) * uz;
+      const R ea = (R)Lat<D>::cx(i) * ax + (R)Lat<D>::cy(i) * ay + (R)Lat<D>::cz(i) * az;
+      const R fe_even = w * rho * (base + (R)4.5 * eu * eu), fe_odd = w * rho * (R)3 * eu;
+      const R f_even = (R)0.5 * (fi[i] + fi[k]), f_odd = (R)0.5 * (fi[i] - fi[k]);
+      const R even = f_even - (f_even - fe_even) * om + w * ge * ((R)9 * eu * ea - (R)3 * ua);
+      const R odd = f_odd - (f_odd - fe_odd) * om_m + w * go * (R)3 * ea;
+      st(plane(f, p, dir_out<D>(i, 1 - PAR)), cell_out<D>(p, c, i, 1 - PAR), even + odd, fshift<S, D>(p, i));
+      st(plane(f, p, dir_out<D>(k, 1 - PAR)), cell_out<D>(p, c, k, 1 - PAR), even - odd, fshift<S, D>(p, k));
+    }
+    return;
+  }
   if (p.has_force) {
     // Guo forcing: F_i = w_i rho [3 (e_i - u).a + 9 (e_i.u)(e_i.a)]
     const R ax = PV(R, ax), ay = PV(R, ay), az = PV(R, az);
@@ -246,7 +279,7 @@ __device__ __forceinline__ void relax_store(const Params &p, const Cell &c, long
 // a liquid cell: its lattice neighbours are liquid, interface or walls
 // (liquid never touches gas); walls bounce back by reading the cell's own
 // outgoing population from the wall cell's slot
-template <int D, class S, int PAR>
+template <int D, class S, int PAR, bool TRT>
 __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long long n, uint8_t fl, bool wallwarp) {
   using R = typename ST<S>::R;
   constexpr int Q = Lat<D>::Q, QA = Lat<D>::QA;
@@ -305,7 +338,7 @@ __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long
   const R ux = (jx + (R)0.5 * rho * PV(R, ax)) / rho;
   const R uy = (jy + (R)0.5 * rho * PV(R, ay)) / rho;
   const R uz = (jz + (R)0.5 * rho * PV(R, az)) / rho;
-  relax_store<D, S, PAR>(p, c, n, f, fi, rho, ux, uy, uz, local_tau<D, R>(p, fi, rho, ux, uy, uz));
+  relax_store<D, S, PAR, TRT>(p, c, n, f, fi, rho, ux, uy, uz, local_tau<D, R>(p, fi, rho, ux, uy, uz));
   R cg = 0;
 #pragma unroll
   for (int i = 0; i < QA; ++i) cg += gi[i];
@@ -319,7 +352,7 @@ __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long
 
 // the liquid cells of the lattice, one thread per cell along x rows; every
 // warp takes the liquid path (interface cells are k_stream_interface's)
-template <int D, class S, int PAR>
+template <int D, class S, int PAR, bool TRT>
 __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_stream_liquid(Params p) {
   Cell c;
   const bool inr = grid_cell(p, c);
@@ -327,7 +360,7 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
   const uint8_t fl = inr ? p.flags[n] : (uint8_t)T_GAS;
   const bool active = inr && ftype(fl) == T_LIQ;
   const bool wallwarp = __any_sync(0xffffffffu, active && (fl & NEARWALL));
-  if (active) liquid_cell<D, S, PAR>(p, c, n, fl, wallwarp);
+  if (active) liquid_cell<D, S, PAR, TRT>(p, c, n, fl, wallwarp);
   if (p.pf.q != 0.f) {
     const unsigned b = __ballot_sync(0xffffffffu, active);
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(p.fluid_updates, (unsigned long long)__popc(b));
@@ -338,7 +371,7 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
 // neighbours, relaxation, fill level and marks, dissolved gas with Henry's
 // law at gas links; returns the cell's gas current and its bubble label, and
 // its conversion mark
-template <int D, class S, int PAR>
+template <int D, class S, int PAR, bool TRT>
 __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, long long n, uint8_t fl, double &flux,
                                               int &lab) {
   using R = typename ST<S>::R;
@@ -396,7 +429,7 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
   const R ux = (jx + (R)0.5 * rho * PV(R, ax)) / rho;
   const R uy = (jy + (R)0.5 * rho * PV(R, ay)) / rho;
   const R uz = (jz + (R)0.5 * rho * PV(R, az)) / rho;
-  relax_store<D, S, PAR>(p, c, n, f, fi, rho, ux, uy, uz, local_tau<D, R>(p, fi, rho, ux, uy, uz));
+  relax_store<D, S, PAR, TRT>(p, c, n, f, fi, rho, ux, uy, uz, local_tau<D, R>(p, fi, rho, ux, uy, uz));
 
   R *phi = (R *)p.phi;
   const R Mn = ((const R *)p.M)[n];
@@ -444,7 +477,7 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
 // and one lane per cell; cells that fill or empty are listed for the
 // conversion.  Block 0 also resets the counters of the lists that the
 // conversion fills.
-template <int D, class S, int PAR>
+template <int D, class S, int PAR, bool TRT>
 __global__ void __launch_bounds__(128) k_stream_interface(Params p) {
   __shared__ double wbuf[128];
   const int lane = threadIdx.x & 31;
@@ -464,7 +497,7 @@ __global__ void __launch_bounds__(128) k_stream_interface(Params p) {
     const uint8_t fl = inr ? p.flags[c.n] : (uint8_t)T_GAS;
     double flux = 0.0;
     int lab = -1, mk = MK_NONE;
-    if (ftype(fl) == T_IFC) mk = interface_cell<D, S, PAR>(p, c, c.n, fl, flux, lab);
+    if (ftype(fl) == T_IFC) mk = interface_cell<D, S, PAR, TRT>(p, c, c.n, fl, flux, lab);
     if (lane == 0) p.segflag[seg] = 0;  // free for the conversion's next list
     list_append(p.mlist, p.mcount, mk != MK_NONE, c.n);
     if (__any_sync(0xffffffffu, lab >= 0)) agg_add(p.told.dm, lab, flux, wbuf + (threadIdx.x & ~31));

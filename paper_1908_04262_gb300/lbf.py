@@ -48,6 +48,7 @@ class Config(ctypes.Structure):
         ("atmosphere", ctypes.c_int), ("eps", ctypes.c_double),
         ("bubble_capacity", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("collision", ctypes.c_int), ("trt_magic", ctypes.c_double),
     ]
 
 
