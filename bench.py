@@ -109,9 +109,9 @@ def stop_clocks(proc, path):
 # DRAM bytes (read + write) per launch of the FP32 liquid sweep on this
 # workload, mean of the two parities, from profiles/k_stream_liquid_128cube_fp32.md,
 # valid while the sweep's sources are the ones that were profiled
-SWEEP_TRAFFIC_BYTES = 265.2e6
+SWEEP_TRAFFIC_BYTES = 263.1e6
 SWEEP_SOURCES = ("paper_1908_04262_gb300/csrc/lbf_stream.cuh", "paper_1908_04262_gb300/csrc/lbf_common.cuh")
-SWEEP_SOURCES_SHA256_16 = "cc0ec90be3110eb2"
+SWEEP_SOURCES_SHA256_16 = "bd7cfcb32b41df6b"
 
 
 def sweep_traffic():
