@@ -162,6 +162,24 @@ int lbf_fields(lbf_sim *s, unsigned mask, void *const *dst, int dst_is_device, i
  * Returns LBF_ENONFINITE when [7] > 0. */
 int lbf_ledger(lbf_sim *s, double *out8);
 
+/* Checkpoint and resume (the paper has no counterpart; its Palabos base
+ * writes checkpoints of its own).  A checkpoint holds every device array the
+ * sim made at creation (populations, flags, masses, fill levels, geometry,
+ * labels, union-find forest, bubble tables, lists, ledgers), the step count
+ * and the nuclei still queued: loading it into a sim created with the same
+ * configuration (and with the learned curvature attached alike) resumes the
+ * run where it was saved.
+ * lbf_checkpoint_bytes: *bytes = size of the checkpoint.
+ * lbf_checkpoint_save: writes it to host memory dst (bytes >= that size);
+ *   synchronises.  Errors: LBF_EINVAL, LBF_ECUDA.
+ * lbf_checkpoint_load: restores from host memory src (bytes long);
+ *   synchronises.  Errors: LBF_EINVAL (not a checkpoint, too short, another
+ *   lattice or storage, the learned curvature attached differently),
+ *   LBF_ECUDA. */
+int lbf_checkpoint_bytes(lbf_sim *s, size_t *bytes);
+int lbf_checkpoint_save(lbf_sim *s, void *dst, size_t bytes);
+int lbf_checkpoint_load(lbf_sim *s, const void *src, size_t bytes);
+
 /* Kernel timing for measurements: while enabled, lbf_step replays a second
  * CUDA graph of the same step in which every kernel group is bracketed by
  * CUDA event records on cfg.stream, and synchronises after each step to read

@@ -56,6 +56,8 @@ struct lbf_sim {
               fin = nullptr, applied = nullptr, joink = nullptr;
   Ops *ops = nullptr;
   std::vector<void *> allocs;
+  std::vector<size_t> alloc_bytes;  // sizes of allocs, in order
+  size_t n_state_allocs = 0;        // the arrays made at creation (the checkpoint)
   // device state
   void *f = nullptr, *g = nullptr;
   uint8_t *flags = nullptr;
@@ -122,6 +124,7 @@ int dev_alloc(lbf_sim *s, void **p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) return fail(LBF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   s->allocs.push_back(*p);
+  s->alloc_bytes.push_back(bytes);
   return 0;
 }
 
@@ -843,6 +846,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     lbf_destroy(s);
     return fail(rc, msg);
   }
+  s->n_state_allocs = s->allocs.size();
   *out = s;
   return 0;
 }
@@ -941,6 +945,17 @@ int lbf_mlp_harvest(lbf_sim *s, float *x, float *y, int *cells, int cap, int *co
   return 0;
 }
 
+// the captured step graphs, rebuilt on the next step
+static void drop_graphs(lbf_sim *s) {
+  for (int k = 0; k < 2; ++k) {
+    if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
+    if (s->tgraph[k]) cudaGraphExecDestroy(s->tgraph[k]);
+    if (s->graph2[k]) cudaGraphExecDestroy(s->graph2[k]);
+    if (s->graph4[k]) cudaGraphExecDestroy(s->graph4[k]);
+    s->graph[k] = s->tgraph[k] = s->graph2[k] = s->graph4[k] = nullptr;
+  }
+}
+
 int lbf_mlp_attach(lbf_sim *s, const float *theta) {
   if (!s) return fail(LBF_EINVAL, "NULL sim");
   if (theta && s->dim != 3) return fail(LBF_EINVAL, "the learned curvature is three-dimensional");
@@ -962,13 +977,96 @@ int lbf_mlp_attach(lbf_sim *s, const float *theta) {
     s->mlp_theta = nullptr;  // the buffer stays owned by the sim until destroy
   }
   // the step graphs change shape
-  for (int k = 0; k < 2; ++k) {
-    if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
-    if (s->tgraph[k]) cudaGraphExecDestroy(s->tgraph[k]);
-    if (s->graph2[k]) cudaGraphExecDestroy(s->graph2[k]);
-    if (s->graph4[k]) cudaGraphExecDestroy(s->graph4[k]);
-    s->graph[k] = s->tgraph[k] = s->graph2[k] = s->graph4[k] = nullptr;
+  drop_graphs(s);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint: every device array made at creation, the step count and the
+// queued nuclei, after a header; restored into a sim of the same layout
+
+namespace {
+struct CkptHeader {
+  unsigned long long magic;
+  long long step, n_arrays, n_queue;
+  int mlp_attached, dim;
+};
+constexpr unsigned long long kCkptMagic = 0x3154504b4346424cull;  // "LBFCKPT1"
+
+size_t ckpt_bytes(const lbf_sim *s) {
+  size_t b = sizeof(CkptHeader) + s->n_state_allocs * sizeof(unsigned long long) + s->queue.size() * sizeof(Nucleus);
+  for (size_t k = 0; k < s->n_state_allocs; ++k) b += s->alloc_bytes[k];
+  return b;
+}
+}  // namespace
+
+int lbf_checkpoint_bytes(lbf_sim *s, size_t *bytes) {
+  if (!s || !bytes) return fail(LBF_EINVAL, "NULL argument");
+  *bytes = ckpt_bytes(s);
+  return 0;
+}
+
+int lbf_checkpoint_save(lbf_sim *s, void *dst, size_t bytes) {
+  if (!s || !dst) return fail(LBF_EINVAL, "NULL argument");
+  if (bytes < ckpt_bytes(s)) return fail(LBF_EINVAL, "buffer smaller than lbf_checkpoint_bytes");
+  CK(cudaStreamSynchronize(s->st));
+  unsigned char *o = (unsigned char *)dst;
+  CkptHeader h;
+  std::memset(&h, 0, sizeof h);
+  h.magic = kCkptMagic;
+  h.step = s->step;
+  h.n_arrays = (long long)s->n_state_allocs;
+  h.n_queue = (long long)s->queue.size();
+  h.mlp_attached = s->mlp_theta != nullptr;
+  h.dim = s->dim;
+  std::memcpy(o, &h, sizeof h);
+  o += sizeof h;
+  for (size_t k = 0; k < s->n_state_allocs; ++k) {
+    const unsigned long long b = s->alloc_bytes[k];
+    std::memcpy(o, &b, sizeof b);
+    o += sizeof b;
   }
+  if (!s->queue.empty()) std::memcpy(o, s->queue.data(), s->queue.size() * sizeof(Nucleus));
+  o += s->queue.size() * sizeof(Nucleus);
+  for (size_t k = 0; k < s->n_state_allocs; ++k) {
+    CK(cudaMemcpy(o, s->allocs[k], s->alloc_bytes[k], cudaMemcpyDeviceToHost));
+    o += s->alloc_bytes[k];
+  }
+  return 0;
+}
+
+int lbf_checkpoint_load(lbf_sim *s, const void *src, size_t bytes) {
+  if (!s || !src) return fail(LBF_EINVAL, "NULL argument");
+  const unsigned char *i = (const unsigned char *)src;
+  CkptHeader h;
+  if (bytes < sizeof h) return fail(LBF_EINVAL, "checkpoint too short");
+  std::memcpy(&h, i, sizeof h);
+  i += sizeof h;
+  if (h.magic != kCkptMagic) return fail(LBF_EINVAL, "not a checkpoint");
+  if (h.dim != s->dim || h.n_arrays != (long long)s->n_state_allocs || h.n_queue < 0)
+    return fail(LBF_EINVAL, "checkpoint of a sim with another layout");
+  if ((h.mlp_attached != 0) != (s->mlp_theta != nullptr))
+    return fail(LBF_EINVAL, "attach the learned curvature alike before loading");
+  size_t need = sizeof h + s->n_state_allocs * sizeof(unsigned long long) + (size_t)h.n_queue * sizeof(Nucleus);
+  for (size_t k = 0; k < s->n_state_allocs; ++k) {
+    unsigned long long b;
+    std::memcpy(&b, i + k * sizeof b, sizeof b);
+    if (b != s->alloc_bytes[k]) return fail(LBF_EINVAL, "checkpoint of a sim with another layout");
+    need += b;
+  }
+  if (bytes < need) return fail(LBF_EINVAL, "checkpoint too short");
+  i += s->n_state_allocs * sizeof(unsigned long long);
+  std::vector<Nucleus> q((size_t)h.n_queue);
+  if (h.n_queue) std::memcpy(q.data(), i, q.size() * sizeof(Nucleus));
+  i += q.size() * sizeof(Nucleus);
+  CK(cudaStreamSynchronize(s->st));
+  for (size_t k = 0; k < s->n_state_allocs; ++k) {
+    CK(cudaMemcpy(s->allocs[k], i, s->alloc_bytes[k], cudaMemcpyHostToDevice));
+    i += s->alloc_bytes[k];
+  }
+  s->step = h.step;
+  s->queue.swap(q);
+  drop_graphs(s);
   return 0;
 }
 

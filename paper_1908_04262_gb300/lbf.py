@@ -69,7 +69,8 @@ EXPORTS = ("lbf_create", "lbf_destroy", "lbf_nucleate", "lbf_set_cells", "lbf_st
            "lbf_bubbles", "lbf_fields", "lbf_ledger", "lbf_timing_enable", "lbf_timing_read",
            "lbf_timing_name", "lbf_cell_counts", "lbf_step_count", "lbf_last_error",
            "lbf_label_gas_noalloc", "lbf_mlp_forward", "lbf_mlp_loss_grad", "lbf_mlp_generate",
-           "lbf_mlp_stencils_from_params", "lbf_mlp_train", "lbf_mlp_harvest", "lbf_mlp_attach")
+           "lbf_mlp_stencils_from_params", "lbf_mlp_train", "lbf_mlp_harvest", "lbf_mlp_attach",
+           "lbf_checkpoint_bytes", "lbf_checkpoint_save", "lbf_checkpoint_load")
 
 MLP_NPARAM = 6017
 
@@ -111,6 +112,9 @@ def load(path: str = LIB_PATH):
     lib.lbf_mlp_train.argtypes = [ctypes.POINTER(MlpTrainCfg), P, P]
     lib.lbf_mlp_attach.argtypes = [P, P]
     lib.lbf_mlp_harvest.argtypes = [P, P, P, P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.lbf_checkpoint_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.lbf_checkpoint_save.argtypes = [P, P, ctypes.c_size_t]
+    lib.lbf_checkpoint_load.argtypes = [P, P, ctypes.c_size_t]
     _lib = lib
     return lib
 
@@ -284,6 +288,20 @@ class Sim:
             ptrs[i] = tensors[k].data_ptr()
             mask |= 1 << FIELD_BITS[k]
         self._check(self.lib.lbf_fields(self.h, mask, ctypes.cast(ptrs, ctypes.c_void_p), 1, dtype_code))
+
+    def checkpoint(self) -> np.ndarray:
+        """The whole simulation state as a host byte array (``lbf_checkpoint_save``)."""
+        n = ctypes.c_size_t()
+        self._check(self.lib.lbf_checkpoint_bytes(self.h, ctypes.byref(n)))
+        buf = np.empty(n.value, np.uint8)
+        self._check(self.lib.lbf_checkpoint_save(self.h, _p(buf), buf.nbytes))
+        return buf
+
+    def restore(self, buf: np.ndarray):
+        """Resume from a checkpoint of a sim with the same configuration
+        (``lbf_checkpoint_load``)."""
+        buf = np.ascontiguousarray(buf, np.uint8)
+        self._check(self.lib.lbf_checkpoint_load(self.h, _p(buf), buf.nbytes))
 
     def ledger(self) -> np.ndarray:
         out = np.zeros(8)
