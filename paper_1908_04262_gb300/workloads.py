@@ -286,3 +286,17 @@ def foam_2d_crop(seed=DEFAULT_SEED, storage="fp64", drainage=False):
     pts, rad = poisson_disk(rng, 6, (2.0, 2.0), (62.0, h - 4.0), 12.0, 3.0, 3.0)
     return cfg, as3(pts), rad
 
+
+def dissolution_2d(seed=DEFAULT_SEED, storage="fp64"):
+    """Dissolution of a bubble into a liquid without dissolved gas (Sec. 4.3,
+    the dissolution figure): tau 0.98, tau_g 0.8 (D = 0.1 on D2Q5), c0 0,
+    kH 5e-3, gamma 4.2e-3, no disjoining pressure, no gravity; 48 x 64 cells
+    with walls, free surface at y = 52, one bubble of radius 8.  RT = 5: the
+    printed RT = 500 drives the oracle's bubble pressure to NaN within 500
+    steps (the gas mass of a bubble in Laplace equilibrium is p V / RT)."""
+    cfg = config(nx=48, ny=64, nz=1, storage=storage, tau=0.98, D=0.1, kH=5e-3, RT=5.0, c0=0.0,
+                 k_pi=0.0, sigma=4.2e-3, fill_height=52.0, walls=0xF)
+    rng = np.random.default_rng(seed)
+    c = np.array([[24.0, 26.0, 0.0]]) + np.concatenate([rng.uniform(-0.5, 0.5, (1, 2)), np.zeros((1, 1))], 1)
+    return cfg, c, np.array([8.0])
+
