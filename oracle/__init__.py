@@ -92,6 +92,7 @@ def _load():
         lib.or_debug_relabel.argtypes = [P]
         lib.or_plic_liquid_fraction.restype = ctypes.c_double
         lib.or_plic_liquid_fraction.argtypes = [ctypes.c_int, dp, ctypes.c_double]
+        lib.or_hf_curvature.argtypes = [P, P]
         lib.or_plic_offset.restype = ctypes.c_double
         lib.or_plic_offset.argtypes = [ctypes.c_int, dp, ctypes.c_double]
         _lib = lib
@@ -160,6 +161,13 @@ class OracleSim:
         out = np.zeros(self.N * width, dtype=np.float64)
         self._check(self.lib.or_get(self.h, FIELDS[name], _ptr(out)))
         return out.reshape(self.N, width) if width > 1 else out
+
+    def hf_curvature(self) -> np.ndarray:
+        """Height-function curvature of the interface cells (0 elsewhere,
+        NaN where a column meets a wall)."""
+        out = np.zeros(self.N, dtype=np.float64)
+        self._check(self.lib.or_hf_curvature(self.h, _ptr(out)))
+        return out
 
     def types(self) -> np.ndarray:
         out = np.zeros(self.N, dtype=np.uint8)

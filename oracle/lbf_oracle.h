@@ -73,6 +73,15 @@ int or_bubbles(const or_sim *s, int32_t *id, int64_t *root, double *vol,
  * the source term, [7] non-finite population count */
 int or_ledger(const or_sim *s, double *out8);
 
+/* Height-function curvature of every interface cell (the second classical
+ * curvature Sec. 2.2 names besides the smoothed gradient): columns of
+ * 7 cells along the dominant axis of the cell's geometry normal, 3 (2D) or
+ * 3 x 3 (3D) of them around the cell, summed fill levels as heights,
+ * centred differences; same sign and scale as the least-squares kappa
+ * (1/(2R) on a gas disk, 1/R on a gas sphere).  out[n] = 0 for other cells,
+ * NaN where a column meets a wall or the normal is zero. */
+int or_hf_curvature(const or_sim *s, double *out);
+
 /* test hooks for the merge/split pins */
 int or_debug_set_types(or_sim *s, const uint8_t *type);
 int or_debug_relabel(or_sim *s);
