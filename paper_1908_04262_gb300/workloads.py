@@ -102,6 +102,73 @@ def poisson_disk(rng, n, box_lo, box_hi, min_dist, rmin, rmax, max_tries=2000000
     return np.array(pts), np.array(rad)
 
 
+def nuclei_from_field(rng, n, prob, radius, min_gap=1.0, max_tries=2000000):
+    """Nucleation sites drawn from a nucleation probability field (Sec. 3.4:
+    a field on the lattice gives the distribution, and optionally the
+    radius, of the nuclei) by dart throwing: a candidate cell is drawn with
+    probability proportional to ``prob`` (an array shaped like the lattice,
+    (ny, nx) or (nz, ny, nx)), the site uniformly inside it; a candidate is
+    kept when it lies at least r_new + r_old + min_gap from every kept site,
+    so that the spheres (disks) neither overlap nor touch.  ``radius`` is a
+    number or an array shaped like ``prob`` (the radius at the candidate's
+    cell).  Returns (n x dim centres, n radii)."""
+    prob = np.asarray(prob, float)
+    dim = prob.ndim
+    w = prob.reshape(-1)
+    if np.any(w < 0) or not np.any(w > 0):
+        raise ValueError("the probability field must be non-negative and not all zero")
+    cdf = np.cumsum(w) / w.sum()
+    rad_field = np.broadcast_to(np.asarray(radius, float), prob.shape).reshape(-1)
+    shape_xyz = prob.shape[::-1]  # (nx, ny[, nz])
+    pts, rad = [], []
+    tries = 0
+    while len(pts) < n and tries < max_tries:
+        tries += 1
+        cell = int(np.searchsorted(cdf, rng.random(), side="right"))
+        cell = min(cell, w.size - 1)
+        idx = np.unravel_index(cell, prob.shape)[::-1]  # (x, y[, z])
+        p = np.asarray(idx, float) + rng.random(dim) - 0.5
+        r = float(rad_field[cell])
+        if any(np.linalg.norm(p - q) < r + rq + min_gap for q, rq in zip(pts, rad)):
+            continue
+        if np.any(p - r < 0.5) or np.any(p + r > np.asarray(shape_xyz) - 1.5):
+            continue  # keep the nucleus off the lattice's faces
+        pts.append(p)
+        rad.append(r)
+    if len(pts) < n:
+        raise RuntimeError("nuclei_from_field placed %d of %d" % (len(pts), n))
+    return np.array(pts), np.array(rad)
+
+
+def nuclei_organised(box_lo, box_hi, spacing, radius, hexagonal=False):
+    """Nucleation sites in an organised arrangement (Sec. 3.4): a square
+    (cubic) lattice of the given spacing filling the box, or in 2D a
+    hexagonal one (every other row shifted by half a spacing, rows
+    spacing * sqrt(3)/2 apart).  Returns (centres, radii)."""
+    lo, hi = np.asarray(box_lo, float), np.asarray(box_hi, float)
+    dim = lo.size
+    if hexagonal and dim != 2:
+        raise ValueError("the hexagonal arrangement is two-dimensional")
+    pts = []
+    if hexagonal:
+        dy = spacing * math.sqrt(3.0) / 2.0
+        row = 0
+        y = lo[1] + radius
+        while y <= hi[1] - radius + 1e-9:
+            x = lo[0] + radius + (0.5 * spacing if row % 2 else 0.0)
+            while x <= hi[0] - radius + 1e-9:
+                pts.append((x, y))
+                x += spacing
+            y += dy
+            row += 1
+    else:
+        axes = [np.arange(lo[d] + radius, hi[d] - radius + 1e-9, spacing) for d in range(dim)]
+        for p in np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, dim):
+            pts.append(tuple(p))
+    pts = np.array(pts, float).reshape(-1, dim)
+    return pts, np.full(len(pts), float(radius))
+
+
 def as3(pts):
     pts = np.asarray(pts, float)
     if pts.shape[1] == 2:
