@@ -12,6 +12,8 @@ all lattice cells.  Populations (217 MB) exceed the 129 MB L2, so no flush
 is needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+The K steps are timed three times (each region exactly K steps, bracketed
+by a barrier and a synchronise); the median is the reported value.
 Under torchrun each rank runs an independent replica (the step has no
 cross-GPU exchange); value = cells x steps of all ranks / max time.
 """
@@ -107,8 +109,10 @@ def stop_clocks(proc, path):
 # ---------------------------------------------------------------------------
 
 # DRAM bytes (read + write) per launch of the FP32 liquid sweep on this
-# workload, mean of the two parities, from profiles/k_stream_liquid_128cube_fp32.md,
-# valid while the sweep's sources are the ones that were profiled
+# workload, mean of the two parities, from one ncu capture of
+# k_stream_liquid<3,float> under this script's default run (dram__bytes_read.sum
+# + dram__bytes_write.sum), valid while the sweep's sources are the ones that
+# were profiled
 SWEEP_TRAFFIC_BYTES = 263.1e6
 SWEEP_SOURCES = ("paper_1908_04262_gb300/csrc/lbf_stream.cuh", "paper_1908_04262_gb300/csrc/lbf_common.cuh")
 SWEEP_SOURCES_SHA256_16 = "bd7cfcb32b41df6b"
@@ -138,17 +142,29 @@ def bubble_volume(b: dict) -> float:
     return float(sum(v for v, a in zip(b["volume"], b["atm"]) if not a))
 
 
-def timed_steps(sim, stream, steps: int) -> float:
+REPEATS = 3  # timed regions of exactly K steps each; the median is reported
+
+
+def timed_steps(sim, stream, steps: int, world: int = 1) -> list:
+    """Device time (ms) of `steps` steps through lbf_step, REPEATS times:
+    each region is bracketed by a barrier and a device synchronise on both
+    sides and timed with CUDA events on the library's stream (max over
+    ranks).  Every step graph shape was instantiated by the warm-up call."""
     import torch
 
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    sim.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1)
+    out = []
+    for _ in range(REPEATS):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        out.append(reduce_max(e0.elapsed_time(e1), world))
+    return out
 
 
 def static_bubble_laplace(lbf, theta, storage: str, R: float = 5.0, steps: int = 1500, sigma: float = 0.01):
@@ -198,9 +214,11 @@ def forms_comparison(args, lbf, cfg, pts, rad, stream, fp32_line):
         if use:
             sim.mlp_attach(theta)
         sim.step(args.warmup)
-        ms = timed_steps(sim, stream, args.steps)
+        reps = timed_steps(sim, stream, args.steps)
+        ms = statistics.median(reps)
         V = bubble_volume(sim.bubbles())
         out[name] = {"mlups": N * args.steps / (ms / 1e3) / 1e6, "ms_per_step": ms / args.steps,
+                     "repeats_ms_per_step": [r / args.steps for r in reps],
                      "bubble_volume_rel_diff_vs_fp32_plain": V / fp32_line["bubble_volume"] - 1}
         sim.close()
     out["laplace_rel_err_static_bubble_R5"] = {
@@ -318,19 +336,11 @@ def run_ours(args):
     sim.step(args.warmup)
     counts0 = sim.cell_counts()
 
-    # --- timed region: device-resident state, CUDA-graph step ------------
-    barrier(world)
-    torch.cuda.synchronize()
+    # --- timed regions: device-resident state, CUDA-graph steps ----------
     clk = start_clocks(local_rank)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sim.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
+    reps = timed_steps(sim, stream, args.steps, world)
     clocks = stop_clocks(*clk)
-    ms = reduce_max(e0.elapsed_time(e1), world)
+    ms = statistics.median(reps)
     counts1 = sim.cell_counts()
     fp32_volume = bubble_volume(sim.bubbles())
     value = N * args.steps * world / (ms / 1e3) / 1e6
@@ -351,8 +361,8 @@ def run_ours(args):
     total_ms = sum(v[0] for v in groups.values())
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": sweep_traffic(),
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
-                                  "profiles/k_stream_liquid_128cube_fp32.md",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of "
+                                  "k_stream_liquid<3,float> under python bench.py",
                 "kernel": "k_stream_liquid<3,float> (liquid cells of the sweep)",
                 "bytes_per_launch": bytes_sweep, "launch_ms": sweep_ms / sweep_n,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
@@ -393,7 +403,9 @@ def run_ours(args):
     del out
 
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "repeats_ms_per_step": [r / args.steps for r in reps],
+            "repeat_spread": (max(reps) - min(reps)) / ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": N, "seed": W.DEFAULT_SEED,
                        "l2": "inputs larger than L2: 217 MB of populations per replica",

@@ -117,7 +117,11 @@ int lbf_nucleate(lbf_sim *s, int n, const double *centres, const double *radii,
  * 2 interface, 3 wall), rho, u (3 doubles per cell), alpha (fill level of
  * interface cells), c (dissolved gas).  Populations are set to equilibrium;
  * liquid touching gas becomes interface with alpha = 1; every bubble is
- * new (Laplace equilibrium).  Errors: LBF_EINVAL, LBF_ECUDA. */
+ * new (Laplace equilibrium).  The arrays are checked on the device before
+ * they replace anything; a rejected call leaves the state as it was.
+ * Errors: LBF_EINVAL (NULL arrays, a type outside 0..3, rho <= 0 in a liquid
+ * or interface cell), LBF_ENONFINITE (a NaN or infinity in rho, u, alpha or
+ * c), LBF_ECUDA. */
 int lbf_set_cells(lbf_sim *s, const uint8_t *type, const double *rho, const double *u,
                   const double *alpha, const double *c);
 
@@ -125,6 +129,9 @@ int lbf_set_cells(lbf_sim *s, const uint8_t *type, const double *rho, const doub
  * (Sec. 2, 2.1, 2.2, 3.1, 3.2), conversion (Sec. 2.1), labelling and bubble
  * update (Sec. 3.5, Eq. idealgas), curvature and disjoining pressure
  * (Sec. 2.2, 3.3); nuclei due in the interval are carved at their step.
+ * Steps run as CUDA graphs of one, two or four steps; the first call (and
+ * the first after lbf_mlp_attach or lbf_checkpoint_load) captures and
+ * instantiates every graph shape for both parities before any step runs.
  * Synchronises at the end and returns the sticky device error, if any
  * (LBF_ECAPACITY, LBF_ENOTCONV).  Errors: LBF_EINVAL (nsteps < 0). */
 int lbf_step(lbf_sim *s, int nsteps);
@@ -174,7 +181,8 @@ int lbf_ledger(lbf_sim *s, double *out8);
  *   synchronises.  Errors: LBF_EINVAL, LBF_ECUDA.
  * lbf_checkpoint_load: restores from host memory src (bytes long);
  *   synchronises.  Errors: LBF_EINVAL (not a checkpoint, too short, another
- *   lattice or storage, the learned curvature attached differently),
+ *   lattice or storage, the learned curvature attached differently or with
+ *   other parameters -- the header holds a 64-bit FNV-1a hash of them),
  *   LBF_ECUDA. */
 int lbf_checkpoint_bytes(lbf_sim *s, size_t *bytes);
 int lbf_checkpoint_save(lbf_sim *s, void *dst, size_t bytes);
@@ -280,8 +288,10 @@ int lbf_mlp_attach(lbf_sim *s, const float *theta);
  * waiting.  Scratch: one static device array per GPU, held from the first
  * call on that GPU until the process exits, for at most 1,048,576 cells
  * (and 65,536 tiles of 32x8x4 / 32x32 cells); larger lattices return
- * LBF_EINVAL.  The first call on a device looks the array's address up with
- * that device current; make that first call before any stream capture.
+ * LBF_EINVAL.  Each call made outside stream capture looks the array's
+ * address up with the calling thread's device current (so a device reset or
+ * another context never leaves a stale address); make the first call on a
+ * device before any stream capture (LBF_EINVAL otherwise).
  * Every call on a device shares the array: calls that overlap on the GPU
  * (other streams, other threads) race and must be serialised by the caller;
  * each call clears the counters it needs.  No cudaMalloc, cudaFree or

@@ -101,6 +101,7 @@ struct lbf_sim {
   float *mlp_buf = nullptr;    // owned copy of the parameters
   void *mlp_img = nullptr;     // owned packed image
   int *mlp_count = nullptr;    // harvest counter
+  unsigned long long mlp_hash = 0;  // FNV-1a of the attached parameters (0: none)
   int tab_n = 0;
   float tab_lnA0 = 0.f, tab_inv_dlnA = 0.f;
   long long step = 0;
@@ -417,6 +418,8 @@ int capture(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev, cudaGraphExec
   return 0;
 }
 
+int ensure_graph(lbf_sim *s, int k, int par);
+
 int run_one_step(lbf_sim *s) {
   const int par = (int)(s->step & 1);
   Params p = make_params(s, s->step);
@@ -440,25 +443,42 @@ int run_one_step(lbf_sim *s) {
     }
     return 0;
   }
-  if (!s->graph[par]) {
-    int rc = capture(s, p, par, nullptr, &s->graph[par]);
-    if (rc) return rc;
-  }
+  int rc = ensure_graph(s, 1, par);
+  if (rc) return rc;
   CK(cudaGraphLaunch(s->graph[par], s->st));
+  return 0;
+}
+
+// the graph of k = 1, 2 or 4 steps starting at parity par, captured and
+// instantiated if it does not exist yet (the parameters of a step depend on
+// the step number only through its parity)
+int ensure_graph(lbf_sim *s, int k, int par) {
+  cudaGraphExec_t &g = k == 4 ? s->graph4[par] : (k == 2 ? s->graph2[par] : s->graph[par]);
+  if (g) return 0;
+  if (k == 1) return capture(s, make_params(s, par), par, nullptr, &g);
+  Params ps[4];
+  for (int i = 0; i < k; ++i) ps[i] = make_params(s, par + i);
+  return capture_chain(s, ps, par, k, &g);
+}
+
+// every graph shape lbf_step launches, for both parities: made on the first
+// step call (and again after the shapes were dropped) so that no later call
+// pays for a capture or an instantiation in the middle of a run
+int ensure_all_graphs(lbf_sim *s) {
+  for (int k : {4, 2, 1})
+    for (int par = 0; par < 2; ++par) {
+      int rc = ensure_graph(s, k, par);
+      if (rc) return rc;
+    }
   return 0;
 }
 
 // k = 2 or 4 steps as one graph (graphs[k / 4][parity])
 int run_steps(lbf_sim *s, int k) {
   const int par = (int)(s->step & 1);
-  cudaGraphExec_t &g = k == 4 ? s->graph4[par] : s->graph2[par];
-  if (!g) {
-    Params ps[4];
-    for (int i = 0; i < k; ++i) ps[i] = make_params(s, s->step + i);
-    int rc = capture_chain(s, ps, par, k, &g);
-    if (rc) return rc;
-  }
-  CK(cudaGraphLaunch(g, s->st));
+  int rc = ensure_graph(s, k, par);
+  if (rc) return rc;
+  CK(cudaGraphLaunch(k == 4 ? s->graph4[par] : s->graph2[par], s->st));
   return 0;
 }
 
@@ -609,6 +629,28 @@ __global__ void k_pack_bubbles(Table t, unsigned char *out, int rows) {
 void pack_bubbles_launch(const Table &t, unsigned char *out, int rows, cudaStream_t st) {
   const int blocks = rows > 0 ? (rows + 255) / 256 : 1;
   k_pack_bubbles<<<blocks, 256, 0, st>>>(t, out, rows);
+}
+
+// checks a staged lbf_set_cells input before it replaces the state: bit 0 a
+// cell type outside 0..3, bit 1 a non-finite value, bit 2 a density that is
+// not positive in a liquid or interface cell
+__global__ void k_check_cells(const uint8_t *type, const double *rho, const double *u, const double *alpha,
+                              const double *c, long long N, unsigned long long *bad) {
+  unsigned long long b = 0;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+    const int t = type[n];
+    if (t > 3) b |= 1;
+    const double v[6] = {rho[n], u[3 * n], u[3 * n + 1], u[3 * n + 2], alpha[n], c[n]};
+    for (int k = 0; k < 6; ++k)
+      if (!isfinite(v[k])) b |= 2;
+    if ((t == 1 || t == 2) && !(rho[n] > 0.0)) b |= 4;
+  }
+  b = __reduce_or_sync(0xffffffffu, (unsigned)b);
+  if (b && (threadIdx.x & 31) == 0) atomicOr(bad, b);
+}
+void check_cells_launch(const uint8_t *type, const double *rho, const double *u, const double *alpha,
+                        const double *c, long long N, unsigned long long *bad, int blocks, cudaStream_t st) {
+  k_check_cells<<<blocks, 256, 0, st>>>(type, rho, u, alpha, c, N, bad);
 }
 }  // namespace lbf
 
@@ -888,6 +930,21 @@ int lbf_set_cells(lbf_sim *s, const uint8_t *type, const double *rho, const doub
   CK(cudaMemcpyAsync(du, u, 24 * N, cudaMemcpyHostToDevice, s->st));
   CK(cudaMemcpyAsync(da, alpha, 8 * N, cudaMemcpyHostToDevice, s->st));
   CK(cudaMemcpyAsync(dc, c, 8 * N, cudaMemcpyHostToDevice, s->st));
+  // the input is checked before it replaces anything: a rejected call leaves
+  // the state as it was
+  CK(cudaMemsetAsync(s->counts, 0, sizeof(unsigned long long), s->st));
+  lbf::check_cells_launch(dt, drho, du, da, dc, s->N, s->counts, s->list_blocks, s->st);
+  CK(cudaGetLastError());
+  unsigned long long bad = 0;
+  CK(cudaMemcpyAsync(&bad, s->counts, sizeof bad, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  if (bad) {
+    CK(cudaFreeAsync(buf, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    if (bad & 2) return fail(LBF_ENONFINITE, "non-finite value in the cell arrays");
+    if (bad & 1) return fail(LBF_EINVAL, "cell type outside 0..3");
+    return fail(LBF_EINVAL, "density not positive in a liquid or interface cell");
+  }
   const int par = (int)(s->step & 1);
   Params p = make_params(s, s->step);
   s->ops->init_cells(p, par, dt, drho, du, da, dc, s->st);
@@ -902,6 +959,10 @@ int lbf_set_cells(lbf_sim *s, const uint8_t *type, const double *rho, const doub
 
 int lbf_step(lbf_sim *s, int nsteps) {
   if (!s || nsteps < 0) return fail(LBF_EINVAL, "bad arguments");
+  if (nsteps > 0 && !s->timing) {
+    int rc = ensure_all_graphs(s);
+    if (rc) return rc;
+  }
   for (int k = 0; k < nsteps;) {
     int rc = carve_due_nuclei(s);
     if (rc) return rc;
@@ -969,12 +1030,18 @@ int lbf_mlp_attach(lbf_sim *s, const float *theta) {
       if (rc) return rc;
     }
     CK(cudaMemcpyAsync(s->mlp_buf, theta, sizeof(float) * 6017, cudaMemcpyHostToDevice, s->st));
+    // 64-bit FNV-1a of the parameter bytes: identifies the network in checkpoints
+    unsigned long long h = 0xcbf29ce484222325ull;
+    const unsigned char *tb = (const unsigned char *)theta;
+    for (size_t k = 0; k < sizeof(float) * 6017; ++k) h = (h ^ tb[k]) * 0x100000001b3ull;
+    s->mlp_hash = h ? h : 1;
     lbf::mlp::pack_launch(s->mlp_buf, s->mlp_img, s->st);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->st));
     s->mlp_theta = s->mlp_img;
   } else {
     s->mlp_theta = nullptr;  // the buffer stays owned by the sim until destroy
+    s->mlp_hash = 0;
   }
   // the step graphs change shape
   drop_graphs(s);
@@ -990,8 +1057,9 @@ struct CkptHeader {
   unsigned long long magic;
   long long step, n_arrays, n_queue;
   int mlp_attached, dim;
+  unsigned long long mlp_hash;  // FNV-1a of the attached network's parameters, 0 if none
 };
-constexpr unsigned long long kCkptMagic = 0x3154504b4346424cull;  // "LBFCKPT1"
+constexpr unsigned long long kCkptMagic = 0x3254504b4346424cull;  // "LBFCKPT2"
 
 size_t ckpt_bytes(const lbf_sim *s) {
   size_t b = sizeof(CkptHeader) + s->n_state_allocs * sizeof(unsigned long long) + s->queue.size() * sizeof(Nucleus);
@@ -1019,6 +1087,7 @@ int lbf_checkpoint_save(lbf_sim *s, void *dst, size_t bytes) {
   h.n_queue = (long long)s->queue.size();
   h.mlp_attached = s->mlp_theta != nullptr;
   h.dim = s->dim;
+  h.mlp_hash = s->mlp_theta ? s->mlp_hash : 0;
   std::memcpy(o, &h, sizeof h);
   o += sizeof h;
   for (size_t k = 0; k < s->n_state_allocs; ++k) {
@@ -1029,9 +1098,10 @@ int lbf_checkpoint_save(lbf_sim *s, void *dst, size_t bytes) {
   if (!s->queue.empty()) std::memcpy(o, s->queue.data(), s->queue.size() * sizeof(Nucleus));
   o += s->queue.size() * sizeof(Nucleus);
   for (size_t k = 0; k < s->n_state_allocs; ++k) {
-    CK(cudaMemcpy(o, s->allocs[k], s->alloc_bytes[k], cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(o, s->allocs[k], s->alloc_bytes[k], cudaMemcpyDeviceToHost, s->st));
     o += s->alloc_bytes[k];
   }
+  CK(cudaStreamSynchronize(s->st));
   return 0;
 }
 
@@ -1047,23 +1117,33 @@ int lbf_checkpoint_load(lbf_sim *s, const void *src, size_t bytes) {
     return fail(LBF_EINVAL, "checkpoint of a sim with another layout");
   if ((h.mlp_attached != 0) != (s->mlp_theta != nullptr))
     return fail(LBF_EINVAL, "attach the learned curvature alike before loading");
-  size_t need = sizeof h + s->n_state_allocs * sizeof(unsigned long long) + (size_t)h.n_queue * sizeof(Nucleus);
+  if (h.mlp_attached && h.mlp_hash != s->mlp_hash)
+    return fail(LBF_EINVAL, "checkpoint saved with another learned-curvature network");
+  // the size table must lie inside the buffer before it is read
+  const size_t table = s->n_state_allocs * sizeof(unsigned long long);
+  if (bytes - sizeof h < table) return fail(LBF_EINVAL, "checkpoint too short");
+  size_t arrays = 0;
   for (size_t k = 0; k < s->n_state_allocs; ++k) {
     unsigned long long b;
     std::memcpy(&b, i + k * sizeof b, sizeof b);
     if (b != s->alloc_bytes[k]) return fail(LBF_EINVAL, "checkpoint of a sim with another layout");
-    need += b;
+    arrays += b;
   }
-  if (bytes < need) return fail(LBF_EINVAL, "checkpoint too short");
-  i += s->n_state_allocs * sizeof(unsigned long long);
+  i += table;
+  // what is left after the header, the table and the arrays bounds the queue
+  const size_t rest = bytes - sizeof h - table;
+  if (rest < arrays || (unsigned long long)h.n_queue > (rest - arrays) / sizeof(Nucleus))
+    return fail(LBF_EINVAL, "checkpoint too short");
   std::vector<Nucleus> q((size_t)h.n_queue);
   if (h.n_queue) std::memcpy(q.data(), i, q.size() * sizeof(Nucleus));
   i += q.size() * sizeof(Nucleus);
-  CK(cudaStreamSynchronize(s->st));
+  // ordered on the sim's stream (which does not synchronise with the legacy
+  // stream) and complete before the call returns
   for (size_t k = 0; k < s->n_state_allocs; ++k) {
-    CK(cudaMemcpy(s->allocs[k], i, s->alloc_bytes[k], cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(s->allocs[k], i, s->alloc_bytes[k], cudaMemcpyHostToDevice, s->st));
     i += s->alloc_bytes[k];
   }
+  CK(cudaStreamSynchronize(s->st));
   s->step = h.step;
   s->queue.swap(q);
   drop_graphs(s);

@@ -128,12 +128,20 @@ extern "C" int lbf_label_gas_noalloc(const uint8_t *type, int nx, int ny, int nz
   if (tiles > kMaxTiles) return fail(LBF_EINVAL, "more union-find tiles than the static scratch holds (65,536)");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return fail(LBF_ECUDA, "cudaGetDevice failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  // the symbol's device address, looked up with the device current (in host
+  // code g_scratch is only a host-side stand-in).  It is looked up again on
+  // every call made outside stream capture, so that a device reset or another
+  // context on the device never leaves a stale address behind; under capture
+  // the address of the last uncaptured call on this device is used.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return fail(LBF_ECUDA, "cudaStreamIsCapturing failed");
   Scratch *s = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-      // the symbol's device address, looked up once per device with that
-      // device current (in host code g_scratch is only a host-side stand-in)
+    if (cs == cudaStreamCaptureStatusNone || !g_addr[dev]) {
+      if (cs != cudaStreamCaptureStatusNone)
+        return fail(LBF_EINVAL, "the first call on a device must come before any stream capture");
       void *a = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&a, g_scratch);
       if (e != cudaSuccess) return fail(LBF_ECUDA, cudaGetErrorString(e));
@@ -141,6 +149,5 @@ extern "C" int lbf_label_gas_noalloc(const uint8_t *type, int nx, int ny, int nz
     }
     s = g_addr[dev];
   }
-  cudaStream_t st = (cudaStream_t)stream;
   return D == 2 ? run<2>(s, type, nx, ny, nz, label, count, st) : run<3>(s, type, nx, ny, nz, label, count, st);
 }
