@@ -345,10 +345,16 @@ static void stream_collide(or_sim *s) {
       gcn[n * QA + i] = g[i] + (geq(s, i, c, u) - g[i]) / taug + s->wa[i] * s->c.q;
     s->led[6] += s->c.q;
 
-    /* gas flux into the cell's bubble (Sec. 3.1 Eq. gascurrent) */
+    /* gas flux into the cell's bubble (Sec. 3.1 Eq. gascurrent), measured
+     * where it crosses the interface: at the gas links, what the cell sends
+     * into the gas minus what the Henry condition returns.  Only the
+     * diffusive exchange crosses there, so the advective part that the
+     * equation's last term, -c (alpha(t) - alpha(t-1)), deducts from a
+     * liquid-side measure is never in this sum and nothing is deducted;
+     * with the cells that change between gas and interface carrying their
+     * dissolved gas (convert), bubbles plus dissolved gas are conserved. */
     if (t == IFC) {
       const int b = s->label[n];
-      flux -= c * (phin[n] - s->phi[n]);
       if (b >= 0)
         s->bdm[b] += flux;
       else

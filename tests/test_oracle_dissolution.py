@@ -31,7 +31,7 @@ def test_bubble_dissolves_into_gas_free_liquid(oracle_mod):
     assert np.all(np.diff(dissolved) > 0)
     assert V[-1] < 0.9 * V[0]
     # gas is accounted for: dissolved + bubbles + exchanged with the outside
-    # (the headspace also dissolves into the liquid) - source moves by far
-    # less than the gas that changed hands (a moving interface keeps the
-    # per-cell current of Eq. gascurrent from being exact)
-    assert np.max(np.abs(total - total[0])) < 1e-2 * (dissolved[-1] - dissolved[0])
+    # (the headspace also dissolves into the liquid) - source is conserved to
+    # round-off (the flux of Eq. gascurrent is the exchange at the gas links,
+    # and cells changing between gas and interface carry their dissolved gas)
+    assert np.max(np.abs(total - total[0])) < 1e-11 * (dissolved[-1] - dissolved[0])
