@@ -95,6 +95,8 @@ def _load():
         lib.or_hf_curvature.argtypes = [P, P]
         lib.or_plic_offset.restype = ctypes.c_double
         lib.or_plic_offset.argtypes = [ctypes.c_int, dp, ctypes.c_double]
+        lib.or_lsq_kappa.restype = ctypes.c_double
+        lib.or_lsq_kappa.argtypes = [ctypes.c_int, P, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -211,3 +213,10 @@ def plic_offset(dim: int, n, alpha: float) -> float:
     lib = _load()
     a = (ctypes.c_double * 3)(*[float(x) for x in (list(n) + [0.0] * 3)[:3]])
     return lib.or_plic_offset(dim, a, float(alpha))
+
+
+def lsq_kappa(dim: int, pts) -> float:
+    """Least-squares curvature of the given points (n x 3, local frame)."""
+    lib = _load()
+    a = np.ascontiguousarray(np.asarray(pts, dtype=np.float64).reshape(-1, 3))
+    return lib.or_lsq_kappa(dim, _ptr(a), a.shape[0])

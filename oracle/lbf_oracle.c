@@ -862,11 +862,41 @@ static int lsq_fit(const double (*pts)[3], int np, int k, int kind, double *beta
   return solve_small(A, b, k, beta);
 }
 
+/* kappa of the least-squares surface through np points given in the local
+ * frame (t1, t2, m) of the centre cell: 2D z = A x^2 + H x, kappa = minus
+ * the curvature of that curve at 0; 3D z = A x^2 + B y^2 + C xy + H x + I y,
+ * kappa = minus the mean curvature of that surface at 0 (one parameter
+ * fits when there are too few points); limited to [-1, 1] */
+static double kappa_from_points(int dim, const double (*pts)[3], int np) {
+  double beta[5], kap = 0.0;
+  if (dim == 2) {
+    if (np >= 2 && lsq_fit(pts, np, 2, 2, beta))
+      kap = -beta[0] / pow(1.0 + beta[1] * beta[1], 1.5);
+    else if (np >= 1 && lsq_fit(pts, np, 1, 1, beta))
+      kap = -beta[0];
+  } else {
+    if (np >= 5 && lsq_fit(pts, np, 5, 3, beta)) {
+      const double H = beta[3], I = beta[4];
+      kap = -((1.0 + I * I) * beta[0] - H * I * beta[2] + (1.0 + H * H) * beta[1]) /
+            pow(1.0 + H * H + I * I, 1.5);
+    } else if (np >= 1 && lsq_fit(pts, np, 1, 1, beta)) {
+      kap = -2.0 * beta[0];
+    }
+  }
+  return kap < -1.0 ? -1.0 : (kap > 1.0 ? 1.0 : kap);
+}
+
+/* test hook: the curvature of np (<= 27) points, x y z each */
+double or_lsq_kappa(int dim, const double *pts, int np) {
+  if (np < 0 || np > 27) return 0.0;
+  return kappa_from_points(dim, (const double(*)[3])pts, np);
+}
+
 static void normals_curvature(or_sim *s) {
   const int dim = s->dim;
   long n;
   for (n = 0; n < s->N; ++n) {
-    double A[3][3][3], g[3] = {0.0, 0.0, 0.0}, gn, m[3], t1[3], t2[3], pts[27][3], beta[5];
+    double A[3][3][3], g[3] = {0.0, 0.0, 0.0}, gn, m[3], t1[3], t2[3], pts[27][3];
     int act[3][3][3], dx, dy, dz, d, np = 0, kmin;
     s->kappa[n] = 0.0;
     s->dst[n] = 0.0;
@@ -937,24 +967,7 @@ static void normals_curvature(or_sim *s) {
           pts[np][2] = o[0] * m[0] + o[1] * m[1] + o[2] * m[2] + sj - s->dst[n];
           ++np;
         }
-    {
-      double kap = 0.0;
-      if (dim == 2) {
-        if (np >= 2 && lsq_fit((const double(*)[3])pts, np, 2, 2, beta))
-          kap = -beta[0] / pow(1.0 + beta[1] * beta[1], 1.5);
-        else if (np >= 1 && lsq_fit((const double(*)[3])pts, np, 1, 1, beta))
-          kap = -beta[0];
-      } else {
-        if (np >= 5 && lsq_fit((const double(*)[3])pts, np, 5, 3, beta)) {
-          const double H = beta[3], I = beta[4];
-          kap = -((1.0 + I * I) * beta[0] - H * I * beta[2] + (1.0 + H * H) * beta[1]) /
-                pow(1.0 + H * H + I * I, 1.5);
-        } else if (np >= 1 && lsq_fit((const double(*)[3])pts, np, 1, 1, beta)) {
-          kap = -2.0 * beta[0];
-        }
-      }
-      s->kappa[n] = kap < -1.0 ? -1.0 : (kap > 1.0 ? 1.0 : kap);
-    }
+    s->kappa[n] = kappa_from_points(dim, (const double(*)[3])pts, np);
   }
 }
 

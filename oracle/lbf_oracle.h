@@ -89,6 +89,9 @@ int or_debug_relabel(or_sim *s);
 /* geometry helpers exposed for pins */
 double or_plic_liquid_fraction(int dim, const double *n, double s);
 double or_plic_offset(int dim, const double *n, double alpha);
+/* test hook: least-squares curvature of np (<= 27) points (x, y, z in the
+ * local frame of a cell: tangents, then the normal into the liquid) */
+double or_lsq_kappa(int dim, const double *pts, int np);
 
 #ifdef __cplusplus
 }

@@ -166,6 +166,11 @@ def ellipsoid_stencil(centre, axes, rot, gas_inside, cell, sub=6):
         liquid = ~inside if gas_inside else inside
         alpha[q] = np.mean(liquid)
     x = np.asarray(cell, dtype=np.float64) - centre
+    if not np.any(x):
+        # a cell centred on the ellipsoid: the nearest surface points lie
+        # along the shortest axis (the Newton direction is undefined there)
+        k = int(np.argmin(axes))
+        x = rot[:, k] * axes[k]
     for _ in range(8):
         F = x @ A @ x - 1.0
         gF = 2 * A @ x

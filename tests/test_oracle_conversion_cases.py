@@ -1,0 +1,218 @@
+"""Hand-made 2D cases for the oracle's mass exchange (Sec. 2.1 Eq.
+massexchange and its weights Theta) and cell conversion (Sec. 2.1, last
+paragraph: interface cells fill at alpha >= 1 and empty at alpha <= 0, the
+surplus or shortage going in equal parts to neighbouring interface cells).
+
+Every expected value below is worked out by hand from those rules on a 7 x 6
+box (periodic in x, bounce-back walls at y = 0 and y = 5):
+
+    y = 5   W W W W W W W
+    y = 4   G G G G G G G
+    y = 3   I I I I I I I      interface row
+    y = 2   L L L L L L L
+    y = 1   L L L L L L L
+    y = 0   W W W W W W W
+
+Mass conservation alone cannot see a wrong Theta or a wrong conflict rule;
+these cases can.  Cells are written (x, y), index x + 7 y.
+"""
+import numpy as np
+import pytest
+
+from paper_1908_04262_gb300 import workloads as W
+
+NX, NY = 7, 6
+G_, L_, I_, W_ = 0, 1, 2, 3
+# D2Q9 (Sec. 2): velocity vectors and weights
+E = [(0, 0), (1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1), (1, -1), (-1, 1)]
+WT = [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4
+
+
+def idx(x, y):
+    return (x % NX) + NX * y
+
+
+def layout():
+    t = np.full(NX * NY, L_, np.uint8)
+    for x in range(NX):
+        t[idx(x, 0)] = t[idx(x, 5)] = W_
+        t[idx(x, 4)] = G_
+        t[idx(x, 3)] = I_
+    return t
+
+
+def cfg():
+    return W.config(nx=NX, ny=NY, nz=1, storage="fp64", walls=0b1100, atmosphere=0, sigma=0.0, k_pi=0.0,
+                    tau=0.8, rho0=1.0, p0=1.0 / 3.0, RT=1.0, kH=0.0, c0=0.0, eps=1e-3)
+
+
+def run_one_step(oracle_mod, types, rho, u, alpha):
+    s = oracle_mod.OracleSim(cfg())
+    s.set_cells(types, rho, u, alpha, np.zeros(NX * NY))
+    assert np.array_equal(s.types(), types), "the hand-made layout must be kept by set_cells"
+    M0 = s.get("mass").copy()
+    s.step(1)
+    return s, M0
+
+
+def feq(rho, u):
+    """D2Q9 equilibrium (Sec. 2 Eq. equilibrium), all nine directions."""
+    out = np.zeros(9)
+    uu = u[0] * u[0] + u[1] * u[1]
+    for i, (ex, ey) in enumerate(E):
+        eu = ex * u[0] + ey * u[1]
+        out[i] = WT[i] * rho * (1 + 3 * eu + 4.5 * eu * eu - 1.5 * uu)
+    return out
+
+
+def test_mass_exchange_weights_theta(oracle_mod):
+    """Random densities and velocities, fill levels 0.3..0.7 (no conversion),
+    an extra interface cell in the gas row at (1, 4) and an interior wall at
+    (3, 2), so that interface cells see liquid, interface, gas and wall
+    neighbours.  After one step M = alpha rho + sum_i Theta_i
+    (f_ibar(x + e_i) - f_i(x)) with Theta = 1 (liquid), (alpha_x +
+    alpha_nb)/2 (interface), 0 (gas or wall), from the populations the state
+    was set to."""
+    rng = np.random.default_rng(7)
+    t = layout()
+    t[idx(1, 4)] = I_
+    t[idx(3, 2)] = W_
+    N = NX * NY
+    rho = rng.uniform(0.98, 1.02, N)
+    u = rng.uniform(-0.02, 0.02, (N, 2))
+    alpha = np.where(t == I_, rng.uniform(0.3, 0.7, N), 0.0)
+    u3 = np.zeros((N, 3))
+    u3[:, :2] = u
+    s, M0 = run_one_step(oracle_mod, t, rho, u3.reshape(-1), alpha)
+    assert np.array_equal(s.types(), t), "no cell may convert in this case"
+    M1 = s.get("mass")
+    f = {n: feq(rho[n], u[n]) for n in range(N) if t[n] in (L_, I_)}
+    checked = 0
+    for y in range(NY):
+        for x in range(NX):
+            n = idx(x, y)
+            if t[n] != I_:
+                continue
+            dM = 0.0
+            kinds = set()
+            for i in range(1, 9):
+                ex, ey = E[i]
+                m = idx(x + ex, y + ey)
+                ibar = E.index((-ex, -ey))
+                if t[m] == L_:
+                    theta = 1.0
+                elif t[m] == I_:
+                    theta = 0.5 * (alpha[n] + alpha[m])
+                else:
+                    theta = 0.0
+                kinds.add(int(t[m]))
+                if theta:
+                    dM += theta * (f[m][ibar] - f[n][i])
+            assert abs(M0[n] - alpha[n] * rho[n]) < 1e-15
+            assert abs(M1[n] - (M0[n] + dM)) < 1e-14, ((x, y), M1[n], M0[n] + dM)
+            checked += 1
+            if (x, y) == (2, 3):
+                assert kinds == {G_, L_, I_, W_}
+    assert checked == 8
+
+
+def _uniform_case(alpha_of):
+    """rho = 1 and u = 0 everywhere: every exchange term is w_i - w_i = 0, so
+    only the conversion changes the masses."""
+    t = layout()
+    N = NX * NY
+    alpha = np.where(t == I_, 0.5, 0.0)
+    for (x, y), a in alpha_of.items():
+        alpha[idx(x, y)] = a
+    return t, np.ones(N), np.zeros(3 * N), alpha
+
+
+def _check(s, types_expected, mass_expected):
+    ty = s.types()
+    for (x, y), k in types_expected.items():
+        assert ty[idx(x, y)] == k, ((x, y), int(ty[idx(x, y)]), k)
+    M = s.get("mass")
+    for (x, y), m in mass_expected.items():
+        assert abs(M[idx(x, y)] - m) < 1e-13, ((x, y), M[idx(x, y)], m)
+    # liquid never touches gas
+    for n in np.flatnonzero(ty == L_):
+        x, y = n % NX, n // NX
+        for ex, ey in E[1:]:
+            assert ty[idx(x + ex, y + ey)] != G_
+
+
+def test_filling_cell(oracle_mod):
+    """(3, 3) holds 1.3: it becomes liquid; its gas neighbours (2..4, 4)
+    become interface; its surplus 0.3 goes in equal parts (0.06) to the five
+    neighbours that are interface after the conversion -- (2, 3), (4, 3) and
+    the three new ones.  An interface cell buried in liquid at (5, 1) with
+    1.3 fills too; it has no interface neighbour, so its 0.3 goes to the
+    ledger of unplaced mass."""
+    t, rho, u, alpha = _uniform_case({(3, 3): 1.3})
+    t[idx(5, 1)] = I_
+    alpha[idx(5, 1)] = 1.3
+    s, M0 = run_one_step(oracle_mod, t, rho, u, alpha)
+    types = {(3, 3): L_, (2, 4): I_, (3, 4): I_, (4, 4): I_, (1, 4): G_, (5, 4): G_, (5, 1): L_}
+    for x in (0, 1, 2, 4, 5, 6):
+        types[(x, 3)] = I_
+    mass = {(2, 3): 0.56, (4, 3): 0.56, (2, 4): 0.06, (3, 4): 0.06, (4, 4): 0.06,
+            (0, 3): 0.5, (1, 3): 0.5, (5, 3): 0.5, (6, 3): 0.5}
+    _check(s, types, mass)
+    assert abs(s.ledger()[1] - 0.3) < 1e-13
+
+
+def test_emptying_cell(oracle_mod):
+    """(3, 3) holds -0.3: it becomes gas; its liquid neighbours (2..4, 2)
+    become interface with M = rho = 1; its shortage -0.3 is shared by the
+    five neighbours interface after the conversion: (2, 3), (4, 3) -> 0.44,
+    (2..4, 2) -> 0.94."""
+    t, rho, u, alpha = _uniform_case({(3, 3): -0.3})
+    s, M0 = run_one_step(oracle_mod, t, rho, u, alpha)
+    types = {(3, 3): G_, (2, 2): I_, (3, 2): I_, (4, 2): I_, (1, 2): L_, (5, 2): L_}
+    mass = {(2, 3): 0.44, (4, 3): 0.44, (2, 2): 0.94, (3, 2): 0.94, (4, 2): 0.94, (1, 3): 0.5}
+    _check(s, types, mass)
+    assert abs(s.ledger()[1]) < 1e-15
+
+
+def test_filling_wins_over_emptying(oracle_mod):
+    """(3, 3) fills (1.3) next to (4, 3), which would empty (-0.3): filling
+    wins, so (4, 3) stays interface and keeps its mass plus its share of the
+    surplus (-0.3 + 0.06); its liquid neighbours stay liquid; the gas
+    neighbours of the filling cell, (2..4, 4), become interface -- (4, 4)
+    although it also borders the would-be emptying cell -- and (5, 4)
+    stays gas."""
+    t, rho, u, alpha = _uniform_case({(3, 3): 1.3, (4, 3): -0.3})
+    s, M0 = run_one_step(oracle_mod, t, rho, u, alpha)
+    types = {(3, 3): L_, (4, 3): I_, (2, 4): I_, (3, 4): I_, (4, 4): I_, (5, 4): G_,
+             (3, 2): L_, (4, 2): L_, (5, 2): L_}
+    mass = {(4, 3): -0.24, (2, 3): 0.56, (2, 4): 0.06, (3, 4): 0.06, (4, 4): 0.06, (5, 3): 0.5}
+    _check(s, types, mass)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_least_squares_curvature_of_exact_quadrics(oracle_mod, dim):
+    """The least-squares fit of the curvature (Sec. 2.2 Eq. rhob, the
+    paraboloid reading) on points that lie exactly on a quadric with a tilt:
+    its result is minus the mean curvature at the origin, computed here from
+    the first and second fundamental forms; the ridge 1e-3 added to the
+    normal equations biases it by less than 0.2 % of |kappa| + 1e-4."""
+    rng = np.random.default_rng(3)
+    offs = [(dx, dy) for dx in (-1, 0, 1) for dy in (-1, 0, 1) if (dx, dy) != (0, 0)]
+    for _ in range(40):
+        if dim == 3:
+            A, B, C, H, I = rng.uniform(-0.25, 0.25, 5)
+            pts = [(x, y, A * x * x + B * y * y + C * x * y + H * x + I * y) for x, y in offs]
+            # fundamental forms of z = f(x, y) at 0: fx = H, fy = I,
+            # fxx = 2A, fyy = 2B, fxy = C
+            Iform = np.array([[1 + H * H, H * I], [H * I, 1 + I * I]])
+            nrm = np.sqrt(1 + H * H + I * I)
+            IIform = np.array([[2 * A, C], [C, 2 * B]]) / nrm
+            mean = 0.5 * np.trace(np.linalg.solve(Iform, IIform))
+        else:
+            A, H = rng.uniform(-0.25, 0.25, 2)
+            pts = [(x, 0.0, A * x * x + H * x) for x in (-1.0, 1.0)]
+            # a curve taken as a cylinder: the mean curvature is half the
+            # curve's, 2A / (1 + H^2)^(3/2)
+            mean = 0.5 * 2 * A / (1 + H * H) ** 1.5
+        k = oracle_mod.lsq_kappa(dim, pts)
+        assert abs(k - (-mean)) <= 2e-3 * abs(mean) + 1e-4, (dim, k, -mean)

@@ -1,5 +1,5 @@
 """Pins of the oracle's height-function curvature (the second classical
-curvature Sec. 2.2 names; SURVEY's NEXT-2): exact fill levels of planes and
+curvature Sec. 2.2 names): exact fill levels of planes and
 parabolas, whose column heights are exact integrals, give the exact
 curvature; voxelised disks and spheres give 1/(2R) and 1/R."""
 import numpy as np
