@@ -433,7 +433,6 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
 
   R *phi = (R *)p.phi;
   const R Mn = ((const R *)p.M)[n];
-  const R pho = phi[n];
   const R phin = Mn / rho;
   phi[n] = phin;
   int mk = MK_NONE;
@@ -467,7 +466,10 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
     const R v = gi[i] + (geq<R, D>(i, cgas, ux, uy, uz) - gi[i]) * omg + (R)Lat<D>::wa(i) * PV(R, q);
     st(plane(g, p, dir_out<D>(i, 1 - PAR)), cell_out<D>(p, c, i, 1 - PAR), v, gshift<S, D>(p, i));
   }
-  flux = (double)(fl_gas - cgas * (phin - pho));
+  // Sec. 3.1 Eq. gascurrent at the gas links: what the cell sends into the
+  // gas minus what the Henry condition returns (only diffusive exchange
+  // crosses there, so there is no advective part to deduct)
+  flux = (double)fl_gas;
   lab = p.label_old[n];
   if (lab < 0) atomicAdd(p.led + 5, flux);
   return mk;
