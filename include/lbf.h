@@ -80,6 +80,12 @@ typedef struct {
   double trt_magic;         /* collision 1: (tau - 1/2)(tau_m - 1/2) > 0; 3/16
                                puts half-way bounce-back walls exactly
                                half-way for every tau                           */
+  int kappa;                /* curvature of Eq. rhob: 0 least squares; 1 height
+                               function, the second method Sec. 2.2 names
+                               (summed fill levels of 7-cell columns along the
+                               normal's dominant axis, 3 columns in 2D, 3 x 3
+                               in 3D, centred differences; the least-squares
+                               value stays where a column meets a wall)        */
 } lbf_config;
 
 /* one row of the bubble table */

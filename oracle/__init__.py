@@ -63,6 +63,7 @@ class _Config(ctypes.Structure):
         ("atmosphere", ctypes.c_int), ("eps", ctypes.c_double),
         ("bubble_capacity", ctypes.c_int),
         ("collision", ctypes.c_int), ("trt_magic", ctypes.c_double),
+        ("kappa", ctypes.c_int),
     ]
 
 

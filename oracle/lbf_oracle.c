@@ -976,55 +976,56 @@ static void normals_curvature(or_sim *s) {
  * convex gas cap grows away from the cap's apex, so h'' > 0 gives kappa > 0
  * whichever side the liquid is on, and the curvature of the height
  * function is halved to the scale of the least-squares kappa. */
-int or_hf_curvature(const or_sim *s, double *out) {
+/* height-function curvature of interface cell n; returns 0 where it is
+ * undefined (a zero normal, a wall in one of the columns) */
+static int hf_kappa(const or_sim *s, long n, double *out) {
   const int dim = s->dim;
+  const double *m = s->nrm + 3 * n;
+  double h[3][3];
+  int d = 0, a, b, i, j, k, wall = 0;
+  if (m[0] == 0.0 && m[1] == 0.0 && m[2] == 0.0) return 0;
+  for (k = 1; k < dim; ++k)
+    if (fabs(m[k]) > fabs(m[d])) d = k;
+  a = d == 0 ? 1 : 0;
+  b = 3 - d - a;
+  for (j = -1; j <= 1; ++j)
+    for (i = -1; i <= 1; ++i) {
+      double sum = 0.0;
+      h[j + 1][i + 1] = 0.0;
+      if (dim == 2 && j != 0) continue;
+      for (k = -3; k <= 3; ++k) {
+        int off[3] = {0, 0, 0};
+        long y;
+        off[a] = i;
+        off[b] = dim == 2 ? 0 : j;
+        off[d] = k;
+        y = shift(s, n, off[0], off[1], off[2]);
+        if (s->type[y] == WALL) wall = 1;
+        sum += alpha_for_geometry(s, y, n);
+      }
+      h[j + 1][i + 1] = sum;
+    }
+  if (wall) return 0;
+  if (dim == 2) {
+    const double ha = 0.5 * (h[1][2] - h[1][0]);
+    const double haa = h[1][2] - 2.0 * h[1][1] + h[1][0];
+    *out = haa / (2.0 * pow(1.0 + ha * ha, 1.5));
+  } else {
+    const double ha = 0.5 * (h[1][2] - h[1][0]), hb = 0.5 * (h[2][1] - h[0][1]);
+    const double haa = h[1][2] - 2.0 * h[1][1] + h[1][0], hbb = h[2][1] - 2.0 * h[1][1] + h[0][1];
+    const double hab = 0.25 * (h[2][2] - h[0][2] - h[2][0] + h[0][0]);
+    *out = (haa * (1.0 + hb * hb) + hbb * (1.0 + ha * ha) - 2.0 * hab * ha * hb) /
+           (2.0 * pow(1.0 + ha * ha + hb * hb, 1.5));
+  }
+  return 1;
+}
+
+int or_hf_curvature(const or_sim *s, double *out) {
   long n;
   for (n = 0; n < s->N; ++n) {
-    const double *m = s->nrm + 3 * n;
-    double h[3][3];
-    int d = 0, a, b, i, j, k, wall = 0;
     out[n] = 0.0;
     if (s->type[n] != IFC) continue;
-    if (m[0] == 0.0 && m[1] == 0.0 && m[2] == 0.0) {
-      out[n] = NAN;
-      continue;
-    }
-    for (k = 1; k < dim; ++k)
-      if (fabs(m[k]) > fabs(m[d])) d = k;
-    a = d == 0 ? 1 : 0;
-    b = 3 - d - a;
-    for (j = -1; j <= 1; ++j)
-      for (i = -1; i <= 1; ++i) {
-        double sum = 0.0;
-        h[j + 1][i + 1] = 0.0;
-        if (dim == 2 && j != 0) continue;
-        for (k = -3; k <= 3; ++k) {
-          int off[3] = {0, 0, 0};
-          long y;
-          off[a] = i;
-          off[b] = dim == 2 ? 0 : j;
-          off[d] = k;
-          y = shift(s, n, off[0], off[1], off[2]);
-          if (s->type[y] == WALL) wall = 1;
-          sum += alpha_for_geometry(s, y, n);
-        }
-        h[j + 1][i + 1] = sum;
-      }
-    if (wall) {
-      out[n] = NAN;
-      continue;
-    }
-    if (dim == 2) {
-      const double ha = 0.5 * (h[1][2] - h[1][0]);
-      const double haa = h[1][2] - 2.0 * h[1][1] + h[1][0];
-      out[n] = haa / (2.0 * pow(1.0 + ha * ha, 1.5));
-    } else {
-      const double ha = 0.5 * (h[1][2] - h[1][0]), hb = 0.5 * (h[2][1] - h[0][1]);
-      const double haa = h[1][2] - 2.0 * h[1][1] + h[1][0], hbb = h[2][1] - 2.0 * h[1][1] + h[0][1];
-      const double hab = 0.25 * (h[2][2] - h[0][2] - h[2][0] + h[0][0]);
-      out[n] = (haa * (1.0 + hb * hb) + hbb * (1.0 + ha * ha) - 2.0 * hab * ha * hb) /
-               (2.0 * pow(1.0 + ha * ha + hb * hb, 1.5));
-    }
+    if (!hf_kappa(s, n, &out[n])) out[n] = NAN;
   }
   return 0;
 }
@@ -1085,6 +1086,16 @@ static void disjoining(or_sim *s) {
 
 static void geometry(or_sim *s) {
   normals_curvature(s);
+  if (s->c.kappa == 1) {
+    /* the height-function curvature (the second method Sec. 2.2 names)
+     * replaces the least-squares one wherever it is defined, limited to
+     * [-1, 1] like it */
+    long n;
+    for (n = 0; n < s->N; ++n) {
+      double k;
+      if (s->type[n] == IFC && hf_kappa(s, n, &k)) s->kappa[n] = k < -1.0 ? -1.0 : (k > 1.0 ? 1.0 : k);
+    }
+  }
   disjoining(s);
 }
 

@@ -39,6 +39,8 @@ typedef struct {
   int bubble_capacity;
   int collision;             /* 0 BGK, 1 two relaxation times (TRT)             */
   double trt_magic;          /* TRT: (tau - 1/2)(tau_minus - 1/2)               */
+  int kappa;                 /* curvature in the step: 0 least squares, 1 height
+                                function (least squares where it is undefined)  */
 } or_config;
 
 typedef struct or_sim or_sim;

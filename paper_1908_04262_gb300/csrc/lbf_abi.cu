@@ -192,6 +192,7 @@ Params make_params(lbf_sim *s, long long step) {
   p.top_layer = n_up - 1 - ((c.walls >> (2 * up + 1)) & 1);
   p.ray_steps = (int)std::ceil(c.d_max) + 1;
   p.trt = c.collision == 1;
+  p.kappa_hf = c.kappa == 1;
   p.trt_magic = c.trt_magic;
   p.pf = {(float)p.tau, (float)p.rho0, (float)p.ax, (float)p.ay, (float)p.az, (float)p.rn, (float)p.rk,
           (float)p.rlam, (float)p.ra, (float)p.tau0, (float)p.tau_inf, (float)p.tau_min, (float)p.tau_max,
@@ -455,10 +456,18 @@ int run_one_step(lbf_sim *s) {
 int ensure_graph(lbf_sim *s, int k, int par) {
   cudaGraphExec_t &g = k == 4 ? s->graph4[par] : (k == 2 ? s->graph2[par] : s->graph[par]);
   if (g) return 0;
-  if (k == 1) return capture(s, make_params(s, par), par, nullptr, &g);
-  Params ps[4];
-  for (int i = 0; i < k; ++i) ps[i] = make_params(s, par + i);
-  return capture_chain(s, ps, par, k, &g);
+  int rc;
+  if (k == 1) {
+    rc = capture(s, make_params(s, par), par, nullptr, &g);
+  } else {
+    Params ps[4];
+    for (int i = 0; i < k; ++i) ps[i] = make_params(s, par + i);
+    rc = capture_chain(s, ps, par, k, &g);
+  }
+  if (rc) return rc;
+  // moved to the device now rather than at its first launch
+  CK(cudaGraphUpload(g, s->st));
+  return 0;
 }
 
 // every graph shape lbf_step launches, for both parities: made on the first
@@ -598,6 +607,7 @@ int validate(const lbf_config *c) {
   if (!(c->D > 0.0)) return fail(LBF_EINVAL, "D must be positive");
   if (c->collision < 0 || c->collision > 1) return fail(LBF_EINVAL, "bad collision");
   if (c->collision == 1 && !(c->trt_magic > 0.0)) return fail(LBF_EINVAL, "trt_magic must be positive");
+  if (c->kappa < 0 || c->kappa > 1) return fail(LBF_EINVAL, "bad curvature method");
   if (!(c->RT > 0.0) || !(c->rho0 > 0.0)) return fail(LBF_EINVAL, "RT and rho0 must be positive");
   if (c->bubble_capacity < 1 || c->bubble_capacity > 16384) return fail(LBF_EINVAL, "bubble_capacity must be in [1, 16384]");
   if (c->k_pi != 0.0 && !(c->d_max > 0.0 && c->d_max <= 64.0)) return fail(LBF_EINVAL, "d_max must be in (0, 64]");

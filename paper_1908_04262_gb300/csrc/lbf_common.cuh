@@ -160,6 +160,7 @@ struct Params {
   double tau, rho0, ax, ay, az;
   int has_force, rheo;
   int trt;            // two relaxation times (else BGK)
+  int kappa_hf;       // height-function curvature (else least squares)
   double trt_magic;   // (tau - 1/2)(tau_m - 1/2)
   double rn, rk, rlam, ra, tau0, tau_inf, tau_min, tau_max;
   double sigma, k_pi, d_max, taug, kH, RT, c0, q, p0, eps;

@@ -311,6 +311,81 @@ __global__ void __launch_bounds__(128) k_geometry(Params p) {
   }
 }
 
+// height-function curvature, the second method Sec. 2.2 names (switched on
+// by cfg.kappa = 1): heights are the summed fill levels of 7-cell columns
+// along the dominant axis of the cell's normal, 3 columns (2D) or 3 x 3
+// (3D) around the cell; centred differences give the curvature of the
+// height function, halved like the least-squares kappa (a gas disk 1/(2R),
+// a gas sphere 1/R).  The summed liquid fraction makes the sign independent
+// of the side the liquid is on.  It replaces the least-squares kappa
+// wherever no column meets a wall, limited to [-1, 1].  One thread per
+// interface cell, after k_geometry (it needs the normal).
+template <int D, class R>
+__global__ void __launch_bounds__(128) k_hf_kappa(Params p) {
+  const int cnt = *p.icount;
+  const R *phi = (const R *)p.phi, *nr = (const R *)p.nrm;
+  R *kap = (R *)p.kappa;
+  FOR_LIST(kk, cnt) {
+    const long long n = p.ilist[kk];
+    const R m[3] = {nr[n], nr[p.N + n], D == 3 ? nr[2 * p.N + n] : (R)0};
+    if (m[0] == (R)0 && m[1] == (R)0 && m[2] == (R)0) continue;
+    int d = 0;
+#pragma unroll
+    for (int q = 1; q < D; ++q)
+      if (fabs(m[q]) > fabs(m[d])) d = q;
+    const int a = d == 0 ? 1 : 0, b = 3 - d - a;
+    const Cell c = make_cell(p, n);
+    R ac = phi[n];
+    ac = ac < (R)0 ? (R)0 : (ac > (R)1 ? (R)1 : ac);
+    R h[3][3];
+    bool wall = false;
+#pragma unroll
+    for (int j = -1; j <= 1; ++j)
+#pragma unroll
+      for (int i = -1; i <= 1; ++i) {
+        R sum = 0;
+        h[j + 1][i + 1] = 0;
+        if (D == 2 && j != 0) continue;
+        for (int k = -3; k <= 3; ++k) {
+          int off[3] = {0, 0, 0};
+          off[a] = i;
+          off[b] = D == 2 ? 0 : j;
+          off[d] = k;
+          const long long y = at_far(p, c.x + off[0], c.y + off[1], c.z + off[2]);
+          const int ty = post_type(p.flags[y]);
+          R v;
+          if (ty == T_WALL) {
+            wall = true;
+            v = ac;  // walls repeat the centre value
+          } else if (ty == T_LIQ) {
+            v = 1;
+          } else if (ty == T_IFC) {
+            v = phi[y];
+            v = v < (R)0 ? (R)0 : (v > (R)1 ? (R)1 : v);
+          } else {
+            v = 0;
+          }
+          sum += v;
+        }
+        h[j + 1][i + 1] = sum;
+      }
+    if (wall) continue;
+    R kv;
+    if (D == 2) {
+      const R ha = (R)0.5 * (h[1][2] - h[1][0]);
+      const R haa = h[1][2] - (R)2 * h[1][1] + h[1][0];
+      kv = haa / ((R)2 * pow((R)1 + ha * ha, (R)1.5));
+    } else {
+      const R ha = (R)0.5 * (h[1][2] - h[1][0]), hb = (R)0.5 * (h[2][1] - h[0][1]);
+      const R haa = h[1][2] - (R)2 * h[1][1] + h[1][0], hbb = h[2][1] - (R)2 * h[1][1] + h[0][1];
+      const R hab = (R)0.25 * (h[2][2] - h[0][2] - h[2][0] + h[0][0]);
+      kv = (haa * ((R)1 + hb * hb) + hbb * ((R)1 + ha * ha) - (R)2 * hab * ha * hb) /
+           ((R)2 * pow((R)1 + ha * ha + hb * hb, (R)1.5));
+    }
+    kap[n] = kv < (R)-1 ? (R)-1 : (kv > (R)1 ? (R)1 : kv);
+  }
+}
+
 template <int D, class R>
 __global__ void k_disjoining(Params p) {
   const int cnt = *p.icount;

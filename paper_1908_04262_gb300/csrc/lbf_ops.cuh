@@ -108,6 +108,7 @@ struct OpsImpl final : Ops {
   void bubble_update(const Params &p, cudaStream_t s) override { k_bubble_update<<<1, 1024, 0, s>>>(p); }
   void geometry(const Params &p, cudaStream_t s) override {
     k_geometry<D, R><<<p.warp_blocks, 128, 0, s>>>(p);
+    if (p.kappa_hf) k_hf_kappa<D, R><<<p.list_blocks, 128, 0, s>>>(p);
   }
   void mlp_kappa(const Params &p, const void *img, cudaStream_t s) override {
     // one block of MLP_WARPS warps per SM (list_blocks holds 4 per SM)

@@ -49,6 +49,7 @@ class Config(ctypes.Structure):
         ("bubble_capacity", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("collision", ctypes.c_int), ("trt_magic", ctypes.c_double),
+        ("kappa", ctypes.c_int),
     ]
 
 

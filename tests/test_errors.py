@@ -41,6 +41,7 @@ BAD_CONFIGS = [
     ("bad collision", dict(collision=3)),
     ("TRT without magic", dict(collision=1, trt_magic=0.0)),
     ("disjoining range 0", dict(k_pi=1e-3, d_max=0.0)),
+    ("bad curvature method", dict(kappa=2)),
 ]
 
 

@@ -303,9 +303,17 @@ def test_in_loop_kappa_matches_oracle_and_beats_least_squares(env, oracle_mod, t
     kt = _true_kappa(ifc, (nx, ny, nz))
     e_lsq = np.sqrt(np.mean(((f0["kappa"][ifc] - kt) / kt)[used] ** 2))
     e_mlp = np.sqrt(np.mean(((f1["kappa"][ifc] - kt) / kt)[used] ** 2))
-    print("interface cells %d (network on %d): relative RMS kappa error LSQ %.4f, MLP %.4f"
-          % (ifc.size, used.sum(), e_lsq, e_mlp))
+    # second judge: the height-function curvature (cfg kappa = 1) of the same
+    # state, on the same cells
+    sim_hf = L.Sim(dict(cfg, kappa=1))
+    sim_hf.set_cells(t, rho, u, a, c)
+    k_hf = sim_hf.fields(["kappa"])["kappa"]
+    sim_hf.close()
+    e_hf = np.sqrt(np.mean(((k_hf[ifc] - kt) / kt)[used] ** 2))
+    print("interface cells %d (network on %d): relative RMS kappa error LSQ %.4f, height function %.4f, MLP %.4f"
+          % (ifc.size, used.sum(), e_lsq, e_hf, e_mlp))
     assert e_mlp < 0.7 * e_lsq
+    assert e_mlp < 0.8 * e_hf
 
 
 def test_harvest_matches_oracle(env, oracle_mod):

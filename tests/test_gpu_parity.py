@@ -191,3 +191,37 @@ def test_reduced_precision_crop(lbf, oracle_mod, storage):
     assert nflag == 0
     for k, bound in REDUCED_TOL[storage].items():
         assert errs[k] < bound, (storage, k, errs[k], bound)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_height_function_curvature_fp64(lbf, oracle_mod, dim):
+    """The height-function curvature in the step (cfg kappa = 1): the 2D
+    bubble-in-a-box case and the 32^3 crop in FP64 -- flags and labels
+    bit-exact, fields, bubble table and curvature within 1e-10 -- and the
+    curvature of every interface cell equal to the oracle's height-function
+    read-out (limited to [-1, 1]) wherever no column meets a wall."""
+    if dim == 2:
+        cfg, c, r = _c1_small()
+        chunks, per = 4, 25
+    else:
+        cfg, c, r = W.c2_crop_3d_32(storage="fp64")
+        chunks, per = 3, 10
+    cfg = dict(cfg, kappa=1)
+    sim, ora = _pair(lbf, oracle_mod, cfg)
+    for s in (sim, ora):
+        s.nucleate(c, r)
+    for _ in range(chunks):
+        sim.step(per)
+        ora.step(per)
+        errs, nflag = compare_state(sim, ora)
+        assert nflag == 0
+        assert np.array_equal(sim.fields(["label"])["label"], ora.labels())
+        for k, e in errs.items():
+            assert e < FP64_TOL, (k, e)
+        _check_bubbles(sim, ora, FP64_TOL)
+        kg = sim.fields(["kappa"])["kappa"]
+        assert rel_err(kg, ora.get("kappa")) < FP64_TOL
+        hf = ora.hf_curvature()
+        ok = np.isfinite(hf) & (ora.types() == oracle_mod.IFC)
+        assert ok.sum() > 20
+        assert np.max(np.abs(kg[ok] - np.clip(hf[ok], -1, 1))) < 1e-10

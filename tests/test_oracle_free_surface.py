@@ -64,9 +64,9 @@ def test_mass_conserved_3d(oracle_mod):
         assert not liquid_touches_gas(s.types(), (16, 16, 16), 3, oracle_mod)
 
 
-def _laplace(oracle_mod, dim, n, R, sigma, steps):
+def _laplace(oracle_mod, dim, n, R, sigma, steps, kappa=0):
     nz = 1 if dim == 2 else n
-    cfg = W.config(nx=n, ny=n, nz=nz, tau=0.9, sigma=sigma, kH=0.0, c0=0.0, atmosphere=0)
+    cfg = W.config(nx=n, ny=n, nz=nz, tau=0.9, sigma=sigma, kH=0.0, c0=0.0, atmosphere=0, kappa=kappa)
     s = oracle_mod.OracleSim(cfg)
     c = [n / 2, n / 2, 0.0 if dim == 2 else n / 2]
     s.nucleate([c], [R])
@@ -90,4 +90,16 @@ def test_laplace_jump_2d(oracle_mod):
 def test_laplace_jump_3d(oracle_mod):
     """p_g - p_l = 2 sigma / R for a sphere (kappa = 1/R in Eq. rhob)."""
     ratio = _laplace(oracle_mod, 3, 16, 4.5, 0.01, 400)
+    assert 0.9 < ratio < 1.1
+
+
+def test_laplace_jump_height_function_2d(oracle_mod):
+    """The same disk with the height-function curvature in the step (the
+    second method Sec. 2.2 names, cfg kappa = 1)."""
+    ratio = _laplace(oracle_mod, 2, 40, 9.0, 0.01, 3000, kappa=1)
+    assert 0.92 < ratio < 1.08
+
+
+def test_laplace_jump_height_function_3d(oracle_mod):
+    ratio = _laplace(oracle_mod, 3, 16, 4.5, 0.01, 400, kappa=1)
     assert 0.9 < ratio < 1.1
