@@ -193,6 +193,39 @@ def static_bubble_laplace(lbf, theta, storage: str, R: float = 5.0, steps: int =
     return float(np.mean(rel[-4:]))
 
 
+def crop_field_errors(lbf, steps: int = 20):
+    """Per-field norm-relative errors of each storage form after `steps`
+    steps of the 32^3 crop, against the FP64 CUDA form of the same crop
+    (which the parity tests hold to the FP64 oracle within 1e-10): max |form
+    - fp64| / max |fp64| over the cells liquid or interface in both."""
+    import numpy as np
+
+    from paper_1908_04262_gb300 import workloads as W
+
+    names = ["rho", "u", "alpha", "mass", "conc"]
+    got = {}
+    for st in ("fp64", "fp32", "fp16s", "bf16s"):
+        cfg, c, r = W.c2_crop_3d_32(storage=st)
+        sim = lbf.Sim(cfg)
+        sim.nucleate(c, r)
+        sim.step(steps)
+        got[st] = (sim.fields(names + ["flags"]), sim.bubbles()["volume"])
+        sim.close()
+    ref, vref = got["fp64"]
+    out = {}
+    for st in ("fp32", "fp16s", "bf16s"):
+        g, v = got[st]
+        both = ((g["flags"] == 1) | (g["flags"] == 2)) & ((ref["flags"] == 1) | (ref["flags"] == 2))
+        e = {}
+        for k in names:
+            a, b = np.asarray(g[k], float)[both], np.asarray(ref[k], float)[both]
+            e[k] = float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+        e["volume"] = float(np.max(np.abs(v - vref)) / np.max(np.abs(vref))) if len(v) == len(vref) else None
+        e["flag_mismatches"] = int(np.sum(g["flags"] != ref["flags"]))
+        out[st] = e
+    return out
+
+
 def forms_comparison(args, lbf, cfg, pts, rad, stream, fp32_line):
     """The same workload in shifted-FP16 storage with the learned curvature
     (and the two halves of that change alone) against FP32 with least
@@ -224,8 +257,10 @@ def forms_comparison(args, lbf, cfg, pts, rad, stream, fp32_line):
     out["laplace_rel_err_static_bubble_R5"] = {
         "fp32_plain": static_bubble_laplace(lbf, None, "fp32"),
         "fp16s_mlp": static_bubble_laplace(lbf, theta, "fp16s")}
+    out["field_errors_vs_fp64_32cube_20steps"] = crop_field_errors(lbf)
     out["note"] = ("same workload, steps and warm-up as the headline; bubble volume = total over the "
-                   "bubbles after warm-up + timed steps; Laplace error of a static R=5 bubble, 48^3")
+                   "bubbles after warm-up + timed steps; Laplace error of a static R=5 bubble, 48^3; "
+                   "field errors: 32^3 crop after 20 steps against the FP64 CUDA form")
     return out
 
 

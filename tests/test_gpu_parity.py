@@ -193,6 +193,37 @@ def test_reduced_precision_crop(lbf, oracle_mod, storage):
         assert errs[k] < bound, (storage, k, errs[k], bound)
 
 
+def test_reduced_precision_error_follows_storage_roundoff(lbf):
+    """The shifted 16-bit forms differ from the FP32 form only in how the
+    populations are stored (the arithmetic is FP32 in all three), so each
+    field's deviation from the FP32 form is storage roundoff: after 10 steps
+    of the 32^3 crop it stays below two unit roundoffs of the format (2^-11
+    for FP16, 2^-8 for BF16) in every field, and the BF16 deviation is the
+    FP16 one times the ratio of the unit roundoffs, 8, within a factor 2.5.
+    This is what the derived per-field bounds of the 20-step test rest on."""
+    fields = ("rho", "u", "alpha", "mass", "conc")
+    sims = {}
+    for st in ("fp32", "fp16s", "bf16s"):
+        cfg, c, r = W.c2_crop_3d_32(storage=st)
+        sims[st] = lbf.Sim(cfg)
+        sims[st].nucleate(c, r)
+        sims[st].step(10)
+    ref = sims["fp32"].fields(list(fields) + ["flags"])
+    unit = {"fp16s": 2.0 ** -11, "bf16s": 2.0 ** -8}
+    err = {}
+    for st in ("fp16s", "bf16s"):
+        g = sims[st].fields(list(fields) + ["flags"])
+        assert np.array_equal(g["flags"], ref["flags"]), st
+        both = (ref["flags"] == 1) | (ref["flags"] == 2)
+        err[st] = {f: rel_err(g[f], ref[f], both) for f in fields}
+        print("\n%s against FP32 after 10 steps: %s" % (st, {f: "%.2e" % v for f, v in err[st].items()}))
+        for f in fields:
+            assert err[st][f] < 2.0 * unit[st], (st, f, err[st][f])
+    for f in fields:
+        q = err["bf16s"][f] / err["fp16s"][f]
+        assert 8.0 / 2.5 < q < 8.0 * 2.5, (f, q)
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_height_function_curvature_fp64(lbf, oracle_mod, dim):
     """The height-function curvature in the step (cfg kappa = 1): the 2D
