@@ -1058,8 +1058,12 @@ static void disjoining(or_sim *s) {
       long y;
       int ty;
       tent = tm;
+      /* axes whose next boundary lies at the same ray parameter are crossed
+       * together (a diagonal step); "the same" within a relative 1e-9, so
+       * that round-off in a normal with equal components cannot turn one
+       * diagonal step into two axis steps */
       for (d = 0; d < 3; ++d)
-        if (tmax[d] == tm) {
+        if (tmax[d] <= tm * (1.0 + 1e-9)) {
           tmax[d] += tdel[d];
           off[d] += step[d];
         }
