@@ -50,6 +50,9 @@ struct lbf_sim {
   cudaStream_t st = nullptr;
   bool own_stream = false;
   cudaStream_t st2 = nullptr, st3 = nullptr, st4 = nullptr;  // further branches of the step graphs
+  cudaStream_t stc = nullptr;  // captures the bodies of conditional nodes
+  bool use_cond = true;        // step graphs choose the labelling branch on the device
+  int capture_err = 0;         // first failure while adding conditional nodes
   int prio_least = 0, prio_greatest = 0;      // stream priority range of the device
   std::vector<cudaGraphNode_t> low_nodes;      // liquid sweeps captured on the third branch
   cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr}, joinx = nullptr, joinex = nullptr,
@@ -84,6 +87,8 @@ struct lbf_sim {
   unsigned long long *fluid_updates = nullptr;
   int *err = nullptr;
   int *gas_dirty = nullptr;
+  int *lab_slow = nullptr;
+  int *forest_stale = nullptr;
   uint8_t *tdirty = nullptr;
   size_t ntiles_alloc = 0;
   unsigned *wmask = nullptr;
@@ -155,7 +160,9 @@ Params make_params(lbf_sim *s, long long step) {
   p.segnext_count = s->segcount[1 - par];
   p.segflag = s->segflag;
   p.mlist = s->mlist;
-  p.mcount = s->mcount;
+  // one counter per parity: the next step's mass exchange clears its own
+  // while this step's labelling may still read this one
+  p.mcount = s->mcount + par;
   p.nlist = s->nlist;
   p.ncount = s->ncount;
   p.list_blocks = s->list_blocks;
@@ -175,6 +182,8 @@ Params make_params(lbf_sim *s, long long step) {
   p.gheir = s->gheir; p.gmold = s->gmold; p.gvnew = s->gvnew; p.gvmax = s->gvmax;
   p.next_id = s->next_id; p.led = s->led; p.fluid_updates = s->fluid_updates; p.err = s->err;
   p.gas_dirty = s->gas_dirty;
+  p.lab_slow = s->lab_slow;
+  p.forest_stale = s->forest_stale;
   p.tdirty = s->tdirty;
   p.rlabel = s->rlabel;
   p.tau_tab = s->tau_tab; p.tab_n = s->tab_n; p.tab_lnA0 = s->tab_lnA0; p.tab_inv_dlnA = s->tab_inv_dlnA;
@@ -225,6 +234,7 @@ int relabel_in_place(lbf_sim *s) {
   CK(cudaMemcpyAsync(a.id, b.id, sizeof(int) * cap, cudaMemcpyDeviceToDevice, s->st));
   CK(cudaMemcpyAsync(a.atm, b.atm, sizeof(int) * cap, cudaMemcpyDeviceToDevice, s->st));
   CK(cudaMemcpyAsync(a.root, b.root, sizeof(int) * cap, cudaMemcpyDeviceToDevice, s->st));
+  CK(cudaMemcpyAsync(a.ng, b.ng, sizeof(int) * cap, cudaMemcpyDeviceToDevice, s->st));
   CK(cudaMemcpyAsync(a.count, b.count, sizeof(int), cudaMemcpyDeviceToDevice, s->st));
   p.label_new = s->label[par];
   s->ops->geometry(p, s->st);
@@ -256,6 +266,94 @@ Params next_geometry_params(const Params &p) {
 void enqueue_geometry(lbf_sim *s, const Params &pn, cudaStream_t st) {
   s->ops->geometry(pn, st);
   if (s->mlp_theta) s->ops->mlp_kappa(pn, s->mlp_theta, st);
+}
+
+// kernel nodes of a graph (a conditional node's body) at the greatest stream
+// priority
+cudaError_t body_priorities(lbf_sim *s, cudaGraph_t gr) {
+  size_t nn = 0;
+  cudaError_t e = cudaGraphGetNodes(gr, nullptr, &nn);
+  if (e != cudaSuccess || nn == 0) return e;
+  std::vector<cudaGraphNode_t> nodes(nn);
+  e = cudaGraphGetNodes(gr, nodes.data(), &nn);
+  for (size_t j = 0; j < nn && e == cudaSuccess; ++j) {
+    cudaGraphNodeType t;
+    e = cudaGraphNodeGetType(nodes[j], &t);
+    if (e != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+    cudaLaunchAttributeValue v;
+    std::memset(&v, 0, sizeof(v));
+    v.priority = s->prio_greatest;
+    e = cudaGraphKernelNodeSetAttribute(nodes[j], cudaLaunchAttributePriority, &v);
+  }
+  return e;
+}
+
+// adds, at the current point of the capture on the main stream, a
+// conditional IF node with `size` bodies (body 0 runs when the handle's
+// value is non-zero, body 1 otherwise) and fills each body by running
+// fill(k, stream) under a capture into that body
+template <class F> void add_conditional(lbf_sim *s, cudaGraphConditionalHandle h, int size, F &&fill) {
+  if (s->capture_err) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *ed = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s->st, &cs, nullptr, &g, &deps, &ed, &nd);
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};  // every other field zero
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeIf;
+  np.conditional.size = (unsigned)size;
+  cudaGraphNode_t node = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, deps, ed, nd, &np);
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(s->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  for (int k = 0; k < size && e == cudaSuccess; ++k) {
+    cudaGraph_t body = np.conditional.phGraph_out[k];
+    e = cudaStreamBeginCaptureToGraph(s->stc, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) break;
+    fill(k, s->stc);
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(s->stc, &out);
+    if (e == cudaSuccess) e = body_priorities(s, body);
+  }
+  if (e != cudaSuccess) s->capture_err = (int)e;
+}
+
+// The labelling branch of a step is chosen on the device: the full
+// union-find labelling, or, after a conversion that kept every bubble's
+// cells, number and root, the labels of the last step patched
+// (k_label_fast).  label_choice sets the branch value (after the marking)
+// and runs the union-find forest when it is needed; label_finish relabels or
+// patches (after the excess pass: both read fill levels); bubble_branches
+// updates the bubble table to match.
+cudaGraphConditionalHandle label_choice(lbf_sim *s, const Params &p) {
+  cudaGraphConditionalHandle h = 0;
+  if (!s->capture_err) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(s->st, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) s->capture_err = (int)e;
+  }
+  if (!s->capture_err) s->ops->label_cond(p, h, s->st);
+  add_conditional(s, h, 1, [&](int, cudaStream_t b) { s->ops->label_forest(p, b); });
+  return h;
+}
+void label_finish(lbf_sim *s, const Params &p, cudaGraphConditionalHandle h) {
+  add_conditional(s, h, 2, [&](int k, cudaStream_t b) {
+    if (k == 0)
+      s->ops->label_relabel(p, b);
+    else
+      s->ops->label_fast(p, b);
+  });
+}
+void bubble_branches(lbf_sim *s, const Params &p, cudaGraphConditionalHandle h) {
+  add_conditional(s, h, 2, [&](int k, cudaStream_t b) {
+    if (k == 0)
+      s->ops->bubble_update(p, b);
+    else
+      s->ops->bubble_update_fast(p, b);
+  });
 }
 
 // everything of a step after its interface sweep.  The marking runs first;
@@ -313,11 +411,19 @@ void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const
       s->low_nodes.insert(s->low_nodes.end(), deps, deps + nd);
     cudaEventRecord(s->joinx, s->st3);
   }
-  s->ops->label_forest(p, s->st);
-  cudaStreamWaitEvent(s->st, s->applied, 0);
-  s->ops->label_relabel(p, s->st);
-  cudaEventRecord(s->fork[1], s->st);
-  s->ops->bubble_update(p, s->st);
+  if (s->use_cond) {
+    const cudaGraphConditionalHandle h = label_choice(s, p);
+    cudaStreamWaitEvent(s->st, s->applied, 0);
+    label_finish(s, p, h);
+    cudaEventRecord(s->fork[1], s->st);
+    bubble_branches(s, p, h);
+  } else {
+    s->ops->label_forest(p, s->st);
+    cudaStreamWaitEvent(s->st, s->applied, 0);
+    s->ops->label_relabel(p, s->st);
+    cudaEventRecord(s->fork[1], s->st);
+    s->ops->bubble_update(p, s->st);
+  }
   cudaStreamWaitEvent(s->st4, s->fork[1], 0);
   cudaStreamWaitEvent(s->st4, s->join[0], 0);
   s->ops->disjoining(pn, s->st4);
@@ -344,8 +450,17 @@ void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
       s->ops->convert_finalize(p, s->st);
     });
     const Params pn = next_geometry_params(p);
-    group(G_LABEL, [&] { s->ops->label(p, s->st); });
-    group(G_BUBBLE, [&] { s->ops->bubble_update(p, s->st); });
+    if (s->use_cond) {
+      cudaGraphConditionalHandle h = 0;
+      group(G_LABEL, [&] {
+        h = label_choice(s, p);
+        label_finish(s, p, h);
+      });
+      group(G_BUBBLE, [&] { bubble_branches(s, p, h); });
+    } else {
+      group(G_LABEL, [&] { s->ops->label(p, s->st); });
+      group(G_BUBBLE, [&] { s->ops->bubble_update(p, s->st); });
+    }
     group(G_GEOMETRY, [&] { enqueue_geometry(s, pn, s->st); });
     group(G_DISJOIN, [&] { s->ops->disjoining(pn, s->st); });
     return;
@@ -390,12 +505,28 @@ int set_node_priorities(lbf_sim *s, cudaGraph_t gr) {
   return 0;
 }
 
+// a capture that could not add its conditional nodes is discarded and
+// redone with the full labelling in every step
+int conditional_fallback(lbf_sim *s, cudaGraph_t gr) {
+  if (!s->capture_err) return 0;
+  if (gr) cudaGraphDestroy(gr);
+  cudaGetLastError();
+  s->capture_err = 0;
+  s->use_cond = false;
+  return 1;
+}
+
 int capture_chain(lbf_sim *s, const Params *ps, int par, int k, cudaGraphExec_t *out) {
-  cudaGraph_t gr;
+  cudaGraph_t gr = nullptr;
   s->low_nodes.clear();
+  s->capture_err = 0;
   CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
   enqueue_chain(s, ps, par, k);
-  CK(cudaStreamEndCapture(s->st, &gr));
+  {
+    const cudaError_t e = cudaStreamEndCapture(s->st, &gr);
+    if (conditional_fallback(s, gr)) return capture_chain(s, ps, par, k, out);
+    if (e != cudaSuccess) return fail(LBF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  }
   int rc = set_node_priorities(s, gr);
   s->low_nodes.clear();
   if (rc) {
@@ -409,10 +540,15 @@ int capture_chain(lbf_sim *s, const Params *ps, int par, int k, cudaGraphExec_t 
 }
 
 int capture(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev, cudaGraphExec_t *out) {
-  cudaGraph_t gr;
+  cudaGraph_t gr = nullptr;
+  s->capture_err = 0;
   CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
   enqueue_step(s, p, par, ev);
-  CK(cudaStreamEndCapture(s->st, &gr));
+  {
+    const cudaError_t e = cudaStreamEndCapture(s->st, &gr);
+    if (conditional_fallback(s, gr)) return capture(s, p, par, ev, out);
+    if (e != cudaSuccess) return fail(LBF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  }
   cudaError_t e = cudaGraphInstantiate(out, gr, 0);
   cudaGraphDestroy(gr);
   if (e != cudaSuccess) return fail(LBF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
@@ -699,6 +835,7 @@ void lbf_destroy(lbf_sim *s) {
   if (s->st2) cudaStreamDestroy(s->st2);
   if (s->st3) cudaStreamDestroy(s->st3);
   if (s->st4) cudaStreamDestroy(s->st4);
+  if (s->stc) cudaStreamDestroy(s->stc);
   if (s->own_stream && s->st) cudaStreamDestroy(s->st);
   delete s->ops;
   delete s;
@@ -740,6 +877,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->st2, cudaStreamNonBlocking, s->prio_greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->st3, cudaStreamNonBlocking, s->prio_least);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->st4, cudaStreamNonBlocking, s->prio_greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->stc, cudaStreamNonBlocking, s->prio_greatest);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joinx, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joinex, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fin, cudaEventDisableTiming);
@@ -789,7 +927,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   AL(dalloc(s, &s->segcount[1], 1));
   AL(dalloc(s, &s->segflag, s->nseg));
   AL(dalloc(s, &s->mlist, N));
-  AL(dalloc(s, &s->mcount, 1));
+  AL(dalloc(s, &s->mcount, 2));
   AL(dalloc(s, &s->ncount, 1));
   AL(dev_alloc(s, &s->M, N * s->rsz));
   AL(dev_alloc(s, &s->phi, N * s->rsz));
@@ -826,6 +964,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     AL(dalloc(s, &t.id, s->cap));
     AL(dalloc(s, &t.atm, s->cap));
     AL(dalloc(s, &t.root, s->cap));
+    AL(dalloc(s, &t.ng, s->cap));
     AL(dalloc(s, &t.count, 1));
   }
   const size_t G2 = 2 * (size_t)s->cap;
@@ -843,6 +982,8 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   AL(dalloc(s, &s->fluid_updates, 1));
   AL(dalloc(s, &s->err, 1));
   AL(dalloc(s, &s->gas_dirty, 1));
+  AL(dalloc(s, &s->lab_slow, 1));
+  AL(dalloc(s, &s->forest_stale, 1));
   AL(dalloc(s, &s->wmask, N));
   AL(dalloc(s, &s->rlabel, N));
   AL(dalloc(s, &s->acc, 4));
@@ -863,6 +1004,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   for (int k = 0; k < 2; ++k) {
     e = e ? e : zero(s->tab[k].count, sizeof(int));
     e = e ? e : zero(s->tab[k].dm, sizeof(double) * s->cap);
+    e = e ? e : zero(s->tab[k].ng, sizeof(int) * s->cap);
   }
   e = e ? e : zero(s->next_id, sizeof(int));
   e = e ? e : zero(s->icount[0], sizeof(int));
@@ -871,12 +1013,14 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   e = e ? e : zero(s->segcount[0], sizeof(int));
   e = e ? e : zero(s->segcount[1], sizeof(int));
   e = e ? e : zero(s->segflag, sizeof(int) * s->nseg);
-  e = e ? e : zero(s->mcount, sizeof(int));
+  e = e ? e : zero(s->mcount, 2 * sizeof(int));
   e = e ? e : zero(s->hcount, sizeof(int));
   e = e ? e : zero(s->led, 8 * sizeof(double));
   e = e ? e : zero(s->fluid_updates, sizeof(unsigned long long));
   e = e ? e : zero(s->err, sizeof(int));
   e = e ? e : zero(s->gas_dirty, sizeof(int));
+  e = e ? e : zero(s->lab_slow, sizeof(int));
+  e = e ? e : zero(s->forest_stale, sizeof(int));
   e = e ? e : zero(s->tdirty, s->ntiles_alloc);
   if (e != cudaSuccess) {
     lbf_destroy(s);

@@ -95,6 +95,7 @@ __device__ __forceinline__ void st(__nv_bfloat16 *p, int k, float v, float sh) {
 struct Table {
   double *m, *p, *V, *dm;  // gas mass, pressure, volume, gas gained this step
   int *id, *atm, *root;    // stable id, atmosphere flag, canonical label
+  int *ng;                 // gas cells of the bubble (V = ng + interface shares)
   int *count;              // number of rows (device)
 };
 
@@ -109,6 +110,7 @@ struct Params {
   int *inext, *inext_count;  // interface cells after the conversion
   int *nlist, *ncount;   // gas/liquid cells turning interface this step
   int *mlist, *mcount;   // interface cells the sweep marked to fill or empty this step
+                         // (the count is kept per parity: see make_params)
   // 32-cell segments along x that hold interface cells (the interface
   // kernels run one warp per segment, one lane per cell)
   int *seglist, *segcount;       // at the start of the step
@@ -142,7 +144,15 @@ struct Params {
   // tdirty, are redone), anything else removed some or the state was set
   // from outside (full labelling).  NULL means always full.
   int *gas_dirty;
-  uint8_t *tdirty;  // per union-find tile: touched by added gas cells this step
+  uint8_t *tdirty;  // per union-find tile: touched by added gas cells since the last forest update
+  // set by the marking when an added gas cell could join two bubbles or
+  // move a bubble's smallest cell index: the step then needs the full
+  // labelling (else the labels of the last step, patched, are exact)
+  int *lab_slow;
+  // 1 after a step labelled without the union-find added gas cells: the
+  // forest lags behind in the touched tiles (tdirty) until the next
+  // union-find labelling redoes them
+  int *forest_stale;
   // label of each current root cell (rank among the sorted roots, -1 past
   // the bubble capacity); read only at cells that are roots
   int *rlabel;
@@ -324,9 +334,10 @@ enum : int { LABEL_SKIP = 0, LABEL_ADDED = 1, LABEL_FULL = 2 };
 __device__ __forceinline__ int label_mode(const Params &p) {
   if (!p.gas_dirty || !p.tdirty) return LABEL_FULL;
   const int d = *p.gas_dirty;
-  return d == 0 ? LABEL_SKIP : (d == 1 ? LABEL_ADDED : LABEL_FULL);
+  if (d == 0) return (p.forest_stale && *p.forest_stale) ? LABEL_ADDED : LABEL_SKIP;
+  return d == 1 ? LABEL_ADDED : LABEL_FULL;
 }
-__device__ __forceinline__ bool gas_unchanged(const Params &p) { return p.gas_dirty && *p.gas_dirty == 0; }
+__device__ __forceinline__ bool gas_unchanged(const Params &p) { return label_mode(p) == LABEL_SKIP; }
 
 // union-find tiles: 32 x-rows of 32 cells
 template <int D> struct Tile;
@@ -346,6 +357,15 @@ __device__ __forceinline__ int post_type(uint8_t f) {
 }
 
 // warp-aggregated FP64 atomic add keyed by a bubble index: lanes holding the
+// integer counts per key, one atomic per distinct key of the warp; must be
+// reached by all 32 lanes; lanes with key < 0 contribute nothing
+__device__ __forceinline__ void agg_count(int *base, int key, int v) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int s = (int)__reduce_add_sync(peers, (unsigned)v);  // each key group sums its own lanes
+  if (key >= 0 && lane == __ffs(peers) - 1 && s) atomicAdd(base + key, s);
+}
+
 // same key are summed in lane order by their lowest lane.  Must be reached by
 // all 32 lanes of the warp; lanes with key < 0 contribute nothing.
 __device__ __forceinline__ void agg_add(double *base, int key, double v, double *wbuf) {

@@ -91,6 +91,22 @@ __device__ __forceinline__ bool mark_byte(uint8_t *flags, long long m, int mk) {
   return ((old >> sh) & (7u << 2)) == 0;
 }
 
+// An added gas cell n keeps the bubble structure of the last labelling when
+// it carries a bubble label L (the smallest of its gas neighbours' as an
+// interface cell), lies above that bubble's root (so the bubble's smallest
+// cell index stays), and every gas or emptying neighbour carries L as well
+// (so it joins no other bubble).  The labelling then needs no union-find.
+template <int D>
+__device__ __forceinline__ bool joins_own_bubble(const Params &p, const Cell &c, int n, const uint8_t *fn) {
+  const int L = p.label_old[n];
+  if (L < 0 || n <= p.told.root[L]) return false;
+  bool ok = true;
+#pragma unroll
+  for (int i = 1; i < Lat<D>::Q; ++i)
+    if ((ftype(fn[i]) == T_GAS || fmark(fn[i]) == MK_EMPTY) && p.label_old[nb<D>(p, c, i)] != L) ok = false;
+  return ok;
+}
+
 // An emptying cell next to a filling cell stays interface (filling wins);
 // gas next to a filling cell and liquid next to a (still) emptying cell
 // become interface, so that liquid never meets gas.  The first marker lists
@@ -138,6 +154,7 @@ __global__ void __launch_bounds__(128) k_conv_mark(Params p) {
           if (mk == MK_EMPTY) {  // this cell turns gas
             atomicOr(p.gas_dirty, 1);
             if (p.tdirty) p.tdirty[tile_of<D>(p, c)] = 1;
+            if (p.lab_slow && !joins_own_bubble<D>(p, c, n, fn)) atomicOr(p.lab_slow, 1);
           }
           if (put == MK_GI && claimed) atomicOr(p.gas_dirty, 2);  // gas cells turn interface
         }

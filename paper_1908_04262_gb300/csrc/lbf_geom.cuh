@@ -15,7 +15,8 @@
 // kappa = -(mean curvature), so a gas sphere
 // has kappa = 1/R and a gas disk 1/(2R); limited to [-1, 1].
 // Disjoining pressure: march from the cell centre along the normal, cell
-// boundary by cell boundary (Algorithm 1, ties step diagonally), until an
+// boundary by cell boundary (Algorithm 1, ties -- equal within a relative
+// 1e-9, 1e-5 in single precision -- step diagonally), until an
 // interface or gas cell of another bubble is met; d is the distance from this
 // cell's plane to the other cell's plane along the ray (or to where the ray
 // enters it when that plane does not face the ray); Pi = k_Pi (d_max - d)
@@ -409,10 +410,14 @@ __global__ void k_disjoining(Params p) {
   }
   R dist = -1;
   const R s0 = ds[n];
+  // axes whose next boundary lies at the same ray parameter (within a
+  // relative 1e-9, 1e-5 in single precision) are crossed together, so that
+  // round-off in a normal with equal components cannot split a diagonal step
+  const R tie = (R)1 + (R)(sizeof(R) == 4 ? 1e-5 : 1e-9);
   for (int it = 1; it <= p.ray_steps; ++it) {
     const R tm = fmin(tmax[0], fmin(tmax[1], tmax[2]));
     for (int d = 0; d < 3; ++d)
-      if (tmax[d] == tm) {
+      if (tmax[d] <= tm * tie) {
         tmax[d] += tdel[d];
         off[d] += step[d];
       }

@@ -85,6 +85,7 @@ static __global__ void k_label_prep(Params p) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cap; k += gridDim.x * blockDim.x) {
     p.tnew.V[k] = 0.0;
     p.tnew.atm[k] = 0;
+    p.tnew.ng[k] = 0;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *p.nroots = 0;
 }
@@ -443,7 +444,12 @@ static __global__ void k_sort_roots(Params p) {
     p.roots[k] = sr[k];
     if (p.rlabel) p.rlabel[sr[k]] = k;
   }
-  if (threadIdx.x == 0) *p.tnew.count = cnt;
+  if (threadIdx.x == 0) {
+    *p.tnew.count = cnt;
+    // every thread read the labelling mode before the sort's barriers: the
+    // forest is current again
+    if (p.forest_stale) *p.forest_stale = 0;
+  }
 }
 
 __device__ __forceinline__ int root_index(const int *roots, int cnt, int r) {
@@ -486,11 +492,11 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
   const long long n = c.n;
   const uint8_t fl = inr ? p.flags[n] : (uint8_t)T_WALL;
   const int t = post_type(fl);
-  int knew = -1;
+  int knew = -1, ngas = 0;
   double v = 0.0;
   if (t == T_GAS) {
     knew = p.rlabel[p.parent[n]];
-    v = (double)p.lsize[n];  // non-zero only at tile-local roots
+    ngas = p.lsize[n];  // non-zero only at tile-local roots
     if (p.atmosphere && knew >= 0 && (D == 2 ? c.y : c.z) == p.top_layer && !p.tnew.atm[knew]) p.tnew.atm[knew] = 1;
   } else if (t == T_IFC) {
 #pragma unroll
@@ -504,6 +510,10 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
     if (knew >= 0) v = 1.0 - (double)((const R *)p.phi)[n];
   }
   if (inr) p.label_new[n] = knew;
+  // gas cells are counted (the bubble update adds them to the volume),
+  // interface cells add their gas share 1 - alpha
+  const bool gcontrib = knew >= 0 && ngas != 0;
+  if (__any_sync(0xffffffffu, gcontrib)) agg_count(p.tnew.ng, gcontrib ? knew : -1, ngas);
   const bool contrib = knew >= 0 && v != 0.0;
   if (__any_sync(0xffffffffu, contrib)) agg_add(p.tnew.V, contrib ? knew : -1, v, wbuf + (threadIdx.x & ~31));
   // old -> new overlap pairs (cells without a new label have none: no
@@ -547,6 +557,7 @@ static __global__ void __launch_bounds__(1024) k_bubble_update(Params p) {
     gvmax[k] = 0ull;
   }
   for (int j = tid; j < nold; j += nt) p.told.m[j] += p.told.dm[j];
+  for (int k = tid; k < nnew; k += nt) p.tnew.V[k] += (double)p.tnew.ng[k];
   __syncthreads();
   bool ok = true;
   for (int h = tid; h < nh; h += nt) {
@@ -658,6 +669,122 @@ static __global__ void __launch_bounds__(1024) k_bubble_update(Params p) {
   for (int k = tid; k < p.cap; k += nt) {
     p.told.V[k] = 0.0;
     p.told.atm[k] = 0;
+    p.told.ng[k] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Labelling of a step whose conversion only added gas cells, none of which
+// touches a gas cell of another bubble or has a smaller index than its
+// bubble's root (the marking checks this and sets lab_slow otherwise): every
+// bubble keeps its cells, its number and its root, so the labels of the last
+// step stand except at the filled cells (-1), the added gas cells (the label
+// they had as interface cells, which is their bubble's) and the interface
+// cells after the conversion (smallest label of their gas neighbours).  The
+// result equals the full labelling's.  The step graph picks this branch or
+// the full one on the device: k_label_cond sets the conditional node's value
+// (1 full, 0 this one).
+static __global__ void k_label_cond(Params p, cudaGraphConditionalHandle h) {
+  const int d = *p.gas_dirty;
+  const bool fast = (d == 0 || d == 1) && *p.lab_slow == 0;
+  cudaGraphSetConditional(h, fast ? 0u : 1u);
+  *p.lab_slow = 0;
+}
+
+// label_new holds a copy of label_old when this runs.  One thread per marked
+// cell, then per interface cell after the conversion; gas counts grow by the
+// added cells; volumes collect the interface shares 1 - alpha.
+template <int D, class R>
+__global__ void __launch_bounds__(128) k_label_fast(Params p) {
+  __shared__ double wbuf[128];
+  const int nb = *p.told.count, nm = *p.mcount, ni = *p.inext_count;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthreads = gridDim.x * blockDim.x;
+  if (tid == 0) {
+    *p.tnew.count = nb;
+    if (*p.gas_dirty == 1) *p.forest_stale = 1;  // added gas cells the forest does not hold
+  }
+  for (int k = tid; k < nb; k += nthreads) {
+    atomicAdd(p.tnew.ng + k, p.told.ng[k]);
+    if (p.told.atm[k]) p.tnew.atm[k] = 1;
+  }
+  const int total = nm + ni;
+  for (int base = 0; base < total; base += nthreads) {
+    const int k = base + tid;
+    int kg = -1, kv = -1;
+    double v = 0.0;
+    if (k < nm) {
+      const int n = p.mlist[k];
+      const int t = post_type(p.flags[n]);
+      if (t == T_LIQ) {
+        p.label_new[n] = -1;
+      } else if (t == T_GAS) {
+        kg = p.label_old[n];
+        if (p.atmosphere && kg >= 0) {
+          const Cell c = make_cell(p, n);
+          if ((D == 2 ? c.y : c.z) == p.top_layer) p.tnew.atm[kg] = 1;
+        }
+      }
+    } else if (k < total) {
+      const int n = p.inext[k - nm];
+      const Cell c = make_cell(p, n);
+      int knew = -1;
+#pragma unroll
+      for (int i = 1; i < Lat<D>::Q; ++i) {
+        const int m = nb<D>(p, c, i);
+        if (post_type(p.flags[m]) == T_GAS) {
+          const int l = p.label_old[m];
+          if (l >= 0 && (knew < 0 || l < knew)) knew = l;
+        }
+      }
+      p.label_new[n] = knew;
+      if (knew >= 0) {
+        v = 1.0 - (double)((const R *)p.phi)[n];
+        if (v != 0.0) kv = knew;
+      }
+    }
+    if (__any_sync(0xffffffffu, kg >= 0)) agg_count(p.tnew.ng, kg, 1);
+    if (__any_sync(0xffffffffu, kv >= 0)) agg_add(p.tnew.V, kv, v, wbuf + (threadIdx.x & ~31));
+  }
+}
+
+// the bubble update of such a step: every group is one old and one new
+// bubble with the same number, so each bubble keeps its id and gas (plus the
+// flux of this step); the arithmetic is the general update's for such a
+// group.  One thread per bubble.
+static __global__ void k_bubble_update_fast(Params p) {
+  const int nb = *p.tnew.count;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  for (int k = tid; k < nb; k += nt) {
+    const double mold = p.told.m[k] + p.told.dm[k];
+    p.told.m[k] = mold;
+    const double V = p.tnew.V[k] + (double)p.tnew.ng[k];
+    p.tnew.V[k] = V;
+    double m, pr;
+    if (p.tnew.atm[k]) {
+      atomicAdd(p.led + 5, mold);
+      pr = p.p0;
+      m = p.p0 * V / p.RT;
+      atomicAdd(p.led + 5, -m);
+    } else {
+      m = mold * V / V;
+      pr = m * p.RT / V;
+    }
+    p.tnew.m[k] = m;
+    p.tnew.p[k] = pr;
+    p.tnew.dm[k] = 0.0;
+    p.tnew.root[k] = p.told.root[k];
+    p.tnew.id[k] = p.told.id[k];
+  }
+  if (tid == 0) {
+    *p.hcount = 0;
+    *p.nroots = 0;
+    if (p.gas_dirty) *p.gas_dirty = 0;
+  }
+  // the old table is the next step's new table: clear its accumulators
+  for (int k = tid; k < p.cap; k += nt) {
+    p.told.V[k] = 0.0;
+    p.told.atm[k] = 0;
+    p.told.ng[k] = 0;
   }
 }
 

@@ -106,6 +106,17 @@ struct OpsImpl final : Ops {
     k_relabel<D, R><<<row_grid(p), row_block(p), 0, s>>>(p);
   }
   void bubble_update(const Params &p, cudaStream_t s) override { k_bubble_update<<<1, 1024, 0, s>>>(p); }
+  void label_cond(const Params &p, cudaGraphConditionalHandle h, cudaStream_t s) override {
+    k_label_cond<<<1, 1, 0, s>>>(p, h);
+  }
+  void label_fast(const Params &p, cudaStream_t s) override {
+    cudaMemcpyAsync(p.label_new, p.label_old, sizeof(int) * (size_t)p.N, cudaMemcpyDeviceToDevice, s);
+    k_label_fast<D, R><<<p.list_blocks, 128, 0, s>>>(p);
+  }
+  void bubble_update_fast(const Params &p, cudaStream_t s) override {
+    const unsigned g = blocks_for(p.cap, 128);
+    k_bubble_update_fast<<<g < (unsigned)p.list_blocks ? g : (unsigned)p.list_blocks, 128, 0, s>>>(p);
+  }
   void geometry(const Params &p, cudaStream_t s) override {
     k_geometry<D, R><<<p.warp_blocks, 128, 0, s>>>(p);
     if (p.kappa_hf) k_hf_kappa<D, R><<<p.list_blocks, 128, 0, s>>>(p);

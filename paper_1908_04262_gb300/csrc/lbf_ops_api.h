@@ -42,6 +42,13 @@ struct Ops {
   }
   virtual void label_prep(const Params &p, cudaStream_t s) = 0;
   virtual void bubble_update(const Params &p, cudaStream_t s) = 0;
+  // a step whose added gas cells keep every bubble's cells, number and root
+  // (decided on the device after the marking): the branch value of the step
+  // graph's conditional nodes (1 full labelling, 0 this path), the labels
+  // of the last step patched, and the bubble update of one-to-one groups
+  virtual void label_cond(const Params &p, cudaGraphConditionalHandle h, cudaStream_t s) = 0;
+  virtual void label_fast(const Params &p, cudaStream_t s) = 0;
+  virtual void bubble_update_fast(const Params &p, cudaStream_t s) = 0;
   virtual void geometry(const Params &p, cudaStream_t s) = 0;
   virtual void disjoining(const Params &p, cudaStream_t s) = 0;
   virtual void mlp_kappa(const Params &p, const void *img, cudaStream_t s) = 0;
