@@ -210,6 +210,7 @@ int lbf_cell_counts(lbf_sim *s, long long *out4);
 /* Number of completed steps. */
 long long lbf_step_count(const lbf_sim *s);
 
+
 const char *lbf_last_error(void);
 
 /* ------------------------------------------------------------------------

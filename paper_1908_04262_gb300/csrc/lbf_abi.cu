@@ -50,9 +50,6 @@ struct lbf_sim {
   cudaStream_t st = nullptr;
   bool own_stream = false;
   cudaStream_t st2 = nullptr, st3 = nullptr, st4 = nullptr;  // further branches of the step graphs
-  cudaStream_t stc = nullptr;  // captures the bodies of conditional nodes
-  bool use_cond = true;        // step graphs choose the labelling branch on the device
-  int capture_err = 0;         // first failure while adding conditional nodes
   int prio_least = 0, prio_greatest = 0;      // stream priority range of the device
   std::vector<cudaGraphNode_t> low_nodes;      // liquid sweeps captured on the third branch
   cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr}, joinx = nullptr, joinex = nullptr,
@@ -89,6 +86,8 @@ struct lbf_sim {
   int *gas_dirty = nullptr;
   int *lab_slow = nullptr;
   int *forest_stale = nullptr;
+  int *lab_fast = nullptr;
+  int tile_blocks = 0;
   uint8_t *tdirty = nullptr;
   size_t ntiles_alloc = 0;
   unsigned *wmask = nullptr;
@@ -184,6 +183,8 @@ Params make_params(lbf_sim *s, long long step) {
   p.gas_dirty = s->gas_dirty;
   p.lab_slow = s->lab_slow;
   p.forest_stale = s->forest_stale;
+  p.lab_fast = s->lab_fast;
+  p.tile_blocks = s->tile_blocks;
   p.tdirty = s->tdirty;
   p.rlabel = s->rlabel;
   p.tau_tab = s->tau_tab; p.tab_n = s->tab_n; p.tab_lnA0 = s->tab_lnA0; p.tab_inv_dlnA = s->tab_inv_dlnA;
@@ -222,6 +223,7 @@ int relabel_in_place(lbf_sim *s) {
   s->ops->label_prep(p, s->st);
   // the state was set from outside: label from scratch
   CK(cudaMemsetAsync(s->gas_dirty, 0xff, sizeof(int), s->st));
+  CK(cudaMemsetAsync(s->lab_fast, 0, sizeof(int), s->st));
   s->ops->label(p, s->st);
   s->ops->bubble_update(p, s->st);
   const size_t cap = (size_t)s->cap;
@@ -268,94 +270,6 @@ void enqueue_geometry(lbf_sim *s, const Params &pn, cudaStream_t st) {
   if (s->mlp_theta) s->ops->mlp_kappa(pn, s->mlp_theta, st);
 }
 
-// kernel nodes of a graph (a conditional node's body) at the greatest stream
-// priority
-cudaError_t body_priorities(lbf_sim *s, cudaGraph_t gr) {
-  size_t nn = 0;
-  cudaError_t e = cudaGraphGetNodes(gr, nullptr, &nn);
-  if (e != cudaSuccess || nn == 0) return e;
-  std::vector<cudaGraphNode_t> nodes(nn);
-  e = cudaGraphGetNodes(gr, nodes.data(), &nn);
-  for (size_t j = 0; j < nn && e == cudaSuccess; ++j) {
-    cudaGraphNodeType t;
-    e = cudaGraphNodeGetType(nodes[j], &t);
-    if (e != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
-    cudaLaunchAttributeValue v;
-    std::memset(&v, 0, sizeof(v));
-    v.priority = s->prio_greatest;
-    e = cudaGraphKernelNodeSetAttribute(nodes[j], cudaLaunchAttributePriority, &v);
-  }
-  return e;
-}
-
-// adds, at the current point of the capture on the main stream, a
-// conditional IF node with `size` bodies (body 0 runs when the handle's
-// value is non-zero, body 1 otherwise) and fills each body by running
-// fill(k, stream) under a capture into that body
-template <class F> void add_conditional(lbf_sim *s, cudaGraphConditionalHandle h, int size, F &&fill) {
-  if (s->capture_err) return;
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  cudaGraph_t g = nullptr;
-  const cudaGraphNode_t *deps = nullptr;
-  const cudaGraphEdgeData *ed = nullptr;
-  size_t nd = 0;
-  cudaError_t e = cudaStreamGetCaptureInfo(s->st, &cs, nullptr, &g, &deps, &ed, &nd);
-  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};  // every other field zero
-  np.conditional.handle = h;
-  np.conditional.type = cudaGraphCondTypeIf;
-  np.conditional.size = (unsigned)size;
-  cudaGraphNode_t node = nullptr;
-  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, deps, ed, nd, &np);
-  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(s->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
-  for (int k = 0; k < size && e == cudaSuccess; ++k) {
-    cudaGraph_t body = np.conditional.phGraph_out[k];
-    e = cudaStreamBeginCaptureToGraph(s->stc, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-    if (e != cudaSuccess) break;
-    fill(k, s->stc);
-    cudaGraph_t out = nullptr;
-    e = cudaStreamEndCapture(s->stc, &out);
-    if (e == cudaSuccess) e = body_priorities(s, body);
-  }
-  if (e != cudaSuccess) s->capture_err = (int)e;
-}
-
-// The labelling branch of a step is chosen on the device: the full
-// union-find labelling, or, after a conversion that kept every bubble's
-// cells, number and root, the labels of the last step patched
-// (k_label_fast).  label_choice sets the branch value (after the marking)
-// and runs the union-find forest when it is needed; label_finish relabels or
-// patches (after the excess pass: both read fill levels); bubble_branches
-// updates the bubble table to match.
-cudaGraphConditionalHandle label_choice(lbf_sim *s, const Params &p) {
-  cudaGraphConditionalHandle h = 0;
-  if (!s->capture_err) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamGetCaptureInfo(s->st, &cs, nullptr, &g, nullptr, nullptr, nullptr);
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) s->capture_err = (int)e;
-  }
-  if (!s->capture_err) s->ops->label_cond(p, h, s->st);
-  add_conditional(s, h, 1, [&](int, cudaStream_t b) { s->ops->label_forest(p, b); });
-  return h;
-}
-void label_finish(lbf_sim *s, const Params &p, cudaGraphConditionalHandle h) {
-  add_conditional(s, h, 2, [&](int k, cudaStream_t b) {
-    if (k == 0)
-      s->ops->label_relabel(p, b);
-    else
-      s->ops->label_fast(p, b);
-  });
-}
-void bubble_branches(lbf_sim *s, const Params &p, cudaGraphConditionalHandle h) {
-  add_conditional(s, h, 2, [&](int k, cudaStream_t b) {
-    if (k == 0)
-      s->ops->bubble_update(p, b);
-    else
-      s->ops->bubble_update_fast(p, b);
-  });
-}
-
 // everything of a step after its interface sweep.  The marking runs first;
 // then every cell's post-conversion type is known and the union-find passes
 // start, beside the excess pass (which with `waitx` also waits for the
@@ -377,6 +291,9 @@ void bubble_branches(lbf_sim *s, const Params &p, cudaGraphConditionalHandle h) 
 void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const Params *pnext, int parnext) {
   const Params pn = next_geometry_params(p);
   s->ops->convert_mark(p, s->st);
+  // reads the marks of the gas cells turned interface: before the excess
+  // pass, so before the flag rewrite
+  s->ops->label_check(p, s->st);
   cudaEventRecord(s->fork[0], s->st);
   cudaStreamWaitEvent(s->st2, s->fork[0], 0);
   if (waitx) cudaStreamWaitEvent(s->st2, s->joinx, 0);
@@ -411,19 +328,16 @@ void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const
       s->low_nodes.insert(s->low_nodes.end(), deps, deps + nd);
     cudaEventRecord(s->joinx, s->st3);
   }
-  if (s->use_cond) {
-    const cudaGraphConditionalHandle h = label_choice(s, p);
-    cudaStreamWaitEvent(s->st, s->applied, 0);
-    label_finish(s, p, h);
-    cudaEventRecord(s->fork[1], s->st);
-    bubble_branches(s, p, h);
-  } else {
-    s->ops->label_forest(p, s->st);
-    cudaStreamWaitEvent(s->st, s->applied, 0);
-    s->ops->label_relabel(p, s->st);
-    cudaEventRecord(s->fork[1], s->st);
-    s->ops->bubble_update(p, s->st);
-  }
+  // the labelling branch is chosen on the device after the marking (see
+  // k_label_choose): the kernels of the branch not taken return at once
+  s->ops->label_choose(p, s->st);
+  s->ops->label_forest(p, s->st);
+  cudaStreamWaitEvent(s->st, s->applied, 0);
+  s->ops->label_relabel(p, s->st);
+  s->ops->label_fast(p, s->st);
+  cudaEventRecord(s->fork[1], s->st);
+  s->ops->bubble_update(p, s->st);
+  s->ops->bubble_update_fast(p, s->st);
   cudaStreamWaitEvent(s->st4, s->fork[1], 0);
   cudaStreamWaitEvent(s->st4, s->join[0], 0);
   s->ops->disjoining(pn, s->st4);
@@ -446,21 +360,21 @@ void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
   group(G_IFACE, [&] { s->ops->stream_interface(p, par, s->st); });
   if (ev) {
     group(G_CONVERT, [&] {
-      s->ops->convert(p, par, s->st);
+      s->ops->convert_mark(p, s->st);
+      s->ops->label_check(p, s->st);
+      s->ops->convert_excess(p, par, s->st);
       s->ops->convert_finalize(p, s->st);
     });
     const Params pn = next_geometry_params(p);
-    if (s->use_cond) {
-      cudaGraphConditionalHandle h = 0;
-      group(G_LABEL, [&] {
-        h = label_choice(s, p);
-        label_finish(s, p, h);
-      });
-      group(G_BUBBLE, [&] { bubble_branches(s, p, h); });
-    } else {
-      group(G_LABEL, [&] { s->ops->label(p, s->st); });
-      group(G_BUBBLE, [&] { s->ops->bubble_update(p, s->st); });
-    }
+    group(G_LABEL, [&] {
+      s->ops->label_choose(p, s->st);
+      s->ops->label(p, s->st);
+      s->ops->label_fast(p, s->st);
+    });
+    group(G_BUBBLE, [&] {
+      s->ops->bubble_update(p, s->st);
+      s->ops->bubble_update_fast(p, s->st);
+    });
     group(G_GEOMETRY, [&] { enqueue_geometry(s, pn, s->st); });
     group(G_DISJOIN, [&] { s->ops->disjoining(pn, s->st); });
     return;
@@ -505,28 +419,12 @@ int set_node_priorities(lbf_sim *s, cudaGraph_t gr) {
   return 0;
 }
 
-// a capture that could not add its conditional nodes is discarded and
-// redone with the full labelling in every step
-int conditional_fallback(lbf_sim *s, cudaGraph_t gr) {
-  if (!s->capture_err) return 0;
-  if (gr) cudaGraphDestroy(gr);
-  cudaGetLastError();
-  s->capture_err = 0;
-  s->use_cond = false;
-  return 1;
-}
-
 int capture_chain(lbf_sim *s, const Params *ps, int par, int k, cudaGraphExec_t *out) {
   cudaGraph_t gr = nullptr;
   s->low_nodes.clear();
-  s->capture_err = 0;
   CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
   enqueue_chain(s, ps, par, k);
-  {
-    const cudaError_t e = cudaStreamEndCapture(s->st, &gr);
-    if (conditional_fallback(s, gr)) return capture_chain(s, ps, par, k, out);
-    if (e != cudaSuccess) return fail(LBF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
-  }
+  CK(cudaStreamEndCapture(s->st, &gr));
   int rc = set_node_priorities(s, gr);
   s->low_nodes.clear();
   if (rc) {
@@ -541,14 +439,9 @@ int capture_chain(lbf_sim *s, const Params *ps, int par, int k, cudaGraphExec_t 
 
 int capture(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev, cudaGraphExec_t *out) {
   cudaGraph_t gr = nullptr;
-  s->capture_err = 0;
   CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
   enqueue_step(s, p, par, ev);
-  {
-    const cudaError_t e = cudaStreamEndCapture(s->st, &gr);
-    if (conditional_fallback(s, gr)) return capture(s, p, par, ev, out);
-    if (e != cudaSuccess) return fail(LBF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
-  }
+  CK(cudaStreamEndCapture(s->st, &gr));
   cudaError_t e = cudaGraphInstantiate(out, gr, 0);
   cudaGraphDestroy(gr);
   if (e != cudaSuccess) return fail(LBF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
@@ -835,7 +728,6 @@ void lbf_destroy(lbf_sim *s) {
   if (s->st2) cudaStreamDestroy(s->st2);
   if (s->st3) cudaStreamDestroy(s->st3);
   if (s->st4) cudaStreamDestroy(s->st4);
-  if (s->stc) cudaStreamDestroy(s->stc);
   if (s->own_stream && s->st) cudaStreamDestroy(s->st);
   delete s->ops;
   delete s;
@@ -877,7 +769,6 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->st2, cudaStreamNonBlocking, s->prio_greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->st3, cudaStreamNonBlocking, s->prio_least);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->st4, cudaStreamNonBlocking, s->prio_greatest);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->stc, cudaStreamNonBlocking, s->prio_greatest);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joinx, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joinex, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fin, cudaEventDisableTiming);
@@ -899,6 +790,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     s->list_blocks = 4 * (sms > 0 ? sms : 132);
     s->warp_blocks = 16 * (sms > 0 ? sms : 132);
+    s->tile_blocks = 2 * (sms > 0 ? sms : 132);
   }
   s->cap = cfg->bubble_capacity;
   int hs = 1024;
@@ -984,6 +876,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   AL(dalloc(s, &s->gas_dirty, 1));
   AL(dalloc(s, &s->lab_slow, 1));
   AL(dalloc(s, &s->forest_stale, 1));
+  AL(dalloc(s, &s->lab_fast, 1));
   AL(dalloc(s, &s->wmask, N));
   AL(dalloc(s, &s->rlabel, N));
   AL(dalloc(s, &s->acc, 4));
@@ -1021,6 +914,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   e = e ? e : zero(s->gas_dirty, sizeof(int));
   e = e ? e : zero(s->lab_slow, sizeof(int));
   e = e ? e : zero(s->forest_stale, sizeof(int));
+  e = e ? e : zero(s->lab_fast, sizeof(int));
   e = e ? e : zero(s->tdirty, s->ntiles_alloc);
   if (e != cudaSuccess) {
     lbf_destroy(s);
@@ -1141,6 +1035,7 @@ int lbf_step(lbf_sim *s, int nsteps) {
 }
 
 long long lbf_step_count(const lbf_sim *s) { return s ? s->step : -1; }
+
 
 int lbf_mlp_harvest(lbf_sim *s, float *x, float *y, int *cells, int cap, int *count) {
   if (!s || !x || !y || cap < 0 || !count) return fail(LBF_EINVAL, "bad arguments");

@@ -149,10 +149,16 @@ struct Params {
   // move a bubble's smallest cell index: the step then needs the full
   // labelling (else the labels of the last step, patched, are exact)
   int *lab_slow;
-  // 1 after a step labelled without the union-find added gas cells: the
-  // forest lags behind in the touched tiles (tdirty) until the next
-  // union-find labelling redoes them
+  // after steps labelled without the union-find: bit 0, gas cells were
+  // added (the forest lags behind in the touched tiles, tdirty, which the
+  // next union-find labelling redoes); bit 1, gas cells were removed (the
+  // next union-find labelling rebuilds the forest)
   int *forest_stale;
+  // 1 while this step labels by patching the last labels (set on the device
+  // after the marking; the union-find kernels then return at once, and the
+  // patch kernels do otherwise).  NULL means the union-find labelling.
+  int *lab_fast;
+  int tile_blocks;  // grid of the tile loops of the union-find (two blocks per SM)
   // label of each current root cell (rank among the sorted roots, -1 past
   // the bubble capacity); read only at cells that are roots
   int *rlabel;
@@ -334,10 +340,18 @@ enum : int { LABEL_SKIP = 0, LABEL_ADDED = 1, LABEL_FULL = 2 };
 __device__ __forceinline__ int label_mode(const Params &p) {
   if (!p.gas_dirty || !p.tdirty) return LABEL_FULL;
   const int d = *p.gas_dirty;
-  if (d == 0) return (p.forest_stale && *p.forest_stale) ? LABEL_ADDED : LABEL_SKIP;
+  const int stale = p.forest_stale ? *p.forest_stale : 0;
+  if (stale & 2) return LABEL_FULL;  // the forest still holds removed gas cells
+  if (d == 0) return stale ? LABEL_ADDED : LABEL_SKIP;
   return d == 1 ? LABEL_ADDED : LABEL_FULL;
 }
 __device__ __forceinline__ bool gas_unchanged(const Params &p) { return label_mode(p) == LABEL_SKIP; }
+__device__ __forceinline__ bool label_fast(const Params &p) { return p.lab_fast && *p.lab_fast; }
+
+// linear block index and block count of any grid shape (loops over work
+// items that take one block each)
+__device__ __forceinline__ int block_id() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
+__device__ __forceinline__ int block_count() { return gridDim.x * gridDim.y * gridDim.z; }
 
 // union-find tiles: 32 x-rows of 32 cells
 template <int D> struct Tile;

@@ -91,22 +91,6 @@ __device__ __forceinline__ bool mark_byte(uint8_t *flags, long long m, int mk) {
   return ((old >> sh) & (7u << 2)) == 0;
 }
 
-// An added gas cell n keeps the bubble structure of the last labelling when
-// it carries a bubble label L (the smallest of its gas neighbours' as an
-// interface cell), lies above that bubble's root (so the bubble's smallest
-// cell index stays), and every gas or emptying neighbour carries L as well
-// (so it joins no other bubble).  The labelling then needs no union-find.
-template <int D>
-__device__ __forceinline__ bool joins_own_bubble(const Params &p, const Cell &c, int n, const uint8_t *fn) {
-  const int L = p.label_old[n];
-  if (L < 0 || n <= p.told.root[L]) return false;
-  bool ok = true;
-#pragma unroll
-  for (int i = 1; i < Lat<D>::Q; ++i)
-    if ((ftype(fn[i]) == T_GAS || fmark(fn[i]) == MK_EMPTY) && p.label_old[nb<D>(p, c, i)] != L) ok = false;
-  return ok;
-}
-
 // An emptying cell next to a filling cell stays interface (filling wins);
 // gas next to a filling cell and liquid next to a (still) emptying cell
 // become interface, so that liquid never meets gas.  The first marker lists
@@ -154,7 +138,6 @@ __global__ void __launch_bounds__(128) k_conv_mark(Params p) {
           if (mk == MK_EMPTY) {  // this cell turns gas
             atomicOr(p.gas_dirty, 1);
             if (p.tdirty) p.tdirty[tile_of<D>(p, c)] = 1;
-            if (p.lab_slow && !joins_own_bubble<D>(p, c, n, fn)) atomicOr(p.lab_slow, 1);
           }
           if (put == MK_GI && claimed) atomicOr(p.gas_dirty, 2);  // gas cells turn interface
         }
@@ -184,6 +167,106 @@ __global__ void __launch_bounds__(128) k_conv_mark(Params p) {
 // cell k of the marked list followed by the new-interface list
 __device__ __forceinline__ long long list_cell(const Params &p, int k, int nm) {
   return k < nm ? p.mlist[k] : p.nlist[k - nm];
+}
+
+// An added gas cell (an emptied interface cell) keeps the bubble structure
+// of the last labelling when it carries a bubble label L (the smallest of
+// its gas neighbours' as an interface cell), lies above that bubble's root
+// (the bubble's smallest cell index stays), every gas neighbour after the
+// conversion carries L (it joins no other bubble) and one of them is a gas
+// cell of the last step that stays gas (it is joined to its bubble).
+template <int D>
+__device__ __forceinline__ bool addition_keeps_bubble(const Params &p, const Cell &c, int n) {
+  const int L = p.label_old[n];
+  if (L < 0 || n <= p.told.root[L]) return false;
+  bool anchored = false;
+#pragma unroll
+  for (int i = 1; i < Lat<D>::Q; ++i) {
+    const int m = nb<D>(p, c, i);
+    const uint8_t f = p.flags[m];
+    if (post_type(f) != T_GAS) continue;
+    if (p.label_old[m] != L) return false;
+    if (ftype(f) == T_GAS) anchored = true;  // gas before, and no mark turns it interface
+  }
+  return anchored;
+}
+
+// A gas cell turning interface (a filling neighbour claimed it) keeps the
+// bubble structure of the last labelling when it is not its bubble's root,
+// not in the top layer (the headspace flag), its gas neighbours after the
+// conversion stay connected to one another inside its own 3^d neighbourhood
+// (over D2Q9 / D3Q19 links between neighbourhood cells), and it shares a
+// gas neighbour with every linked cell that turns interface with it.  Then
+// any path of gas cells through a run of such cells can go round them
+// (from one shared neighbour to the next), so no bubble splits or vanishes.
+template <int D>
+__device__ __forceinline__ bool cube_link(int a, int b) {
+  const int ddx = abs(a % 3 - b % 3), ddy = abs((a / 3) % 3 - (b / 3) % 3), ddz = D == 3 ? abs(a / 9 - b / 9) : 0;
+  return a != b && ddx <= 1 && ddy <= 1 && ddz <= 1 && (D == 2 || ddx + ddy + ddz <= 2);
+}
+template <int D>
+__device__ __forceinline__ bool removal_keeps_bubble(const Params &p, const Cell &c, int n) {
+  constexpr int NS = D == 3 ? 27 : 9, CTR = D == 3 ? 13 : 4;
+  const int L = p.label_old[n];
+  if (L < 0 || n == p.told.root[L]) return false;
+  if (p.atmosphere && (D == 2 ? c.y : c.z) == p.top_layer) return false;
+  unsigned gas = 0, link = 0, gone = 0;  // bit k: stencil cell k is gas after the conversion /
+                                         // a gas neighbour of the centre / linked and turning interface
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    if (k == CTR) continue;
+    const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = D == 3 ? k / 9 - 1 : 0;
+    const uint8_t f = p.flags[at(p, c, dx, dy, dz)];
+    const bool centre_link = cube_link<D>(k, CTR);
+    if (centre_link && ftype(f) == T_GAS && fmark(f) == MK_GI) gone |= 1u << k;
+    if (post_type(f) == T_GAS) {
+      gas |= 1u << k;
+      if (centre_link) link |= 1u << k;
+    }
+  }
+  if (!link) return false;  // it was a bubble of its own
+  // a shared gas neighbour with every linked cell turning interface
+  for (unsigned g = gone; g; g &= g - 1) {
+    const int b = __ffs(g) - 1;
+    bool shared = false;
+    for (unsigned q = link; q; q &= q - 1) shared |= cube_link<D>(__ffs(q) - 1, b);
+    if (!shared) return false;
+  }
+  // flood fill over the gas cells of the neighbourhood from one linked cell
+  unsigned reach = link & (~link + 1u), grown = 0;
+  while (reach != grown) {
+    grown = reach;
+    for (unsigned r = reach; r; r &= r - 1) {
+      const int a = __ffs(r) - 1;
+      for (unsigned q = gas & ~reach; q; q &= q - 1) {
+        const int b = __ffs(q) - 1;
+        if (cube_link<D>(a, b)) reach |= 1u << b;
+      }
+    }
+  }
+  return (link & ~reach) == 0;
+}
+
+// after the marking (every mark final): the emptied cells are on the marked
+// list, the gas cells turned interface on the new-interface list; any of
+// them that could join, split, empty or re-root a bubble vetoes the patched
+// labelling of this step (lab_slow)
+template <int D>
+__global__ void __launch_bounds__(128) k_label_check(Params p) {
+  const int nm = *p.mcount, total = nm + *p.ncount;
+  for (int base = 0; base < total; base += gridDim.x * blockDim.x) {
+    const int k = spread_index(base);
+    if (k >= total) continue;
+    const int n = (int)list_cell(p, k, nm);
+    const uint8_t f = p.flags[n];
+    bool ok = true;
+    if (k < nm) {
+      if (post_type(f) == T_GAS) ok = addition_keeps_bubble<D>(p, make_cell(p, n), n);
+    } else if (ftype(f) == T_GAS) {  // (liquid turning interface changes no bubble)
+      ok = removal_keeps_bubble<D>(p, make_cell(p, n), n);
+    }
+    if (!ok) atomicOr(p.lab_slow, 1);
+  }
 }
 
 // par: parity of the populations after the sweep

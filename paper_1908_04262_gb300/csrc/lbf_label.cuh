@@ -165,113 +165,120 @@ template <int D>
 __global__ void __launch_bounds__(TILE_THREADS) k_uf_local(Params p) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ, NR = TY * TZ;
   static_assert(TX == 32 && NR == 32, "a tile is 32 rows of 32 cells");
+  if (label_fast(p)) return;
   const int mode = label_mode(p);
   if (mode == LABEL_SKIP) return;
-  // a step that only added gas cells redoes the tiles it touched only
-  if (mode == LABEL_ADDED && !p.tdirty[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)]) return;
   __shared__ int lp[TN];
   __shared__ int lsz[TN];
   __shared__ unsigned rowm[NR];
   __shared__ int sg, sc, nroot, rfirst;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
   const long long nx = p.nx, nxy = (long long)p.nx * p.ny;
-  if (threadIdx.x == 0) {
-    sg = 0;
-    sc = 0;
-    nroot = 0;
-    rfirst = TN;
-  }
-  __syncthreads();
-  // row masks, runs
-  for (int r = warp; r < NR; r += TILE_THREADS / 32) {
-    const int x = x0 + lane, y = y0 + r % TY, z = z0 + r / TY;
-    const bool inside = x < p.nx && y < p.ny && z < p.nz;
-    const bool gas = inside && post_type(p.flags[x + nx * y + nxy * z]) == T_GAS;
-    const unsigned m = __ballot_sync(0xffffffffu, gas), in = __ballot_sync(0xffffffffu, inside);
-    if (lane == 0) {
-      rowm[r] = m;
-      if (m) atomicAdd(&sg, __popc(m));
-      atomicAdd(&sc, __popc(in));
-    }
-    const unsigned starts = m & ~(m << 1);
-    lp[r * TX + lane] = gas ? r * TX + (31 - __clz(starts & (0xffffffffu >> (31 - lane)))) : -1;
-    lsz[r * TX + lane] = 0;
-  }
-  __syncthreads();
-  const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  const long long root0 = x0 + nx * y0 + nxy * z0;
-  if (sg == 0) {
-    if (threadIdx.x == 0) p.tstat[tile] = 0;
-    return;
-  }
-  if (sg == sc) {  // every cell is gas: one component rooted at the first cell
+  const TileGrid<D> tgd(p);
+  const int ntiles = tgd.ntx * tgd.nty * tgd.ntz;
+  // blocks walk the tiles (one block per tile when the grid has as many)
+  for (int tile = block_id(); tile < ntiles; tile += block_count()) {
+    // a step that only added gas cells redoes the tiles it touched only
+    if (mode == LABEL_ADDED && !p.tdirty[tile]) continue;
+    const int bx = tile % tgd.ntx, by = (tile / tgd.ntx) % tgd.nty, bz = tile / (tgd.ntx * tgd.nty);
+    const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+    __syncthreads();  // the shared arrays of the last tile are no longer read
     if (threadIdx.x == 0) {
-      p.tstat[tile] = 1;
-      p.troot[tile] = (int)root0;
+      sg = 0;
+      sc = 0;
+      nroot = 0;
+      rfirst = TN;
+    }
+    __syncthreads();
+    // row masks, runs
+    for (int r = warp; r < NR; r += TILE_THREADS / 32) {
+      const int x = x0 + lane, y = y0 + r % TY, z = z0 + r / TY;
+      const bool inside = x < p.nx && y < p.ny && z < p.nz;
+      const bool gas = inside && post_type(p.flags[x + nx * y + nxy * z]) == T_GAS;
+      const unsigned m = __ballot_sync(0xffffffffu, gas), in = __ballot_sync(0xffffffffu, inside);
+      if (lane == 0) {
+        rowm[r] = m;
+        if (m) atomicAdd(&sg, __popc(m));
+        atomicAdd(&sc, __popc(in));
+      }
+      const unsigned starts = m & ~(m << 1);
+      lp[r * TX + lane] = gas ? r * TX + (31 - __clz(starts & (0xffffffffu >> (31 - lane)))) : -1;
+      lsz[r * TX + lane] = 0;
+    }
+    __syncthreads();
+    const long long root0 = x0 + nx * y0 + nxy * z0;
+    if (sg == 0) {
+      if (threadIdx.x == 0) p.tstat[tile] = 0;
+      continue;
+    }
+    if (sg == sc) {  // every cell is gas: one component rooted at the first cell
+      if (threadIdx.x == 0) {
+        p.tstat[tile] = 1;
+        p.troot[tile] = (int)root0;
+      }
+      for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
+        const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
+        if (x < p.nx && y < p.ny && z < p.nz) {
+          const long long n = x + nx * y + nxy * z;
+          p.parent[n] = (int)root0;
+          p.lsize[n] = t == 0 ? sg : 0;
+        }
+      }
+      continue;
+    }
+    // rows joined at the first cell of each overlapping segment
+    bool ok = true;
+    for (int r = warp; r < NR; r += TILE_THREADS / 32) {
+      const unsigned a = rowm[r];
+      if (!a) continue;
+      const int ly = r % TY, lz = r / TY;
+#pragma unroll
+      for (int k = 0; k < RowLinks<D>::n; ++k) {
+        const int dx = RowLinks<D>::dx(k), ry = ly + RowLinks<D>::dy(k), rz = lz + RowLinks<D>::dz(k);
+        if (ry < 0 || ry >= TY || rz < 0 || rz >= TZ) continue;  // across the tile face: the merge pass
+        const int rr = ry + TY * rz;
+        const unsigned b = rowm[rr];
+        const unsigned bs = dx > 0 ? (b >> 1) : (dx < 0 ? (b << 1) : b);  // bit x: gas at x + dx in row rr
+        const unsigned ov = a & bs;
+        const unsigned seg = ov & ~(ov << 1);
+        if ((seg >> lane) & 1u) ok &= sm_union(lp, r * TX + lane, rr * TX + lane + dx);
+      }
+    }
+    if (!ok) atomicOr(p.err, ERR_NOTCONV);
+    __syncthreads();
+    // flatten, count roots, sizes per run
+    for (int r = warp; r < NR; r += TILE_THREADS / 32) {
+      const unsigned m = rowm[r];
+      const int t = r * TX + lane;
+      int root = -1;
+      if ((m >> lane) & 1u) root = sm_find(lp, t);
+      __syncwarp();
+      if (root >= 0) lp[t] = root;
+      const unsigned starts = m & ~(m << 1);
+      if ((starts >> lane) & 1u) {
+        const int len = __ffs(~(m >> lane)) - 1;
+        atomicAdd(&lsz[root], len > 0 ? len : 32 - lane);
+      }
+      if (root == t) {
+        atomicAdd(&nroot, 1);
+        atomicMin(&rfirst, t);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      p.tstat[tile] = nroot == 1 ? 1 : 2;
+      const int r = rfirst;
+      p.troot[tile] = (int)(x0 + r % TX + nx * (y0 + (r / TX) % TY) + nxy * (z0 + r / (TX * TY)));
     }
     for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
       const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
-      if (x < p.nx && y < p.ny && z < p.nz) {
-        const long long n = x + nx * y + nxy * z;
-        p.parent[n] = (int)root0;
-        p.lsize[n] = t == 0 ? sg : 0;
-      }
+      if (lp[t] < 0 || x >= p.nx || y >= p.ny || z >= p.nz) continue;
+      const int r = lp[t];
+      const int rx = x0 + r % TX, ry = y0 + (r / TX) % TY, rz = z0 + r / (TX * TY);
+      const long long n = x + nx * y + nxy * z;
+      p.parent[n] = (int)(rx + nx * ry + nxy * rz);
+      p.lsize[n] = r == t ? lsz[t] : 0;
     }
-    return;
-  }
-  // rows joined at the first cell of each overlapping segment
-  bool ok = true;
-  for (int r = warp; r < NR; r += TILE_THREADS / 32) {
-    const unsigned a = rowm[r];
-    if (!a) continue;
-    const int ly = r % TY, lz = r / TY;
-#pragma unroll
-    for (int k = 0; k < RowLinks<D>::n; ++k) {
-      const int dx = RowLinks<D>::dx(k), ry = ly + RowLinks<D>::dy(k), rz = lz + RowLinks<D>::dz(k);
-      if (ry < 0 || ry >= TY || rz < 0 || rz >= TZ) continue;  // across the tile face: the merge pass
-      const int rr = ry + TY * rz;
-      const unsigned b = rowm[rr];
-      const unsigned bs = dx > 0 ? (b >> 1) : (dx < 0 ? (b << 1) : b);  // bit x: gas at x + dx in row rr
-      const unsigned ov = a & bs;
-      const unsigned seg = ov & ~(ov << 1);
-      if ((seg >> lane) & 1u) ok &= sm_union(lp, r * TX + lane, rr * TX + lane + dx);
-    }
-  }
-  if (!ok) atomicOr(p.err, ERR_NOTCONV);
-  __syncthreads();
-  // flatten, count roots, sizes per run
-  for (int r = warp; r < NR; r += TILE_THREADS / 32) {
-    const unsigned m = rowm[r];
-    const int t = r * TX + lane;
-    int root = -1;
-    if ((m >> lane) & 1u) root = sm_find(lp, t);
-    __syncwarp();
-    if (root >= 0) lp[t] = root;
-    const unsigned starts = m & ~(m << 1);
-    if ((starts >> lane) & 1u) {
-      const int len = __ffs(~(m >> lane)) - 1;
-      atomicAdd(&lsz[root], len > 0 ? len : 32 - lane);
-    }
-    if (root == t) {
-      atomicAdd(&nroot, 1);
-      atomicMin(&rfirst, t);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    p.tstat[tile] = nroot == 1 ? 1 : 2;
-    const int r = rfirst;
-    p.troot[tile] = (int)(x0 + r % TX + nx * (y0 + (r / TX) % TY) + nxy * (z0 + r / (TX * TY)));
-  }
-  for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
-    const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
-    if (lp[t] < 0 || x >= p.nx || y >= p.ny || z >= p.nz) continue;
-    const int r = lp[t];
-    const int rx = x0 + r % TX, ry = y0 + (r / TX) % TY, rz = z0 + r / (TX * TY);
-    const long long n = x + nx * y + nxy * z;
-    p.parent[n] = (int)(rx + nx * ry + nxy * rz);
-    p.lsize[n] = r == t ? lsz[t] : 0;
   }
 }
 
@@ -281,77 +288,79 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_local(Params p) {
 template <int D>
 __global__ void __launch_bounds__(TILE_THREADS) k_uf_merge(Params p) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ;
+  if (label_fast(p)) return;
   const int mode = label_mode(p);
   if (mode == LABEL_SKIP) return;
   const TileGrid<D> tgd(p);
-  const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  const int own = p.tstat[tile];
-  if (own == 0) return;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
   const long long nx = p.nx, nxy = (long long)p.nx * p.ny;
+  const int ntiles = tgd.ntx * tgd.nty * tgd.ntz;
   // statuses of the 3^d neighbouring tiles (periodic); after a step that
   // only added gas cells, only links near a touched tile can be new
   __shared__ int nst[27];
   __shared__ int near_dirty;
-  if (threadIdx.x == 0) near_dirty = 0;
-  __syncthreads();
-  if (threadIdx.x < 27) {
-    const int ox = threadIdx.x % 3 - 1, oy = (threadIdx.x / 3) % 3 - 1, oz = threadIdx.x / 9 - 1;
-    const bool in = !(D == 2 && oz != 0);
-    const int nt = tgd.id(blockIdx.x + ox, blockIdx.y + oy, blockIdx.z + oz);
-    nst[threadIdx.x] = in ? p.tstat[nt] : 0;
-    if (mode == LABEL_ADDED && in && p.tdirty[nt]) near_dirty = 1;
-  }
-  __syncthreads();
-  if (mode == LABEL_ADDED && !near_dirty) return;
-  bool ok = true;
   // one gas link suffices between two single-component tiles: the first
   // thread that meets one claims the neighbour offset
   __shared__ int claimed[27];
   // per neighbouring tile, the last pair of representatives joined: links
   // between the same two local components need one union only
   __shared__ unsigned long long lastpair[27];
-  if (threadIdx.x < 27) {
-    claimed[threadIdx.x] = 0;
-    lastpair[threadIdx.x] = ~0ull;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
-    const int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
-    const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-    if (x >= p.nx || y >= p.ny || z >= p.nz) continue;
-    const bool onface = lx == 0 || lx == TX - 1 || x == p.nx - 1 || ly == 0 || ly == TY - 1 || y == p.ny - 1 ||
-                        (D == 3 && (lz == 0 || lz == TZ - 1 || z == p.nz - 1));
-    if (!onface) continue;
-    const long long n = x + nx * y + nxy * z;
-    if (post_type(p.flags[n]) != T_GAS) continue;
-#pragma unroll
-    for (int i = 1; i < Lat<D>::Q; i += 2) {
-      const int dx = Lat<D>::cx(i), dy = Lat<D>::cy(i), dz = Lat<D>::cz(i);
-      const int ax = x + dx, ay = y + dy, az = z + dz;
-      const bool wraps = ax < 0 || ax >= p.nx || ay < 0 || ay >= p.ny || az < 0 || az >= p.nz;
-      // tile offset of the link's far end
-      const int ox = (lx + dx < 0) ? -1 : ((lx + dx >= TX || ax >= p.nx) ? 1 : 0);
-      const int oy = (ly + dy < 0) ? -1 : ((ly + dy >= TY || ay >= p.ny) ? 1 : 0);
-      const int oz = (lz + dz < 0) ? -1 : ((lz + dz >= TZ || az >= p.nz) ? 1 : 0);
-      if (!wraps && ox == 0 && oy == 0 && oz == 0) continue;  // joined by the local pass
-      const int oi = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
-      const int ns = nst[oi];
-      if (ns == 0) continue;
-      if (own == 1 && ns == 1 && claimed[oi]) continue;
-      const long long m = at_far(p, ax, ay, az);
-      if (post_type(p.flags[m]) != T_GAS) continue;
-      if (own == 1 && ns == 1 && atomicExch(&claimed[oi], 1)) continue;
-      // representatives: the parents the local pass left (any ancestor
-      // stands for the same component)
-      const int ra = __ldcg(p.parent + n), rb = __ldcg(p.parent + m);
-      const unsigned long long key = ((unsigned long long)(unsigned)ra << 32) | (unsigned)rb;
-      if (lastpair[oi] == key) continue;
-      lastpair[oi] = key;
-      ok &= uf_union(p.parent, ra, rb);
+  for (int tile = block_id(); tile < ntiles; tile += block_count()) {
+    const int own = p.tstat[tile];
+    if (own == 0) continue;
+    const int bx = tile % tgd.ntx, by = (tile / tgd.ntx) % tgd.nty, bz = tile / (tgd.ntx * tgd.nty);
+    const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+    __syncthreads();  // the shared arrays of the last tile are no longer read
+    if (threadIdx.x == 0) near_dirty = 0;
+    __syncthreads();
+    if (threadIdx.x < 27) {
+      const int ox = threadIdx.x % 3 - 1, oy = (threadIdx.x / 3) % 3 - 1, oz = threadIdx.x / 9 - 1;
+      const bool in = !(D == 2 && oz != 0);
+      const int nt = tgd.id(bx + ox, by + oy, bz + oz);
+      nst[threadIdx.x] = in ? p.tstat[nt] : 0;
+      if (mode == LABEL_ADDED && in && p.tdirty[nt]) near_dirty = 1;
+      claimed[threadIdx.x] = 0;
+      lastpair[threadIdx.x] = ~0ull;
     }
+    __syncthreads();
+    if (mode == LABEL_ADDED && !near_dirty) continue;
+    bool ok = true;
+    for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
+      const int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
+      const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+      if (x >= p.nx || y >= p.ny || z >= p.nz) continue;
+      const bool onface = lx == 0 || lx == TX - 1 || x == p.nx - 1 || ly == 0 || ly == TY - 1 || y == p.ny - 1 ||
+                          (D == 3 && (lz == 0 || lz == TZ - 1 || z == p.nz - 1));
+      if (!onface) continue;
+      const long long n = x + nx * y + nxy * z;
+      if (post_type(p.flags[n]) != T_GAS) continue;
+#pragma unroll
+      for (int i = 1; i < Lat<D>::Q; i += 2) {
+        const int dx = Lat<D>::cx(i), dy = Lat<D>::cy(i), dz = Lat<D>::cz(i);
+        const int ax = x + dx, ay = y + dy, az = z + dz;
+        const bool wraps = ax < 0 || ax >= p.nx || ay < 0 || ay >= p.ny || az < 0 || az >= p.nz;
+        // tile offset of the link's far end
+        const int ox = (lx + dx < 0) ? -1 : ((lx + dx >= TX || ax >= p.nx) ? 1 : 0);
+        const int oy = (ly + dy < 0) ? -1 : ((ly + dy >= TY || ay >= p.ny) ? 1 : 0);
+        const int oz = (lz + dz < 0) ? -1 : ((lz + dz >= TZ || az >= p.nz) ? 1 : 0);
+        if (!wraps && ox == 0 && oy == 0 && oz == 0) continue;  // joined by the local pass
+        const int oi = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
+        const int ns = nst[oi];
+        if (ns == 0) continue;
+        if (own == 1 && ns == 1 && claimed[oi]) continue;
+        const long long m = at_far(p, ax, ay, az);
+        if (post_type(p.flags[m]) != T_GAS) continue;
+        if (own == 1 && ns == 1 && atomicExch(&claimed[oi], 1)) continue;
+        // representatives: the parents the local pass left (any ancestor
+        // stands for the same component)
+        const int ra = __ldcg(p.parent + n), rb = __ldcg(p.parent + m);
+        const unsigned long long key = ((unsigned long long)(unsigned)ra << 32) | (unsigned)rb;
+        if (lastpair[oi] == key) continue;
+        lastpair[oi] = key;
+        ok &= uf_union(p.parent, ra, rb);
+      }
+    }
+    if (!ok) atomicOr(p.err, ERR_NOTCONV);
   }
-  if (!ok) atomicOr(p.err, ERR_NOTCONV);
 }
 
 // one block per tile: every gas cell points at its component's root; roots
@@ -359,54 +368,59 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_merge(Params p) {
 template <int D>
 __global__ void __launch_bounds__(TILE_THREADS) k_uf_compress(Params p) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, TN = TX * TY * TZ;
-  if (gas_unchanged(p)) return;
-  const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  // the merge pass has read the touched-tile marks: clear them for the next step
-  if (threadIdx.x == 0 && p.tdirty) p.tdirty[tile] = 0;
-  const int own = p.tstat[tile];
-  if (own == 0) return;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  if (label_fast(p) || gas_unchanged(p)) return;
+  const TileGrid<D> tgd(p);
+  const int ntiles = tgd.ntx * tgd.nty * tgd.ntz;
   const long long nx = p.nx, nxy = (long long)p.nx * p.ny;
   __shared__ int sroot;
-  if (own == 1) {
-    const int r0 = p.troot[tile];
-    if (threadIdx.x == 0) {
-      sroot = uf_find(p.parent, r0);
-      if (sroot == r0) {
-        const int k = atomicAdd(p.nroots, 1);
-        if (k < p.cap) {
-          p.roots[k] = r0;
-        } else {
-          atomicOr(p.err, ERR_CAPACITY);
-          if (p.rlabel) p.rlabel[r0] = -1;
+  for (int tile = block_id(); tile < ntiles; tile += block_count()) {
+    // the merge pass has read the touched-tile marks: clear them for the next step
+    if (threadIdx.x == 0 && p.tdirty) p.tdirty[tile] = 0;
+    const int own = p.tstat[tile];
+    if (own == 0) continue;
+    const int bx = tile % tgd.ntx, by = (tile / tgd.ntx) % tgd.nty, bz = tile / (tgd.ntx * tgd.nty);
+    const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+    if (own == 1) {
+      const int r0 = p.troot[tile];
+      __syncthreads();  // sroot of the last tile is no longer read
+      if (threadIdx.x == 0) {
+        sroot = uf_find(p.parent, r0);
+        if (sroot == r0) {
+          const int k = atomicAdd(p.nroots, 1);
+          if (k < p.cap) {
+            p.roots[k] = r0;
+          } else {
+            atomicOr(p.err, ERR_CAPACITY);
+            if (p.rlabel) p.rlabel[r0] = -1;
+          }
         }
       }
+      __syncthreads();
+      const int r = sroot;
+      for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
+        const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
+        if (x < p.nx && y < p.ny && z < p.nz) {
+          const long long n = x + nx * y + nxy * z;
+          if (post_type(p.flags[n]) == T_GAS) p.parent[n] = r;
+        }
+      }
+      continue;
     }
-    __syncthreads();
-    const int r = sroot;
     for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
       const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
-      if (x < p.nx && y < p.ny && z < p.nz) {
-        const long long n = x + nx * y + nxy * z;
-        if (post_type(p.flags[n]) == T_GAS) p.parent[n] = r;
-      }
-    }
-    return;
-  }
-  for (int t = threadIdx.x; t < TN; t += TILE_THREADS) {
-    const int x = x0 + t % TX, y = y0 + (t / TX) % TY, z = z0 + t / (TX * TY);
-    if (x >= p.nx || y >= p.ny || z >= p.nz) continue;
-    const long long n = x + nx * y + nxy * z;
-    if (post_type(p.flags[n]) != T_GAS) continue;
-    const int r = uf_find(p.parent, (int)n);
-    p.parent[n] = r;
-    if (r == (int)n) {
-      const int k = atomicAdd(p.nroots, 1);
-      if (k < p.cap) {
-        p.roots[k] = r;
-      } else {
-        atomicOr(p.err, ERR_CAPACITY);
-        if (p.rlabel) p.rlabel[r] = -1;
+      if (x >= p.nx || y >= p.ny || z >= p.nz) continue;
+      const long long n = x + nx * y + nxy * z;
+      if (post_type(p.flags[n]) != T_GAS) continue;
+      const int r = uf_find(p.parent, (int)n);
+      p.parent[n] = r;
+      if (r == (int)n) {
+        const int k = atomicAdd(p.nroots, 1);
+        if (k < p.cap) {
+          p.roots[k] = r;
+        } else {
+          atomicOr(p.err, ERR_CAPACITY);
+          if (p.rlabel) p.rlabel[r] = -1;
+        }
       }
     }
   }
@@ -415,6 +429,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_uf_compress(Params p) {
 // one block: sort the roots (bitonic, in shared memory) and publish the count
 static __global__ void k_sort_roots(Params p) {
   extern __shared__ int sr[];
+  if (label_fast(p)) return;
   if (gas_unchanged(p)) {  // the sorted roots of the last labelling stand
     if (threadIdx.x == 0) *p.tnew.count = *p.told.count;
     return;
@@ -487,8 +502,14 @@ __device__ __forceinline__ void hash_insert(const Params &p, unsigned long long 
 template <int D, class R>
 __global__ void __launch_bounds__(256) k_relabel(Params p) {
   __shared__ double wbuf[256];
-  Cell c;
-  const bool inr = grid_cell(p, c);
+  if (label_fast(p)) return;
+  // row blocks of blockDim.x cells along x, walked by a grid of any size
+  const int nbx = (p.nx + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int nrb = nbx * p.ny * p.nz;
+  for (int rb = block_id(); rb < nrb; rb += block_count()) {
+  const int yz = rb / nbx, xb = (rb - yz * nbx) * (int)blockDim.x + (int)threadIdx.x;
+  Cell c = cell_at(p, xb < p.nx ? xb : p.nx - 1, yz % p.ny, yz / p.ny);
+  const bool inr = xb < p.nx;
   const long long n = c.n;
   const uint8_t fl = inr ? p.flags[n] : (uint8_t)T_WALL;
   const int t = post_type(fl);
@@ -520,10 +541,11 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
   // old label read, and warps without any pair skip the match)
   const int kold = (inr && knew >= 0) ? p.label_old[n] : -1;
   const bool pair = kold >= 0 && knew >= 0;
-  if (!__any_sync(0xffffffffu, pair)) return;
+  if (!__any_sync(0xffffffffu, pair)) continue;
   const unsigned long long key = pair ? (((unsigned long long)kold << 32) | (unsigned)knew) : HASH_EMPTY;
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   if (pair && (threadIdx.x & 31) == __ffs(peers) - 1) hash_insert(p, key);
+  }
 }
 
 // one block of 1024 threads: carry gas content from the old to the new table.
@@ -531,6 +553,7 @@ __global__ void __launch_bounds__(256) k_relabel(Params p) {
 // K10_SMEM old + new bubbles, in the global scratch arrays otherwise.
 constexpr int K10_SMEM = 512;
 static __global__ void __launch_bounds__(1024) k_bubble_update(Params p) {
+  if (label_fast(p)) return;
   __shared__ int sfresh[1024];
   __shared__ int sbase;
   __shared__ int s_par[K10_SMEM], s_nold[K10_SMEM], s_nnew[K10_SMEM], s_atm[K10_SMEM], s_minid[K10_SMEM],
@@ -674,45 +697,68 @@ static __global__ void __launch_bounds__(1024) k_bubble_update(Params p) {
 }
 
 // ---------------------------------------------------------------------------
-// Labelling of a step whose conversion only added gas cells, none of which
-// touches a gas cell of another bubble or has a smaller index than its
-// bubble's root (the marking checks this and sets lab_slow otherwise): every
+// Labelling of a step whose conversion kept every bubble's cells, number and
+// root: added gas cells touch no gas cell of another bubble and lie above
+// their bubble's root (checked by the marking), removed gas cells leave
+// their bubble connected (k_label_check); otherwise lab_slow is set.  Every
 // bubble keeps its cells, its number and its root, so the labels of the last
 // step stand except at the filled cells (-1), the added gas cells (the label
 // they had as interface cells, which is their bubble's) and the interface
 // cells after the conversion (smallest label of their gas neighbours).  The
 // result equals the full labelling's.  The step graph picks this branch or
-// the full one on the device: k_label_cond sets the conditional node's value
-// (1 full, 0 this one).
-static __global__ void k_label_cond(Params p, cudaGraphConditionalHandle h) {
-  const int d = *p.gas_dirty;
-  const bool fast = (d == 0 || d == 1) && *p.lab_slow == 0;
-  cudaGraphSetConditional(h, fast ? 0u : 1u);
+// the full one on the device: k_label_choose sets lab_fast, and the kernels
+// of the branch not taken return at once.
+static __global__ void k_label_choose(Params p) {
+  const int d = *p.gas_dirty;  // -1: the state was set from outside
+  *p.lab_fast = d >= 0 && *p.lab_slow == 0;
   *p.lab_slow = 0;
 }
 
-// label_new holds a copy of label_old when this runs.  One thread per marked
+// the patch starts from a copy of the last labels (int4 words and a tail)
+static __global__ void k_label_copy(Params p) {
+  if (!label_fast(p)) return;
+  const long long n4 = p.N >> 2;
+  const int4 *src = reinterpret_cast<const int4 *>(p.label_old);
+  int4 *dst = reinterpret_cast<int4 *>(p.label_new);
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+  for (long long k = tid; k < n4; k += nt) dst[k] = __ldcs(src + k);
+  for (long long k = (n4 << 2) + tid; k < p.N; k += nt) p.label_new[k] = p.label_old[k];
+}
+
+// label_new holds a copy of label_old when this runs (k_label_copy).  One thread per marked
 // cell, then per interface cell after the conversion; gas counts grow by the
 // added cells; volumes collect the interface shares 1 - alpha.
 template <int D, class R>
 __global__ void __launch_bounds__(128) k_label_fast(Params p) {
   __shared__ double wbuf[128];
-  const int nb = *p.told.count, nm = *p.mcount, ni = *p.inext_count;
+  if (!label_fast(p)) return;
+  const int nbub = *p.told.count, nm = *p.mcount, ni = *p.inext_count, nn = *p.ncount;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthreads = gridDim.x * blockDim.x;
   if (tid == 0) {
-    *p.tnew.count = nb;
-    if (*p.gas_dirty == 1) *p.forest_stale = 1;  // added gas cells the forest does not hold
+    *p.tnew.count = nbub;
+    // the forest lacks the added gas cells (bit 0: redo the touched tiles)
+    // or still holds removed ones (bit 1: rebuild it)
+    const int d = *p.gas_dirty;
+    if (d & 1) atomicOr(p.forest_stale, 1);
+    if (d & 2) atomicOr(p.forest_stale, 2);
   }
-  for (int k = tid; k < nb; k += nthreads) {
+  for (int k = tid; k < nbub; k += nthreads) {
     atomicAdd(p.tnew.ng + k, p.told.ng[k]);
     if (p.told.atm[k]) p.tnew.atm[k] = 1;
   }
-  const int total = nm + ni;
+  const int total = nm + ni + nn;
   for (int base = 0; base < total; base += nthreads) {
     const int k = base + tid;
-    int kg = -1, kv = -1;
+    int kg = -1, kv = -1, dg = 1;
     double v = 0.0;
-    if (k < nm) {
+    if (k >= nm + ni) {
+      // a new interface cell that was gas (it carries its bubble's label)
+      // leaves its bubble's gas count
+      if (k < total) {
+        kg = p.label_old[p.nlist[k - nm - ni]];
+        dg = -1;
+      }
+    } else if (k < nm) {
       const int n = p.mlist[k];
       const int t = post_type(p.flags[n]);
       if (t == T_LIQ) {
@@ -742,7 +788,7 @@ __global__ void __launch_bounds__(128) k_label_fast(Params p) {
         if (v != 0.0) kv = knew;
       }
     }
-    if (__any_sync(0xffffffffu, kg >= 0)) agg_count(p.tnew.ng, kg, 1);
+    if (__any_sync(0xffffffffu, kg >= 0)) agg_count(p.tnew.ng, kg, dg);
     if (__any_sync(0xffffffffu, kv >= 0)) agg_add(p.tnew.V, kv, v, wbuf + (threadIdx.x & ~31));
   }
 }
@@ -752,9 +798,10 @@ __global__ void __launch_bounds__(128) k_label_fast(Params p) {
 // flux of this step); the arithmetic is the general update's for such a
 // group.  One thread per bubble.
 static __global__ void k_bubble_update_fast(Params p) {
-  const int nb = *p.tnew.count;
+  if (!label_fast(p)) return;
+  const int nbub = *p.tnew.count;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-  for (int k = tid; k < nb; k += nt) {
+  for (int k = tid; k < nbub; k += nt) {
     const double mold = p.told.m[k] + p.told.dm[k];
     p.told.m[k] = mold;
     const double V = p.tnew.V[k] + (double)p.tnew.ng[k];

@@ -95,22 +95,28 @@ struct OpsImpl final : Ops {
   void label_forest(const Params &p, cudaStream_t s) override {
     const dim3 tg((unsigned)((p.nx + Tile<D>::TX - 1) / Tile<D>::TX), (unsigned)((p.ny + Tile<D>::TY - 1) / Tile<D>::TY),
                   (unsigned)((p.nz + Tile<D>::TZ - 1) / Tile<D>::TZ));
-    k_uf_local<D><<<tg, TILE_THREADS, 0, s>>>(p);
-    k_uf_merge<D><<<tg, TILE_THREADS, 0, s>>>(p);
-    k_uf_compress<D><<<tg, TILE_THREADS, 0, s>>>(p);
+    // tile loops on a grid of two blocks per SM (a block of the
+    // graph's patch steps then costs one short wave)
+    const unsigned ntiles = tg.x * tg.y * tg.z;
+    const unsigned g = p.tile_blocks > 0 && (unsigned)p.tile_blocks < ntiles ? (unsigned)p.tile_blocks : ntiles;
+    k_uf_local<D><<<g, TILE_THREADS, 0, s>>>(p);
+    k_uf_merge<D><<<g, TILE_THREADS, 0, s>>>(p);
+    k_uf_compress<D><<<g, TILE_THREADS, 0, s>>>(p);
     int P = 1;
     while (P < p.cap) P <<= 1;
     k_sort_roots<<<1, 1024, P * sizeof(int), s>>>(p);
   }
   void label_relabel(const Params &p, cudaStream_t s) override {
-    k_relabel<D, R><<<row_grid(p), row_block(p), 0, s>>>(p);
+    // row blocks walked by a grid of 16 blocks per SM
+    const unsigned nrb = row_grid(p).x * (unsigned)p.ny * (unsigned)p.nz;
+    const unsigned g = (unsigned)p.warp_blocks < nrb ? (unsigned)p.warp_blocks : nrb;
+    k_relabel<D, R><<<g, row_block(p), 0, s>>>(p);
   }
   void bubble_update(const Params &p, cudaStream_t s) override { k_bubble_update<<<1, 1024, 0, s>>>(p); }
-  void label_cond(const Params &p, cudaGraphConditionalHandle h, cudaStream_t s) override {
-    k_label_cond<<<1, 1, 0, s>>>(p, h);
-  }
+  void label_check(const Params &p, cudaStream_t s) override { k_label_check<D><<<p.list_blocks, 128, 0, s>>>(p); }
+  void label_choose(const Params &p, cudaStream_t s) override { k_label_choose<<<1, 1, 0, s>>>(p); }
   void label_fast(const Params &p, cudaStream_t s) override {
-    cudaMemcpyAsync(p.label_new, p.label_old, sizeof(int) * (size_t)p.N, cudaMemcpyDeviceToDevice, s);
+    k_label_copy<<<p.warp_blocks, 128, 0, s>>>(p);
     k_label_fast<D, R><<<p.list_blocks, 128, 0, s>>>(p);
   }
   void bubble_update_fast(const Params &p, cudaStream_t s) override {

@@ -43,10 +43,13 @@ struct Ops {
   virtual void label_prep(const Params &p, cudaStream_t s) = 0;
   virtual void bubble_update(const Params &p, cudaStream_t s) = 0;
   // a step whose added gas cells keep every bubble's cells, number and root
-  // (decided on the device after the marking): the branch value of the step
-  // graph's conditional nodes (1 full labelling, 0 this path), the labels
-  // of the last step patched, and the bubble update of one-to-one groups
-  virtual void label_cond(const Params &p, cudaGraphConditionalHandle h, cudaStream_t s) = 0;
+  // (decided on the device after the marking, label_choose) patches the
+  // labels of the last step (label_fast) and updates one-to-one bubble
+  // groups (bubble_update_fast); the union-find kernels, the relabelling and
+  // the general bubble update return at once in such a step, the patch
+  // kernels in every other
+  virtual void label_check(const Params &p, cudaStream_t s) = 0;  // after the marking
+  virtual void label_choose(const Params &p, cudaStream_t s) = 0;
   virtual void label_fast(const Params &p, cudaStream_t s) = 0;
   virtual void bubble_update_fast(const Params &p, cudaStream_t s) = 0;
   virtual void geometry(const Params &p, cudaStream_t s) = 0;

@@ -245,6 +245,7 @@ class Sim:
     def step_count(self) -> int:
         return int(self.lib.lbf_step_count(self.h))
 
+
     def bubbles(self) -> dict:
         """The bubble table (one library call: rows up to the capacity)."""
         if getattr(self, "_bub", None) is None:

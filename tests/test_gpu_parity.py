@@ -90,7 +90,8 @@ def test_free_surface_fp64_2d(lbf, oracle_mod):
 
 def test_free_surface_fp64_3d_crop(lbf, oracle_mod):
     """The 32^3 crop workload (power law, disjoining pressure, D3Q7 gas) in
-    FP64 for 40 steps."""
+    FP64 for 40 steps (both labelling branches run: growing bubbles add gas
+    cells)."""
     cfg, c, r = W.c2_crop_3d_32(storage="fp64")
     sim, ora = _pair(lbf, oracle_mod, cfg)
     for s in (sim, ora):
