@@ -117,8 +117,8 @@ template <int D, class R> struct Plic {
     m3 = a3;
   }
   // offset s of the plane n.p = s leaving liquid fraction alpha on the +n
-  // side of the cell [-1/2, 1/2]^d (out of line: called once per stencil
-  // neighbour)
+  // side of the cell [-1/2, 1/2]^d (out of line: inlining the several cuts of
+  // a thread raised registers and was measured slower)
   __device__ __noinline__ R offset(R alpha) const {
     if (!(sum > (R)0)) return (R)0;
     if (alpha >= (R)1) return (R)-0.5 * sum;
@@ -181,65 +181,91 @@ __device__ __forceinline__ bool chol_solve(R (&A)[K][K], R (&b)[K], R (&x)[K]) {
 // axis-aligned planes) then give a smooth, bounded curvature
 constexpr double kLsqRidge = 1e-3;
 
-template <class R> __device__ __forceinline__ R warp_sum(R v) {
+// sum over the G consecutive lanes of a group (G a power of two <= 32);
+// every lane of the warp takes part
+template <int G, class R> __device__ __forceinline__ R group_sum(R v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
   return v;
 }
 
-// one warp per interface cell, one lane per stencil cell (27 in 3D, 9 in 2D)
+// GEO_LANES lanes per interface cell (32 / GEO_LANES cells per warp): lane t
+// of a cell's group takes the stencil cells t, t + GEO_LANES, ... (27 in 3D,
+// 9 in 2D), so the gradient, the PLIC cuts and the least-squares sums are
+// spread over the group and reduced in log2(GEO_LANES) shuffles; the first
+// lane of each group solves the normal equations and stores the results.
+constexpr int GEO_LANES = 8;
+
 template <int D, class R>
 __global__ void __launch_bounds__(128) k_geometry(Params p) {
   constexpr int K = D == 3 ? 5 : 2;
   constexpr int NS = D == 3 ? 27 : 9;
   constexpr int CTR = D == 3 ? 13 : 4;
-  const int lane = threadIdx.x & 31;
+  constexpr int G = GEO_LANES, CPW = 32 / G, PER = (NS + G - 1) / G;
+  const int lane = threadIdx.x & 31, sub = lane / G, t = lane % G;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int cnt = *p.icount;
   const R *phi = (const R *)p.phi;
   R *kap = (R *)p.kappa, *nr = (R *)p.nrm, *ds = (R *)p.dst;
-  const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = D == 3 ? lane / 9 - 1 : 0;
-  const bool mine = lane < NS;
-  for (int k = warp; k < cnt; k += nwarps) {
-    const long long n = p.ilist[k];
+  // the lane of the group that holds the centre stencil cell
+  constexpr int CT = CTR % G, CJ = CTR / G;
+  for (int base = warp * CPW; base < cnt; base += nwarps * CPW) {
+    const int k = base + sub;
+    const bool valid = k < cnt;
+    const long long n = valid ? p.ilist[k] : p.ilist[base];
     const Cell c = make_cell(p, n);
-    int tm = T_LIQ;
-    R a = 0;
-    if (mine) {
-      const long long m = at(p, c, dx, dy, dz);
-      tm = post_type(p.flags[m]);  // may run while the conversion's marks are replaced
-      if (tm == T_LIQ) a = 1;
-      else if (tm == T_IFC) {
-        a = phi[m];
-        a = a < (R)0 ? (R)0 : (a > (R)1 ? (R)1 : a);
+    R a[PER];
+    int tm[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int q = t + G * j;
+      a[j] = 0;
+      tm[j] = T_LIQ;
+      if (q < NS) {
+        const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = D == 3 ? q / 9 - 1 : 0;
+        const long long m = at(p, c, dx, dy, dz);
+        tm[j] = post_type(p.flags[m]);  // may run while the conversion's marks are replaced
+        if (tm[j] == T_LIQ) a[j] = 1;
+        else if (tm[j] == T_IFC) {
+          R v = phi[m];
+          a[j] = v < (R)0 ? (R)0 : (v > (R)1 ? (R)1 : v);
+        }
       }
     }
-    const R ac = __shfl_sync(0xffffffffu, a, CTR);
-    if (tm == T_WALL) a = ac;  // walls repeat the centre value
-    const bool act = mine && lane != CTR && tm == T_IFC && a > (R)0 && a < (R)1;
+    const R ac = __shfl_sync(0xffffffffu, a[CJ], sub * G + CT);
     // Parker-Youngs weighted centred differences
-    const R wz = D == 3 ? (dz == 0 ? (R)2 : (R)1) : (R)1;
-    const R gx = warp_sum<R>(mine ? (R)dx * (dy == 0 ? (R)2 : (R)1) * wz * a : (R)0);
-    const R gy = warp_sum<R>(mine ? (R)dy * (dx == 0 ? (R)2 : (R)1) * wz * a : (R)0);
-    const R gz = D == 3 ? warp_sum<R>(mine ? (R)dz * (dx == 0 ? (R)2 : (R)1) * (dy == 0 ? (R)2 : (R)1) * a : (R)0)
-                        : (R)0;
-    const R gn = sqrt(gx * gx + gy * gy + gz * gz);
-    if (!(gn > (R)1e-12)) {
-      if (lane == 0) {
-        kap[n] = 0;
-        ds[n] = 0;
-        nr[n] = 0;
-        nr[p.N + n] = 0;
-        nr[2 * p.N + n] = 0;
-      }
-      continue;
+    R gx = 0, gy = 0, gz = 0;
+    bool act[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int q = t + G * j;
+      act[j] = false;
+      if (q >= NS) continue;
+      if (tm[j] == T_WALL) a[j] = ac;  // walls repeat the centre value
+      act[j] = q != CTR && tm[j] == T_IFC && a[j] > (R)0 && a[j] < (R)1;
+      const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = D == 3 ? q / 9 - 1 : 0;
+      const R wz = D == 3 ? (dz == 0 ? (R)2 : (R)1) : (R)1;
+      gx += (R)dx * (dy == 0 ? (R)2 : (R)1) * wz * a[j];
+      gy += (R)dy * (dx == 0 ? (R)2 : (R)1) * wz * a[j];
+      if (D == 3) gz += (R)dz * (dx == 0 ? (R)2 : (R)1) * (dy == 0 ? (R)2 : (R)1) * a[j];
     }
-    const R mx = gx / gn, my = gy / gn, mz = gz / gn;
+    gx = group_sum<G, R>(gx);
+    gy = group_sum<G, R>(gy);
+    if (D == 3) gz = group_sum<G, R>(gz);
+    const R gn = sqrt(gx * gx + gy * gy + gz * gz);
+    const bool flat = !(gn > (R)1e-12);
+    const R ign = flat ? (R)0 : (R)1 / gn;
+    const R mx = gx * ign, my = gy * ign, mz = gz * ign;
     const Plic<D, R> plic(mx, my, mz);
-    // every lane cuts its own cell (the centre lane cuts the centre)
-    const R sj = (act || lane == CTR) ? plic.offset(lane == CTR ? ac : a) : (R)0;
-    const R s0 = __shfl_sync(0xffffffffu, sj, CTR);
+    // every thread cuts its own stencil cells (and the centre's holder the centre)
+    R sj[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int q = t + G * j;
+      sj[j] = (!flat && (act[j] || q == CTR)) ? plic.offset(q == CTR ? ac : a[j]) : (R)0;
+    }
+    const R s0 = __shfl_sync(0xffffffffu, sj[CJ], sub * G + CT);
     // local frame (t1, t2, m)
     R t1x, t1y, t1z, t2x = 0, t2y = 0, t2z = 0;
     if (D == 2) {
@@ -251,64 +277,93 @@ __global__ void __launch_bounds__(128) k_geometry(Params p) {
       t1x = (kmin == 0 ? (R)1 : (R)0) - mk * mx;
       t1y = (kmin == 1 ? (R)1 : (R)0) - mk * my;
       t1z = (kmin == 2 ? (R)1 : (R)0) - mk * mz;
-      const R l = (R)1 / sqrt(t1x * t1x + t1y * t1y + t1z * t1z);
+      const R l2 = t1x * t1x + t1y * t1y + t1z * t1z;
+      const R l = l2 > (R)0 ? (R)1 / sqrt(l2) : (R)0;
       t1x *= l; t1y *= l; t1z *= l;
       t2x = my * t1z - mz * t1y;
       t2y = mz * t1x - mx * t1z;
       t2z = mx * t1y - my * t1x;
     }
-    R ph[K], z = 0, r2 = 0;
+    // this thread's share of the normal equations of the least-squares
+    // paraboloid
+    R NA[K][K], Nb[K], N1 = 0, b1 = 0;
 #pragma unroll
-    for (int i = 0; i < K; ++i) ph[i] = 0;
-    if (act) {
+    for (int i = 0; i < K; ++i) {
+      Nb[i] = 0;
+#pragma unroll
+      for (int jj = 0; jj < K; ++jj) NA[i][jj] = 0;
+    }
+    int np = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      if (!act[j]) continue;
+      const int q = t + G * j;
+      const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = D == 3 ? q / 9 - 1 : 0;
       const R x = (R)dx * t1x + (R)dy * t1y + (R)dz * t1z;
       const R y = (R)dx * t2x + (R)dy * t2y + (R)dz * t2z;
-      z = (R)dx * mx + (R)dy * my + (R)dz * mz + sj - s0;
+      const R z = (R)dx * mx + (R)dy * my + (R)dz * mz + sj[j] - s0;
+      R ph[K];
       if constexpr (D == 3) {
         ph[0] = x * x; ph[1] = y * y; ph[2] = x * y; ph[3] = x; ph[4] = y;
       } else {
         ph[0] = x * x; ph[1] = x;
       }
-      r2 = x * x + y * y;
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+#pragma unroll
+        for (int jj = 0; jj <= i; ++jj) NA[i][jj] += ph[i] * ph[jj];
+        Nb[i] += ph[i] * z;
+      }
+      const R r2 = x * x + y * y;
+      N1 += r2 * r2;
+      b1 += r2 * z;
+      ++np;
     }
-    // normal equations of the least-squares paraboloid, summed over lanes
-    R NA[K][K], Nb[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
 #pragma unroll
-      for (int j = 0; j <= i; ++j) NA[i][j] = warp_sum<R>(ph[i] * ph[j]);
-      Nb[i] = warp_sum<R>(ph[i] * z);
+      for (int jj = 0; jj <= i; ++jj) NA[i][jj] = group_sum<G, R>(NA[i][jj]);
+      Nb[i] = group_sum<G, R>(Nb[i]);
     }
-    const R N1 = warp_sum<R>(r2 * r2), b1 = warp_sum<R>(r2 * z);
-    const int np = __popc(__ballot_sync(0xffffffffu, act));
-    if (lane == 0) {
+    N1 = group_sum<G, R>(N1);
+    b1 = group_sum<G, R>(b1);
 #pragma unroll
-      for (int i = 0; i < K; ++i) {
-        NA[i][i] += (R)kLsqRidge;
-#pragma unroll
-        for (int j = i + 1; j < K; ++j) NA[i][j] = NA[j][i];
-      }
-      R kv = 0;
-      R beta[K];
-      const bool full = np >= (D == 3 ? 5 : 2) && chol_solve<R, K>(NA, Nb, beta);
-      if (full) {
-        if constexpr (D == 3) {
-          const R H = beta[3], I = beta[4];
-          const R q2 = (R)1 + H * H + I * I;
-          kv = -(((R)1 + I * I) * beta[0] - H * I * beta[2] + ((R)1 + H * H) * beta[1]) / (q2 * sqrt(q2));
-        } else {
-          const R q2 = (R)1 + beta[1] * beta[1];
-          kv = -beta[0] / (q2 * sqrt(q2));
-        }
-      } else if (np >= 1) {
-        kv = (D == 3 ? (R)-2 : (R)-1) * (b1 / (N1 + (R)kLsqRidge));
-      }
-      kap[n] = kv < (R)-1 ? (R)-1 : (kv > (R)1 ? (R)1 : kv);
-      nr[n] = mx;
-      nr[p.N + n] = my;
-      nr[2 * p.N + n] = mz;
-      ds[n] = s0;
+    for (int o = G / 2; o > 0; o >>= 1) np += __shfl_xor_sync(0xffffffffu, np, o, G);
+    if (!valid || t != 0) continue;
+    if (flat) {
+      kap[n] = 0;
+      ds[n] = 0;
+      nr[n] = 0;
+      nr[p.N + n] = 0;
+      nr[2 * p.N + n] = 0;
+      continue;
     }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      NA[i][i] += (R)kLsqRidge;
+#pragma unroll
+      for (int jj = i + 1; jj < K; ++jj) NA[i][jj] = NA[jj][i];
+    }
+    R kv = 0;
+    R beta[K];
+    const bool full = np >= (D == 3 ? 5 : 2) && chol_solve<R, K>(NA, Nb, beta);
+    if (full) {
+      if constexpr (D == 3) {
+        const R H = beta[3], I = beta[4];
+        const R q2 = (R)1 + H * H + I * I;
+        kv = -(((R)1 + I * I) * beta[0] - H * I * beta[2] + ((R)1 + H * H) * beta[1]) / (q2 * sqrt(q2));
+      } else {
+        const R q2 = (R)1 + beta[1] * beta[1];
+        kv = -beta[0] / (q2 * sqrt(q2));
+      }
+    } else if (np >= 1) {
+      kv = (D == 3 ? (R)-2 : (R)-1) * (b1 / (N1 + (R)kLsqRidge));
+    }
+    kap[n] = kv < (R)-1 ? (R)-1 : (kv > (R)1 ? (R)1 : kv);
+    nr[n] = mx;
+    nr[p.N + n] = my;
+    nr[2 * p.N + n] = mz;
+    ds[n] = s0;
   }
 }
 
