@@ -33,7 +33,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS (D3Q19 FSLBM + D3Q7 ADE) and % HBM roofline; FP16+learned-κ vs FP32 plain"
 WORKLOAD = "3D D3Q19 FSLBM + D3Q7 ADE, 128^3, FP32 storage, 8 bubbles (R 4-6), power-law n=0.6, disjoining on"
-KERNELS_PER_STEP = 15  # exchange 1, sweep 2, conversion 4, labelling 5, bubble update 1, geometry 1, disjoining 1
+# exchange 1, sweep 2, conversion 4, labelling check and choice 2, union-find 4, relabel 1, label copy
+# and patch 2, bubble update 2, geometry 1, disjoining 1 (one of the two labelling branches returns at once)
+KERNELS_PER_STEP = 20
 
 
 def parse():
@@ -44,7 +46,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16S + learned-curvature comparison")
-    return ap.parse_args()
+    ap.add_argument("--config", default="default", choices=["default", "c1", "c3", "c5", "oracle"],
+                    help="c1: 128^2 FP64 bubble, R(t) and Laplace jump; c3: 256^3 FP16S Carreau foam with the "
+                         "learned curvature and its error; c5: 512x512x384 BF16S + learned curvature against FP32, "
+                         "histograms; oracle: CPU oracle timings (single thread and all host cores)")
+    args = ap.parse_args()
+    args.steps_given = any(a == "--steps" or a.startswith("--steps=") for a in sys.argv[1:])
+    return args
 
 
 def dist_env():
@@ -113,9 +121,9 @@ def stop_clocks(proc, path):
 # k_stream_liquid<3,float> under this script's default run (dram__bytes_read.sum
 # + dram__bytes_write.sum), valid while the sweep's sources are the ones that
 # were profiled
-SWEEP_TRAFFIC_BYTES = 263.1e6
+SWEEP_TRAFFIC_BYTES = 263.3e6
 SWEEP_SOURCES = ("paper_1908_04262_gb300/csrc/lbf_stream.cuh", "paper_1908_04262_gb300/csrc/lbf_common.cuh")
-SWEEP_SOURCES_SHA256_16 = "bd7cfcb32b41df6b"
+SWEEP_SOURCES_SHA256_16 = "a42d72f6aa39b9e3"
 
 
 def sweep_traffic():
@@ -293,19 +301,73 @@ def barrier(world: int):
         dist.barrier()
 
 
-def cpu_baseline_oracle(cfg, pts, rad, steps=1):
-    """The FP64 CPU oracle, as it stands, on the same 128^3 workload:
-    construction and nucleation untimed, `steps` full steps timed."""
+def host_cpu():
+    """Core count and model string of the host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        import platform
+
+        model = platform.processor() or platform.machine()
+    return os.cpu_count() or 1, model
+
+
+def _oracle_worker(cfg, pts, rad, steps, barrier, queue):
+    """One oracle instance in its own process: build and nucleate, wait for
+    every worker, then time `steps` steps (wall clock)."""
+    sys.path.insert(0, ROOT)
     import oracle
 
+    ora = oracle.OracleSim(cfg)
+    ora.nucleate(pts, rad)
+    barrier.wait()
+    t0 = time.time()
+    ora.step(steps)
+    queue.put((t0, time.time()))
+
+
+def cpu_baseline_oracle(cfg, pts, rad, steps=1, parallel=True):
+    """The FP64 CPU oracle, as it stands (one thread per instance), on the
+    same workload: single thread, then one instance per host core at once
+    (processes started with spawn), each timing `steps` steps after its
+    construction and nucleation."""
+    import multiprocessing as mp
+
+    import oracle
+
+    N = cfg["nx"] * cfg["ny"] * cfg["nz"]
     ora = oracle.OracleSim(cfg)
     ora.nucleate(pts, rad)
     t0 = time.perf_counter()
     ora.step(steps)
     dt = time.perf_counter() - t0
-    N = cfg["nx"] * cfg["ny"] * cfg["nz"]
-    return {"value": N * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%d full step(s) of the 128^3 workload (%.1f s, single thread)" % (steps, dt)}
+    del ora
+    ncores, model = host_cpu()
+    single = N * steps / dt / 1e6
+    out = {"value": single, "unit": "MLUPS", "cores": 1, "kind": "oracle", "nproc": ncores, "cpu_model": model,
+           "sample": "%d full step(s) of the workload (%.1f s, one thread)" % (steps, dt)}
+    if parallel and ncores > 1:
+        workers = min(ncores, 16)
+        ctx = mp.get_context("spawn")
+        barrier, queue = ctx.Barrier(workers), ctx.Queue()
+        procs = [ctx.Process(target=_oracle_worker, args=(cfg, pts, rad, steps, barrier, queue)) for _ in range(workers)]
+        for pr in procs:
+            pr.start()
+        spans = [queue.get() for _ in procs]
+        for pr in procs:
+            pr.join()
+        wall = max(b for _, b in spans) - min(a for a, _ in spans)
+        out["all_cores"] = {"value": workers * N * steps / wall / 1e6, "unit": "MLUPS", "cores": workers,
+                            "sample": "%d concurrent single-thread instances, %d step(s) each, %.1f s wall"
+                                      % (workers, steps, wall)}
+    return out
 
 
 def reference_sample_cfg():
@@ -465,8 +527,212 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# the paper-derived configurations (--config), one JSON line each
+
+
+def _timed(sim, stream, steps):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def config_c1(args, lbf, W, stream):
+    """128^2 D2Q9 FP64, free surface at y = 112, one bubble R = 8: the bubble
+    radius against time and the Laplace jump p_g - p_l against sigma / R
+    (2D), every 100 steps."""
+    import numpy as np
+
+    steps = args.steps if args.steps_given else 2000
+    cfg, c, r = W.c1_2d_128_fp64()
+    sim = lbf.Sim(cfg, stream=stream.cuda_stream)
+    sim.nucleate(c, r)
+    nx, ny = cfg["nx"], cfg["ny"]
+    idx = np.arange(nx * ny)
+    x, y = idx % nx, idx // nx
+    rows, ms = [], 0.0
+    for t in range(100, steps + 1, 100):
+        ms += _timed(sim, stream, 100)
+        b = sim.bubbles()
+        k = int(np.flatnonzero(b["atm"] == 0)[0])
+        R = float(np.sqrt(b["volume"][k] / np.pi))
+        f = sim.fields(["rho", "flags"])
+        far = (f["flags"] == 1) & (np.hypot(x - c[0][0], y - c[0][1]) > R + 6) & (y < 100)
+        pl = float(f["rho"][far].mean() / 3.0)
+        jump = float(b["pressure"][k] - pl)
+        rows.append([t, R, jump, cfg["sigma"] / R, jump / (cfg["sigma"] / R)])
+    sim.close()
+    return {"config": "c1", "workload": "2D D2Q9 FSLBM + D2Q5 ADE, 128^2, FP64, one bubble R = 8, free surface y = 112",
+            "metric": "MLUPS", "value": nx * ny * steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "steps": steps,
+            "note": "16,384 cells: launch-bound, no roofline claim",
+            "R_t_and_laplace": {"columns": ["step", "R = sqrt(V/pi)", "p_g - p_l", "sigma / R", "ratio"], "rows": rows}}
+
+
+def _kappa_errors(lbf, cfg, fields, vols, labels, theta):
+    """Curvature of every interface cell of a state, by the least squares and
+    by the learned network (the state set into fresh sims), against 1/R_eq of
+    the cell's bubble (R_eq = (3V/4pi)^(1/3)); relative RMS over the cells of
+    bubbles with R_eq in [2, 40]."""
+    import numpy as np
+
+    out = {}
+    types = fields["flags"].astype(np.uint8)
+    for name, th in (("least_squares", None), ("learned", theta)):
+        s2 = lbf.Sim(cfg)
+        if th is not None:
+            s2.mlp_attach(th)
+        s2.set_cells(types, fields["rho"], fields["u"].reshape(-1), fields["alpha"], fields["conc"])
+        kap = s2.fields(["kappa"])["kappa"]
+        s2.close()
+        ifc = np.flatnonzero((types == 2) & (labels >= 0))
+        R = np.cbrt(3.0 * vols[labels[ifc]] / (4.0 * np.pi))
+        keep = (R >= 2.0) & (R <= 40.0)
+        kt = 1.0 / R[keep]
+        e = (kap[ifc][keep] - kt) / kt
+        out[name] = {"rel_rms": float(np.sqrt(np.mean(e * e))), "cells": int(keep.sum())}
+    return out
+
+
+def config_c3(args, lbf, W, stream):
+    """256^3 D3Q19 shifted FP16, Carreau, 200 nuclei appearing over the first
+    5000 steps, with the learned curvature in the loop: MLUPS, the step
+    roofline, and the curvature error of the final state against the bubbles'
+    equivalent spheres, learned against least squares."""
+    import numpy as np
+
+    from paper_1908_04262_gb300 import curvature
+
+    steps = args.steps if args.steps_given else 20000
+    cfg, pts, rad, times = W.c3_3d_256_fp16s()
+    theta, _ = curvature.train(seed=1, rounds=3, stream=stream.cuda_stream)
+    sim = lbf.Sim(cfg, stream=stream.cuda_stream)
+    sim.nucleate(pts, rad, times)
+    sim.mlp_attach(theta)
+    ms = _timed(sim, stream, steps)
+    N = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    counts = np.asarray(sim.cell_counts(), float)
+    f = sim.fields(["flags", "rho", "u", "alpha", "conc", "label"])
+    b = sim.bubbles()
+    peak, kind = peaks()
+    step_bytes = algorithmic_bytes_step(counts, 2)
+    out = {"config": "c3", "workload": "3D D3Q19 + D3Q7, 256^3, shifted FP16, Carreau n=0.5 lambda=50, "
+                                       "200 nuclei (times U[0,5000]), learned curvature in the loop",
+           "metric": "MLUPS", "value": N * steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "steps": steps,
+           "ms_per_step": ms / steps, "bubbles": int(np.sum(b["atm"] == 0)),
+           "step_roofline": {"achieved": step_bytes / (ms / steps / 1e3) / 1e9, "peak": peak,
+                             "frac": step_bytes / (ms / steps / 1e3) / 1e9 / peak, "unit": "GB/s",
+                             "peak_source": kind + " hbm_gbs", "bytes_per_step": step_bytes}}
+    vols = np.asarray(b["volume"])
+    out["kappa_error_final_state"] = _kappa_errors(lbf, cfg, f, vols, np.asarray(f["label"]), theta)
+    sim.close()
+    return out
+
+
+def _histograms(b):
+    import numpy as np
+
+    v = np.asarray(b["volume"])[np.asarray(b["atm"]) == 0]
+    edges = [0, 10, 20, 40, 80, 160, 320, 640, 1280, 1e12]
+    h, _ = np.histogram(v, bins=edges)
+    return {"count": int(v.size), "volume_bin_edges": edges[:-1] + ["inf"], "volume_histogram": h.tolist(),
+            "total_volume": float(v.sum())}
+
+
+def config_c5(args, lbf, W, stream):
+    """512x512x384 D3Q19 shifted BF16 with the learned curvature (least-squares
+    fallback) against the plain FP32 form, same nuclei and steps: MLUPS, the
+    step roofline, bubble count and volume histograms."""
+    import numpy as np
+
+    from paper_1908_04262_gb300 import curvature
+
+    steps = args.steps if args.steps_given else 2000
+    cfg, pts, rad = W.c5_3d_512x512x384_bf16s()
+    theta, _ = curvature.train(seed=1, rounds=3, stream=stream.cuda_stream)
+    N = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    peak, kind = peaks()
+    out = {"config": "c5", "workload": "3D D3Q19 + D3Q7, 512x512x384, power law n=0.7, 2000 nuclei",
+           "metric": "MLUPS", "unit": "MLUPS", "steps": steps, "forms": {}}
+    for name, storage, use in (("bf16s_mlp", "bf16s", True), ("fp32_plain", "fp32", False)):
+        sim = lbf.Sim(dict(cfg, storage=storage), stream=stream.cuda_stream)
+        sim.nucleate(pts, rad)
+        if use:
+            sim.mlp_attach(theta)
+        sim.step(5)
+        ms = _timed(sim, stream, steps)
+        counts = np.asarray(sim.cell_counts(), float)
+        sb = 2 if storage == "bf16s" else 4
+        step_bytes = algorithmic_bytes_step(counts, sb)
+        ach = step_bytes / (ms / steps / 1e3) / 1e9
+        out["forms"][name] = {"mlups": N * steps / (ms / 1e3) / 1e6, "ms_per_step": ms / steps,
+                              "step_roofline": {"achieved": ach, "peak": peak, "frac": ach / peak, "unit": "GB/s",
+                                                "peak_source": kind + " hbm_gbs"},
+                              "bubbles": _histograms(sim.bubbles())}
+        sim.close()
+    out["value"] = out["forms"]["bf16s_mlp"]["mlups"]
+    a, b = out["forms"]["bf16s_mlp"]["bubbles"], out["forms"]["fp32_plain"]["bubbles"]
+    out["bf16s_mlp_vs_fp32_plain"] = {"count_diff": a["count"] - b["count"],
+                                      "total_volume_rel_diff": a["total_volume"] / b["total_volume"] - 1}
+    return out
+
+
+def config_oracle(args):
+    """The CPU oracle on the paper-derived cases (timings only): the 128^2
+    case for 2000 steps (one thread), the 32^3 crop for 20 steps and a 128^3
+    window of steps, each on one thread and on all host cores."""
+    import oracle
+
+    from paper_1908_04262_gb300 import workloads as W
+
+    out = {"config": "oracle", "metric": "MLUPS", "unit": "MLUPS"}
+    ncores, model = host_cpu()
+    out["nproc"], out["cpu_model"] = ncores, model
+    cfg, c, r = W.c1_2d_128_fp64()
+    ora = oracle.OracleSim(cfg)
+    ora.nucleate(c, r)
+    t0 = time.perf_counter()
+    ora.step(2000)
+    dt = time.perf_counter() - t0
+    out["c1_128sq_2000_steps"] = {"value": 128 * 128 * 2000 / dt / 1e6, "seconds": dt, "cores": 1}
+    cfg, c, r = W.c2_crop_3d_32(storage="fp64")
+    out["c2_crop_32cube_20_steps"] = cpu_baseline_oracle(cfg, c, r, steps=20)
+    cfg, c, r = W.c2_3d_128_fp32()
+    cfg = dict(cfg, storage="fp64")
+    window = args.steps if args.steps_given else 5
+    out["c2_128cube_window"] = cpu_baseline_oracle(cfg, c, r, steps=window)
+    out["value"] = out["c2_128cube_window"]["value"]
+    return out
+
+
+def run_config(args):
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1908_04262_gb300 import build as B
+
+    B.build()
+    from paper_1908_04262_gb300 import lbf
+    from paper_1908_04262_gb300 import workloads as W
+
+    stream = torch.cuda.Stream()
+    fn = {"c1": config_c1, "c3": config_c3, "c5": config_c5}[args.config]
+    print(json.dumps(fn(args, lbf, W, stream)), flush=True)
+
+
 def main():
     args = parse()
+    if args.config == "oracle":
+        print(json.dumps(config_oracle(args)), flush=True)
+        return
+    if args.config != "default":
+        run_config(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
