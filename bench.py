@@ -469,8 +469,8 @@ def run_ours(args):
     step_achieved = step_bytes / (ms / args.steps / 1e3) / 1e9 * world
     step_roofline = {"bound": "hbm", "achieved": step_achieved, "peak": peak, "unit": "GB/s",
                      "frac": step_achieved / (peak * world), "bytes_per_step": step_bytes,
-                     "note": "whole step (all 15 kernels) against the per-step byte model; "
-                             "the step is latency- and instruction-bound outside the sweep"}
+                     "note": "whole step (all %d kernels) against the per-step byte model; "
+                             "the step is latency- and instruction-bound outside the sweep" % KERNELS_PER_STEP}
 
     # --- end to end through the public API with host buffers -------------
     f = sim.fields(["flags", "rho", "u", "alpha", "conc"])
