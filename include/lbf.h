@@ -163,8 +163,10 @@ int lbf_bubbles(lbf_sim *s, lbf_bubble *out, int capacity, int *count);
 #define LBF_F_NORMAL (1u << 9) /* interface normal, into the liquid            */
 #define LBF_F_DSTAR (1u << 10) /* PLIC offset of the interface plane           */
 /* Copy the requested fields.  dst_is_device: 1 if every dst[k] is device
- * memory, 0 for host memory (the call then synchronises).  dtype: 0 float,
- * 1 double for the floating-point fields.  Errors: LBF_EINVAL. */
+ * memory, 0 for host memory (the call then synchronises; page-locked host
+ * memory is written by one direct copy per field, pageable memory through
+ * two page-locked chunks of the library's).  dtype: 0 float, 1 double for
+ * the floating-point fields.  Errors: LBF_EINVAL. */
 int lbf_fields(lbf_sim *s, unsigned mask, void *const *dst, int dst_is_device, int dtype);
 
 /* FP64 ledgers (synchronises): [0] liquid mass on the lattice (sum of rho

@@ -53,7 +53,7 @@ struct lbf_sim {
   int prio_least = 0, prio_greatest = 0;      // stream priority range of the device
   std::vector<cudaGraphNode_t> low_nodes;      // liquid sweeps captured on the third branch
   cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr}, joinx = nullptr, joinex = nullptr,
-              fin = nullptr, applied = nullptr, joink = nullptr;
+              fin = nullptr, applied = nullptr, joink = nullptr, checked = nullptr;
   Ops *ops = nullptr;
   std::vector<void *> allocs;
   std::vector<size_t> alloc_bytes;  // sizes of allocs, in order
@@ -291,16 +291,18 @@ void enqueue_geometry(lbf_sim *s, const Params &pn, cudaStream_t st) {
 void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const Params *pnext, int parnext) {
   const Params pn = next_geometry_params(p);
   s->ops->convert_mark(p, s->st);
-  // reads the marks of the gas cells turned interface: before the excess
-  // pass, so before the flag rewrite
-  s->ops->label_check(p, s->st);
   cudaEventRecord(s->fork[0], s->st);
+  // the labelling check reads the marks (and writes nothing the excess pass
+  // reads): beside the excess pass, before the flag rewrite
+  s->ops->label_check(p, s->st);
+  cudaEventRecord(s->checked, s->st);
   cudaStreamWaitEvent(s->st2, s->fork[0], 0);
   if (waitx) cudaStreamWaitEvent(s->st2, s->joinx, 0);
   s->ops->convert_excess(p, par, s->st2);
   cudaEventRecord(s->applied, s->st2);
   const bool early_geometry = s->mlp_theta != nullptr;
   if (!early_geometry) {
+    cudaStreamWaitEvent(s->st2, s->checked, 0);
     s->ops->convert_finalize(p, s->st2);
     cudaEventRecord(s->fin, s->st2);
   }
@@ -310,6 +312,7 @@ void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const
   cudaEventRecord(s->joink, s->st2);
   if (early_geometry) {
     cudaStreamWaitEvent(s->st3, s->applied, 0);
+    cudaStreamWaitEvent(s->st3, s->checked, 0);
     s->ops->convert_finalize(p, s->st3);
     cudaEventRecord(s->fin, s->st3);
   }
@@ -355,31 +358,39 @@ void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
     fn();
     if (ev) cudaEventRecordWithFlags(ev[2 * gidx + 1], s->st, cudaEventRecordExternal);
   };
+  if (!ev) {
+    // the liquid sweep on the third branch beside the interface sweep (the
+    // two commute); the excess pass waits for it
+    s->ops->exchange(p, par, s->st);
+    cudaEventRecord(s->joinex, s->st);
+    cudaStreamWaitEvent(s->st3, s->joinex, 0);
+    s->ops->stream_liquid(p, par, s->st3);
+    cudaEventRecord(s->joinx, s->st3);
+    s->ops->stream_interface(p, par, s->st);
+    enqueue_after_sweep(s, p, par, true, nullptr, 0);
+    return;
+  }
   group(G_EXCHANGE, [&] { s->ops->exchange(p, par, s->st); });
   group(G_LIQUID, [&] { s->ops->stream_liquid(p, par, s->st); });
   group(G_IFACE, [&] { s->ops->stream_interface(p, par, s->st); });
-  if (ev) {
-    group(G_CONVERT, [&] {
-      s->ops->convert_mark(p, s->st);
-      s->ops->label_check(p, s->st);
-      s->ops->convert_excess(p, par, s->st);
-      s->ops->convert_finalize(p, s->st);
-    });
-    const Params pn = next_geometry_params(p);
-    group(G_LABEL, [&] {
-      s->ops->label_choose(p, s->st);
-      s->ops->label(p, s->st);
-      s->ops->label_fast(p, s->st);
-    });
-    group(G_BUBBLE, [&] {
-      s->ops->bubble_update(p, s->st);
-      s->ops->bubble_update_fast(p, s->st);
-    });
-    group(G_GEOMETRY, [&] { enqueue_geometry(s, pn, s->st); });
-    group(G_DISJOIN, [&] { s->ops->disjoining(pn, s->st); });
-    return;
-  }
-  enqueue_after_sweep(s, p, par, false, nullptr, 0);
+  group(G_CONVERT, [&] {
+    s->ops->convert_mark(p, s->st);
+    s->ops->label_check(p, s->st);
+    s->ops->convert_excess(p, par, s->st);
+    s->ops->convert_finalize(p, s->st);
+  });
+  const Params pn = next_geometry_params(p);
+  group(G_LABEL, [&] {
+    s->ops->label_choose(p, s->st);
+    s->ops->label(p, s->st);
+    s->ops->label_fast(p, s->st);
+  });
+  group(G_BUBBLE, [&] {
+    s->ops->bubble_update(p, s->st);
+    s->ops->bubble_update_fast(p, s->st);
+  });
+  group(G_GEOMETRY, [&] { enqueue_geometry(s, pn, s->st); });
+  group(G_DISJOIN, [&] { s->ops->disjoining(pn, s->st); });
 }
 
 // k consecutive steps in one graph (parities alternating from par): every
@@ -548,6 +559,14 @@ int carve_due_nuclei(lbf_sim *s) {
 // device -> caller's (possibly pageable) host memory through two pinned
 // chunks: the copy of one chunk overlaps the host copy of the other
 int copy_to_host(lbf_sim *s, void *dst, const void *src, size_t bytes) {
+  // page-locked destination: one direct copy
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, dst) == cudaSuccess && pa.type == cudaMemoryTypeHost) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return 0;
+  }
+  cudaGetLastError();  // a pageable pointer is not an error
   constexpr size_t kChunk = size_t(4) << 20;
   if (!s->pin[0]) {
     for (int b = 0; b < 2; ++b) {
@@ -725,6 +744,7 @@ void lbf_destroy(lbf_sim *s) {
   if (s->fin) cudaEventDestroy(s->fin);
   if (s->applied) cudaEventDestroy(s->applied);
   if (s->joink) cudaEventDestroy(s->joink);
+  if (s->checked) cudaEventDestroy(s->checked);
   if (s->st2) cudaStreamDestroy(s->st2);
   if (s->st3) cudaStreamDestroy(s->st3);
   if (s->st4) cudaStreamDestroy(s->st4);
@@ -774,6 +794,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fin, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->applied, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joink, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->checked, cudaEventDisableTiming);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
       e = cudaEventCreateWithFlags(&s->fork[k], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join[k], cudaEventDisableTiming);

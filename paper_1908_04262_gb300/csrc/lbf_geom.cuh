@@ -26,6 +26,21 @@
 
 namespace lbf {
 
+// 1 / sqrt(x): the correctly rounded quotient in double, the hardware
+// reciprocal square root in single precision
+__device__ __forceinline__ double rsqrt_r(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+
+// arccos for single precision: Abramowitz and Stegun 4.4.45,
+// acos x = sqrt(1 - x) (a0 + a1 x + a2 x^2 + a3 x^3) on [0, 1] with absolute
+// error below 6.7e-5, and acos(-x) = pi - acos x.  Only a starting value:
+// the cubic's root taken from it is polished by Newton steps.
+__device__ __forceinline__ float acos_as(float x) {
+  const float ax = fabsf(x);
+  const float v = sqrtf(1.f - ax) * (1.5707288f + ax * (-0.2121144f + ax * (0.0742610f + ax * -0.0187293f)));
+  return x < 0.f ? 3.14159265358979f - v : v;
+}
+
 // real root of a^3 + b a^2 + c a + d = 0 closest to [lo, hi], polished
 template <class R>
 __device__ __forceinline__ R cubic_root_in(R b, R c, R d, R lo, R hi) {
@@ -44,9 +59,20 @@ __device__ __forceinline__ R cubic_root_in(R b, R c, R d, R lo, R hi) {
     const R r = (R)2 * sqrt(-P / (R)3);
     R arg = (R)3 * Qc / (P * r);
     arg = arg < (R)-1 ? (R)-1 : (arg > (R)1 ? (R)1 : arg);
-    const R th = acos(arg) / (R)3;
-    const R twopi3 = (R)2.0943951023931954923;
-    for (int k = 0; k < 3; ++k) consider(r * cos(th - twopi3 * (R)k) - b3);
+    if constexpr (sizeof(R) == 4) {
+      // the three cosines cos(th - 2 pi k / 3) from one sine and cosine
+      const float th = acos_as(arg) * (1.f / 3.f);
+      float sn, cs;
+      __sincosf(th, &sn, &cs);
+      const float h = 0.8660254037844386f * sn;
+      consider(r * cs - b3);
+      consider(r * (-0.5f * cs + h) - b3);
+      consider(r * (-0.5f * cs - h) - b3);
+    } else {
+      const R th = acos(arg) / (R)3;
+      const R twopi3 = (R)2.0943951023931954923;
+      for (int k = 0; k < 3; ++k) consider(r * cos(th - twopi3 * (R)k) - b3);
+    }
   } else {
     const R disc = Qc * Qc / (R)4 + P * P * P / (R)27;
     const R sq = sqrt(disc > (R)0 ? disc : (R)0);
@@ -138,24 +164,24 @@ __device__ __forceinline__ R plic_offset(R nx, R ny, R nz, R alpha) {
 }
 
 // Cholesky solve of the k x k symmetric positive definite system A x = b
-// (the ridge keeps the least-squares normal matrix definite)
+// (the ridge keeps the least-squares normal matrix definite); the
+// reciprocals of the factor's diagonal turn every division into a product
 template <class R, int K>
 __device__ __forceinline__ bool chol_solve(R (&A)[K][K], R (&b)[K], R (&x)[K]) {
+  R il[K];
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     R d = A[j][j];
 #pragma unroll
     for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
     if (!(d > (R)1e-9)) return false;
-    const R l = sqrt(d);
-    A[j][j] = l;
-    const R il = (R)1 / l;
+    il[j] = rsqrt_r(d);
 #pragma unroll
     for (int i = j + 1; i < K; ++i) {
       R v = A[i][j];
 #pragma unroll
       for (int k = 0; k < j; ++k) v -= A[i][k] * A[j][k];
-      A[i][j] = v * il;
+      A[i][j] = v * il[j];
     }
   }
   R y[K];
@@ -164,14 +190,14 @@ __device__ __forceinline__ bool chol_solve(R (&A)[K][K], R (&b)[K], R (&x)[K]) {
     R v = b[i];
 #pragma unroll
     for (int k = 0; k < i; ++k) v -= A[i][k] * y[k];
-    y[i] = v / A[i][i];
+    y[i] = v * il[i];
   }
 #pragma unroll
   for (int i = K - 1; i >= 0; --i) {
     R v = y[i];
 #pragma unroll
     for (int k = i + 1; k < K; ++k) v -= A[k][i] * x[k];
-    x[i] = v / A[i][i];
+    x[i] = v * il[i];
   }
   return true;
 }
@@ -194,10 +220,12 @@ template <int G, class R> __device__ __forceinline__ R group_sum(R v) {
 // 9 in 2D), so the gradient, the PLIC cuts and the least-squares sums are
 // spread over the group and reduced in log2(GEO_LANES) shuffles; the first
 // lane of each group solves the normal equations and stores the results.
+// Eight blocks of 128 threads per SM (64 registers, no spills) were measured
+// faster than the six that 80 registers allow.
 constexpr int GEO_LANES = 8;
 
 template <int D, class R>
-__global__ void __launch_bounds__(128) k_geometry(Params p) {
+__global__ void __launch_bounds__(128, 8) k_geometry(Params p) {
   constexpr int K = D == 3 ? 5 : 2;
   constexpr int NS = D == 3 ? 27 : 9;
   constexpr int CTR = D == 3 ? 13 : 4;
@@ -350,11 +378,11 @@ __global__ void __launch_bounds__(128) k_geometry(Params p) {
     if (full) {
       if constexpr (D == 3) {
         const R H = beta[3], I = beta[4];
-        const R q2 = (R)1 + H * H + I * I;
-        kv = -(((R)1 + I * I) * beta[0] - H * I * beta[2] + ((R)1 + H * H) * beta[1]) / (q2 * sqrt(q2));
+        const R iq = rsqrt_r((R)1 + H * H + I * I);
+        kv = -(((R)1 + I * I) * beta[0] - H * I * beta[2] + ((R)1 + H * H) * beta[1]) * (iq * iq * iq);
       } else {
-        const R q2 = (R)1 + beta[1] * beta[1];
-        kv = -beta[0] / (q2 * sqrt(q2));
+        const R iq = rsqrt_r((R)1 + beta[1] * beta[1]);
+        kv = -beta[0] * (iq * iq * iq);
       }
     } else if (np >= 1) {
       kv = (D == 3 ? (R)-2 : (R)-1) * (b1 / (N1 + (R)kLsqRidge));

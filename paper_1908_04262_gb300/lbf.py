@@ -262,8 +262,11 @@ class Sim:
                     mass=np.array([b.gas_mass for b in rows]),
                     pressure=np.array([b.pressure for b in rows]))
 
-    def fields(self, names, dtype=np.float64) -> dict:
-        """Host copies of the named fields (``FIELD_BITS`` keys)."""
+    def fields(self, names, dtype=np.float64, out=None) -> dict:
+        """Host copies of the named fields (``FIELD_BITS`` keys).  ``out``
+        optionally maps names to caller-owned contiguous host arrays of the
+        right size and dtype (page-locked ones are filled by one direct
+        copy each)."""
         names = sorted(set(names), key=lambda k: FIELD_BITS[k])
         outs = {}
         ptrs = (ctypes.c_void_p * len(names))()
@@ -271,7 +274,13 @@ class Sim:
         for i, k in enumerate(names):
             width = 3 if k in VECTOR_FIELDS else 1
             dt = np.int32 if k in INT_FIELDS else dtype
-            a = np.zeros(self.N * width, dt)
+            if out is not None and k in out:
+                a = out[k]
+                if a.dtype != dt or a.size != self.N * width or not a.flags["C_CONTIGUOUS"]:
+                    raise ValueError("out[%r] must be a contiguous %s array of %d values" % (k, np.dtype(dt), self.N * width))
+                a = a.reshape(-1)
+            else:
+                a = np.zeros(self.N * width, dt)
             outs[k] = a
             ptrs[i] = a.ctypes.data
             mask |= 1 << FIELD_BITS[k]
