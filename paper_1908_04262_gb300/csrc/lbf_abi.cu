@@ -51,7 +51,7 @@ struct lbf_sim {
   bool own_stream = false;
   cudaStream_t st2 = nullptr, st3 = nullptr, st4 = nullptr;  // further branches of the step graphs
   int prio_least = 0, prio_greatest = 0;      // stream priority range of the device
-  std::vector<cudaGraphNode_t> low_nodes;      // liquid sweeps captured on the third branch
+  std::vector<cudaGraphNode_t> low_nodes;      // kernels captured for the lowest priority
   cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr}, joinx = nullptr, joinex = nullptr,
               fin = nullptr, applied = nullptr, joink = nullptr, checked = nullptr;
   Ops *ops = nullptr;
@@ -270,6 +270,17 @@ void enqueue_geometry(lbf_sim *s, const Params &pn, cudaStream_t st) {
   if (s->mlp_theta) s->ops->mlp_kappa(pn, s->mlp_theta, st);
 }
 
+// the kernel just captured on stream `st` takes the lowest priority in the
+// instantiated graph (set_node_priorities)
+void mark_low_priority(lbf_sim *s, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess &&
+      cs == cudaStreamCaptureStatusActive)
+    s->low_nodes.insert(s->low_nodes.end(), deps, deps + nd);
+}
+
 // everything of a step after its interface sweep.  The marking runs first;
 // then every cell's post-conversion type is known and the union-find passes
 // start, beside the excess pass (which with `waitx` also waits for the
@@ -321,14 +332,8 @@ void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const
     s->ops->exchange(*pnext, parnext, s->st3);
     cudaEventRecord(s->joinex, s->st3);
     s->ops->stream_liquid(*pnext, parnext, s->st3);
-    // the liquid sweep is the branch's last node: remembered so that it can
-    // take the lowest priority (the labelling's blocks go first)
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    const cudaGraphNode_t *deps = nullptr;
-    size_t nd = 0;
-    if (cudaStreamGetCaptureInfo(s->st3, &cs, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess &&
-        cs == cudaStreamCaptureStatusActive)
-      s->low_nodes.insert(s->low_nodes.end(), deps, deps + nd);
+    // the lowest priority: the labelling's blocks go first
+    mark_low_priority(s, s->st3);
     cudaEventRecord(s->joinx, s->st3);
   }
   // the labelling branch is chosen on the device after the marking (see
@@ -450,10 +455,17 @@ int capture_chain(lbf_sim *s, const Params *ps, int par, int k, cudaGraphExec_t 
 
 int capture(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev, cudaGraphExec_t *out) {
   cudaGraph_t gr = nullptr;
+  s->low_nodes.clear();
   CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
   enqueue_step(s, p, par, ev);
   CK(cudaStreamEndCapture(s->st, &gr));
-  cudaError_t e = cudaGraphInstantiate(out, gr, 0);
+  int rc = set_node_priorities(s, gr);
+  s->low_nodes.clear();
+  if (rc) {
+    cudaGraphDestroy(gr);
+    return rc;
+  }
+  cudaError_t e = cudaGraphInstantiate(out, gr, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(gr);
   if (e != cudaSuccess) return fail(LBF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
   return 0;

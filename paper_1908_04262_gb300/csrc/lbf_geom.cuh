@@ -470,59 +470,101 @@ __global__ void __launch_bounds__(128) k_hf_kappa(Params p) {
   }
 }
 
+// lattice index of (x, y, z) a few cells outside the lattice at most, wrapped
+__device__ __forceinline__ int wrap_near(const Params &p, int x, int y, int z) {
+  while (x < 0) x += p.nx;
+  while (x >= p.nx) x -= p.nx;
+  while (y < 0) y += p.ny;
+  while (y >= p.ny) y -= p.ny;
+  while (z < 0) z += p.nz;
+  while (z >= p.nz) z -= p.nz;
+  return x + p.nx * (y + p.ny * z);
+}
+
+// The march visits cells fixed by the normal alone, so the cells of RAY_CHUNK
+// consecutive boundary crossings are found first and their labels and flags
+// loaded together; then the crossings are examined in order.
+constexpr int RAY_CHUNK = 4;
+
 template <int D, class R>
 __global__ void k_disjoining(Params p) {
   const int cnt = *p.icount;
-  FOR_LIST(kk, cnt) {
-  const long long n = p.ilist[kk];
   R *Pi = (R *)p.Pi;
-  const int b = p.label_new[n];
   const R *nr = (const R *)p.nrm, *ds = (const R *)p.dst;
-  const R dir[3] = {nr[n], nr[p.N + n], nr[2 * p.N + n]};
-  if (p.pf.k_pi == 0.f || b < 0 || (dir[0] == (R)0 && dir[1] == (R)0 && dir[2] == (R)0)) {
-    Pi[n] = 0;
-    continue;
-  }
-  const Cell c = make_cell(p, n);
-  R tmax[3], tdel[3];
-  int step[3], off[3] = {0, 0, 0};
-  for (int d = 0; d < 3; ++d) {
-    tmax[d] = dir[d] != (R)0 ? fabs((R)0.5 / dir[d]) : (R)INFINITY;
-    tdel[d] = (R)2 * tmax[d];
-    step[d] = dir[d] >= (R)0 ? 1 : -1;
-  }
-  R dist = -1;
-  const R s0 = ds[n];
-  // axes whose next boundary lies at the same ray parameter (within a
-  // relative 1e-9, 1e-5 in single precision) are crossed together, so that
-  // round-off in a normal with equal components cannot split a diagonal step
-  const R tie = (R)1 + (R)(sizeof(R) == 4 ? 1e-5 : 1e-9);
-  for (int it = 1; it <= p.ray_steps; ++it) {
-    const R tm = fmin(tmax[0], fmin(tmax[1], tmax[2]));
-    for (int d = 0; d < 3; ++d)
-      if (tmax[d] <= tm * tie) {
-        tmax[d] += tdel[d];
-        off[d] += step[d];
-      }
-    const long long y = at_far(p, c.x + off[0], c.y + off[1], c.z + off[2]);
-    const int ly = p.label_new[y];
-    if (ly == b) continue;
-    const int ty = post_type(p.flags[y]);
-    if (ty == T_WALL) break;
-    if ((ty == T_IFC || ty == T_GAS) && ly >= 0) {
-      const R ny0 = nr[y], ny1 = nr[p.N + y], ny2 = nr[2 * p.N + y];
-      const R den = ny0 * dir[0] + ny1 * dir[1] + ny2 * dir[2];
-      if (ty == T_IFC && den < (R)-1e-6) {
-        const R ncy = ny0 * (R)off[0] + ny1 * (R)off[1] + ny2 * (R)off[2];
-        dist = (ds[y] + ncy) / den - s0;
-      } else {
-        dist = tm - s0;
-      }
-      if (dist < (R)0) dist = 0;
-      break;
+  FOR_LIST(kk, cnt) {
+    const long long n = p.ilist[kk];
+    const int b = p.label_new[n];
+    const R dir[3] = {nr[n], nr[p.N + n], nr[2 * p.N + n]};
+    if (p.pf.k_pi == 0.f || b < 0 || (dir[0] == (R)0 && dir[1] == (R)0 && dir[2] == (R)0)) {
+      Pi[n] = 0;
+      continue;
     }
-  }
-  Pi[n] = (dist >= (R)0 && dist < PV(R, d_max)) ? PV(R, k_pi) * (PV(R, d_max) - dist) : (R)0;
+    const Cell c = make_cell(p, n);
+    R tmax[3], tdel[3];
+    int step[3], off[3] = {0, 0, 0};
+    for (int d = 0; d < 3; ++d) {
+      tmax[d] = dir[d] != (R)0 ? fabs((R)0.5 / dir[d]) : (R)INFINITY;
+      tdel[d] = (R)2 * tmax[d];
+      step[d] = dir[d] >= (R)0 ? 1 : -1;
+    }
+    R dist = -1;
+    const R s0 = ds[n];
+    // axes whose next boundary lies at the same ray parameter (within a
+    // relative 1e-9, 1e-5 in single precision) are crossed together, so that
+    // round-off in a normal with equal components cannot split a diagonal step
+    const R tie = (R)1 + (R)(sizeof(R) == 4 ? 1e-5 : 1e-9);
+    bool done = false;
+    for (int it0 = 1; it0 <= p.ray_steps && !done; it0 += RAY_CHUNK) {
+      const int nst = min(RAY_CHUNK, p.ray_steps - it0 + 1);
+      int yy[RAY_CHUNK], ox[RAY_CHUNK], oy[RAY_CHUNK], oz[RAY_CHUNK];
+      R tms[RAY_CHUNK];
+#pragma unroll
+      for (int j = 0; j < RAY_CHUNK; ++j) {
+        yy[j] = (int)n;
+        ox[j] = oy[j] = oz[j] = 0;
+        tms[j] = 0;
+        if (j >= nst) continue;
+        const R tm = fmin(tmax[0], fmin(tmax[1], tmax[2]));
+        for (int d = 0; d < 3; ++d)
+          if (tmax[d] <= tm * tie) {
+            tmax[d] += tdel[d];
+            off[d] += step[d];
+          }
+        tms[j] = tm;
+        ox[j] = off[0];
+        oy[j] = off[1];
+        oz[j] = off[2];
+        yy[j] = wrap_near(p, c.x + off[0], c.y + off[1], c.z + off[2]);
+      }
+      int ly[RAY_CHUNK];
+      uint8_t fy[RAY_CHUNK];
+#pragma unroll
+      for (int j = 0; j < RAY_CHUNK; ++j) {
+        ly[j] = j < nst ? p.label_new[yy[j]] : b;
+        fy[j] = j < nst ? p.flags[yy[j]] : (uint8_t)T_LIQ;
+      }
+#pragma unroll
+      for (int j = 0; j < RAY_CHUNK; ++j) {
+        if (done || j >= nst || ly[j] == b) continue;
+        const int ty = post_type(fy[j]);
+        if (ty == T_WALL) {
+          done = true;
+        } else if ((ty == T_IFC || ty == T_GAS) && ly[j] >= 0) {
+          const int y = yy[j];
+          const R ny0 = nr[y], ny1 = nr[p.N + y], ny2 = nr[2 * p.N + y];
+          const R den = ny0 * dir[0] + ny1 * dir[1] + ny2 * dir[2];
+          if (ty == T_IFC && den < (R)-1e-6) {
+            const R ncy = ny0 * (R)ox[j] + ny1 * (R)oy[j] + ny2 * (R)oz[j];
+            dist = (ds[y] + ncy) / den - s0;
+          } else {
+            dist = tms[j] - s0;
+          }
+          if (dist < (R)0) dist = 0;
+          done = true;
+        }
+      }
+    }
+    Pi[n] = (dist >= (R)0 && dist < PV(R, d_max)) ? PV(R, k_pi) * (PV(R, d_max) - dist) : (R)0;
   }
 }
 
