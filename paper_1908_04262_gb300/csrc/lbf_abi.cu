@@ -100,7 +100,7 @@ struct lbf_sim {
   double *acc = nullptr;
   unsigned long long *counts = nullptr;
   void *staging = nullptr;
-  float *tau_tab = nullptr;
+  float *om_tab = nullptr;
   void *mlp_theta = nullptr;   // packed network image when attached, else NULL
   float *mlp_buf = nullptr;    // owned copy of the parameters
   void *mlp_img = nullptr;     // owned packed image
@@ -187,7 +187,7 @@ Params make_params(lbf_sim *s, long long step) {
   p.tile_blocks = s->tile_blocks;
   p.tdirty = s->tdirty;
   p.rlabel = s->rlabel;
-  p.tau_tab = s->tau_tab; p.tab_n = s->tab_n; p.tab_lnA0 = s->tab_lnA0; p.tab_inv_dlnA = s->tab_inv_dlnA;
+  p.om_tab = s->om_tab; p.tab_n = s->tab_n; p.tab_lnA0 = s->tab_lnA0; p.tab_inv_dlnA = s->tab_inv_dlnA;
   p.tau = c.tau; p.rho0 = c.rho0; p.ax = c.accel[0]; p.ay = c.accel[1]; p.az = c.accel[2];
   p.has_force = (c.accel[0] != 0.0 || c.accel[1] != 0.0 || c.accel[2] != 0.0);
   p.rheo = c.rheo; p.rn = c.rheo_n; p.rk = c.rheo_k; p.rlam = c.rheo_lambda; p.ra = c.rheo_a;
@@ -204,10 +204,13 @@ Params make_params(lbf_sim *s, long long step) {
   p.trt = c.collision == 1;
   p.kappa_hf = c.kappa == 1;
   p.trt_magic = c.trt_magic;
+  p.omg = 1.0 / p.taug;
+  p.om = 1.0 / p.tau;
   p.pf = {(float)p.tau, (float)p.rho0, (float)p.ax, (float)p.ay, (float)p.az, (float)p.rn, (float)p.rk,
           (float)p.rlam, (float)p.ra, (float)p.tau0, (float)p.tau_inf, (float)p.tau_min, (float)p.tau_max,
           (float)p.sigma, (float)p.k_pi, (float)p.d_max, (float)p.taug, (float)p.kH, (float)p.RT, (float)p.c0,
-          (float)p.q, (float)p.p0, (float)p.eps, (float)p.uwx, (float)p.uwy, (float)p.uwz, (float)c.trt_magic};
+          (float)p.q, (float)p.p0, (float)p.eps, (float)p.uwx, (float)p.uwy, (float)p.uwz, (float)c.trt_magic,
+          (float)p.omg, (float)p.om};
   return p;
 }
 
@@ -644,10 +647,10 @@ int build_tau_table(lbf_sim *s) {
   const double lnA0 = std::log(1e-14), lnA1 = std::log(1e2);
   const double dl = (lnA1 - lnA0) / (n - 1);
   std::vector<float> tab(n);
-  for (int k = 0; k < n; ++k) tab[k] = (float)host_solve_tau(c, std::exp(lnA0 + k * dl));
-  int rc = dalloc(s, &s->tau_tab, (size_t)n);
+  for (int k = 0; k < n; ++k) tab[k] = (float)(1.0 / host_solve_tau(c, std::exp(lnA0 + k * dl)));
+  int rc = dalloc(s, &s->om_tab, (size_t)n);
   if (rc) return rc;
-  CK(cudaMemcpy(s->tau_tab, tab.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->om_tab, tab.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
   s->tab_n = n;
   s->tab_lnA0 = (float)lnA0;
   s->tab_inv_dlnA = (float)(1.0 / dl);

@@ -163,15 +163,16 @@ struct Params {
   // the bubble capacity); read only at cells that are roots
   int *rlabel;
   // tabulated relaxation time tau(A) of the non-Newtonian models for the
-  // single-precision forms: tau_tab[k] at ln A = tab_lnA0 + k * tab_dlnA
-  const float *tau_tab;
+  // single-precision forms, as the relaxation rate 1 / tau: om_tab[k] at
+  // ln A = tab_lnA0 + k * tab_dlnA
+  const float *om_tab;
   int tab_n;
   float tab_lnA0, tab_inv_dlnA;
   // physics, in double and as float copies (the single-precision kernels
   // must not touch the FP64 pipe)
   struct PF {
     float tau, rho0, ax, ay, az, rn, rk, rlam, ra, tau0, tau_inf, tau_min, tau_max;
-    float sigma, k_pi, d_max, taug, kH, RT, c0, q, p0, eps, uwx, uwy, uwz, trt_magic;
+    float sigma, k_pi, d_max, taug, kH, RT, c0, q, p0, eps, uwx, uwy, uwz, trt_magic, omg, om;
   } pf;
   double tau, rho0, ax, ay, az;
   int has_force, rheo;
@@ -181,6 +182,8 @@ struct Params {
   double rn, rk, rlam, ra, tau0, tau_inf, tau_min, tau_max;
   double sigma, k_pi, d_max, taug, kH, RT, c0, q, p0, eps;
   double uwx, uwy, uwz;
+  double omg;  // 1 / taug
+  double om;   // 1 / tau (the Newtonian relaxation rate)
   int walls, atmosphere, top_layer, ray_steps;
 };
 

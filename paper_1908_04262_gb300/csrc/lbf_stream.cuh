@@ -152,9 +152,10 @@ __global__ void __launch_bounds__(128) k_exchange(Params p) {
       }
     }
     R *uI = (R *)p.uI;
-    uI[n] = (jx - (R)0.5 * rho * PV(R, ax)) / rho;
-    uI[p.N + n] = (jy - (R)0.5 * rho * PV(R, ay)) / rho;
-    uI[2 * p.N + n] = (jz - (R)0.5 * rho * PV(R, az)) / rho;
+    const R irho = (R)1 / rho;
+    uI[n] = (jx - (R)0.5 * rho * PV(R, ax)) * irho;
+    uI[p.N + n] = (jy - (R)0.5 * rho * PV(R, ay)) * irho;
+    uI[2 * p.N + n] = (jz - (R)0.5 * rho * PV(R, az)) * irho;
     M[n] = M[n] + dM;
   }
 }
@@ -163,30 +164,30 @@ template <class R> struct SweepOcc;
 template <> struct SweepOcc<double> { static constexpr int blocks = 3; };
 template <> struct SweepOcc<float> { static constexpr int blocks = 8; };
 
-// tau(A) of the single-precision forms: linear interpolation in ln A of a
-// table built on the host by bisection (constant beyond its ends)
-__device__ __forceinline__ float tau_lookup(const Params &p, float A) {
+// 1 / tau(A) of the single-precision forms: linear interpolation in ln A
+// of a table built on the host by bisection (constant beyond its ends)
+__device__ __forceinline__ float om_lookup(const Params &p, float A) {
   const float x = (__logf(fmaxf(A, 1e-30f)) - p.tab_lnA0) * p.tab_inv_dlnA;
-  if (!(x > 0.f)) return __ldg(p.tau_tab);
-  if (x >= (float)(p.tab_n - 1)) return __ldg(p.tau_tab + p.tab_n - 1);
+  if (!(x > 0.f)) return __ldg(p.om_tab);
+  if (x >= (float)(p.tab_n - 1)) return __ldg(p.om_tab + p.tab_n - 1);
   const int k = (int)x;
   const float fr = x - (float)k;
-  const float a = __ldg(p.tau_tab + k), b = __ldg(p.tau_tab + k + 1);
+  const float a = __ldg(p.om_tab + k), b = __ldg(p.om_tab + k + 1);
   return a + fr * (b - a);
 }
-template <class R> __device__ __forceinline__ R model_tau(const Params &p, R A) {
+template <class R> __device__ __forceinline__ R model_om(const Params &p, R A) {
   if constexpr (sizeof(R) == 4)
-    return tau_lookup(p, A);
+    return om_lookup(p, A);
   else
-    return solve_tau<R>(p, A);
+    return (R)1 / solve_tau<R>(p, A);
 }
 
-// Sec. 2.3: local relaxation time.  The non-equilibrium stress is the raw
+// Sec. 2.3: local relaxation rate 1 / tau.  The non-equilibrium stress is the raw
 // second moment minus its equilibrium value rho (u u + cs^2 I) (identical
 // to sum e e (f - f_eq) for the second-order equilibrium).
 template <int D, class R>
-__device__ __forceinline__ R local_tau(const Params &p, const R *fi, R rho, R ux, R uy, R uz) {
-  if (p.rheo == 0) return PV(R, tau);
+__device__ __forceinline__ R local_om(const Params &p, const R *fi, R rho, R irho, R ux, R uy, R uz) {
+  if (p.rheo == 0) return PV(R, om);
   R mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
 #pragma unroll
   for (int i = 1; i < Lat<D>::Q; ++i) {
@@ -206,7 +207,8 @@ __device__ __forceinline__ R local_tau(const Params &p, const R *fi, R rho, R ux
   const R pzz = D == 3 ? mzz - rho * uz * uz - third : (R)0;
   const R pxy = mxy - rho * ux * uy, pxz = mxz - rho * ux * uz, pyz = myz - rho * uy * uz;
   const R nrm2 = pxx * pxx + pyy * pyy + pzz * pzz + (R)2 * (pxy * pxy + pxz * pxz + pyz * pyz);
-  return model_tau<R>(p, sqrt(nrm2) / ((R)1.4142135623730951 * rho / (R)3));
+  // A = |Pi_neq| / (sqrt(2) rho c_s^2) with c_s^2 = 1/3
+  return model_om<R>(p, sqrt(nrm2) * ((R)2.1213203435596424 * irho));
 }
 
 // relaxation with Guo forcing of one cell (BGK, or with TRT two relaxation
@@ -214,10 +216,9 @@ __device__ __forceinline__ R local_tau(const Params &p, const R *fi, R rho, R ux
 template <int D, class S, int PAR, bool TRT>
 __device__ __forceinline__ void relax_store(const Params &p, const Cell &c, long long n, S *f, const typename ST<S>::R *fi,
                                             typename ST<S>::R rho, typename ST<S>::R ux, typename ST<S>::R uy,
-                                            typename ST<S>::R uz, typename ST<S>::R tau) {
+                                            typename ST<S>::R uz, typename ST<S>::R om) {
   using R = typename ST<S>::R;
   constexpr int Q = Lat<D>::Q;
-  const R om = (R)1 / tau;
   const R base = (R)1 - (ux * ux + uy * uy + uz * uz) * (R)1.5;
   if constexpr (TRT) {
     // two relaxation times: per pair (i, opp(i) = i + 1) the even part of
@@ -226,6 +227,7 @@ __device__ __forceinline__ void relax_store(const Params &p, const Cell &c, long
     // w_i rho [3 (e_i - u).a + 9 (e_i.u)(e_i.a)] splits alike (even part
     // w_i rho (9 (e.u)(e.a) - 3 u.a), odd part 3 w_i rho e.a), each scaled by
     // 1 - om/2 or 1 - om_m/2
+    const R tau = (R)1 / om;
     const R om_m = (R)1 / ((R)0.5 + PV(R, trt_magic) / (tau - (R)0.5));
     const R ax = p.has_force ? PV(R, ax) : (R)0, ay = p.has_force ? PV(R, ay) : (R)0,
             az = p.has_force ? PV(R, az) : (R)0;
@@ -267,11 +269,21 @@ __device__ __forceinline__ void relax_store(const Params &p, const Cell &c, long
          fi[i] - (fi[i] - fe) * om + (R)Lat<D>::w(i) * fr * F, fshift<S, D>(p, i));
     }
   } else {
+    // opposite directions (i, i + 1) share the even part w rho (base +
+    // 4.5 (e.u)^2) of the equilibrium and differ in the sign of its odd part
+    // 3 w rho e.u
+    {
+      const R fe = (R)Lat<D>::w(0) * rho * base;
+      st(plane(f, p, dir_out<D>(0, 1 - PAR)), cell_out<D>(p, c, 0, 1 - PAR), fi[0] - (fi[0] - fe) * om, fshift<S, D>(p, 0));
+    }
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int i = 1; i < Q; i += 2) {
+      const int k = i + 1;
       const R eu = (R)Lat<D>::cx(i) * ux + (R)Lat<D>::cy(i) * uy + (R)Lat<D>::cz(i) * uz;
-      const R fe = (R)Lat<D>::w(i) * rho * (base + eu * ((R)3 + eu * (R)4.5));
-      st(plane(f, p, dir_out<D>(i, 1 - PAR)), cell_out<D>(p, c, i, 1 - PAR), fi[i] - (fi[i] - fe) * om, fshift<S, D>(p, i));
+      const R wr = (R)Lat<D>::w(i) * rho;
+      const R even = wr * (base + (R)4.5 * eu * eu), odd = (R)3 * wr * eu;
+      st(plane(f, p, dir_out<D>(i, 1 - PAR)), cell_out<D>(p, c, i, 1 - PAR), fi[i] - (fi[i] - (even + odd)) * om, fshift<S, D>(p, i));
+      st(plane(f, p, dir_out<D>(k, 1 - PAR)), cell_out<D>(p, c, k, 1 - PAR), fi[k] - (fi[k] - (even - odd)) * om, fshift<S, D>(p, k));
     }
   }
 }
@@ -335,14 +347,15 @@ __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long
     if (Lat<D>::cy(i)) jy += Lat<D>::cy(i) > 0 ? fi[i] : -fi[i];
     if (Lat<D>::cz(i)) jz += Lat<D>::cz(i) > 0 ? fi[i] : -fi[i];
   }
-  const R ux = (jx + (R)0.5 * rho * PV(R, ax)) / rho;
-  const R uy = (jy + (R)0.5 * rho * PV(R, ay)) / rho;
-  const R uz = (jz + (R)0.5 * rho * PV(R, az)) / rho;
-  relax_store<D, S, PAR, TRT>(p, c, n, f, fi, rho, ux, uy, uz, local_tau<D, R>(p, fi, rho, ux, uy, uz));
+  const R irho = (R)1 / rho;
+  const R ux = (jx + (R)0.5 * rho * PV(R, ax)) * irho;
+  const R uy = (jy + (R)0.5 * rho * PV(R, ay)) * irho;
+  const R uz = (jz + (R)0.5 * rho * PV(R, az)) * irho;
+  relax_store<D, S, PAR, TRT>(p, c, n, f, fi, rho, ux, uy, uz, local_om<D, R>(p, fi, rho, irho, ux, uy, uz));
   R cg = 0;
 #pragma unroll
   for (int i = 0; i < QA; ++i) cg += gi[i];
-  const R omg = (R)1 / PV(R, taug);
+  const R omg = PV(R, omg);
 #pragma unroll
   for (int i = 0; i < QA; ++i) {
     const R v = gi[i] + (geq<R, D>(i, cg, ux, uy, uz) - gi[i]) * omg + (R)Lat<D>::wa(i) * PV(R, q);
@@ -426,10 +439,11 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
     jy += fi[i] * (R)Lat<D>::cy(i);
     jz += fi[i] * (R)Lat<D>::cz(i);
   }
-  const R ux = (jx + (R)0.5 * rho * PV(R, ax)) / rho;
-  const R uy = (jy + (R)0.5 * rho * PV(R, ay)) / rho;
-  const R uz = (jz + (R)0.5 * rho * PV(R, az)) / rho;
-  relax_store<D, S, PAR, TRT>(p, c, n, f, fi, rho, ux, uy, uz, local_tau<D, R>(p, fi, rho, ux, uy, uz));
+  const R irho = (R)1 / rho;
+  const R ux = (jx + (R)0.5 * rho * PV(R, ax)) * irho;
+  const R uy = (jy + (R)0.5 * rho * PV(R, ay)) * irho;
+  const R uz = (jz + (R)0.5 * rho * PV(R, az)) * irho;
+  relax_store<D, S, PAR, TRT>(p, c, n, f, fi, rho, ux, uy, uz, local_om<D, R>(p, fi, rho, irho, ux, uy, uz));
 
   R *phi = (R *)p.phi;
   const R Mn = ((const R *)p.M)[n];
@@ -460,7 +474,7 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
     }
     cgas += gi[i];
   }
-  const R omg = (R)1 / PV(R, taug);
+  const R omg = PV(R, omg);
 #pragma unroll
   for (int i = 0; i < QA; ++i) {
     const R v = gi[i] + (geq<R, D>(i, cgas, ux, uy, uz) - gi[i]) * omg + (R)Lat<D>::wa(i) * PV(R, q);
