@@ -133,22 +133,32 @@ __global__ void __launch_bounds__(128) k_exchange(Params p) {
     const int n = c.n;
     if (ftype(p.flags[n]) != T_IFC) continue;
     const R phn = phi[n];
+    // every load issued at once (none waits for a neighbour's type; the
+    // slots and fill levels of gas and wall neighbours are read and unused)
+    R fo[Q], fin[Q], phm[Q];
+    uint8_t fn[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      fo[i] = ld(plane(f, p, dir_out<D>(i, PAR)), cell_out<D>(p, c, i, PAR), fshift<S, D>(p, i));
+      if (i > 0) {
+        const int m = nb<D>(p, c, i);
+        fn[i] = p.flags[m];
+        // arriving along opp(i) from m: the slot holding m's outgoing f_opp(i)
+        fin[i] = ld(plane(f, p, dir_in<D>(opp(i), PAR)), cell_in<D>(p, c, opp(i), PAR), fshift<S, D>(p, opp(i)));
+        phm[i] = phi[m];
+      }
+    }
     R rho = 0, jx = 0, jy = 0, jz = 0, dM = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const R fo = ld(plane(f, p, dir_out<D>(i, PAR)), cell_out<D>(p, c, i, PAR), fshift<S, D>(p, i));
-      rho += fo;
-      jx += fo * (R)Lat<D>::cx(i);
-      jy += fo * (R)Lat<D>::cy(i);
-      jz += fo * (R)Lat<D>::cz(i);
+      rho += fo[i];
+      jx += fo[i] * (R)Lat<D>::cx(i);
+      jy += fo[i] * (R)Lat<D>::cy(i);
+      jz += fo[i] * (R)Lat<D>::cz(i);
       if (i > 0) {
-        const int m = nb<D>(p, c, i);
-        const int tn = ftype(p.flags[m]);
-        if (tn == T_LIQ || tn == T_IFC) {
-          // arriving along opp(i) from m: the slot holding m's outgoing f_opp(i)
-          const R fin = ld(plane(f, p, dir_in<D>(opp(i), PAR)), cell_in<D>(p, c, opp(i), PAR), fshift<S, D>(p, opp(i)));
-          dM += tn == T_LIQ ? fin - fo : (R)0.5 * (phn + phi[m]) * (fin - fo);
-        }
+        const int tn = ftype(fn[i]);
+        if (tn == T_LIQ || tn == T_IFC)
+          dM += tn == T_LIQ ? fin[i] - fo[i] : (R)0.5 * (phn + phm[i]) * (fin[i] - fo[i]);
       }
     }
     R *uI = (R *)p.uI;
@@ -391,19 +401,38 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
   constexpr int Q = Lat<D>::Q, QA = Lat<D>::QA;
   S *f = (S *)p.f;
   S *g = (S *)p.g;
-  // kinds of the source cells: bit i set when x - e_i is gas / a wall
-  unsigned gasm = 0, wallm = 0;
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const int ts = ftype(p.flags[src<D>(p, c, i)]);
-    gasm |= (ts == T_GAS ? 1u : 0u) << i;
-    wallm |= (ts == T_WALL ? 1u : 0u) << i;
-  }
+  // The loads are issued in two rounds: first every neighbour's type and
+  // label and every streamed population (f and g; those from gas and wall
+  // neighbours are replaced below, an in-bounds read of a slot that is not
+  // used), then what the kinds of the neighbours decide (the bubble
+  // pressures, the cell's own outgoing populations towards gas and walls).
+  unsigned gasm = 0, wallm = 0;  // bit i set when x - e_i is gas / a wall
+  int lsrc[Q];                   // label of x - e_i
   R fi[Q];
+  R gi[QA];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    if (i == 0 || !((gasm | wallm) >> i & 1u)) fi[i] = ld(plane(f, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), fshift<S, D>(p, i));
+    if (i > 0) {
+      const int s = src<D>(p, c, i);
+      const int ts = ftype(p.flags[s]);
+      gasm |= (ts == T_GAS ? 1u : 0u) << i;
+      wallm |= (ts == T_WALL ? 1u : 0u) << i;
+      lsrc[i] = p.label_old[s];
+    }
+    fi[i] = ld(plane(f, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), fshift<S, D>(p, i));
   }
+#pragma unroll
+  for (int i = 0; i < QA; ++i) gi[i] = ld(plane(g, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), gshift<S, D>(p, i));
+  // the bubble pressure seen across each gas link (Eq. rhob), and the ADE
+  // populations of gas and wall links (Henry's law, bounce-back)
+  R pgs[Q];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) pgs[i] = (gasm >> i & 1u) ? (lsrc[i] >= 0 ? (R)p.told.p[lsrc[i]] : PV(R, p0)) : (R)0;
+  R gb[QA];
+#pragma unroll
+  for (int i = 1; i < QA; ++i)
+    if ((gasm | wallm) >> i & 1u)
+      gb[i] = ld(plane(g, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), gshift<S, D>(p, opp(i)));
   if (gasm | wallm) {
     const R *uI = (const R *)p.uI;
     const R uIx = uI[n], uIy = uI[p.N + n], uIz = uI[2 * p.N + n];
@@ -422,9 +451,7 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
         fi[i] = v;
       } else if (gasm >> i & 1u) {
         // Sec. 2.2 Eq. reconstruct with rho_g of Eq. rhob / rhobplusdisjoining
-        const int b = p.label_old[src<D>(p, c, i)];
-        const R pg = b >= 0 ? (R)p.told.p[b] : PV(R, p0);
-        const R rg = (pg - (R)2 * PV(R, sigma) * kap - pi) * (R)3;
+        const R rg = (pgs[i] - (R)2 * PV(R, sigma) * kap - pi) * (R)3;
         const R fo = ld(plane(f, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), fshift<S, D>(p, opp(i)));
         fi[i] = feq<R, D>(i, rg, uIx, uIy, uIz) + feq<R, D>(opp(i), rg, uIx, uIy, uIz) - fo;
       }
@@ -457,20 +484,15 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
   if (mk) p.flags[n] = (uint8_t)(fl | (mk << 2));
 
   // dissolved gas (Sec. 3.1-3.2)
-  R gi[QA];
   R cgas = 0, fl_gas = 0;
 #pragma unroll
   for (int i = 0; i < QA; ++i) {
     if (i > 0 && (wallm >> i & 1u)) {
-      gi[i] = ld(plane(g, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), gshift<S, D>(p, opp(i)));
+      gi[i] = gb[i];
     } else if (i > 0 && (gasm >> i & 1u)) {
-      const int b = p.label_old[src<D>(p, c, i)];
-      const R cH = PV(R, kH) * (b >= 0 ? (R)p.told.p[b] : PV(R, p0));
-      const R go = ld(plane(g, p, dir_out<D>(opp(i), PAR)), cell_out<D>(p, c, opp(i), PAR), gshift<S, D>(p, opp(i)));
-      gi[i] = (R)2 * (R)Lat<D>::wa(i) * cH - go;
-      fl_gas += go - gi[i];
-    } else {
-      gi[i] = ld(plane(g, p, dir_in<D>(i, PAR)), cell_in<D>(p, c, i, PAR), gshift<S, D>(p, i));
+      const R cH = PV(R, kH) * pgs[i];
+      gi[i] = (R)2 * (R)Lat<D>::wa(i) * cH - gb[i];
+      fl_gas += gb[i] - gi[i];
     }
     cgas += gi[i];
   }
@@ -494,7 +516,7 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
 // conversion.  Block 0 also resets the counters of the lists that the
 // conversion fills.
 template <int D, class S, int PAR, bool TRT>
-__global__ void __launch_bounds__(128) k_stream_interface(Params p) {
+__global__ void __launch_bounds__(128, 4) k_stream_interface(Params p) {
   __shared__ double wbuf[128];
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
