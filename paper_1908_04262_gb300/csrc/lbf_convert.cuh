@@ -178,15 +178,22 @@ __device__ __forceinline__ long long list_cell(const Params &p, int k, int nm) {
 template <int D>
 __device__ __forceinline__ bool addition_keeps_bubble(const Params &p, const Cell &c, int n) {
   const int L = p.label_old[n];
+  // the neighbours' flags and labels in one round of loads
+  uint8_t fn[Lat<D>::Q];
+  int ln[Lat<D>::Q];
+#pragma unroll
+  for (int i = 1; i < Lat<D>::Q; ++i) {
+    const int m = nb<D>(p, c, i);
+    fn[i] = p.flags[m];
+    ln[i] = p.label_old[m];
+  }
   if (L < 0 || n <= p.told.root[L]) return false;
   bool anchored = false;
 #pragma unroll
   for (int i = 1; i < Lat<D>::Q; ++i) {
-    const int m = nb<D>(p, c, i);
-    const uint8_t f = p.flags[m];
-    if (post_type(f) != T_GAS) continue;
-    if (p.label_old[m] != L) return false;
-    if (ftype(f) == T_GAS) anchored = true;  // gas before, and no mark turns it interface
+    if (post_type(fn[i]) != T_GAS) continue;
+    if (ln[i] != L) return false;
+    if (ftype(fn[i]) == T_GAS) anchored = true;  // gas before, and no mark turns it interface
   }
   return anchored;
 }
@@ -359,12 +366,21 @@ __device__ __forceinline__ bool apply_cell(const Params &p, const Cell &c, int n
     R *M = (R *)p.M;
     R recv = 0;
     bool has = false;
+    // the neighbours' flags and excess shares in one round of loads (the
+    // share of a neighbour that does not convert is read and unused)
+    uint8_t fn[Lat<D>::Q];
+    R en[Lat<D>::Q];
 #pragma unroll
     for (int i = 1; i < Lat<D>::Q; ++i) {
       const int m = nb<D>(p, c, i);
-      const int fm = fmark(p.flags[m]);
+      fn[i] = p.flags[m];
+      en[i] = ex[m];
+    }
+#pragma unroll
+    for (int i = 1; i < Lat<D>::Q; ++i) {
+      const int fm = fmark(fn[i]);
       if (fm == MK_FILL || fm == MK_EMPTY) {
-        recv += ex[m];
+        recv += en[i];
         has = true;
       }
     }

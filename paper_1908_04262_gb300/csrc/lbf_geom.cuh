@@ -253,12 +253,13 @@ __global__ void __launch_bounds__(128, 8) k_geometry(Params p) {
       if (q < NS) {
         const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = D == 3 ? q / 9 - 1 : 0;
         const long long m = at(p, c, dx, dy, dz);
-        tm[j] = post_type(p.flags[m]);  // may run while the conversion's marks are replaced
+        // flag and fill level in one round of loads (the fill level of a
+        // cell that is not interface is read and unused)
+        const uint8_t fm = p.flags[m];
+        const R v = phi[m];
+        tm[j] = post_type(fm);  // may run while the conversion's marks are replaced
         if (tm[j] == T_LIQ) a[j] = 1;
-        else if (tm[j] == T_IFC) {
-          R v = phi[m];
-          a[j] = v < (R)0 ? (R)0 : (v > (R)1 ? (R)1 : v);
-        }
+        else if (tm[j] == T_IFC) a[j] = v < (R)0 ? (R)0 : (v > (R)1 ? (R)1 : v);
       }
     }
     const R ac = __shfl_sync(0xffffffffu, a[CJ], sub * G + CT);

@@ -774,11 +774,19 @@ __global__ void __launch_bounds__(128) k_label_fast(Params p) {
       const int n = p.inext[k - nm];
       const Cell c = make_cell(p, n);
       int knew = -1;
+      // the neighbours' flags and labels in one round of loads
+      uint8_t fn[Lat<D>::Q];
+      int ln[Lat<D>::Q];
 #pragma unroll
       for (int i = 1; i < Lat<D>::Q; ++i) {
         const int m = nb<D>(p, c, i);
-        if (post_type(p.flags[m]) == T_GAS) {
-          const int l = p.label_old[m];
+        fn[i] = p.flags[m];
+        ln[i] = p.label_old[m];
+      }
+#pragma unroll
+      for (int i = 1; i < Lat<D>::Q; ++i) {
+        if (post_type(fn[i]) == T_GAS) {
+          const int l = ln[i];
           if (l >= 0 && (knew < 0 || l < knew)) knew = l;
         }
       }
