@@ -53,7 +53,8 @@ struct lbf_sim {
   int prio_least = 0, prio_greatest = 0;      // stream priority range of the device
   std::vector<cudaGraphNode_t> low_nodes;      // kernels captured for the lowest priority
   cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr}, joinx = nullptr, joinex = nullptr,
-              fin = nullptr, applied = nullptr, joink = nullptr, checked = nullptr;
+              fin = nullptr, applied = nullptr, joink = nullptr, checked = nullptr,
+              sfork = nullptr, synced = nullptr;
   Ops *ops = nullptr;
   std::vector<void *> allocs;
   std::vector<size_t> alloc_bytes;  // sizes of allocs, in order
@@ -87,6 +88,7 @@ struct lbf_sim {
   int *lab_slow = nullptr;
   int *forest_stale = nullptr;
   int *lab_fast = nullptr;
+  int *lab_full = nullptr;
   int tile_blocks = 0;
   uint8_t *tdirty = nullptr;
   size_t ntiles_alloc = 0;
@@ -148,6 +150,7 @@ Params make_params(lbf_sim *s, long long step) {
   p.nx = c.nx; p.ny = c.ny; p.nz = c.nz; p.dim = s->dim; p.N = s->N;
   p.f = s->f; p.g = s->g;
   p.flags = s->flags;
+  p.par = par;
   p.wmask = s->wmask;
   p.ilist = s->ilist[par];
   p.icount = s->icount[par];
@@ -184,6 +187,7 @@ Params make_params(lbf_sim *s, long long step) {
   p.lab_slow = s->lab_slow;
   p.forest_stale = s->forest_stale;
   p.lab_fast = s->lab_fast;
+  p.lab_full = s->lab_full;
   p.tile_blocks = s->tile_blocks;
   p.tdirty = s->tdirty;
   p.rlabel = s->rlabel;
@@ -227,6 +231,8 @@ int relabel_in_place(lbf_sim *s) {
   // the state was set from outside: label from scratch
   CK(cudaMemsetAsync(s->gas_dirty, 0xff, sizeof(int), s->st));
   CK(cudaMemsetAsync(s->lab_fast, 0, sizeof(int), s->st));
+  // the next patched labelling starts from a full copy
+  CK(cudaMemsetAsync(s->lab_full, 0xff, sizeof(int), s->st));
   s->ops->label(p, s->st);
   s->ops->bubble_update(p, s->st);
   const size_t cap = (size_t)s->cap;
@@ -284,6 +290,16 @@ void mark_low_priority(lbf_sim *s, cudaStream_t st) {
     s->low_nodes.insert(s->low_nodes.end(), deps, deps + nd);
 }
 
+// the step's label sync on the fourth branch, beside its interface sweep
+// (the marking waits for it: it reads the last step's interface list, whose
+// buffer the excess collection refills)
+void enqueue_label_sync(lbf_sim *s, const Params &p) {
+  cudaEventRecord(s->sfork, s->st);
+  cudaStreamWaitEvent(s->st4, s->sfork, 0);
+  s->ops->label_sync(p, s->st4);
+  cudaEventRecord(s->synced, s->st4);
+}
+
 // everything of a step after its interface sweep.  The marking runs first;
 // then every cell's post-conversion type is known and the union-find passes
 // start, beside the excess pass (which with `waitx` also waits for the
@@ -304,6 +320,7 @@ void mark_low_priority(lbf_sim *s, cudaStream_t st) {
 // `joinx`.
 void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const Params *pnext, int parnext) {
   const Params pn = next_geometry_params(p);
+  cudaStreamWaitEvent(s->st, s->synced, 0);
   s->ops->convert_mark(p, s->st);
   cudaEventRecord(s->fork[0], s->st);
   // the labelling check reads the marks (and writes nothing the excess pass
@@ -331,7 +348,9 @@ void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const
     cudaEventRecord(s->fin, s->st3);
   }
   if (pnext) {
-    if (!early_geometry) cudaStreamWaitEvent(s->st3, s->fin, 0);
+    // the next step's mass exchange reads the types through the marks: it
+    // starts once the excess is collected, beside the flag rewrite
+    if (!early_geometry) cudaStreamWaitEvent(s->st3, s->applied, 0);
     s->ops->exchange(*pnext, parnext, s->st3);
     cudaEventRecord(s->joinex, s->st3);
     s->ops->stream_liquid(*pnext, parnext, s->st3);
@@ -344,8 +363,10 @@ void enqueue_after_sweep(lbf_sim *s, const Params &p, int par, bool waitx, const
   s->ops->label_choose(p, s->st);
   s->ops->label_forest(p, s->st);
   cudaStreamWaitEvent(s->st, s->applied, 0);
-  s->ops->label_relabel(p, s->st);
+  // the patch first: ready with the excess collection, it goes ahead of the
+  // geometry's blocks (the relabelling of the other branch returns at once)
   s->ops->label_fast(p, s->st);
+  s->ops->label_relabel(p, s->st);
   cudaEventRecord(s->fork[1], s->st);
   s->ops->bubble_update(p, s->st);
   s->ops->bubble_update_fast(p, s->st);
@@ -374,13 +395,17 @@ void enqueue_step(lbf_sim *s, const Params &p, int par, cudaEvent_t *ev) {
     cudaStreamWaitEvent(s->st3, s->joinex, 0);
     s->ops->stream_liquid(p, par, s->st3);
     cudaEventRecord(s->joinx, s->st3);
+    enqueue_label_sync(s, p);
     s->ops->stream_interface(p, par, s->st);
     enqueue_after_sweep(s, p, par, true, nullptr, 0);
     return;
   }
   group(G_EXCHANGE, [&] { s->ops->exchange(p, par, s->st); });
   group(G_LIQUID, [&] { s->ops->stream_liquid(p, par, s->st); });
-  group(G_IFACE, [&] { s->ops->stream_interface(p, par, s->st); });
+  group(G_IFACE, [&] {
+    s->ops->label_sync(p, s->st);
+    s->ops->stream_interface(p, par, s->st);
+  });
   group(G_CONVERT, [&] {
     s->ops->convert_mark(p, s->st);
     s->ops->label_check(p, s->st);
@@ -412,6 +437,7 @@ void enqueue_chain(lbf_sim *s, const Params *ps, int par, int k) {
   for (int i = 0; i < k; ++i) {
     const int pi = (par + i) & 1;
     if (i > 0) cudaStreamWaitEvent(s->st, s->joinex, 0);
+    enqueue_label_sync(s, ps[i]);
     s->ops->stream_interface(ps[i], pi, s->st);
     enqueue_after_sweep(s, ps[i], pi, i > 0, i + 1 < k ? &ps[i + 1] : nullptr, 1 - pi);
   }
@@ -760,6 +786,8 @@ void lbf_destroy(lbf_sim *s) {
   if (s->applied) cudaEventDestroy(s->applied);
   if (s->joink) cudaEventDestroy(s->joink);
   if (s->checked) cudaEventDestroy(s->checked);
+  if (s->sfork) cudaEventDestroy(s->sfork);
+  if (s->synced) cudaEventDestroy(s->synced);
   if (s->st2) cudaStreamDestroy(s->st2);
   if (s->st3) cudaStreamDestroy(s->st3);
   if (s->st4) cudaStreamDestroy(s->st4);
@@ -810,6 +838,8 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->applied, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->joink, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->checked, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->sfork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->synced, cudaEventDisableTiming);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
       e = cudaEventCreateWithFlags(&s->fork[k], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join[k], cudaEventDisableTiming);
@@ -913,6 +943,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   AL(dalloc(s, &s->lab_slow, 1));
   AL(dalloc(s, &s->forest_stale, 1));
   AL(dalloc(s, &s->lab_fast, 1));
+  AL(dalloc(s, &s->lab_full, 1));
   AL(dalloc(s, &s->wmask, N));
   AL(dalloc(s, &s->rlabel, N));
   AL(dalloc(s, &s->acc, 4));
@@ -951,6 +982,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   e = e ? e : zero(s->lab_slow, sizeof(int));
   e = e ? e : zero(s->forest_stale, sizeof(int));
   e = e ? e : zero(s->lab_fast, sizeof(int));
+  e = e ? e : cudaMemsetAsync(s->lab_full, 0xff, sizeof(int), s->st);
   e = e ? e : zero(s->tdirty, s->ntiles_alloc);
   if (e != cudaSuccess) {
     lbf_destroy(s);

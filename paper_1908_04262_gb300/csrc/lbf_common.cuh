@@ -16,11 +16,19 @@
 
 namespace lbf {
 
-// cell types (bits 0-1 of the flag byte), conversion marks (bits 2-4) and a
+// cell types (bits 0-1 of the flag byte), conversion marks (bits 2-4), a
 // static bit for cells with a wall among their lattice neighbours (bit 5)
+// and the parity of the step that set the mark (bit 6): the liquid sweep of
+// the next step starts before the last conversion has written the new types
+// over its marks, and runs beside the interface sweep that marks cells for
+// its own conversion; the parity tells the two kinds of mark apart
 enum : int { T_GAS = 0, T_LIQ = 1, T_IFC = 2, T_WALL = 3 };
 enum : int { MK_NONE = 0, MK_FILL = 1, MK_EMPTY = 2, MK_GI = 3, MK_LI = 4 };
 constexpr uint8_t NEARWALL = 0x20;
+constexpr uint8_t MARKPAR = 0x40;
+__device__ __forceinline__ uint8_t mark_bits(int mk, int par) {
+  return (uint8_t)((mk << 2) | (par ? MARKPAR : 0));
+}
 __device__ __forceinline__ int ftype(uint8_t f) { return f & 3; }
 __device__ __forceinline__ int fmark(uint8_t f) { return (f >> 2) & 7; }
 
@@ -158,6 +166,11 @@ struct Params {
   // after the marking; the union-find kernels then return at once, and the
   // patch kernels do otherwise).  NULL means the union-find labelling.
   int *lab_fast;
+  // 1 when the labels of the last step are not the labels of the step
+  // before patched at that step's listed cells (a full labelling ran, or the
+  // state was set from outside): the next patched labelling then starts
+  // from a full copy instead of copying the listed cells
+  int *lab_full;
   int tile_blocks;  // grid of the tile loops of the union-find (two blocks per SM)
   // label of each current root cell (rank among the sorted roots, -1 past
   // the bubble capacity); read only at cells that are roots
@@ -185,6 +198,7 @@ struct Params {
   double omg;  // 1 / taug
   double om;   // 1 / tau (the Newtonian relaxation rate)
   int walls, atmosphere, top_layer, ray_steps;
+  int par;  // parity of the step (of the populations when it starts)
 };
 
 // a physics parameter in the arithmetic type R

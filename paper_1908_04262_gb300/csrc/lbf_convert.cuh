@@ -83,11 +83,11 @@ __device__ __forceinline__ int spread_index(int base) {
 }
 
 // set a conversion mark on a neighbour's flag byte; true for the first writer
-__device__ __forceinline__ bool mark_byte(uint8_t *flags, long long m, int mk) {
+__device__ __forceinline__ bool mark_byte(uint8_t *flags, long long m, int mk, int par) {
   const uintptr_t a = (uintptr_t)(flags + m);
   unsigned *word = (unsigned *)(a & ~(uintptr_t)3);
   const int sh = (int)(a & 3) * 8;
-  const unsigned old = atomicOr(word, (unsigned)(mk << 2) << sh);
+  const unsigned old = atomicOr(word, (unsigned)mark_bits(mk, par) << sh);
   return ((old >> sh) & (7u << 2)) == 0;
 }
 
@@ -103,6 +103,9 @@ __global__ void __launch_bounds__(128) k_conv_mark(Params p) {
   constexpr int Q = Lat<D>::Q;
   const int lane = threadIdx.x & 31;
   const int cnt = *p.mcount;
+  // the next interface list is collected afresh (its buffer held the last
+  // step's list until the label sync of this step read it)
+  if (blockIdx.x == 0 && threadIdx.x == 0) *p.inext_count = 0;
   for (int base = 0; base < cnt; base += gridDim.x * blockDim.x) {
     const int k = spread_index(base);
     int mk = MK_NONE;
@@ -127,13 +130,13 @@ __global__ void __launch_bounds__(128) k_conv_mark(Params p) {
         // clear the emptying mark (mark bits only; other threads read the
         // type bits of this byte)
         const uintptr_t a = (uintptr_t)(p.flags + n);
-        atomicAnd((unsigned *)(a & ~(uintptr_t)3), ~((7u << 2) << ((int)(a & 3) * 8)));
+        atomicAnd((unsigned *)(a & ~(uintptr_t)3), ~((unsigned)mark_bits(7, 1) << ((int)(a & 3) * 8)));
       } else {
         const int want = mk == MK_FILL ? T_GAS : T_LIQ;
         const int put = mk == MK_FILL ? MK_GI : MK_LI;
 #pragma unroll
         for (int i = 1; i < Q; ++i)
-          if (ftype(fn[i]) == want && mark_byte(p.flags, nb<D>(p, c, i), put)) claimed |= 1u << i;
+          if (ftype(fn[i]) == want && mark_byte(p.flags, nb<D>(p, c, i), put, p.par)) claimed |= 1u << i;
         if (p.gas_dirty) {
           if (mk == MK_EMPTY) {  // this cell turns gas
             atomicOr(p.gas_dirty, 1);

@@ -710,22 +710,37 @@ static __global__ void __launch_bounds__(1024) k_bubble_update(Params p) {
 // of the branch not taken return at once.
 static __global__ void k_label_choose(Params p) {
   const int d = *p.gas_dirty;  // -1: the state was set from outside
-  *p.lab_fast = d >= 0 && *p.lab_slow == 0;
+  const bool fast = d >= 0 && *p.lab_slow == 0;
+  *p.lab_fast = fast;
+  *p.lab_full = !fast;
   *p.lab_slow = 0;
 }
 
-// the patch starts from a copy of the last labels (int4 words and a tail)
-static __global__ void k_label_copy(Params p) {
-  if (!label_fast(p)) return;
-  const long long n4 = p.N >> 2;
-  const int4 *src = reinterpret_cast<const int4 *>(p.label_old);
-  int4 *dst = reinterpret_cast<int4 *>(p.label_new);
+// At the start of a step, before its marking: bring label_new (the labels
+// of the step before last) up to the last labels wherever they differ.
+// After a patched step they differ only at that step's interface cells
+// before and after its conversion (every cell it patched), which are the
+// two interface lists at hand; otherwise (lab_full) everything is copied,
+// as int4 words and a tail.  The patch of this step then writes only its
+// own cells; a full labelling overwrites every label.
+static __global__ void k_label_sync(Params p) {
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
-  for (long long k = tid; k < n4; k += nt) dst[k] = __ldcs(src + k);
-  for (long long k = (n4 << 2) + tid; k < p.N; k += nt) p.label_new[k] = p.label_old[k];
+  if (*p.lab_full) {
+    const long long n4 = p.N >> 2;
+    const int4 *src = reinterpret_cast<const int4 *>(p.label_old);
+    int4 *dst = reinterpret_cast<int4 *>(p.label_new);
+    for (long long k = tid; k < n4; k += nt) dst[k] = __ldcs(src + k);
+    for (long long k = (n4 << 2) + tid; k < p.N; k += nt) p.label_new[k] = p.label_old[k];
+    return;
+  }
+  const int np = *p.inext_count, nc = *p.icount;  // the last step's interface list, this step's
+  for (long long k = tid; k < np + nc; k += nt) {
+    const int n = k < np ? p.inext[k] : p.ilist[k - np];
+    p.label_new[n] = p.label_old[n];
+  }
 }
 
-// label_new holds a copy of label_old when this runs (k_label_copy).  One thread per marked
+// label_new holds the last labels when this runs (k_label_sync).  One thread per marked
 // cell, then per interface cell after the conversion; gas counts grow by the
 // added cells; volumes collect the interface shares 1 - alpha.
 template <int D, class R>

@@ -115,8 +115,8 @@ struct OpsImpl final : Ops {
   void bubble_update(const Params &p, cudaStream_t s) override { k_bubble_update<<<1, 1024, 0, s>>>(p); }
   void label_check(const Params &p, cudaStream_t s) override { k_label_check<D><<<p.list_blocks, 128, 0, s>>>(p); }
   void label_choose(const Params &p, cudaStream_t s) override { k_label_choose<<<1, 1, 0, s>>>(p); }
+  void label_sync(const Params &p, cudaStream_t s) override { k_label_sync<<<p.list_blocks, 128, 0, s>>>(p); }
   void label_fast(const Params &p, cudaStream_t s) override {
-    k_label_copy<<<p.warp_blocks, 128, 0, s>>>(p);
     k_label_fast<D, R><<<p.list_blocks, 128, 0, s>>>(p);
   }
   void bubble_update_fast(const Params &p, cudaStream_t s) override {

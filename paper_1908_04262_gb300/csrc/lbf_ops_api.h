@@ -50,6 +50,9 @@ struct Ops {
   // kernels in every other
   virtual void label_check(const Params &p, cudaStream_t s) = 0;  // after the marking
   virtual void label_choose(const Params &p, cudaStream_t s) = 0;
+  // at the start of the step, before the marking: label_new brought up to
+  // the last labels (see k_label_sync); label_fast then writes the patch
+  virtual void label_sync(const Params &p, cudaStream_t s) = 0;
   virtual void label_fast(const Params &p, cudaStream_t s) = 0;
   virtual void bubble_update_fast(const Params &p, cudaStream_t s) = 0;
   virtual void geometry(const Params &p, cudaStream_t s) = 0;

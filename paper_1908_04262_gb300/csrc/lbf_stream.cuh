@@ -131,7 +131,9 @@ __global__ void __launch_bounds__(128) k_exchange(Params p) {
     Cell c;
     if (!seg_cell(p, p.seglist[k], lane, c)) continue;
     const int n = c.n;
-    if (ftype(p.flags[n]) != T_IFC) continue;
+    // types through the last conversion's marks: the exchange may run while
+    // that conversion still writes the new types
+    if (post_type(p.flags[n]) != T_IFC) continue;
     const R phn = phi[n];
     // every load issued at once (none waits for a neighbour's type; the
     // slots and fill levels of gas and wall neighbours are read and unused)
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(128) k_exchange(Params p) {
       jy += fo[i] * (R)Lat<D>::cy(i);
       jz += fo[i] * (R)Lat<D>::cz(i);
       if (i > 0) {
-        const int tn = ftype(fn[i]);
+        const int tn = post_type(fn[i]);
         if (tn == T_LIQ || tn == T_IFC)
           dM += tn == T_LIQ ? fin[i] - fo[i] : (R)0.5 * (phn + phm[i]) * (fin[i] - fo[i]);
       }
@@ -374,14 +376,19 @@ __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long
 }
 
 // the liquid cells of the lattice, one thread per cell along x rows; every
-// warp takes the liquid path (interface cells are k_stream_interface's)
+// warp takes the liquid path (interface cells are k_stream_interface's).
+// A mark of the last step's conversion (its parity bit differs from PAR)
+// stands for the type it gives, so that this sweep may start while that
+// conversion still writes the new types; a mark of this step's interface
+// sweep leaves the type as it is
 template <int D, class S, int PAR, bool TRT>
 __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_stream_liquid(Params p) {
   Cell c;
   const bool inr = grid_cell(p, c);
   const long long n = c.n;
   const uint8_t fl = inr ? p.flags[n] : (uint8_t)T_GAS;
-  const bool active = inr && ftype(fl) == T_LIQ;
+  const bool last_mark = fmark(fl) && ((fl & MARKPAR) != 0) != (PAR != 0);
+  const bool active = inr && (last_mark ? post_type(fl) : ftype(fl)) == T_LIQ;
   const bool wallwarp = __any_sync(0xffffffffu, active && (fl & NEARWALL));
   if (active) liquid_cell<D, S, PAR, TRT>(p, c, n, fl, wallwarp);
   if (p.pf.q != 0.f) {
@@ -481,7 +488,7 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
     mk = MK_FILL;
   else if (Mn < -PV(R, eps) * rho)
     mk = MK_EMPTY;
-  if (mk) p.flags[n] = (uint8_t)(fl | (mk << 2));
+  if (mk) p.flags[n] = (uint8_t)(fl | mark_bits(mk, PAR));
 
   // dissolved gas (Sec. 3.1-3.2)
   R cgas = 0, fl_gas = 0;
@@ -524,7 +531,6 @@ __global__ void __launch_bounds__(128, 4) k_stream_interface(Params p) {
   const int cnt = *p.segcount;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *p.ncount = 0;
-    *p.inext_count = 0;
     *p.segnext_count = 0;
     if (p.pf.q != 0.f) atomicAdd(p.fluid_updates, (unsigned long long)*p.icount);
   }
