@@ -200,19 +200,21 @@ template <class R> __device__ __forceinline__ R model_om(const Params &p, R A) {
 template <int D, class R>
 __device__ __forceinline__ R local_om(const Params &p, const R *fi, R rho, R irho, R ux, R uy, R uz) {
   if (p.rheo == 0) return PV(R, om);
+  // opposite directions (i, i + 1) have the same e e: one sum per pair
   R mxx = 0, myy = 0, mzz = 0, mxy = 0, mxz = 0, myz = 0;
 #pragma unroll
-  for (int i = 1; i < Lat<D>::Q; ++i) {
+  for (int i = 1; i < Lat<D>::Q; i += 2) {
+    const R s = fi[i] + fi[i + 1];
     const int ex = Lat<D>::cx(i), ey = Lat<D>::cy(i), ez = Lat<D>::cz(i);
-    if (ex) mxx += fi[i];
-    if (ey) myy += fi[i];
-    if (ez) mzz += fi[i];
-    if (ex * ey > 0) mxy += fi[i];
-    if (ex * ey < 0) mxy -= fi[i];
-    if (ex * ez > 0) mxz += fi[i];
-    if (ex * ez < 0) mxz -= fi[i];
-    if (ey * ez > 0) myz += fi[i];
-    if (ey * ez < 0) myz -= fi[i];
+    if (ex) mxx += s;
+    if (ey) myy += s;
+    if (ez) mzz += s;
+    if (ex * ey > 0) mxy += s;
+    if (ex * ey < 0) mxy -= s;
+    if (ex * ez > 0) mxz += s;
+    if (ex * ez < 0) mxz -= s;
+    if (ey * ez > 0) myz += s;
+    if (ey * ez < 0) myz -= s;
   }
   const R third = rho / (R)3;
   const R pxx = mxx - rho * ux * ux - third, pyy = myy - rho * uy * uy - third;
@@ -351,13 +353,15 @@ __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long
       }
     }
   }
-  R rho = 0, jx = 0, jy = 0, jz = 0;
+  // density and momentum from the sums and differences of opposite pairs
+  R rho = fi[0], jx = 0, jy = 0, jz = 0;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    rho += fi[i];
-    if (Lat<D>::cx(i)) jx += Lat<D>::cx(i) > 0 ? fi[i] : -fi[i];
-    if (Lat<D>::cy(i)) jy += Lat<D>::cy(i) > 0 ? fi[i] : -fi[i];
-    if (Lat<D>::cz(i)) jz += Lat<D>::cz(i) > 0 ? fi[i] : -fi[i];
+  for (int i = 1; i < Q; i += 2) {
+    rho += fi[i] + fi[i + 1];
+    const R d = fi[i] - fi[i + 1];
+    if (Lat<D>::cx(i)) jx += Lat<D>::cx(i) > 0 ? d : -d;
+    if (Lat<D>::cy(i)) jy += Lat<D>::cy(i) > 0 ? d : -d;
+    if (Lat<D>::cz(i)) jz += Lat<D>::cz(i) > 0 ? d : -d;
   }
   const R irho = (R)1 / rho;
   const R ux = (jx + (R)0.5 * rho * PV(R, ax)) * irho;
