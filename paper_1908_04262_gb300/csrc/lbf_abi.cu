@@ -68,7 +68,7 @@ struct lbf_sim {
   size_t nseg = 0;  // 32-cell segments along x: ceil(nx / 32) per row
   int list_blocks = 0, warp_blocks = 0;
   void *M = nullptr, *phi = nullptr, *uI = nullptr, *kappa = nullptr, *Pi = nullptr, *nrm = nullptr,
-       *dst = nullptr, *ex = nullptr;
+       *dst = nullptr, *ex = nullptr, *mom = nullptr;
   int *label[2] = {nullptr, nullptr}, *parent = nullptr, *roots = nullptr, *nroots = nullptr;
   int *lsize = nullptr;
   uint8_t *tstat = nullptr;
@@ -170,7 +170,7 @@ Params make_params(lbf_sim *s, long long step) {
   p.list_blocks = s->list_blocks;
   p.warp_blocks = s->warp_blocks;
   p.M = s->M; p.phi = s->phi; p.uI = s->uI; p.kappa = s->kappa; p.Pi = s->Pi; p.nrm = s->nrm;
-  p.dst = s->dst; p.ex = s->ex;
+  p.dst = s->dst; p.ex = s->ex; p.mom = s->mom;
   p.label_old = s->label[par];
   p.label_new = s->label[1 - par];
   p.parent = s->parent;
@@ -895,6 +895,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   AL(dev_alloc(s, &s->nrm, 3 * N * s->rsz));
   AL(dev_alloc(s, &s->dst, N * s->rsz));
   AL(dev_alloc(s, &s->ex, N * s->rsz));
+  AL(dev_alloc(s, &s->mom, 5 * N * s->rsz));
   AL(dalloc(s, &s->label[0], N));
   AL(dalloc(s, &s->label[1], N));
   AL(dalloc(s, &s->parent, N));
@@ -958,6 +959,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   e = e ? e : zero(s->Pi, N * s->rsz);
   e = e ? e : zero(s->uI, 3 * N * s->rsz);
   e = e ? e : zero(s->ex, N * s->rsz);
+  e = e ? e : zero(s->mom, 5 * N * s->rsz);
   e = e ? e : cudaMemsetAsync(s->label[0], 0xff, sizeof(int) * N, s->st);
   e = e ? e : cudaMemsetAsync(s->label[1], 0xff, sizeof(int) * N, s->st);
   e = e ? e : cudaMemsetAsync(s->hash, 0xff, sizeof(unsigned long long) * hs, s->st);

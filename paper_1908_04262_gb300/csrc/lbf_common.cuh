@@ -129,6 +129,10 @@ struct Params {
   void *M, *phi;         // liquid mass, fill level (arithmetic type)
   void *uI;              // 3N: velocity of interface cells from the last step
   void *kappa, *Pi, *nrm, *dst, *ex;
+  // 5 planes: density, velocity (3) and dissolved gas of each interface
+  // cell after its sweep (the moments of its post-collision populations), which a
+  // gas cell turning interface averages over its neighbours
+  void *mom;
   int *label_old, *label_new, *parent;
   int *lsize;            // size of each tile-local gas component, at its root
   uint8_t *tstat;        // per union-find tile: 0 no gas, 1 one gas component, 2 several

@@ -316,20 +316,28 @@ __global__ void __launch_bounds__(128) k_conv_compute(Params p, int par) {
               atomicAdd(p.led + 5, cg);
           }
         } else if (mk == MK_GI) {
+          // the mean density, velocity and dissolved gas of the interface
+          // neighbours that do not empty, as their sweeps left them
           R rs = 0, us[3] = {0, 0, 0}, cs = 0;
           int cnt = 0;
+          const R *mo = (const R *)p.mom;
+          uint8_t fn[Lat<D>::Q];
+          int mn[Lat<D>::Q];
 #pragma unroll
           for (int i = 1; i < Lat<D>::Q; ++i) {
-            const long long m = nb<D>(p, c, i);
-            const uint8_t fm = p.flags[m];
+            mn[i] = nb<D>(p, c, i);
+            fn[i] = p.flags[mn[i]];
+          }
+#pragma unroll
+          for (int i = 1; i < Lat<D>::Q; ++i) {
+            const uint8_t fm = fn[i];
             if (ftype(fm) == T_IFC && (fmark(fm) == MK_NONE || fmark(fm) == MK_FILL)) {
-              const Cell cm = make_cell(p, m);
-              R u[3];
-              rs += sum_out_f<D, S>(p, cm, m, par, u);
-              us[0] += u[0];
-              us[1] += u[1];
-              us[2] += u[2];
-              cs += sum_out_g<D, S>(p, cm, m, par);
+              const int m = mn[i];
+              rs += mo[m];
+              us[0] += mo[p.N + m];
+              us[1] += mo[2 * p.N + m];
+              us[2] += mo[3 * p.N + m];
+              cs += mo[4 * p.N + m];
               ++cnt;
             }
           }

@@ -508,10 +508,23 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
     cgas += gi[i];
   }
   const R omg = PV(R, omg);
+  R cout = 0;
 #pragma unroll
   for (int i = 0; i < QA; ++i) {
     const R v = gi[i] + (geq<R, D>(i, cgas, ux, uy, uz) - gi[i]) * omg + (R)Lat<D>::wa(i) * PV(R, q);
+    cout += v;
     st(plane(g, p, dir_out<D>(i, 1 - PAR)), cell_out<D>(p, c, i, 1 - PAR), v, gshift<S, D>(p, i));
+  }
+  // the moments of the post-collision populations (the collision keeps the
+  // density; the Guo-shifted velocity is that of the outgoing populations):
+  // a gas neighbour turning interface averages them
+  {
+    R *mo = (R *)p.mom;
+    mo[n] = rho;
+    mo[p.N + n] = ux;
+    mo[2 * p.N + n] = uy;
+    mo[3 * p.N + n] = uz;
+    mo[4 * p.N + n] = cout;
   }
   // Sec. 3.1 Eq. gascurrent at the gas links: what the cell sends into the
   // gas minus what the Henry condition returns (only diffusive exchange
