@@ -89,6 +89,7 @@ struct lbf_sim {
   int *forest_stale = nullptr;
   int *lab_fast = nullptr;
   int *lab_full = nullptr;
+  int *rmv = nullptr;
   int tile_blocks = 0;
   uint8_t *tdirty = nullptr;
   size_t ntiles_alloc = 0;
@@ -188,6 +189,7 @@ Params make_params(lbf_sim *s, long long step) {
   p.forest_stale = s->forest_stale;
   p.lab_fast = s->lab_fast;
   p.lab_full = s->lab_full;
+  p.rmv = s->rmv;
   p.tile_blocks = s->tile_blocks;
   p.tdirty = s->tdirty;
   p.rlabel = s->rlabel;
@@ -945,6 +947,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   AL(dalloc(s, &s->forest_stale, 1));
   AL(dalloc(s, &s->lab_fast, 1));
   AL(dalloc(s, &s->lab_full, 1));
+  AL(dalloc(s, &s->rmv, 2));
   AL(dalloc(s, &s->wmask, N));
   AL(dalloc(s, &s->rlabel, N));
   AL(dalloc(s, &s->acc, 4));
@@ -985,6 +988,8 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   e = e ? e : zero(s->forest_stale, sizeof(int));
   e = e ? e : zero(s->lab_fast, sizeof(int));
   e = e ? e : cudaMemsetAsync(s->lab_full, 0xff, sizeof(int), s->st);
+  e = e ? e : cudaMemsetAsync(s->rmv, 0xff, sizeof(int), s->st);
+  e = e ? e : cudaMemsetAsync(s->rmv + 1, 0, sizeof(int), s->st);
   e = e ? e : zero(s->tdirty, s->ntiles_alloc);
   if (e != cudaSuccess) {
     lbf_destroy(s);

@@ -175,6 +175,10 @@ struct Params {
   // state was set from outside): the next patched labelling then starts
   // from a full copy instead of copying the listed cells
   int *lab_full;
+  // root moves of a patched step: [0] the bubble whose root cell turns
+  // interface (-1 none; one bubble per step), [1] set when some bubble's
+  // root is lowered by an added gas cell
+  int *rmv;
   int tile_blocks;  // grid of the tile loops of the union-find (two blocks per SM)
   // label of each current root cell (rank among the sorted roots, -1 past
   // the bubble capacity); read only at cells that are roots

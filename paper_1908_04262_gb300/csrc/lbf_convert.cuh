@@ -174,10 +174,12 @@ __device__ __forceinline__ long long list_cell(const Params &p, int k, int nm) {
 
 // An added gas cell (an emptied interface cell) keeps the bubble structure
 // of the last labelling when it carries a bubble label L (the smallest of
-// its gas neighbours' as an interface cell), lies above that bubble's root
-// (the bubble's smallest cell index stays), every gas neighbour after the
+// its gas neighbours' as an interface cell), every gas neighbour after the
 // conversion carries L (it joins no other bubble) and one of them is a gas
-// cell of the last step that stays gas (it is joined to its bubble).
+// cell of the last step that stays gas (it is joined to its bubble).  Below
+// the bubble's root it becomes the new root (the patch takes the minimum);
+// the labels, ranks of the roots, stay as they are while it lies above the
+// root of bubble L - 1.
 template <int D>
 __device__ __forceinline__ bool addition_keeps_bubble(const Params &p, const Cell &c, int n) {
   const int L = p.label_old[n];
@@ -190,7 +192,8 @@ __device__ __forceinline__ bool addition_keeps_bubble(const Params &p, const Cel
     fn[i] = p.flags[m];
     ln[i] = p.label_old[m];
   }
-  if (L < 0 || n <= p.told.root[L]) return false;
+  if (L < 0 || (n < p.told.root[L] && L > 0 && n < p.told.root[L - 1])) return false;
+  if (n < p.told.root[L]) p.rmv[1] = 1;
   bool anchored = false;
 #pragma unroll
   for (int i = 1; i < Lat<D>::Q; ++i) {
@@ -202,8 +205,8 @@ __device__ __forceinline__ bool addition_keeps_bubble(const Params &p, const Cel
 }
 
 // A gas cell turning interface (a filling neighbour claimed it) keeps the
-// bubble structure of the last labelling when it is not its bubble's root,
-// not in the top layer (the headspace flag), its gas neighbours after the
+// bubble structure of the last labelling when it is not in the top layer
+// (the headspace flag), its gas neighbours after the
 // conversion stay connected to one another inside its own 3^d neighbourhood
 // (over D2Q9 / D3Q19 links between neighbourhood cells), and it shares a
 // gas neighbour with every linked cell that turns interface with it.  Then
@@ -218,7 +221,12 @@ template <int D>
 __device__ __forceinline__ bool removal_keeps_bubble(const Params &p, const Cell &c, int n) {
   constexpr int NS = D == 3 ? 27 : 9, CTR = D == 3 ? 13 : 4;
   const int L = p.label_old[n];
-  if (L < 0 || n == p.told.root[L]) return false;
+  if (L < 0) return false;
+  if (n == p.told.root[L]) {
+    // the root moves up: k_root_scan finds the new one (one bubble per step)
+    const int prev = atomicCAS(p.rmv, -1, L);
+    if (prev != -1 && prev != L) return false;
+  }
   if (p.atmosphere && (D == 2 ? c.y : c.z) == p.top_layer) return false;
   unsigned gas = 0, link = 0, gone = 0;  // bit k: stencil cell k is gas after the conversion /
                                          // a gas neighbour of the centre / linked and turning interface
@@ -255,6 +263,49 @@ __device__ __forceinline__ bool removal_keeps_bubble(const Params &p, const Cell
     }
   }
   return (link & ~reach) == 0;
+}
+
+// After the labelling check, when a bubble's root cell turns interface: its
+// new root is the smallest cell after the old one that is gas after the
+// conversion and carries the bubble's label (a gas cell that stays, or an
+// emptied interface cell of the bubble).  One block scans forward 8 cells
+// per thread at a time, at most four times; the labels (ranks of the roots)
+// stay valid when the new root lies below the next bubble's and no root was
+// lowered in the same step, otherwise (or when the scan gives up) the step
+// takes the full labelling.
+static __global__ void __launch_bounds__(1024) k_root_scan(Params p) {
+  __shared__ int L, found;
+  if (threadIdx.x == 0) {
+    L = p.rmv[0];
+    found = 0x7fffffff;
+  }
+  __syncthreads();
+  if (L < 0) {
+    if (threadIdx.x == 0) p.rmv[1] = 0;
+    return;
+  }
+  const long long r0 = (long long)p.told.root[L] + 1;
+  for (int it = 0; it < 4; ++it) {
+    const long long base = r0 + (long long)it * (8 * 1024) + 8 * (long long)threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const long long n = base + j;
+      if (n < p.N && post_type(p.flags[n]) == T_GAS && p.label_old[n] == L) atomicMin(&found, (int)n);
+    }
+    __syncthreads();
+    const bool done = found != 0x7fffffff;
+    __syncthreads();
+    if (done) break;
+  }
+  if (threadIdx.x == 0) {
+    const int nb = *p.told.count;
+    if (found == 0x7fffffff || p.rmv[1] || (L + 1 < nb && found > p.told.root[L + 1]))
+      atomicOr(p.lab_slow, 1);
+    else
+      p.tnew.root[L] = found;
+    p.rmv[0] = -1;
+    p.rmv[1] = 0;
+  }
 }
 
 // after the marking (every mark final): the emptied cells are on the marked

@@ -725,6 +725,10 @@ static __global__ void k_label_choose(Params p) {
 // own cells; a full labelling overwrites every label.
 static __global__ void k_label_sync(Params p) {
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+  // the roots of the next table start from the last ones (a patched step
+  // lowers a bubble's root to the gas cells it adds below it)
+  const int nbub = *p.told.count;
+  for (long long k = tid; k < nbub; k += nt) p.tnew.root[k] = p.told.root[k];
   if (*p.lab_full) {
     const long long n4 = p.N >> 2;
     const int4 *src = reinterpret_cast<const int4 *>(p.label_old);
@@ -780,6 +784,7 @@ __global__ void __launch_bounds__(128) k_label_fast(Params p) {
         p.label_new[n] = -1;
       } else if (t == T_GAS) {
         kg = p.label_old[n];
+        if (kg >= 0) atomicMin(p.tnew.root + kg, n);
         if (p.atmosphere && kg >= 0) {
           const Cell c = make_cell(p, n);
           if ((D == 2 ? c.y : c.z) == p.top_layer) p.tnew.atm[kg] = 1;
@@ -842,7 +847,6 @@ static __global__ void k_bubble_update_fast(Params p) {
     p.tnew.m[k] = m;
     p.tnew.p[k] = pr;
     p.tnew.dm[k] = 0.0;
-    p.tnew.root[k] = p.told.root[k];
     p.tnew.id[k] = p.told.id[k];
   }
   if (tid == 0) {

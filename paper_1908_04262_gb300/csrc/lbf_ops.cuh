@@ -113,7 +113,10 @@ struct OpsImpl final : Ops {
     k_relabel<D, R><<<g, row_block(p), 0, s>>>(p);
   }
   void bubble_update(const Params &p, cudaStream_t s) override { k_bubble_update<<<1, 1024, 0, s>>>(p); }
-  void label_check(const Params &p, cudaStream_t s) override { k_label_check<D><<<p.list_blocks, 128, 0, s>>>(p); }
+  void label_check(const Params &p, cudaStream_t s) override {
+    k_label_check<D><<<p.list_blocks, 128, 0, s>>>(p);
+    k_root_scan<<<1, 1024, 0, s>>>(p);
+  }
   void label_choose(const Params &p, cudaStream_t s) override { k_label_choose<<<1, 1, 0, s>>>(p); }
   void label_sync(const Params &p, cudaStream_t s) override { k_label_sync<<<p.list_blocks, 128, 0, s>>>(p); }
   void label_fast(const Params &p, cudaStream_t s) override {
