@@ -89,6 +89,7 @@ struct lbf_sim {
   int *forest_stale = nullptr;
   int *lab_fast = nullptr;
   int *lab_full = nullptr;
+  bool walled = false;  // walls close every face and no fluid cell lies in a face layer
   int *rmv = nullptr;
   int tile_blocks = 0;
   uint8_t *tdirty = nullptr;
@@ -152,6 +153,7 @@ Params make_params(lbf_sim *s, long long step) {
   p.f = s->f; p.g = s->g;
   p.flags = s->flags;
   p.par = par;
+  p.walled = s->walled ? 1 : 0;
   p.wmask = s->wmask;
   p.ilist = s->ilist[par];
   p.icount = s->icount[par];
@@ -798,6 +800,34 @@ void lbf_destroy(lbf_sim *s) {
   delete s;
 }
 
+static void drop_graphs(lbf_sim *s);
+
+// walls on every face of the lattice (cfg.walls)
+bool all_faces_walled(const lbf_sim *s) {
+  const int need = s->dim == 3 ? 0x3F : 0xF;
+  return (s->cfg.walls & need) == need;
+}
+
+// a liquid or interface cell in a face layer of the host type array
+bool fluid_in_faces(const lbf_sim *s, const uint8_t *type) {
+  const long long nx = s->cfg.nx, ny = s->cfg.ny, nz = s->dim == 3 ? s->cfg.nz : 1;
+  auto fluid = [&](long long x, long long y, long long z) {
+    const int t = type[x + nx * (y + ny * z)] & 3;
+    return t == 1 || t == 2;
+  };
+  for (long long z = 0; z < nz; ++z)
+    for (long long y = 0; y < ny; ++y) {
+      const bool face_row = y == 0 || y == ny - 1 || (s->dim == 3 && (z == 0 || z == nz - 1));
+      if (face_row) {
+        for (long long x = 0; x < nx; ++x)
+          if (fluid(x, y, z)) return true;
+      } else if (fluid(0, y, z) || fluid(nx - 1, y, z)) {
+        return true;
+      }
+    }
+  return false;
+}
+
 int lbf_create(const lbf_config *cfg, lbf_sim **out) {
   if (!out) return fail(LBF_EINVAL, "out is NULL");
   *out = nullptr;
@@ -1002,6 +1032,7 @@ int lbf_create(const lbf_config *cfg, lbf_sim **out) {
     return fail(rc, msg);
   }
   Params p = make_params(s, 0);
+  s->walled = all_faces_walled(s);  // the fill makes every face layer a wall
   s->ops->init_fill(p, 0, cfg->fill_height, s->st);
   s->ops->nearwall(p, s->st);
   rc = separate_and_relabel(s);
@@ -1067,6 +1098,13 @@ int lbf_set_cells(lbf_sim *s, const uint8_t *type, const double *rho, const doub
     if (bad & 2) return fail(LBF_ENONFINITE, "non-finite value in the cell arrays");
     if (bad & 1) return fail(LBF_EINVAL, "cell type outside 0..3");
     return fail(LBF_EINVAL, "density not positive in a liquid or interface cell");
+  }
+  // the walled sweep needs fluid-free face layers; the step graphs change
+  // shape when that changes
+  const bool walled = all_faces_walled(s) && !fluid_in_faces(s, type);
+  if (walled != s->walled) {
+    s->walled = walled;
+    drop_graphs(s);
   }
   const int par = (int)(s->step & 1);
   Params p = make_params(s, s->step);
@@ -1182,8 +1220,9 @@ struct CkptHeader {
   long long step, n_arrays, n_queue;
   int mlp_attached, dim;
   unsigned long long mlp_hash;  // FNV-1a of the attached network's parameters, 0 if none
+  int walled, pad;              // the saved state's face layers hold no fluid
 };
-constexpr unsigned long long kCkptMagic = 0x3254504b4346424cull;  // "LBFCKPT2"
+constexpr unsigned long long kCkptMagic = 0x3354504b4346424cull;  // "LBFCKPT3"
 
 size_t ckpt_bytes(const lbf_sim *s) {
   size_t b = sizeof(CkptHeader) + s->n_state_allocs * sizeof(unsigned long long) + s->queue.size() * sizeof(Nucleus);
@@ -1212,6 +1251,7 @@ int lbf_checkpoint_save(lbf_sim *s, void *dst, size_t bytes) {
   h.mlp_attached = s->mlp_theta != nullptr;
   h.dim = s->dim;
   h.mlp_hash = s->mlp_theta ? s->mlp_hash : 0;
+  h.walled = s->walled ? 1 : 0;
   std::memcpy(o, &h, sizeof h);
   o += sizeof h;
   for (size_t k = 0; k < s->n_state_allocs; ++k) {
@@ -1269,6 +1309,7 @@ int lbf_checkpoint_load(lbf_sim *s, const void *src, size_t bytes) {
   }
   CK(cudaStreamSynchronize(s->st));
   s->step = h.step;
+  s->walled = h.walled != 0 && all_faces_walled(s);
   s->queue.swap(q);
   drop_graphs(s);
   return 0;

@@ -207,6 +207,9 @@ struct Params {
   double om;   // 1 / tau (the Newtonian relaxation rate)
   int walls, atmosphere, top_layer, ray_steps;
   int par;  // parity of the step (of the populations when it starts)
+  // 1 when walls close every face and no fluid cell lies in a face layer:
+  // no fluid cell then needs a periodic wrap of its neighbours
+  int walled;
 };
 
 // a physics parameter in the arithmetic type R

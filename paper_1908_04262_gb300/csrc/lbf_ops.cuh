@@ -69,6 +69,9 @@ struct OpsImpl final : Ops {
     const int b = row_block(p);
     if (p.trt)
       par ? k_stream_liquid<D, S, 1, true><<<g, b, 0, s>>>(p) : k_stream_liquid<D, S, 0, true><<<g, b, 0, s>>>(p);
+    else if (p.walled)
+      par ? k_stream_liquid<D, S, 1, false, true><<<g, b, 0, s>>>(p)
+          : k_stream_liquid<D, S, 0, false, true><<<g, b, 0, s>>>(p);
     else
       par ? k_stream_liquid<D, S, 1, false><<<g, b, 0, s>>>(p) : k_stream_liquid<D, S, 0, false><<<g, b, 0, s>>>(p);
   }

@@ -385,10 +385,30 @@ __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long
 // stands for the type it gives, so that this sweep may start while that
 // conversion still writes the new types; a mark of this step's interface
 // sweep leaves the type as it is
-template <int D, class S, int PAR, bool TRT>
+// WALLED: walls close every face and hold no fluid (Params::walled), so
+// the neighbour offsets are the same for every fluid cell (no periodic
+// wrap): they are built from the lattice sizes alone, uniform across the
+// warp, and the face cells that would need a wrap are walls, never swept.
+template <int D, class S, int PAR, bool TRT, bool WALLED = false>
 __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_stream_liquid(Params p) {
   Cell c;
-  const bool inr = grid_cell(p, c);
+  bool inr;
+  if constexpr (WALLED) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, nx = p.nx, nxy = p.nx * p.ny;
+    inr = x < nx;
+    c.x = inr ? x : nx - 1;
+    c.y = blockIdx.y;
+    c.z = blockIdx.z;
+    c.n = c.x + nx * c.y + nxy * c.z;
+    c.dxm = -1;
+    c.dxp = 1;
+    c.dym = -nx;
+    c.dyp = nx;
+    c.dzm = -nxy;
+    c.dzp = nxy;
+  } else {
+    inr = grid_cell(p, c);
+  }
   const long long n = c.n;
   const uint8_t fl = inr ? p.flags[n] : (uint8_t)T_GAS;
   const bool last_mark = fmark(fl) && ((fl & MARKPAR) != 0) != (PAR != 0);
