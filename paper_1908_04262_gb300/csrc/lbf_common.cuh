@@ -273,6 +273,29 @@ __device__ __forceinline__ bool seg_cell(const Params &p, int seg, int lane, Cel
   return x < p.nx;
 }
 
+// the same on a walled lattice (Params::walled): no fluid cell needs a
+// periodic wrap, so the neighbour offsets come from the lattice sizes alone
+// (uniform across the warp; face cells, all walls, get unwrapped offsets
+// they never use)
+__device__ __forceinline__ bool seg_cell_walled(const Params &p, int seg, int lane, Cell &c) {
+  const int nxb = (p.nx + 31) >> 5;
+  const int row = seg / nxb;
+  const int x = (seg - row * nxb) * 32 + lane;
+  const int z = row / p.ny;
+  const int nx = p.nx, nxy = p.nx * p.ny;
+  c.x = x < nx ? x : nx - 1;
+  c.y = row - z * p.ny;
+  c.z = z;
+  c.n = c.x + nx * c.y + nxy * c.z;
+  c.dxm = -1;
+  c.dxp = 1;
+  c.dym = -nx;
+  c.dyp = nx;
+  c.dzm = -nxy;
+  c.dzp = nxy;
+  return x < nx;
+}
+
 // cell from a linear index (rare paths only: uses division)
 __device__ __forceinline__ Cell make_cell(const Params &p, long long n) {
   // lattices hold fewer than 2^31 cells: 32-bit division suffices

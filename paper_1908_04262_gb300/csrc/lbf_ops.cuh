@@ -52,10 +52,10 @@ struct OpsImpl final : Ops {
                                                         z0, bx, by, bz);
   }
   void exchange(const Params &p, int par, cudaStream_t s) override {
-    if (par)
-      k_exchange<D, S, 1><<<p.warp_blocks, 128, 0, s>>>(p);
+    if (p.walled)
+      par ? k_exchange<D, S, 1, true><<<p.warp_blocks, 128, 0, s>>>(p) : k_exchange<D, S, 0, true><<<p.warp_blocks, 128, 0, s>>>(p);
     else
-      k_exchange<D, S, 0><<<p.warp_blocks, 128, 0, s>>>(p);
+      par ? k_exchange<D, S, 1><<<p.warp_blocks, 128, 0, s>>>(p) : k_exchange<D, S, 0><<<p.warp_blocks, 128, 0, s>>>(p);
   }
   void build_ilist(const Params &p, cudaStream_t s) override {
     cudaMemsetAsync(p.icount, 0, sizeof(int), s);
@@ -79,6 +79,9 @@ struct OpsImpl final : Ops {
     const int g = p.list_blocks;
     if (p.trt)
       par ? k_stream_interface<D, S, 1, true><<<g, 128, 0, s>>>(p) : k_stream_interface<D, S, 0, true><<<g, 128, 0, s>>>(p);
+    else if (p.walled)
+      par ? k_stream_interface<D, S, 1, false, true><<<g, 128, 0, s>>>(p)
+          : k_stream_interface<D, S, 0, false, true><<<g, 128, 0, s>>>(p);
     else
       par ? k_stream_interface<D, S, 1, false><<<g, 128, 0, s>>>(p)
           : k_stream_interface<D, S, 0, false><<<g, 128, 0, s>>>(p);

@@ -114,7 +114,7 @@ template <class R> __device__ __forceinline__ R solve_tau(const Params &p, R A) 
 
 // one warp per segment of interface cells, one lane per cell (loads along x
 // coalesce like the lattice sweep's)
-template <int D, class S, int PAR>
+template <int D, class S, int PAR, bool WALLED = false>
 __global__ void __launch_bounds__(128) k_exchange(Params p) {
   using R = typename ST<S>::R;
   constexpr int Q = Lat<D>::Q;
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(128) k_exchange(Params p) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *p.mcount = 0;
   for (int k = warp; k < cnt; k += nwarps) {
     Cell c;
-    if (!seg_cell(p, p.seglist[k], lane, c)) continue;
+    if (!(WALLED ? seg_cell_walled(p, p.seglist[k], lane, c) : seg_cell(p, p.seglist[k], lane, c))) continue;
     const int n = c.n;
     // types through the last conversion's marks: the exchange may run while
     // that conversion still writes the new types
@@ -559,7 +559,7 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
 // and one lane per cell; cells that fill or empty are listed for the
 // conversion.  Block 0 also resets the counters of the lists that the
 // conversion fills.
-template <int D, class S, int PAR, bool TRT>
+template <int D, class S, int PAR, bool TRT, bool WALLED = false>
 __global__ void __launch_bounds__(128, 4) k_stream_interface(Params p) {
   __shared__ double wbuf[128];
   const int lane = threadIdx.x & 31;
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(128, 4) k_stream_interface(Params p) {
   for (int k = warp; k < cnt; k += nwarps) {
     const int seg = p.seglist[k];
     Cell c;
-    const bool inr = seg_cell(p, seg, lane, c);
+    const bool inr = WALLED ? seg_cell_walled(p, seg, lane, c) : seg_cell(p, seg, lane, c);
     const uint8_t fl = inr ? p.flags[c.n] : (uint8_t)T_GAS;
     double flux = 0.0;
     int lab = -1, mk = MK_NONE;
