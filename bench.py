@@ -33,9 +33,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS (D3Q19 FSLBM + D3Q7 ADE) and % HBM roofline; FP16+learned-κ vs FP32 plain"
 WORKLOAD = "3D D3Q19 FSLBM + D3Q7 ADE, 128^3, FP32 storage, 8 bubbles (R 4-6), power-law n=0.6, disjoining on"
-# exchange 1, sweep 2, conversion 4, labelling check and choice 2, union-find 4, relabel 1, label sync
-# and patch 2, bubble update 2, geometry 1, disjoining 1 (one of the two labelling branches returns at once)
-KERNELS_PER_STEP = 20
+# label sync 1, exchange 1, sweep 2, conversion 4, labelling check, root scan and choice 3, union-find 4,
+# relabel 1, label patch 1, bubble update 2, geometry 1, disjoining 1 (one of the two labelling branches
+# returns at once)
+KERNELS_PER_STEP = 21
 
 
 def parse():
@@ -121,9 +122,9 @@ def stop_clocks(proc, path):
 # k_stream_liquid<3,float> under this script's default run (dram__bytes_read.sum
 # + dram__bytes_write.sum), valid while the sweep's sources are the ones that
 # were profiled
-SWEEP_TRAFFIC_BYTES = 265.1e6
+SWEEP_TRAFFIC_BYTES = 264.2e6
 SWEEP_SOURCES = ("paper_1908_04262_gb300/csrc/lbf_stream.cuh", "paper_1908_04262_gb300/csrc/lbf_common.cuh")
-SWEEP_SOURCES_SHA256_16 = "6acdb871611d2eea"
+SWEEP_SOURCES_SHA256_16 = "8c26bc2bcc586118"
 
 
 def sweep_traffic():
