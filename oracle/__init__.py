@@ -63,7 +63,7 @@ class _Config(ctypes.Structure):
         ("atmosphere", ctypes.c_int), ("eps", ctypes.c_double),
         ("bubble_capacity", ctypes.c_int),
         ("collision", ctypes.c_int), ("trt_magic", ctypes.c_double),
-        ("kappa", ctypes.c_int),
+        ("kappa", ctypes.c_int), ("mrt_rates", ctypes.c_double * 4),
     ]
 
 
@@ -98,6 +98,7 @@ def _load():
         lib.or_plic_offset.argtypes = [ctypes.c_int, dp, ctypes.c_double]
         lib.or_lsq_kappa.restype = ctypes.c_double
         lib.or_lsq_kappa.argtypes = [ctypes.c_int, P, ctypes.c_int]
+        lib.or_mrt_basis.argtypes = [ctypes.c_int, P, P]
         _lib = lib
     return _lib
 
@@ -112,9 +113,21 @@ def make_config(d: dict) -> _Config:
         if name in ("accel", "wall_u"):
             v = d.get(name, (0.0, 0.0, 0.0))
             getattr(c, name)[:] = [float(x) for x in v]
+        elif name == "mrt_rates":
+            getattr(c, name)[:] = [float(x) for x in d.get(name, (0.0, 0.0, 0.0, 0.0))]
         elif name in d:
             setattr(c, name, d[name])
     return c
+
+
+def mrt_basis(dim: int):
+    """The MRT moment basis (rows over the oracle's velocity order) and the
+    group id of each row (``or_mrt_basis``)."""
+    q = 9 if dim == 2 else 19
+    M = np.zeros((q, q))
+    g = np.zeros(q, np.int32)
+    _load().or_mrt_basis(dim, _ptr(M), _ptr(g))
+    return M, g
 
 
 class OracleSim:

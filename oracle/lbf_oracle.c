@@ -53,6 +53,8 @@ struct or_sim {
   int next_id;
   double led[8];
   int err;
+  double mrtM[19][19], mrtMi[19][19]; /* MRT moment basis and its inverse     */
+  int mrtg[19];                       /* MRT group of each moment               */
 };
 
 /* ---------------------------------------------------------------------- */
@@ -92,6 +94,102 @@ static void setup_lattice(or_sim *s) {
     for (i = 0; i < 7; ++i) s->wa[i] = i == 0 ? 1.0 / 4.0 : 1.0 / 8.0;
   }
   for (i = 0; i < s->Q; ++i) s->opp[i] = i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+}
+
+/* ---------------------------------------------------------------------- */
+/* multiple relaxation times (the collision variant Sec. 2 names besides    */
+/* BGK): orthogonal polynomial moments of the velocity set, the basis of    */
+/* Lallemand and Luo (2000) for D2Q9 and of d'Humieres et al. (2002) for    */
+/* D3Q19.  The groups relax at s_e (energy), s_eps (energy square), s_q     */
+/* (energy flux), s_nu = 1/tau (stress), s_pi (fourth-order anisotropic)    */
+/* and s_m (third-order); density and momentum are conserved.               */
+
+enum { MG_CONS = 0, MG_E = 1, MG_EPS = 2, MG_Q = 3, MG_NU = 4, MG_PI = 5, MG_M = 6 };
+
+/* moment k of the basis at velocity (x, y, z); *g receives its group */
+static double mrt_moment(int dim, int k, int x, int y, int z, int *g) {
+  const double cx = x, cy = y, cz = z;
+  const double c2 = cx * cx + cy * cy + cz * cz;
+  if (dim == 2) {
+    switch (k) {
+      case 0: *g = MG_CONS; return 1.0;                                   /* rho  */
+      case 1: *g = MG_E; return 3.0 * c2 - 4.0;                           /* e    */
+      case 2: *g = MG_EPS; return (9.0 * c2 * c2 - 21.0 * c2 + 8.0) / 2.0; /* eps  */
+      case 3: *g = MG_CONS; return cx;                                    /* j_x  */
+      case 4: *g = MG_Q; return (3.0 * c2 - 5.0) * cx;                    /* q_x  */
+      case 5: *g = MG_CONS; return cy;                                    /* j_y  */
+      case 6: *g = MG_Q; return (3.0 * c2 - 5.0) * cy;                    /* q_y  */
+      case 7: *g = MG_NU; return cx * cx - cy * cy;                       /* p_xx */
+      default: *g = MG_NU; return cx * cy;                                /* p_xy */
+    }
+  }
+  switch (k) {
+    case 0: *g = MG_CONS; return 1.0;
+    case 1: *g = MG_E; return 19.0 * c2 - 30.0;
+    case 2: *g = MG_EPS; return (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0;
+    case 3: *g = MG_CONS; return cx;
+    case 4: *g = MG_Q; return (5.0 * c2 - 9.0) * cx;
+    case 5: *g = MG_CONS; return cy;
+    case 6: *g = MG_Q; return (5.0 * c2 - 9.0) * cy;
+    case 7: *g = MG_CONS; return cz;
+    case 8: *g = MG_Q; return (5.0 * c2 - 9.0) * cz;
+    case 9: *g = MG_NU; return 3.0 * cx * cx - c2;                        /* 3 p_xx  */
+    case 10: *g = MG_PI; return (3.0 * c2 - 5.0) * (3.0 * cx * cx - c2); /* 3 pi_xx */
+    case 11: *g = MG_NU; return cy * cy - cz * cz;                        /* p_ww    */
+    case 12: *g = MG_PI; return (3.0 * c2 - 5.0) * (cy * cy - cz * cz);   /* pi_ww   */
+    case 13: *g = MG_NU; return cx * cy;
+    case 14: *g = MG_NU; return cy * cz;
+    case 15: *g = MG_NU; return cx * cz;
+    case 16: *g = MG_M; return (cy * cy - cz * cz) * cx;
+    case 17: *g = MG_M; return (cz * cz - cx * cx) * cy;
+    default: *g = MG_M; return (cx * cx - cy * cy) * cz;
+  }
+}
+
+/* the basis matrix of the lattice and its inverse (Gauss-Jordan elimination
+ * with partial pivoting) */
+static void setup_mrt(or_sim *s) {
+  const int Q = s->Q;
+  double a[19][38];
+  int i, k, r, col;
+  for (k = 0; k < Q; ++k)
+    for (i = 0; i < Q; ++i) s->mrtM[k][i] = mrt_moment(s->dim, k, s->e[i][0], s->e[i][1], s->e[i][2], &s->mrtg[k]);
+  for (r = 0; r < Q; ++r)
+    for (col = 0; col < 2 * Q; ++col) a[r][col] = col < Q ? s->mrtM[r][col] : (col - Q == r ? 1.0 : 0.0);
+  for (col = 0; col < Q; ++col) {
+    int piv = col;
+    double t;
+    for (r = col + 1; r < Q; ++r)
+      if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+    for (k = 0; k < 2 * Q; ++k) {
+      t = a[col][k];
+      a[col][k] = a[piv][k];
+      a[piv][k] = t;
+    }
+    t = a[col][col];
+    for (k = 0; k < 2 * Q; ++k) a[col][k] /= t;
+    for (r = 0; r < Q; ++r) {
+      if (r == col || a[r][col] == 0.0) continue;
+      t = a[r][col];
+      for (k = 0; k < 2 * Q; ++k) a[r][k] -= t * a[col][k];
+    }
+  }
+  for (r = 0; r < Q; ++r)
+    for (col = 0; col < Q; ++col) s->mrtMi[r][col] = a[r][Q + col];
+}
+
+int or_mrt_basis(int dim, double *M, int32_t *grp) {
+  or_sim t;
+  int i, k;
+  memset(&t, 0, sizeof t);
+  t.dim = dim == 2 ? 2 : 3;
+  setup_lattice(&t);
+  setup_mrt(&t);
+  for (k = 0; k < t.Q; ++k) {
+    grp[k] = t.mrtg[k];
+    for (i = 0; i < t.Q; ++i) M[k * t.Q + i] = t.mrtM[k][i];
+  }
+  return t.Q;
 }
 
 static void coords(const or_sim *s, long n, long *x, long *y, long *z) {
@@ -301,6 +399,47 @@ static void stream_collide(or_sim *s) {
         const double S_even = 0.5 * (S[i] + S[k]), S_odd = 0.5 * (S[i] - S[k]);
         fcn[n * Q + i] = f[i] - (f_even - fe_even) / tau - (f_odd - fe_odd) / tau_m +
                          (1.0 - 0.5 / tau) * S_even + (1.0 - 0.5 / tau_m) * S_odd;
+      }
+    } else if (s->c.collision == 2) {
+      /* multiple relaxation times: m = M f, each moment relaxes towards the
+         moment of f_eq at its group's rate, the Guo source enters moment by
+         moment scaled by (1 - s_k/2); f = M^-1 m.  The stress moments take
+         1/tau (the local tau of the rheology), the energy flux 1/tau_m of
+         the TRT product trt_magic; density and momentum are conserved (their
+         rate cancels against the source term, 1 is used) */
+      const double tau_m = 0.5 + s->c.trt_magic / (tau - 0.5);
+      const double *rr = s->c.mrt_rates;
+      double rate[7], fe[19], S[19], ms[19];
+      int k;
+      rate[MG_CONS] = 1.0;
+      rate[MG_NU] = 1.0 / tau;
+      rate[MG_Q] = 1.0 / tau_m;
+      rate[MG_E] = rr[0] > 0.0 ? rr[0] : 1.0 / tau;
+      rate[MG_EPS] = rr[1] > 0.0 ? rr[1] : 1.0 / tau;
+      rate[MG_PI] = rr[2] > 0.0 ? rr[2] : 1.0 / tau;
+      rate[MG_M] = rr[3] > 0.0 ? rr[3] : 1.0 / tau_m;
+      for (i = 0; i < Q; ++i) {
+        fe[i] = feq(s, i, rho, u);
+        S[i] = 0.0;
+        for (d = 0; d < 3; ++d)
+          S[i] += ((s->e[i][d] - u[d]) / (1.0 / 3.0) + edot(s, i, u) * s->e[i][d] / (1.0 / 9.0)) *
+                  rho * a[d];
+        S[i] *= s->w[i];
+      }
+      for (k = 0; k < Q; ++k) {
+        double m = 0.0, me = 0.0, mS = 0.0;
+        const double r = rate[s->mrtg[k]];
+        for (i = 0; i < Q; ++i) {
+          m += s->mrtM[k][i] * f[i];
+          me += s->mrtM[k][i] * fe[i];
+          mS += s->mrtM[k][i] * S[i];
+        }
+        ms[k] = m - r * (m - me) + (1.0 - 0.5 * r) * mS;
+      }
+      for (i = 0; i < Q; ++i) {
+        double v = 0.0;
+        for (k = 0; k < Q; ++k) v += s->mrtMi[i][k] * ms[k];
+        fcn[n * Q + i] = v;
       }
     } else {
       /* BGK collision with Guo forcing (Sec. 2 Eq. collision) */
@@ -1178,6 +1317,7 @@ or_sim *or_create(const or_config *cfg) {
   s->dim = cfg->nz == 1 ? 2 : 3;
   s->N = (long)cfg->nx * cfg->ny * cfg->nz;
   setup_lattice(s);
+  setup_mrt(s);
   alloc_fields(s);
   for (n = 0; n < s->N; ++n) {
     long x, y, z;

@@ -7,7 +7,8 @@
  * source, header, table or helper with the CUDA path.
  *
  * Every routine follows the paper's equations in the paper's order:
- *   Sec. 2 (LBE, BGK, equilibrium, moments, bounce-back),
+ *   Sec. 2 (LBE, BGK and the TRT and MRT variants it names, equilibrium,
+ *           moments, bounce-back),
  *   Sec. 2.1 (VOF fill level, mass exchange, cell conversion),
  *   Sec. 2.2 (free-surface reconstruction, gas density, ideal-gas law),
  *   Sec. 2.3 (tau-nu relation, Carreau-Yasuda),
@@ -37,10 +38,14 @@ typedef struct {
   int atmosphere;            /* 1: gas touching the top interior layer is at p0 */
   double eps;                /* conversion margin on alpha                      */
   int bubble_capacity;
-  int collision;             /* 0 BGK, 1 two relaxation times (TRT)             */
-  double trt_magic;          /* TRT: (tau - 1/2)(tau_minus - 1/2)               */
+  int collision;             /* 0 BGK, 1 two relaxation times (TRT), 2 multiple
+                                relaxation times (MRT)                           */
+  double trt_magic;          /* TRT: (tau - 1/2)(tau_minus - 1/2); MRT: the same
+                                product fixes the energy-flux rate s_q           */
   int kappa;                 /* curvature in the step: 0 least squares, 1 height
                                 function (least squares where it is undefined)  */
+  double mrt_rates[4];       /* MRT: s_e, s_eps, s_pi, s_m; 0 takes 1/tau for the
+                                first three and s_q for s_m                      */
 } or_config;
 
 typedef struct or_sim or_sim;
@@ -94,6 +99,13 @@ double or_plic_offset(int dim, const double *n, double alpha);
 /* test hook: least-squares curvature of np (<= 27) points (x, y, z in the
  * local frame of a cell: tangents, then the normal into the liquid) */
 double or_lsq_kappa(int dim, const double *pts, int np);
+
+/* The moment basis of the MRT collision for the oracle's velocity order of
+ * a 2D (D2Q9) or 3D (D3Q19) lattice: M receives Q x Q doubles (row k is
+ * moment k evaluated at every velocity), grp Q group ids (0 conserved,
+ * 1 energy e, 2 energy square eps, 3 energy flux q, 4 stress p, 5 pi,
+ * 6 third-order m).  Returns Q. */
+int or_mrt_basis(int dim, double *M, int32_t *grp);
 
 #ifdef __cplusplus
 }

@@ -27,7 +27,7 @@ BASE = dict(
     D=0.05, kH=0.0, RT=1.0, c0=0.0, q=0.0, p0=1.0 / 3.0,
     fill_height=1e9, walls=0, wall_u=(0.0, 0.0, 0.0),
     atmosphere=1, eps=1e-3, bubble_capacity=4096,
-    collision=0, trt_magic=3.0 / 16.0, kappa=0,
+    collision=0, trt_magic=3.0 / 16.0, kappa=0, mrt_rates=(0.0, 0.0, 0.0, 0.0),
 )
 
 RHEO = {"newtonian": 0, "powerlaw": 1, "carreau": 2}
