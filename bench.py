@@ -122,9 +122,9 @@ def stop_clocks(proc, path):
 # k_stream_liquid<3,float> under this script's default run (dram__bytes_read.sum
 # + dram__bytes_write.sum), valid while the sweep's sources are the ones that
 # were profiled
-SWEEP_TRAFFIC_BYTES = 264.2e6
+SWEEP_TRAFFIC_BYTES = 264.1e6
 SWEEP_SOURCES = ("paper_1908_04262_gb300/csrc/lbf_stream.cuh", "paper_1908_04262_gb300/csrc/lbf_common.cuh")
-SWEEP_SOURCES_SHA256_16 = "8c26bc2bcc586118"
+SWEEP_SOURCES_SHA256_16 = "a6b86d84b81863eb"
 
 
 def sweep_traffic():
@@ -262,6 +262,20 @@ def forms_comparison(args, lbf, cfg, pts, rad, stream, fp32_line):
         out[name] = {"mlups": N * args.steps / (ms / 1e3) / 1e6, "ms_per_step": ms / args.steps,
                      "repeats_ms_per_step": [r / args.steps for r in reps],
                      "bubble_volume_rel_diff_vs_fp32_plain": V / fp32_line["bubble_volume"] - 1}
+        sim.close()
+    # the collision variants of Sec. 2 on the same workload (FP32, least
+    # squares): two relaxation times, and multiple relaxation times at the
+    # rates d'Humieres et al. suggest for D3Q19 (energy 1.19, energy square
+    # and fourth order 1.4, third order 1.98; the energy flux at the TRT rate)
+    out["collisions"] = {}
+    for name, coll, rates in (("fp32_trt", 1, (0.0, 0.0, 0.0, 0.0)), ("fp32_mrt", 2, (1.19, 1.4, 1.4, 1.98))):
+        sim = lbf.Sim(dict(cfg, collision=coll, trt_magic=3.0 / 16.0, mrt_rates=rates), stream=stream.cuda_stream)
+        sim.nucleate(pts, rad)
+        sim.step(args.warmup)
+        reps = timed_steps(sim, stream, args.steps)
+        ms = statistics.median(reps)
+        out["collisions"][name] = {"mlups": N * args.steps / (ms / 1e3) / 1e6, "ms_per_step": ms / args.steps,
+                                   "mrt_rates": list(rates) if coll == 2 else None}
         sim.close()
     out["laplace_rel_err_static_bubble_R5"] = {
         "fp32_plain": static_bubble_laplace(lbf, None, "fp32"),

@@ -73,12 +73,17 @@ typedef struct {
   int bubble_capacity;      /* maximum number of bubbles (<= 16384)             */
   void *stream;             /* cudaStream_t used by every call                  */
   int collision;            /* 0 BGK (Sec. 2 Eq. collision); 1 two relaxation
-                               times, the variant Sec. 2 names: the parts of
+                               times, a variant Sec. 2 names: the parts of
                                f - f_eq even under e -> -e relax at 1/tau, the
-                               odd parts at 1/tau_m (the dissolved gas stays
-                               BGK)                                             */
-  double trt_magic;         /* collision 1: (tau - 1/2)(tau_m - 1/2) > 0; 3/16
-                               puts half-way bounce-back walls exactly
+                               odd parts at 1/tau_m; 2 multiple relaxation
+                               times, the other variant Sec. 2 names: the
+                               moments of the orthogonal basis of Lallemand
+                               and Luo (D2Q9) or d'Humieres et al. (D3Q19)
+                               relax at their own rates, the stress at 1/tau,
+                               the energy flux at 1/tau_m, the rest at
+                               mrt_rates (the dissolved gas stays BGK)         */
+  double trt_magic;         /* collision 1 and 2: (tau - 1/2)(tau_m - 1/2) > 0;
+                               3/16 puts half-way bounce-back walls exactly
                                half-way for every tau                           */
   int kappa;                /* curvature of Eq. rhob: 0 least squares; 1 height
                                function, the second method Sec. 2.2 names
@@ -86,6 +91,12 @@ typedef struct {
                                normal's dominant axis, 3 columns in 2D, 3 x 3
                                in 3D, centred differences; the least-squares
                                value stays where a column meets a wall)        */
+  double mrt_rates[4];      /* collision 2: rates s_e (energy: bulk viscosity
+                               (2/d)(1/s_e - 1/2)/3), s_eps (energy square),
+                               s_pi (fourth-order anisotropic, 3D) and s_m
+                               (third-order, 3D), each in [0, 2); 0 takes 1/tau
+                               for the first three and 1/tau_m for s_m (all 0:
+                               the TRT collision)                               */
 } lbf_config;
 
 /* one row of the bubble table */
@@ -103,7 +114,8 @@ typedef struct {
  * at rest (f = f_eq(rho0, 0), g = g_eq(c0, 0)), walls, headspace; labels
  * bubbles and computes the geometry.  *out receives the handle.
  * Errors: LBF_EINVAL (sizes <= 0, more than 2^31-1 cells, bad enums, tau or
- * tau_min <= 1/2, capacity outside [1, 16384]), LBF_ENOMEM, LBF_ECUDA. */
+ * tau_min <= 1/2, capacity outside [1, 16384], trt_magic <= 0 with
+ * collision 1 or 2, an MRT rate outside [0, 2)), LBF_ENOMEM, LBF_ECUDA. */
 int lbf_create(const lbf_config *cfg, lbf_sim **out);
 
 /* Release every resource; NULL is ignored. */

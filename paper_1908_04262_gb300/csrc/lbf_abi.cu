@@ -209,7 +209,8 @@ Params make_params(lbf_sim *s, long long step) {
   const int n_up = up == 1 ? c.ny : c.nz;
   p.top_layer = n_up - 1 - ((c.walls >> (2 * up + 1)) & 1);
   p.ray_steps = (int)std::ceil(c.d_max) + 1;
-  p.trt = c.collision == 1;
+  p.coll = c.collision;
+  p.mrt_se = c.mrt_rates[0]; p.mrt_seps = c.mrt_rates[1]; p.mrt_spi = c.mrt_rates[2]; p.mrt_sm = c.mrt_rates[3];
   p.kappa_hf = c.kappa == 1;
   p.trt_magic = c.trt_magic;
   p.omg = 1.0 / p.taug;
@@ -218,7 +219,7 @@ Params make_params(lbf_sim *s, long long step) {
           (float)p.rlam, (float)p.ra, (float)p.tau0, (float)p.tau_inf, (float)p.tau_min, (float)p.tau_max,
           (float)p.sigma, (float)p.k_pi, (float)p.d_max, (float)p.taug, (float)p.kH, (float)p.RT, (float)p.c0,
           (float)p.q, (float)p.p0, (float)p.eps, (float)p.uwx, (float)p.uwy, (float)p.uwz, (float)c.trt_magic,
-          (float)p.omg, (float)p.om};
+          (float)p.omg, (float)p.om, (float)p.mrt_se, (float)p.mrt_seps, (float)p.mrt_spi, (float)p.mrt_sm};
   return p;
 }
 
@@ -698,8 +699,11 @@ int validate(const lbf_config *c) {
   if (!(c->tau > 0.5)) return fail(LBF_EINVAL, "tau must exceed 1/2");
   if (c->rheo != 0 && !(c->tau_min > 0.5 && c->tau_max > c->tau_min)) return fail(LBF_EINVAL, "need 1/2 < tau_min < tau_max");
   if (!(c->D > 0.0)) return fail(LBF_EINVAL, "D must be positive");
-  if (c->collision < 0 || c->collision > 1) return fail(LBF_EINVAL, "bad collision");
-  if (c->collision == 1 && !(c->trt_magic > 0.0)) return fail(LBF_EINVAL, "trt_magic must be positive");
+  if (c->collision < 0 || c->collision > 2) return fail(LBF_EINVAL, "bad collision");
+  if (c->collision >= 1 && !(c->trt_magic > 0.0)) return fail(LBF_EINVAL, "trt_magic must be positive");
+  if (c->collision == 2)
+    for (int k = 0; k < 4; ++k)
+      if (!(c->mrt_rates[k] >= 0.0 && c->mrt_rates[k] < 2.0)) return fail(LBF_EINVAL, "mrt_rates must be in [0, 2)");
   if (c->kappa < 0 || c->kappa > 1) return fail(LBF_EINVAL, "bad curvature method");
   if (!(c->RT > 0.0) || !(c->rho0 > 0.0)) return fail(LBF_EINVAL, "RT and rho0 must be positive");
   if (c->bubble_capacity < 1 || c->bubble_capacity > 16384) return fail(LBF_EINVAL, "bubble_capacity must be in [1, 16384]");

@@ -194,12 +194,17 @@ struct Params {
   struct PF {
     float tau, rho0, ax, ay, az, rn, rk, rlam, ra, tau0, tau_inf, tau_min, tau_max;
     float sigma, k_pi, d_max, taug, kH, RT, c0, q, p0, eps, uwx, uwy, uwz, trt_magic, omg, om;
+    float mrt_se, mrt_seps, mrt_spi, mrt_sm;
   } pf;
   double tau, rho0, ax, ay, az;
   int has_force, rheo;
-  int trt;            // two relaxation times (else BGK)
+  int coll;           // collision: 0 BGK, 1 two relaxation times, 2 multiple
   int kappa_hf;       // height-function curvature (else least squares)
   double trt_magic;   // (tau - 1/2)(tau_m - 1/2)
+  // multiple relaxation times: rates of the energy, energy-square,
+  // fourth-order anisotropic and third-order moments (0: the stress rate
+  // 1/tau for the first three, the energy-flux rate for the last)
+  double mrt_se, mrt_seps, mrt_spi, mrt_sm;
   double rn, rk, rlam, ra, tau0, tau_inf, tau_min, tau_max;
   double sigma, k_pi, d_max, taug, kH, RT, c0, q, p0, eps;
   double uwx, uwy, uwz;

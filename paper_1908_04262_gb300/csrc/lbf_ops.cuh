@@ -67,24 +67,28 @@ struct OpsImpl final : Ops {
   void stream_liquid(const Params &p, int par, cudaStream_t s) override {
     const dim3 g = row_grid(p);
     const int b = row_block(p);
-    if (p.trt)
-      par ? k_stream_liquid<D, S, 1, true><<<g, b, 0, s>>>(p) : k_stream_liquid<D, S, 0, true><<<g, b, 0, s>>>(p);
+    if (p.coll == 2)
+      par ? k_stream_liquid<D, S, 1, 2><<<g, b, 0, s>>>(p) : k_stream_liquid<D, S, 0, 2><<<g, b, 0, s>>>(p);
+    else if (p.coll == 1)
+      par ? k_stream_liquid<D, S, 1, 1><<<g, b, 0, s>>>(p) : k_stream_liquid<D, S, 0, 1><<<g, b, 0, s>>>(p);
     else if (p.walled)
-      par ? k_stream_liquid<D, S, 1, false, true><<<g, b, 0, s>>>(p)
-          : k_stream_liquid<D, S, 0, false, true><<<g, b, 0, s>>>(p);
+      par ? k_stream_liquid<D, S, 1, 0, true><<<g, b, 0, s>>>(p)
+          : k_stream_liquid<D, S, 0, 0, true><<<g, b, 0, s>>>(p);
     else
-      par ? k_stream_liquid<D, S, 1, false><<<g, b, 0, s>>>(p) : k_stream_liquid<D, S, 0, false><<<g, b, 0, s>>>(p);
+      par ? k_stream_liquid<D, S, 1, 0><<<g, b, 0, s>>>(p) : k_stream_liquid<D, S, 0, 0><<<g, b, 0, s>>>(p);
   }
   void stream_interface(const Params &p, int par, cudaStream_t s) override {
     const int g = p.list_blocks;
-    if (p.trt)
-      par ? k_stream_interface<D, S, 1, true><<<g, 128, 0, s>>>(p) : k_stream_interface<D, S, 0, true><<<g, 128, 0, s>>>(p);
+    if (p.coll == 2)
+      par ? k_stream_interface<D, S, 1, 2><<<g, 128, 0, s>>>(p) : k_stream_interface<D, S, 0, 2><<<g, 128, 0, s>>>(p);
+    else if (p.coll == 1)
+      par ? k_stream_interface<D, S, 1, 1><<<g, 128, 0, s>>>(p) : k_stream_interface<D, S, 0, 1><<<g, 128, 0, s>>>(p);
     else if (p.walled)
-      par ? k_stream_interface<D, S, 1, false, true><<<g, 128, 0, s>>>(p)
-          : k_stream_interface<D, S, 0, false, true><<<g, 128, 0, s>>>(p);
+      par ? k_stream_interface<D, S, 1, 0, true><<<g, 128, 0, s>>>(p)
+          : k_stream_interface<D, S, 0, 0, true><<<g, 128, 0, s>>>(p);
     else
-      par ? k_stream_interface<D, S, 1, false><<<g, 128, 0, s>>>(p)
-          : k_stream_interface<D, S, 0, false><<<g, 128, 0, s>>>(p);
+      par ? k_stream_interface<D, S, 1, 0><<<g, 128, 0, s>>>(p)
+          : k_stream_interface<D, S, 0, 0><<<g, 128, 0, s>>>(p);
   }
   void convert_mark(const Params &p, cudaStream_t s) override { k_conv_mark<D><<<p.list_blocks, 128, 0, s>>>(p); }
   void convert_excess(const Params &p, int par, cudaStream_t s) override {

@@ -225,16 +225,122 @@ __device__ __forceinline__ R local_om(const Params &p, const R *fi, R rho, R irh
   return model_om<R>(p, sqrt(nrm2) * ((R)2.1213203435596424 * irho));
 }
 
-// relaxation with Guo forcing of one cell (BGK, or with TRT two relaxation
-// times), written to the outgoing slots
-template <int D, class S, int PAR, bool TRT>
+// The multiple-relaxation-time collision (Sec. 2 names it beside BGK and
+// TRT) on the orthogonal moment basis of Lallemand and Luo (D2Q9) and
+// d'Humieres et al. (D3Q19).  It is computed as the TRT collision (every
+// even moment at the stress rate, every odd one at the energy-flux rate)
+// plus a correction on each basis vector b whose rate s_b differs from its
+// parity's TRT rate s_t:  f -= (s_b - s_t) (b.h / b.b) b  with
+// h = f - f_eq + F/2 (F the Guo source), since both the relaxation and the
+// source scaling (1 - s/2) act moment by moment.  The corrected vectors are
+// the energy e and energy square eps (even), and in 3D the fourth-order
+// anisotropic pi_xx, pi_ww (even) and the third-order m_x, m_y, m_z (odd).
+template <int D> struct MrtBasis {
+  static constexpr int NE = D == 3 ? 4 : 2;  // even vectors: e, eps[, pi_xx, pi_ww]
+  static constexpr int NO = D == 3 ? 3 : 0;  // odd vectors: [m_x, m_y, m_z]
+  // vector k (even ones first) at direction i
+  __host__ __device__ static constexpr int val(int k, int i) {
+    const int x = Lat<D>::cx(i), y = Lat<D>::cy(i), z = Lat<D>::cz(i);
+    const int c2 = x * x + y * y + z * z;
+    if (D == 2) return k == 0 ? 3 * c2 - 4 : (9 * c2 * c2 - 21 * c2 + 8) / 2;
+    switch (k) {
+      case 0: return 19 * c2 - 30;
+      case 1: return (21 * c2 * c2 - 53 * c2 + 24) / 2;
+      case 2: return (3 * c2 - 5) * (3 * x * x - c2);
+      case 3: return (3 * c2 - 5) * (y * y - z * z);
+      case 4: return (y * y - z * z) * x;
+      case 5: return (z * z - x * x) * y;
+      default: return (x * x - y * y) * z;
+    }
+  }
+  __host__ __device__ static constexpr int norm2(int k) {
+    int s = 0;
+    for (int i = 0; i < Lat<D>::Q; ++i) s += val(k, i) * val(k, i);
+    return s;
+  }
+};
+
+// relaxation with Guo forcing of one cell (COLL 0 BGK, 1 two relaxation
+// times, 2 multiple relaxation times), written to the outgoing slots
+template <int D, class S, int PAR, int COLL>
 __device__ __forceinline__ void relax_store(const Params &p, const Cell &c, long long n, S *f, const typename ST<S>::R *fi,
                                             typename ST<S>::R rho, typename ST<S>::R ux, typename ST<S>::R uy,
                                             typename ST<S>::R uz, typename ST<S>::R om) {
   using R = typename ST<S>::R;
   constexpr int Q = Lat<D>::Q;
   const R base = (R)1 - (ux * ux + uy * uy + uz * uz) * (R)1.5;
-  if constexpr (TRT) {
+  if constexpr (COLL == 2) {
+    using B = MrtBasis<D>;
+    constexpr int NP = (Q - 1) / 2;
+    const R tau = (R)1 / om;
+    const R om_m = (R)1 / ((R)0.5 + PV(R, trt_magic) / (tau - (R)0.5));
+    const R ax = p.has_force ? PV(R, ax) : (R)0, ay = p.has_force ? PV(R, ay) : (R)0,
+            az = p.has_force ? PV(R, az) : (R)0;
+    const R ua = ux * ax + uy * ay + uz * az;
+    const R ge = ((R)1 - (R)0.5 * om) * rho, go = ((R)1 - (R)0.5 * om_m) * rho;
+    // the TRT values (even part ev, odd part od of each pair) and h
+    const R fe0 = (R)Lat<D>::w(0) * rho * base;
+    const R F0 = (R)Lat<D>::w(0) * rho * (R)-3 * ua;
+    R v0 = fi[0] - (fi[0] - fe0) * om + ((R)1 - (R)0.5 * om) * F0;
+    const R h0 = fi[0] - fe0 + (R)0.5 * F0;
+    R ev[NP], od[NP], he[NP], ho[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const int i = 2 * j + 1, k = i + 1;
+      const R w = (R)Lat<D>::w(i);
+      const R eu = (R)Lat<D>::cx(i) * ux + (R)Lat<D>::cy(i) * uy + (R)Lat<D>::cz(i) * uz;
+      const R ea = (R)Lat<D>::cx(i) * ax + (R)Lat<D>::cy(i) * ay + (R)Lat<D>::cz(i) * az;
+      const R fe_even = w * rho * (base + (R)4.5 * eu * eu), fe_odd = w * rho * (R)3 * eu;
+      const R f_even = (R)0.5 * (fi[i] + fi[k]), f_odd = (R)0.5 * (fi[i] - fi[k]);
+      const R Fe = w * ((R)9 * eu * ea - (R)3 * ua), Fo = w * (R)3 * ea;  // per unit rho
+      ev[j] = f_even - (f_even - fe_even) * om + ge * Fe;
+      od[j] = f_odd - (f_odd - fe_odd) * om_m + go * Fo;
+      he[j] = f_even - fe_even + (R)0.5 * rho * Fe;
+      ho[j] = f_odd - fe_odd + (R)0.5 * rho * Fo;
+    }
+    // rates of the corrected vectors: 0 in the configuration follows the
+    // parity's TRT rate (no correction)
+    const R se = PV(R, mrt_se) > (R)0 ? PV(R, mrt_se) : om;
+    const R seps = PV(R, mrt_seps) > (R)0 ? PV(R, mrt_seps) : om;
+    const R spi = PV(R, mrt_spi) > (R)0 ? PV(R, mrt_spi) : om;
+    const R sm = PV(R, mrt_sm) > (R)0 ? PV(R, mrt_sm) : om_m;
+    R cf[B::NE + B::NO];
+#pragma unroll
+    for (int k = 0; k < B::NE + B::NO; ++k) {
+      const bool even = k < B::NE;
+      // b.h: the rest direction and both members of each pair (an even
+      // vector takes h_i + h_opp = 2 he, an odd one h_i - h_opp = 2 ho)
+      R d = even ? (R)B::val(k, 0) * h0 : (R)0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const int i = 2 * j + 1;
+        if (B::val(k, i) != 0) d += (R)(2 * B::val(k, i)) * (even ? he[j] : ho[j]);
+      }
+      const R s_b = k == 0 ? se : (k == 1 ? seps : (even ? spi : sm));
+      const R s_t = even ? om : om_m;
+      cf[k] = (s_b - s_t) * d * ((R)1 / (R)B::norm2(k));
+    }
+#pragma unroll
+    for (int k = 0; k < B::NE; ++k) v0 -= cf[k] * (R)B::val(k, 0);
+    st(plane(f, p, dir_out<D>(0, 1 - PAR)), cell_out<D>(p, c, 0, 1 - PAR), v0, fshift<S, D>(p, 0));
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const int i = 2 * j + 1, k = i + 1;
+      R e_ = ev[j], o_ = od[j];
+#pragma unroll
+      for (int b = 0; b < B::NE + B::NO; ++b) {
+        if (B::val(b, i) == 0) continue;
+        if (b < B::NE)
+          e_ -= cf[b] * (R)B::val(b, i);
+        else
+          o_ -= cf[b] * (R)B::val(b, i);
+      }
+      st(plane(f, p, dir_out<D>(i, 1 - PAR)), cell_out<D>(p, c, i, 1 - PAR), e_ + o_, fshift<S, D>(p, i));
+      st(plane(f, p, dir_out<D>(k, 1 - PAR)), cell_out<D>(p, c, k, 1 - PAR), e_ - o_, fshift<S, D>(p, k));
+    }
+    return;
+  }
+  if constexpr (COLL == 1) {
     // two relaxation times: per pair (i, opp(i) = i + 1) the even part of
     // f - f_eq relaxes at om, the odd part at om_m with
     // (tau - 1/2)(tau_m - 1/2) = trt_magic; the Guo source
@@ -305,7 +411,7 @@ __device__ __forceinline__ void relax_store(const Params &p, const Cell &c, long
 // a liquid cell: its lattice neighbours are liquid, interface or walls
 // (liquid never touches gas); walls bounce back by reading the cell's own
 // outgoing population from the wall cell's slot
-template <int D, class S, int PAR, bool TRT>
+template <int D, class S, int PAR, int COLL>
 __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long long n, uint8_t fl, bool wallwarp) {
   using R = typename ST<S>::R;
   constexpr int Q = Lat<D>::Q, QA = Lat<D>::QA;
@@ -367,7 +473,7 @@ __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long
   const R ux = (jx + (R)0.5 * rho * PV(R, ax)) * irho;
   const R uy = (jy + (R)0.5 * rho * PV(R, ay)) * irho;
   const R uz = (jz + (R)0.5 * rho * PV(R, az)) * irho;
-  relax_store<D, S, PAR, TRT>(p, c, n, f, fi, rho, ux, uy, uz, local_om<D, R>(p, fi, rho, irho, ux, uy, uz));
+  relax_store<D, S, PAR, COLL>(p, c, n, f, fi, rho, ux, uy, uz, local_om<D, R>(p, fi, rho, irho, ux, uy, uz));
   R cg = 0;
 #pragma unroll
   for (int i = 0; i < QA; ++i) cg += gi[i];
@@ -389,7 +495,7 @@ __device__ __forceinline__ void liquid_cell(const Params &p, const Cell &c, long
 // the neighbour offsets are the same for every fluid cell (no periodic
 // wrap): they are built from the lattice sizes alone, uniform across the
 // warp, and the face cells that would need a wrap are walls, never swept.
-template <int D, class S, int PAR, bool TRT, bool WALLED = false>
+template <int D, class S, int PAR, int COLL, bool WALLED = false>
 __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_stream_liquid(Params p) {
   Cell c;
   bool inr;
@@ -414,7 +520,7 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
   const bool last_mark = fmark(fl) && ((fl & MARKPAR) != 0) != (PAR != 0);
   const bool active = inr && (last_mark ? post_type(fl) : ftype(fl)) == T_LIQ;
   const bool wallwarp = __any_sync(0xffffffffu, active && (fl & NEARWALL));
-  if (active) liquid_cell<D, S, PAR, TRT>(p, c, n, fl, wallwarp);
+  if (active) liquid_cell<D, S, PAR, COLL>(p, c, n, fl, wallwarp);
   if (p.pf.q != 0.f) {
     const unsigned b = __ballot_sync(0xffffffffu, active);
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(p.fluid_updates, (unsigned long long)__popc(b));
@@ -425,7 +531,7 @@ __global__ void __launch_bounds__(128, SweepOcc<typename ST<S>::R>::blocks) k_st
 // neighbours, relaxation, fill level and marks, dissolved gas with Henry's
 // law at gas links; returns the cell's gas current and its bubble label, and
 // its conversion mark
-template <int D, class S, int PAR, bool TRT>
+template <int D, class S, int PAR, int COLL>
 __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, long long n, uint8_t fl, double &flux,
                                               int &lab) {
   using R = typename ST<S>::R;
@@ -501,7 +607,7 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
   const R ux = (jx + (R)0.5 * rho * PV(R, ax)) * irho;
   const R uy = (jy + (R)0.5 * rho * PV(R, ay)) * irho;
   const R uz = (jz + (R)0.5 * rho * PV(R, az)) * irho;
-  relax_store<D, S, PAR, TRT>(p, c, n, f, fi, rho, ux, uy, uz, local_om<D, R>(p, fi, rho, irho, ux, uy, uz));
+  relax_store<D, S, PAR, COLL>(p, c, n, f, fi, rho, ux, uy, uz, local_om<D, R>(p, fi, rho, irho, ux, uy, uz));
 
   R *phi = (R *)p.phi;
   const R Mn = ((const R *)p.M)[n];
@@ -559,7 +665,7 @@ __device__ __forceinline__ int interface_cell(const Params &p, const Cell &c, lo
 // and one lane per cell; cells that fill or empty are listed for the
 // conversion.  Block 0 also resets the counters of the lists that the
 // conversion fills.
-template <int D, class S, int PAR, bool TRT, bool WALLED = false>
+template <int D, class S, int PAR, int COLL, bool WALLED = false>
 __global__ void __launch_bounds__(128, 4) k_stream_interface(Params p) {
   __shared__ double wbuf[128];
   const int lane = threadIdx.x & 31;
@@ -578,7 +684,7 @@ __global__ void __launch_bounds__(128, 4) k_stream_interface(Params p) {
     const uint8_t fl = inr ? p.flags[c.n] : (uint8_t)T_GAS;
     double flux = 0.0;
     int lab = -1, mk = MK_NONE;
-    if (ftype(fl) == T_IFC) mk = interface_cell<D, S, PAR, TRT>(p, c, c.n, fl, flux, lab);
+    if (ftype(fl) == T_IFC) mk = interface_cell<D, S, PAR, COLL>(p, c, c.n, fl, flux, lab);
     if (lane == 0) p.segflag[seg] = 0;  // free for the conversion's next list
     list_append(p.mlist, p.mcount, mk != MK_NONE, c.n);
     if (__any_sync(0xffffffffu, lab >= 0)) agg_add(p.told.dm, lab, flux, wbuf + (threadIdx.x & ~31));

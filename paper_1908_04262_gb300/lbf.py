@@ -49,7 +49,7 @@ class Config(ctypes.Structure):
         ("bubble_capacity", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("collision", ctypes.c_int), ("trt_magic", ctypes.c_double),
-        ("kappa", ctypes.c_int),
+        ("kappa", ctypes.c_int), ("mrt_rates", ctypes.c_double * 4),
     ]
 
 
@@ -125,6 +125,8 @@ def make_config(d: dict, stream: int | None = None) -> Config:
     for name, _ in Config._fields_:
         if name in ("accel", "wall_u"):
             getattr(c, name)[:] = [float(x) for x in d.get(name, (0.0, 0.0, 0.0))]
+        elif name == "mrt_rates":
+            getattr(c, name)[:] = [float(x) for x in d.get(name, (0.0, 0.0, 0.0, 0.0))]
         elif name == "storage":
             s = d.get("storage", "fp32")
             c.storage = STORAGE[s] if isinstance(s, str) else int(s)

@@ -40,6 +40,10 @@ BAD_CONFIGS = [
     ("capacity above 16384", dict(bubble_capacity=20000)),
     ("bad collision", dict(collision=3)),
     ("TRT without magic", dict(collision=1, trt_magic=0.0)),
+    ("MRT without magic", dict(collision=2, trt_magic=-1.0)),
+    ("MRT rate at 2", dict(collision=2, mrt_rates=(1.2, 2.0, 0.0, 0.0))),
+    ("MRT rate negative", dict(collision=2, mrt_rates=(0.0, 0.0, 0.0, -0.5))),
+    ("MRT rate NaN", dict(collision=2, mrt_rates=(float("nan"), 0.0, 0.0, 0.0))),
     ("disjoining range 0", dict(k_pi=1e-3, d_max=0.0)),
     ("bad curvature method", dict(kappa=2)),
 ]
