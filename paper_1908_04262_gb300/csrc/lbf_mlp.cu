@@ -9,6 +9,7 @@
 
 #include "../../include/lbf.h"
 #include "lbf_mlp.cuh"
+#include "lbf_tc.cuh"
 #include "lbf_ops_api.h"
 
 using namespace lbf;
@@ -28,29 +29,31 @@ int fail(int code, const char *msg) {
 
 constexpr int WARPS = 4;  // warps per block of the network kernels
 
-// inference: canonical stencils (n x 27 fp32) -> y = 4 kappa
-__global__ void __launch_bounds__(32 * WARPS) k_forward(const float *theta, const float *x, int n, float *y) {
-  __shared__ NetF s;
-  __shared__ __nv_bfloat16 xs[WARPS][16 * 32];
-  load_netf(s, theta);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2;
-  const int tiles = (n + 15) / 16;
-  for (int tile = blockIdx.x * WARPS + w; tile < tiles; tile += gridDim.x * WARPS) {
-    for (int e = lane; e < 16 * 32; e += 32) {
-      const int r = e / 32, k = e % 32, row = tile * 16 + r;
-      xs[w][e] = __float2bfloat16_rn(k < 27 && row < n ? x[(size_t)row * 27 + k] : 0.f);
+// inference: canonical stencils (n x 27 fp32) -> y = 4 kappa, on the
+// fifth-generation tensor cores: tiles of 128 rows, each CTA (128 threads)
+// walking tiles; a tile whose MMA did not complete within the wait bound
+// (and every later tile of that CTA) gets NaN outputs
+__global__ void __launch_bounds__(128) k_forward_tc(const float *theta, const float *x, int n, float *y) {
+  extern __shared__ __align__(128) unsigned char tsm[];
+  tc::Tile &t = *reinterpret_cast<tc::Tile *>(tsm);
+  tc::pack_image(t.net, theta);
+  tc::setup(t, nullptr);
+  uint32_t phase = 0;
+  bool failed = false;
+  const int tiles = (n + tc::ROWS - 1) / tc::ROWS;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const long long row0 = (long long)tile * tc::ROWS;
+    const int rows = (int)min((long long)tc::ROWS, (long long)n - row0);
+    const float *xt = x + row0 * 27;
+    for (int e = threadIdx.x; e < tc::ROWS * 27; e += blockDim.x) {
+      const int r = e / 27, k = e - 27 * r;
+      tc::put_x(t, r, k, r < rows ? xt[e] : 0.f);
     }
-    __syncwarp();
-    Fwd F;
-    forward16(s, xs[w], F);
-    if ((lane & 3) == 0) {
-      const int r0 = tile * 16 + g, r1 = r0 + 8;
-      if (r0 < n) y[r0] = F.y0;
-      if (r1 < n) y[r1] = F.y1;
-    }
-    __syncwarp();
+    float yv = __int_as_float(0x7fc00000);
+    if (!failed) failed = !tc::forward_tile<128>(t, phase, yv);
+    if ((int)threadIdx.x < rows) y[row0 + threadIdx.x] = yv;
   }
+  tc::teardown(t, phase, failed);
 }
 
 // per-warp staging of the backward pass
@@ -409,22 +412,24 @@ int grad_launch(const float *theta, const float *x, const float *t, int n, const
 }  // namespace
 
 namespace {
-__global__ void k_pack_net(const float *theta, NetF *img) { load_netf(*img, theta); }
+__global__ void k_pack_net(const float *theta, tc::Image *img) { tc::pack_image(*img, theta); }
 }  // namespace
 
 namespace lbf {
 namespace mlp {
-size_t image_bytes() { return sizeof(NetF); }
+size_t image_bytes() { return sizeof(tc::Image); }
 void pack_launch(const float *theta, void *img, cudaStream_t st) {
-  k_pack_net<<<1, 256, 0, st>>>(theta, (NetF *)img);
+  k_pack_net<<<1, 256, 0, st>>>(theta, (tc::Image *)img);
 }
 // in-loop use by the simulation (declared in lbf_ops_api.h)
 void forward_launch(const float *theta, const float *x, int n, float *y, cudaStream_t st) {
-  const int tiles = (n + 15) / 16;
-  int blocks = (tiles + WARPS - 1) / WARPS;
+  const int tiles = (n + tc::ROWS - 1) / tc::ROWS;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int blocks = tiles < sms ? tiles : sms;
   if (blocks < 1) blocks = 1;
-  if (blocks > 1216) blocks = 1216;
-  k_forward<<<blocks, 32 * WARPS, 0, st>>>(theta, x, n, y);
+  k_forward_tc<<<blocks, 128, sizeof(tc::Tile), st>>>(theta, x, n, y);
 }
 }  // namespace mlp
 }  // namespace lbf

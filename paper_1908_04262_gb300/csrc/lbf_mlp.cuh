@@ -1,8 +1,10 @@
 // lbf_mlp.cuh -- learned interface curvature: a 27-64-64-1 SiLU network on
 // the canonically oriented 3x3x3 fill-level stencil, output y = 4 kappa
 // (kappa as in Sec. 2.2 Eq. rhob).  BF16 weights and activations, FP32
-// accumulation, on the tensor cores through mma.sync.m16n8k16 (one warp
-// computes 16 stencils at a time).
+// accumulation.  Inference (the batched forward pass and the in-loop
+// curvature) runs on the fifth-generation tensor cores (lbf_tc.cuh);
+// training's forward and backward passes use the warp-level MMA below
+// (mma.sync.m16n8k16, one warp computes 16 stencils at a time).
 //
 // Parameters, flat FP32 (6017): W1 (64x27 row-major), b1 (64), W2 (64x64),
 // b2 (64), W3 (64), b3 (1).  Stencil index q = (dz+1)*9 + (dy+1)*3 + (dx+1).
@@ -23,8 +25,7 @@ constexpr float Y_SCALE = 4.f;
 constexpr int W1_LD = 40;  // 32 inputs (27 used) + pad, bf16
 constexpr int W2_LD = 72;  // 64 + pad, bf16
 
-// the network as the forward pass reads it (a 16-byte multiple, so a packed
-// image in global memory copies into shared memory with vector loads)
+// the network as the training kernels read it from shared memory
 struct __align__(16) NetF {
   __nv_bfloat16 w1[64 * W1_LD];  // w1[n][k] = W1[n][k]
   __nv_bfloat16 w2[64 * W2_LD];  // w2[n][k] = W2[n][k]
@@ -62,13 +63,6 @@ __device__ __forceinline__ void load_net(Smem &s, const float *theta) {
     const int r = i / W2_LD, k = i % W2_LD;
     s.w2t[i] = __float2bfloat16_rn(k < 64 ? theta[OFF_W2 + k * 64 + r] : 0.f);
   }
-}
-
-// copy a packed image (global, 16-byte aligned) into shared memory
-__device__ __forceinline__ void copy_netf(NetF &s, const NetF *img) {
-  const uint4 *src = reinterpret_cast<const uint4 *>(img);
-  uint4 *dst = reinterpret_cast<uint4 *>(&s);
-  for (int i = threadIdx.x; i < (int)(sizeof(NetF) / 16); i += blockDim.x) dst[i] = src[i];
 }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {

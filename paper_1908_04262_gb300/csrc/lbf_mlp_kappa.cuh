@@ -4,34 +4,40 @@
 #pragma once
 #include "lbf_common.cuh"
 #include "lbf_mlp.cuh"
+#include "lbf_tc.cuh"
 
 namespace lbf {
 
-// In-loop learned curvature (3D): one warp per 16 interface cells of the
-// list; every cell's stencil is gathered, turned into the canonical
-// orientation of its geometry normal and fed to the network (img: the
-// packed BF16 image of the parameters).  The least-squares curvature stays
-// where the network is outside its training range (|kappa| outside
-// [0.02, 0.55], i.e. radii beyond [1.8, 50] cells) or the stencil touches a
-// wall.
-constexpr int MLP_WARPS = 8;
+// In-loop learned curvature (3D): tiles of 128 interface cells of the
+// list, one CTA of 256 threads per tile at a time.  The network's packed
+// image (img) arrives by one bulk copy while the first tile is gathered;
+// warp w gathers the stencils of rows 16w .. 16w + 15 (turned into the
+// canonical orientation of each cell's geometry normal) into the operand
+// tile of the tensor cores, and thread r < 128 writes the curvature of row
+// r.  The least-squares curvature stays where the network is outside its
+// training range (|kappa| outside [0.02, 0.55], i.e. radii beyond [1.8, 50]
+// cells) or the stencil touches a wall, and everywhere once a wait has not
+// completed within its bound.
+constexpr int MLP_THREADS = 256;
 template <int D, class R>
-__global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp_kappa(Params p, const mlp::NetF *img) {
+__global__ void __launch_bounds__(MLP_THREADS) k_mlp_kappa(Params p, const tc::Image *img) {
   if constexpr (D == 3) {
-    __shared__ mlp::NetF s;
-    __shared__ __nv_bfloat16 xs[MLP_WARPS][16 * 32];
-    __shared__ Cell cs[MLP_WARPS][16];
-    __shared__ int ord[MLP_WARPS][16][3], sgn[MLP_WARPS][16][3], use[MLP_WARPS][16];
-    mlp::copy_netf(s, img);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    extern __shared__ __align__(128) unsigned char tsm[];
+    tc::Tile &t = *reinterpret_cast<tc::Tile *>(tsm);
+    __shared__ Cell cs[tc::ROWS];
+    __shared__ int ord[tc::ROWS][3], sgn[tc::ROWS][3], use[tc::ROWS];
     const int cnt = *p.icount;
-    const int tiles = (cnt + 15) / 16;
+    const int tiles = (cnt + tc::ROWS - 1) / tc::ROWS;
+    if ((int)blockIdx.x >= tiles) return;  // uniform over the CTA: no tensor memory taken
+    tc::setup(t, img);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const R *phi = (const R *)p.phi, *nr = (const R *)p.nrm;
     R *kap = (R *)p.kappa;
-    for (int tile = blockIdx.x * MLP_WARPS + w; tile < tiles; tile += gridDim.x * MLP_WARPS) {
-      if (lane < 16) {
-        const int k = tile * 16 + lane;
+    uint32_t phase = 0;
+    bool failed = false, net = false;
+    for (int tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
+      if (tid < tc::ROWS) {
+        const int k = tile * tc::ROWS + tid;
         int ok = 0;
         Cell c;
         c.n = -1;
@@ -40,47 +46,55 @@ __global__ void __launch_bounds__(32 * MLP_WARPS) k_mlp_kappa(Params p, const ml
           const float mx = (float)nr[c.n], my = (float)nr[p.N + c.n], mz = (float)nr[2 * p.N + c.n];
           const float ka = fabsf((float)kap[c.n]);
           ok = (mx != 0.f || my != 0.f || mz != 0.f) && ka >= 0.02f && ka <= 0.55f;
-          mlp::canonical_order(mx, my, mz, ord[w][lane], sgn[w][lane]);
+          mlp::canonical_order(mx, my, mz, ord[tid], sgn[tid]);
         }
-        cs[w][lane] = c;
-        use[w][lane] = ok;
+        cs[tid] = c;
+        use[tid] = ok;
       }
-      __syncwarp();
-      // lane q gathers stencil position q of the 16 cells: every flag and
-      // fill level is loaded before any is used (one round trip, not 16)
+      __syncthreads();
+      // lane q gathers stencil position q of the warp's 16 rows: every flag
+      // and fill level is loaded before any is used
+      const int r0 = 16 * w;
       uint8_t fr[16];
       R pr[16];
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
-        const Cell &c = cs[w][r];
+        const Cell &c = cs[r0 + r];
         fr[r] = (uint8_t)T_GAS;
         pr[r] = (R)0;
-        if (c.n >= 0 && lane < 27 && use[w][r]) {
-          const int src = mlp::canonical_src(lane, ord[w][r], sgn[w][r]);
+        if (c.n >= 0 && lane < 27 && use[r0 + r]) {
+          const int src = mlp::canonical_src(lane, ord[r0 + r], sgn[r0 + r]);
           const int m = at(p, c, src % 3 - 1, (src / 3) % 3 - 1, src / 9 - 1);
           fr[r] = p.flags[m];  // read as post-conversion types below
           pr[r] = phi[m];
         }
       }
+      __syncwarp();
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
         float a = 0.f;
         const int tm = post_type(fr[r]);
         if (tm == T_LIQ) a = 1.f;
         else if (tm == T_IFC) a = fminf(fmaxf((float)pr[r], 0.f), 1.f);
-        else if (tm == T_WALL) use[w][r] = 0;
-        xs[w][r * 32 + lane] = __float2bfloat16_rn(a);
+        else if (tm == T_WALL && lane < 27) use[r0 + r] = 0;
+        if (lane < 27) tc::put_x(t, r0 + r, lane, a);
       }
-      __syncwarp();
-      mlp::Fwd F;
-      mlp::forward16(s, xs[w], F);
-      if (t == 0) {
-        const int n0 = cs[w][g].n, n1 = cs[w][g + 8].n;
-        if (n0 >= 0 && use[w][g]) kap[n0] = (R)fminf(fmaxf(F.y0 / mlp::Y_SCALE, -1.f), 1.f);
-        if (n1 >= 0 && use[w][g + 8]) kap[n1] = (R)fminf(fmaxf(F.y1 / mlp::Y_SCALE, -1.f), 1.f);
+      if (!net) {
+        net = true;
+        if (!tc::wait_net(t, phase)) {
+          failed = true;
+          break;
+        }
       }
-      __syncwarp();
+      float yv = 0.f;
+      failed = !tc::forward_tile<MLP_THREADS>(t, phase, yv);
+      if (tid < tc::ROWS) {
+        const int n0 = cs[tid].n;
+        if (!failed && n0 >= 0 && use[tid]) kap[n0] = (R)fminf(fmaxf(yv / mlp::Y_SCALE, -1.f), 1.f);
+      }
+      __syncthreads();
     }
+    tc::teardown(t, phase, failed);
   }
 }
 

@@ -141,8 +141,11 @@ struct OpsImpl final : Ops {
     if (p.kappa_hf) k_hf_kappa<D, R><<<p.list_blocks, 128, 0, s>>>(p);
   }
   void mlp_kappa(const Params &p, const void *img, cudaStream_t s) override {
-    // one block of MLP_WARPS warps per SM (list_blocks holds 4 per SM)
-    if (D == 3) k_mlp_kappa<D, R><<<p.list_blocks / 4, 32 * MLP_WARPS, 0, s>>>(p, (const mlp::NetF *)img);
+    // up to two CTAs of 128 cells per SM (list_blocks holds 4 per SM);
+    // each holds 128 of the SM's 512 tensor-memory columns, and no more
+    // than four fit on an SM by their shared memory
+    if (D == 3)
+      k_mlp_kappa<D, R><<<p.list_blocks / 2, MLP_THREADS, sizeof(tc::Tile), s>>>(p, (const tc::Image *)img);
   }
   void mlp_harvest(const Params &p, float *x, float *y, int *cells, int cap, int *count, cudaStream_t s) override {
     if (D == 3) k_mlp_harvest<D, R><<<p.warp_blocks, 128, 0, s>>>(p, x, y, cells, cap, count);
