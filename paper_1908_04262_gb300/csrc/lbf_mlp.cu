@@ -27,8 +27,6 @@ int fail(int code, const char *msg) {
     if (e_ != cudaSuccess) return fail(LBF_ECUDA, cudaGetErrorString(e_)); \
   } while (0)
 
-constexpr int WARPS = 4;  // warps per block of the network kernels
-
 // inference: canonical stencils (n x 27 fp32) -> y = 4 kappa, on the
 // fifth-generation tensor cores: tiles of 128 rows, each CTA (128 threads)
 // walking tiles; a tile whose MMA did not complete within the wait bound
@@ -37,7 +35,7 @@ __global__ void __launch_bounds__(128) k_forward_tc(const float *theta, const fl
   extern __shared__ __align__(128) unsigned char tsm[];
   tc::Tile &t = *reinterpret_cast<tc::Tile *>(tsm);
   tc::pack_image(t.net, theta);
-  tc::setup(t, nullptr);
+  tc::setup(t, tc::TCOLS);
   uint32_t phase = 0;
   bool failed = false;
   const int tiles = (n + tc::ROWS - 1) / tc::ROWS;
@@ -56,16 +54,6 @@ __global__ void __launch_bounds__(128) k_forward_tc(const float *theta, const fl
   tc::teardown(t, phase, failed);
 }
 
-// per-warp staging of the backward pass
-struct Stage {
-  __nv_bfloat16 x[16 * 32];
-  __nv_bfloat16 h1[16 * 64];
-  __nv_bfloat16 d2[16 * 64];
-  __nv_bfloat16 d1[16 * 64];
-};
-
-// gradient of L = (1/2n) sum (y - t)^2, accumulated into grad (fp32, global)
-// and L into *loss; each block sums its tiles in shared memory first
 // which rows of the data set a batch takes, and the augmentation: row r of
 // the batch is data row (a (start + r) + b) mod ntot (a coprime to ntot: a
 // cheap per-epoch shuffle); fill levels strictly inside (0, 1) get uniform
@@ -78,27 +66,97 @@ struct Batch {
 
 __device__ __forceinline__ unsigned long long splitmix(unsigned long long x);
 
-__global__ void __launch_bounds__(32 * WARPS) k_grad(const float *theta, const float *x, const float *tgt, int n,
-                                                     Batch bt, float *grad, double *loss) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  Smem &s = *reinterpret_cast<Smem *>(smraw);
-  float *gacc = reinterpret_cast<float *>(smraw + sizeof(Smem));
-  Stage *st = reinterpret_cast<Stage *>(smraw + sizeof(Smem) + ((NP * 4 + 15) / 16) * 16);
-  load_net(s, theta);
-  for (int i = threadIdx.x; i < NP; i += blockDim.x) gacc[i] = 0.f;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  Stage &S = st[w];
+// The network as training reads it: the inference image plus W2^T (row i,
+// K = j: the B operand of delta1 = delta2 W2), packed by Adam after every
+// update so that each gradient CTA fetches it with two bulk copies.
+struct __align__(128) TrainImage {
+  tc::Image net;
+  __nv_bfloat16 w2t[64 * 64];
+};
+static_assert(sizeof(TrainImage) % 16 == 0 && sizeof(tc::Image) % 16 == 0, "bulk copies move multiples of 16 bytes");
+
+// parameter i (value v) into its places in the training image (the pads of
+// W1 stay as the image was cleared)
+__device__ __forceinline__ void place_param(TrainImage &m, int i, float v) {
+  const __nv_bfloat16 b = __float2bfloat16_rn(v);
+  if (i < OFF_B1) {
+    const int r = i / 27, k = i - 27 * r;
+    m.net.w1[tc::kofs(r, k, 32) / 2] = b;
+  } else if (i < OFF_W2) {
+    m.net.b1[i - OFF_B1] = v;
+  } else if (i < OFF_B2) {
+    const int q = i - OFF_W2, r = q >> 6, k = q & 63;
+    m.net.w2[tc::kofs(r, k, 64) / 2] = b;
+    m.w2t[tc::kofs(k, r, 64) / 2] = b;
+  } else if (i < OFF_W3) {
+    m.net.b2[i - OFF_B2] = v;
+  } else if (i < OFF_B3) {
+    m.net.w3[i - OFF_W3] = v;
+  } else {
+    m.net.b3 = v;
+  }
+}
+__global__ void k_place_all(const float *theta, TrainImage *img) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < NP) place_param(*img, i, theta[i]);
+}
+
+// shared memory of a gradient CTA
+struct __align__(128) GradSmem {
+  tc::Tile t;                    // X (a1), H1 then BF16 H2 row-major (a2), the network
+  __nv_bfloat16 w2t[64 * 64];    // W2^T
+  __nv_bfloat16 ad2[128 * 64];   // delta2 (A of delta2 W2)
+  __nv_bfloat16 ag[128 * 128];   // rows 0-63 delta2^T, 64-127 delta1^T; K = the tile's rows
+  __nv_bfloat16 bg[112 * 128];   // rows 0-63 H1^T, 64-90 X^T, 96 ones, the rest zero
+  float d3[128], le[128];        // delta3 and the loss of each row
+  long long src[128];            // data row of each tile row
+};
+constexpr uint32_t GRAD_TCOLS = 512;  // Z1 0-63, Z2 64-127, delta2 W2 128-191, gradients 256-367
+
+// Gradient of L = (1/2n) sum (y - t)^2 on the fifth-generation tensor
+// cores: tiles of 128 rows, one row per thread in the epilogues.  Per tile:
+//   Z1 = X W1^T, H1 = SiLU(Z1 + b1); Z2 = H1 W2^T, y = BF16(SiLU(Z2 + b2)) W3 + b3
+//   delta3 = (y - t) / n, delta2 = delta3 W3 SiLU'(Z2 + b2)
+//   delta1 = (delta2 W2) SiLU'(Z1 + b1)                    (MMA, K = 64)
+//   [delta2^T; delta1^T] [H1^T; X^T; 1]^T accumulated over the tiles  (MMA,
+//   K = 128 rows): its blocks are dW2, dW1, db2 and db1
+// dW3, db3 and the loss are summed in shared memory per tile.  Everything
+// is added into grad and *loss (global) once per CTA.  A timed-out wait
+// adds NaN to *loss.
+__global__ void __launch_bounds__(128) k_grad_tc(const TrainImage *img, const float *x, const float *tgt, int n,
+                                                 Batch bt, float *grad, double *loss) {
+  extern __shared__ __align__(128) unsigned char gsm[];
+  GradSmem &s = *reinterpret_cast<GradSmem *>(gsm);
+  tc::Tile &t = s.t;
+  const int tid = threadIdx.x, w = tid >> 5;
+  const int tiles = (n + tc::ROWS - 1) / tc::ROWS;
+  for (int i = tid; i < 112 * 128; i += 128) {
+    const int r = i >> 7, m = i & 127;
+    s.bg[tc::kofs(r, m, 128) / 2] = __float2bfloat16_rn(r == 96 ? 1.f : 0.f);
+  }
+  tc::setup(t, GRAD_TCOLS, tc::Copy{&t.net, &img->net, (uint32_t)sizeof(tc::Image)},
+            tc::Copy{s.w2t, img->w2t, (uint32_t)sizeof(img->w2t)});
+  const uint32_t tm = t.tmem, lanes = (uint32_t)(32 * w) << 16;
   const float inv_n = 1.f / (float)n;
-  const int tiles = (n + 15) / 16;
-  double lsum = 0.0;
-  for (int tile = blockIdx.x * WARPS + w; tile < tiles; tile += gridDim.x * WARPS) {
-    for (int e = lane; e < 16 * 32; e += 32) {
-      const int r = e / 32, k = e % 32, row = tile * 16 + r;
+  uint32_t phase = 0;
+  bool failed = false, net = false, any = false;
+  for (int tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
+    const int row0 = tile * tc::ROWS, rows = min(tc::ROWS, n - row0);
+    // the tile's data rows (thread = row), then X into a1 and X^T into bg
+    float target = 0.f;
+    if (tid < rows) {
+      const long long src =
+          (long long)((bt.a * (unsigned long long)(bt.start + row0 + tid) + bt.b) % (unsigned long long)bt.ntot);
+      s.src[tid] = src;
+      target = tgt[src];
+    }
+    __syncthreads();
+#pragma unroll 9
+    for (int c = 0; c < 27; ++c) {
+      const int e = tid + 128 * c, r = e / 27, k = e - 27 * r;
       float v = 0.f;
-      if (k < 27 && row < n) {
-        const long long src = (long long)((bt.a * (unsigned long long)(bt.start + row) + bt.b) %
-                                          (unsigned long long)bt.ntot);
+      if (r < rows) {
+        const long long src = s.src[r];
         v = x[(size_t)src * 27 + k];
         if (bt.noise > 0.f && v > 0.f && v < 1.f) {
           const unsigned long long h = splitmix(bt.key ^ splitmix((unsigned long long)src * 32ull + k));
@@ -106,157 +164,164 @@ __global__ void __launch_bounds__(32 * WARPS) k_grad(const float *theta, const f
           v = fminf(fmaxf(v + bt.noise * (2.f * u - 1.f), 0.f), 1.f);
         }
       }
-      S.x[e] = __float2bfloat16_rn(v);
+      const __nv_bfloat16 b = __float2bfloat16_rn(v);
+      t.a1[tc::kofs(r, k, 32) / 2] = b;
+      s.bg[tc::kofs(64 + k, r, 128) / 2] = b;
     }
-    __syncwarp();
-    Fwd F;
-    forward16(s.f, S.x, F);
-    const int r0 = tile * 16 + g, r1 = r0 + 8;
-    auto tg = [&](int row) {
-      return tgt[(bt.a * (unsigned long long)(bt.start + row) + bt.b) % (unsigned long long)bt.ntot];
-    };
-    const float e0 = r0 < n ? F.y0 - tg(r0) : 0.f, e1 = r1 < n ? F.y1 - tg(r1) : 0.f;
-    if (t == 0) lsum += 0.5 * ((double)e0 * e0 + (double)e1 * e1) * (double)inv_n;
-    const float d30 = e0 * inv_n, d31 = e1 * inv_n;
-    // output layer
-    float gb3 = d30 + d31;
-    // delta2 = d3 * W3 * SiLU'(z2); grads of W3 and b2 summed over the rows
+    if (!net) {
+      net = true;
+      if (!tc::wait_net(t, phase)) {
+        failed = true;
+        break;
+      }
+    }
+    // layer 1; H1 into a2 (row tid) and bg rows 0-63 (column tid)
+    tc::to_tensor_cores();
+    if (tid == 0) tc::issue(t, tm, t.a1, t.net.w1, 32, 64, 2, false);
+    if (!tc::wait_mmas(t, phase)) {
+      failed = true;
+      break;
+    }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int c = 0; c < 4; ++c) {
+      float z[16];
+      tc::ld16(tm + lanes + 16 * c, z);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint4 q;
+        uint32_t *qw = reinterpret_cast<uint32_t *>(&q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j = 16 * c + 8 * h + 2 * e;
+          const __nv_bfloat162 hv =
+              __floats2bfloat162_rn(silu(z[8 * h + 2 * e] + t.net.b1[j]), silu(z[8 * h + 2 * e + 1] + t.net.b1[j + 1]));
+          qw[e] = *reinterpret_cast<const uint32_t *>(&hv);
+          s.bg[tc::kofs(j, tid, 128) / 2] = hv.x;
+          s.bg[tc::kofs(j + 1, tid, 128) / 2] = hv.y;
+        }
+        *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(t.a2) + tc::kofs(tid, 16 * c + 8 * h, 64)) = q;
+      }
+    }
+    // layer 2; y, delta3 and the loss of row tid; BF16 H2 into a2 (row-major)
+    tc::to_tensor_cores();
+    if (tid == 0) tc::issue(t, tm + 64, t.a2, t.net.w2, 64, 64, 4, false);
+    if (!tc::wait_mmas(t, phase)) {
+      failed = true;
+      break;
+    }
+    float y = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float z[16];
+      tc::ld16(tm + lanes + 64 + 16 * c, z);
+#pragma unroll
+      for (int e = 0; e < 16; e += 2) {
+        const int j = 16 * c + e;
+        const __nv_bfloat162 hv = __floats2bfloat162_rn(silu(z[e] + t.net.b2[j]), silu(z[e + 1] + t.net.b2[j + 1]));
+        y += __bfloat162float(hv.x) * t.net.w3[j] + __bfloat162float(hv.y) * t.net.w3[j + 1];
+        *reinterpret_cast<__nv_bfloat162 *>(t.a2 + tid * 64 + j) = hv;
+      }
+    }
+    y += t.net.b3;
+    const float err = tid < rows ? y - target : 0.f;
+    const float d3 = err * inv_n;
+    s.d3[tid] = d3;
+    s.le[tid] = 0.5f * err * err * inv_n;
+    // delta2 = delta3 W3 SiLU'(Z2 + b2): into ad2 (row tid) and ag rows 0-63
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float z[16];
+      tc::ld16(tm + lanes + 64 + 16 * c, z);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint4 q;
+        uint32_t *qw = reinterpret_cast<uint32_t *>(&q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j = 16 * c + 8 * h + 2 * e;
+          const __nv_bfloat162 dv = __floats2bfloat162_rn(d3 * t.net.w3[j] * dsilu(z[8 * h + 2 * e] + t.net.b2[j]),
+                                                          d3 * t.net.w3[j + 1] * dsilu(z[8 * h + 2 * e + 1] + t.net.b2[j + 1]));
+          qw[e] = *reinterpret_cast<const uint32_t *>(&dv);
+          s.ag[tc::kofs(j, tid, 128) / 2] = dv.x;
+          s.ag[tc::kofs(j + 1, tid, 128) / 2] = dv.y;
+        }
+        *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(s.ad2) + tc::kofs(tid, 16 * c + 8 * h, 64)) = q;
+      }
+    }
+    // delta2 W2 on the tensor cores while the CTA sums dW3, db3 and the loss
+    tc::to_tensor_cores();
+    if (tid == 0) tc::issue(t, tm + 128, s.ad2, s.w2t, 64, 64, 4, false);
+    if (tid < 64) {
+      float g = 0.f;
+      for (int m = 0; m < tc::ROWS; ++m) g += s.d3[m] * __bfloat162float(t.a2[m * 64 + tid]);
+      atomicAdd(grad + OFF_W3 + tid, g);
+    } else if (tid == 64) {
+      float g = 0.f;
+      for (int m = 0; m < tc::ROWS; ++m) g += s.d3[m];
+      atomicAdd(grad + OFF_B3, g);
+    } else if (tid == 96) {
+      double l = 0.0;
+      for (int m = 0; m < tc::ROWS; ++m) l += (double)s.le[m];
+      atomicAdd(loss, l);
+    }
+    if (!tc::wait_mmas(t, phase)) {
+      failed = true;
+      break;
+    }
+    // delta1 = (delta2 W2) SiLU'(Z1 + b1): into ag rows 64-127
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float z[16], d[16];
+      tc::ld16(tm + lanes + 16 * c, z);
+      tc::ld16(tm + lanes + 128 + 16 * c, d);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int j = 16 * c + e;
+        s.ag[tc::kofs(64 + j, tid, 128) / 2] = __float2bfloat16_rn(d[e] * dsilu(z[e] + t.net.b1[j]));
+      }
+    }
+    // weight and bias gradients of the tile, accumulated in tensor memory
+    tc::to_tensor_cores();
+    if (tid == 0) tc::issue(t, tm + 256, s.ag, s.bg, 128, 112, 8, any);
+    any = true;
+    if (!tc::wait_mmas(t, phase)) {
+      failed = true;
+      break;
+    }
+  }
+  if (failed) {
+    if (tid == 0) atomicAdd(loss, (double)__int_as_float(0x7fc00000));
+  } else if (any) {
+    // row tid of the accumulated block product: rows 0-63 dW2 (columns
+    // 0-63) and db2 (column 96), rows 64-127 dW1 (columns 64-90) and db1
+    float z[16];
+    tc::ld16(tm + lanes + 256 + 96, z);
+    if (tid < 64) {
+      atomicAdd(grad + OFF_B2 + tid, z[0]);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        tc::ld16(tm + lanes + 256 + 16 * c, z);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) atomicAdd(grad + OFF_W2 + tid * 64 + 16 * c + e, z[e]);
+      }
+    } else {
+      const int i = tid - 64;
+      atomicAdd(grad + OFF_B1 + i, z[0]);
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        const int col = 8 * j + 2 * t + c;
-        const float h20 = __bfloat162float(__float2bfloat16_rn(silu(F.z2[j][c])));
-        const float h21 = __bfloat162float(__float2bfloat16_rn(silu(F.z2[j][2 + c])));
-        float gw3 = d30 * h20 + d31 * h21;
-        const float dd0 = d30 * s.f.w3[col] * dsilu(F.z2[j][c]);
-        const float dd1 = d31 * s.f.w3[col] * dsilu(F.z2[j][2 + c]);
-        float gb2 = dd0 + dd1;
-        S.d2[g * 64 + col] = __float2bfloat16_rn(dd0);
-        S.d2[(g + 8) * 64 + col] = __float2bfloat16_rn(dd1);
-        S.h1[g * 64 + col] = __float2bfloat16_rn(silu(F.z1[j][c]));
-        S.h1[(g + 8) * 64 + col] = __float2bfloat16_rn(silu(F.z1[j][2 + c]));
-        // sum over the 8 row groups
-        gw3 += __shfl_xor_sync(0xffffffffu, gw3, 4);
-        gw3 += __shfl_xor_sync(0xffffffffu, gw3, 8);
-        gw3 += __shfl_xor_sync(0xffffffffu, gw3, 16);
-        gb2 += __shfl_xor_sync(0xffffffffu, gb2, 4);
-        gb2 += __shfl_xor_sync(0xffffffffu, gb2, 8);
-        gb2 += __shfl_xor_sync(0xffffffffu, gb2, 16);
-        if (g == 0) {
-          atomicAdd(gacc + OFF_W3 + col, gw3);
-          atomicAdd(gacc + OFF_B2 + col, gb2);
-        }
+        tc::ld16(tm + lanes + 256 + 64 + 16 * c, z);
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          if (16 * c + e < 27) atomicAdd(grad + OFF_W1 + i * 27 + 16 * c + e, z[e]);
       }
     }
-    gb3 += __shfl_xor_sync(0xffffffffu, gb3, 4);
-    gb3 += __shfl_xor_sync(0xffffffffu, gb3, 8);
-    gb3 += __shfl_xor_sync(0xffffffffu, gb3, 16);
-    if (lane == 0) atomicAdd(gacc + OFF_B3, gb3);
-    __syncwarp();
-    // delta1 = (delta2 W2) * SiLU'(z1): A = delta2 (16 x 64), B[n][k] = W2[n][k]
-    {
-      uint32_t a[4][4];
-#pragma unroll
-      for (int kc = 0; kc < 4; ++kc) {
-        a[kc][0] = ld2(S.d2 + g * 64 + kc * 16 + 2 * t);
-        a[kc][1] = ld2(S.d2 + (g + 8) * 64 + kc * 16 + 2 * t);
-        a[kc][2] = ld2(S.d2 + g * 64 + kc * 16 + 8 + 2 * t);
-        a[kc][3] = ld2(S.d2 + (g + 8) * 64 + kc * 16 + 8 + 2 * t);
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int kc = 0; kc < 4; ++kc) {
-          const __nv_bfloat16 *wv = s.w2t + (8 * j + g) * W2_LD + kc * 16 + 2 * t;
-          mma16816(acc, a[kc], ld2(wv), ld2(wv + 8));
-        }
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int col = 8 * j + 2 * t + c;
-          const float dd0 = acc[c] * dsilu(F.z1[j][c]);
-          const float dd1 = acc[2 + c] * dsilu(F.z1[j][2 + c]);
-          S.d1[g * 64 + col] = __float2bfloat16_rn(dd0);
-          S.d1[(g + 8) * 64 + col] = __float2bfloat16_rn(dd1);
-          float gb1 = dd0 + dd1;
-          gb1 += __shfl_xor_sync(0xffffffffu, gb1, 4);
-          gb1 += __shfl_xor_sync(0xffffffffu, gb1, 8);
-          gb1 += __shfl_xor_sync(0xffffffffu, gb1, 16);
-          if (g == 0) atomicAdd(gacc + OFF_B1 + col, gb1);
-        }
-      }
-    }
-    __syncwarp();
-    // weight gradients: dW2[n][k] = sum_rows d2[row][n] h1[row][k] and
-    // dW1[n][k] = sum_rows d1[row][n] x[row][k]; M = units, K = the 16 rows
-#pragma unroll 1
-    for (int mt = 0; mt < 4; ++mt) {
-      uint32_t a2[4], a1[4];
-      const int m0 = mt * 16 + g, m1 = m0 + 8;
-      const int k0 = 2 * t, k1 = 2 * t + 8;
-      auto pk = [](const __nv_bfloat16 *base, int ra, int rb, int col) {
-        __nv_bfloat162 v;
-        v.x = base[ra * 64 + col];
-        v.y = base[rb * 64 + col];
-        return *reinterpret_cast<uint32_t *>(&v);
-      };
-      a2[0] = pk(S.d2, k0, k0 + 1, m0);
-      a2[1] = pk(S.d2, k0, k0 + 1, m1);
-      a2[2] = pk(S.d2, k1, k1 + 1, m0);
-      a2[3] = pk(S.d2, k1, k1 + 1, m1);
-      a1[0] = pk(S.d1, k0, k0 + 1, m0);
-      a1[1] = pk(S.d1, k0, k0 + 1, m1);
-      a1[2] = pk(S.d1, k1, k1 + 1, m0);
-      a1[3] = pk(S.d1, k1, k1 + 1, m1);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        __nv_bfloat162 b0, b1;
-        b0.x = S.h1[(2 * t) * 64 + 8 * j + g];
-        b0.y = S.h1[(2 * t + 1) * 64 + 8 * j + g];
-        b1.x = S.h1[(2 * t + 8) * 64 + 8 * j + g];
-        b1.y = S.h1[(2 * t + 9) * 64 + 8 * j + g];
-        mma16816(acc, a2, *reinterpret_cast<uint32_t *>(&b0), *reinterpret_cast<uint32_t *>(&b1));
-        const int c0 = 8 * j + 2 * t;
-        atomicAdd(gacc + OFF_W2 + m0 * 64 + c0, acc[0]);
-        atomicAdd(gacc + OFF_W2 + m0 * 64 + c0 + 1, acc[1]);
-        atomicAdd(gacc + OFF_W2 + m1 * 64 + c0, acc[2]);
-        atomicAdd(gacc + OFF_W2 + m1 * 64 + c0 + 1, acc[3]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        __nv_bfloat162 b0, b1;
-        b0.x = S.x[(2 * t) * 32 + 8 * j + g];
-        b0.y = S.x[(2 * t + 1) * 32 + 8 * j + g];
-        b1.x = S.x[(2 * t + 8) * 32 + 8 * j + g];
-        b1.y = S.x[(2 * t + 9) * 32 + 8 * j + g];
-        mma16816(acc, a1, *reinterpret_cast<uint32_t *>(&b0), *reinterpret_cast<uint32_t *>(&b1));
-        const int c0 = 8 * j + 2 * t;
-        if (c0 < 27) {
-          atomicAdd(gacc + OFF_W1 + m0 * 27 + c0, acc[0]);
-          atomicAdd(gacc + OFF_W1 + m1 * 27 + c0, acc[2]);
-        }
-        if (c0 + 1 < 27) {
-          atomicAdd(gacc + OFF_W1 + m0 * 27 + c0 + 1, acc[1]);
-          atomicAdd(gacc + OFF_W1 + m1 * 27 + c0 + 1, acc[3]);
-        }
-      }
-    }
-    __syncwarp();
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < NP; i += blockDim.x)
-    if (gacc[i] != 0.f) atomicAdd(grad + i, gacc[i]);
-  lsum += __shfl_xor_sync(0xffffffffu, lsum, 4);
-  lsum += __shfl_xor_sync(0xffffffffu, lsum, 8);
-  lsum += __shfl_xor_sync(0xffffffffu, lsum, 16);
-  if (lane == 0 && lsum != 0.0) atomicAdd(loss, lsum);
+  tc::teardown(t, phase, failed, GRAD_TCOLS);
 }
 
-// Adam on the fp32 master parameters
-__global__ void k_adam(float *theta, float *m, float *v, const float *grad, int step, float lr) {
+// Adam on the fp32 master parameters; the updated parameter also goes into
+// the training image
+__global__ void k_adam(float *theta, float *m, float *v, const float *grad, int step, float lr, TrainImage *img) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NP) return;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
@@ -266,7 +331,9 @@ __global__ void k_adam(float *theta, float *m, float *v, const float *grad, int 
   m[i] = mi;
   v[i] = vi;
   const float mh = mi / (1.f - powf(b1, (float)step)), vh = vi / (1.f - powf(b2, (float)step));
-  theta[i] -= lr * mh / (sqrtf(vh) + eps);
+  const float th = theta[i] - lr * mh / (sqrtf(vh) + eps);
+  theta[i] = th;
+  place_param(*img, i, th);
 }
 
 // ---------------------------------------------------------------------------
@@ -392,19 +459,28 @@ unsigned long long host_gcd(unsigned long long a, unsigned long long b) {
   return a;
 }
 
-size_t grad_smem() { return sizeof(Smem) + ((NP * 4 + 15) / 16) * 16 + WARPS * sizeof(Stage); }
+// a cleared training image made from theta
+int image_init(const float *theta, TrainImage *img, cudaStream_t st) {
+  CKM(cudaMemsetAsync(img, 0, sizeof(TrainImage), st));
+  k_place_all<<<(NP + 255) / 256, 256, 0, st>>>(theta, img);
+  CKM(cudaGetLastError());
+  return 0;
+}
 
-int grad_launch(const float *theta, const float *x, const float *t, int n, const Batch &bt, float *grad, double *loss,
-                cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    CKM(cudaFuncSetAttribute(k_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem()));
-    attr = true;
+int grad_launch(const TrainImage *img, const float *x, const float *t, int n, const Batch &bt, float *grad,
+                double *loss, cudaStream_t st) {
+  int dev = 0;
+  CKM(cudaGetDevice(&dev));
+  static int attr_dev = -1;
+  if (attr_dev != dev) {
+    CKM(cudaFuncSetAttribute(k_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GradSmem)));
+    attr_dev = dev;
   }
-  const int tiles = (n + 15) / 16;
-  int blocks = (tiles + WARPS - 1) / WARPS;
-  if (blocks > 304) blocks = 304;
-  k_grad<<<blocks, 32 * WARPS, grad_smem(), st>>>(theta, x, t, n, bt, grad, loss);
+  int sms = 0;
+  CKM(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int tiles = (n + tc::ROWS - 1) / tc::ROWS;
+  const int blocks = tiles < sms ? tiles : sms;
+  k_grad_tc<<<blocks, 128, sizeof(GradSmem), st>>>(img, x, t, n, bt, grad, loss);
   CKM(cudaGetLastError());
   return 0;
 }
@@ -450,8 +526,13 @@ int lbf_mlp_loss_grad(const float *theta, const float *x, const float *t, int n,
   cudaStream_t st = (cudaStream_t)stream;
   CKM(cudaMemsetAsync(grad, 0, sizeof(float) * NP, st));
   CKM(cudaMemsetAsync(loss, 0, sizeof(double), st));
+  TrainImage *img = nullptr;
+  CKM(cudaMallocAsync((void **)&img, sizeof(TrainImage), st));
   Batch bt{0, n, 1ull, 0ull, 0ull, 0.f};
-  return grad_launch(theta, x, t, n, bt, grad, loss, st);
+  int rc = image_init(theta, img, st);
+  if (!rc) rc = grad_launch(img, x, t, n, bt, grad, loss, st);
+  CKM(cudaFreeAsync(img, st));
+  return rc;
 }
 
 int lbf_mlp_generate(unsigned long long seed, int n, double rmin, double rmax, float *x, float *y, void *stream) {
@@ -497,6 +578,8 @@ int lbf_mlp_train(const lbf_mlp_train_cfg *cfg, float *theta_io, float *loss_cur
   CKM(cudaMallocAsync((void **)&v, sizeof(float) * NP, st));
   CKM(cudaMallocAsync((void **)&grad, sizeof(float) * NP, st));
   CKM(cudaMallocAsync((void **)&loss, sizeof(double) * (size_t)cfg->epochs, st));
+  TrainImage *img = nullptr;
+  CKM(cudaMallocAsync((void **)&img, sizeof(TrainImage), st));
   if (cfg->n_samples > 0) {
     int rc = lbf_mlp_generate(cfg->seed, cfg->n_samples, cfg->rmin, cfg->rmax, x, y, cfg->stream);
     if (rc) return rc;
@@ -511,6 +594,10 @@ int lbf_mlp_train(const lbf_mlp_train_cfg *cfg, float *theta_io, float *loss_cur
   CKM(cudaMemsetAsync(m, 0, sizeof(float) * NP, st));
   CKM(cudaMemsetAsync(v, 0, sizeof(float) * NP, st));
   CKM(cudaMemsetAsync(loss, 0, sizeof(double) * (size_t)cfg->epochs, st));
+  {
+    int rc = image_init(theta, img, st);
+    if (rc) return rc;
+  }
   int step = 0;
   const long long per_epoch = n / B;
   for (int ep = 0; ep < cfg->epochs; ++ep) {
@@ -524,9 +611,9 @@ int lbf_mlp_train(const lbf_mlp_train_cfg *cfg, float *theta_io, float *loss_cur
       CKM(cudaMemsetAsync(grad, 0, sizeof(float) * NP, st));
       Batch bt{k * B, n, a % (unsigned long long)n, b, host_splitmix(h + (unsigned long long)k),
                (float)cfg->noise};
-      int rc = grad_launch(theta, x, y, B, bt, grad, loss + ep, st);
+      int rc = grad_launch(img, x, y, B, bt, grad, loss + ep, st);
       if (rc) return rc;
-      k_adam<<<(NP + 255) / 256, 256, 0, st>>>(theta, m, v, grad, ++step, lr);
+      k_adam<<<(NP + 255) / 256, 256, 0, st>>>(theta, m, v, grad, ++step, lr, img);
     }
     CKM(cudaGetLastError());
   }
@@ -543,6 +630,7 @@ int lbf_mlp_train(const lbf_mlp_train_cfg *cfg, float *theta_io, float *loss_cur
   CKM(cudaFreeAsync(v, st));
   CKM(cudaFreeAsync(grad, st));
   CKM(cudaFreeAsync(loss, st));
+  CKM(cudaFreeAsync(img, st));
   CKM(cudaStreamSynchronize(st));
   return 0;
 }

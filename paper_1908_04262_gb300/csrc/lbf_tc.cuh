@@ -102,11 +102,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
   return true;
 }
 
-// thread 0: copy `bytes` (a multiple of 16, both addresses 16-byte
-// aligned) from global to shared memory with the bulk-copy engine; the
-// mbarrier's current phase completes when the bytes have landed
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+// thread 0: the mbarrier's current phase also waits for `bytes` more
+// bytes of bulk copies
+__device__ __forceinline__ void expect_bytes(uint64_t *mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+// copy `bytes` (a multiple of 16, both addresses 16-byte aligned) from
+// global to shared memory with the bulk-copy engine, counted on mbar
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    smem_u32(dst)),
                "l"(src), "r"(bytes), "r"(smem_u32(mbar))
@@ -175,20 +178,63 @@ __device__ __forceinline__ void pack_image(Image &m, const float *theta) {
   }
 }
 
-// input pads zero, mbarrier and tensor memory; with img (a packed image in
-// global memory, 16-byte aligned) thread 0 also starts the bulk copy of
-// the network, which completes the mbarrier's first phase (wait_net).
-// Every thread of the CTA.
-__device__ __forceinline__ void setup(Tile &t, const Image *img) {
+// one bulk copy of a set-up
+struct Copy {
+  void *dst;
+  const void *src;
+  uint32_t bytes;
+};
+
+// input pads zero, mbarrier and ncols columns of tensor memory; thread 0
+// also starts the bulk copies given (bytes 0: none), which complete the
+// mbarrier's first phase (wait_net).  Every thread of the CTA.
+__device__ __forceinline__ void setup(Tile &t, uint32_t ncols, Copy c0 = {nullptr, nullptr, 0u},
+                                      Copy c1 = {nullptr, nullptr, 0u}) {
   for (int i = threadIdx.x; i < ROWS * 32; i += blockDim.x) t.a1[i] = __float2bfloat16_rn(0.f);
   if (threadIdx.x == 0) {
     mbar_init(&t.mbar, 1);
-    if (img) bulk_load(&t.net, img, (uint32_t)sizeof(Image), &t.mbar);
+    if (c0.bytes + c1.bytes) {
+      expect_bytes(&t.mbar, c0.bytes + c1.bytes);
+      if (c0.bytes) bulk_copy(c0.dst, c0.src, c0.bytes, &t.mbar);
+      if (c1.bytes) bulk_copy(c1.dst, c1.src, c1.bytes, &t.mbar);
+    }
   }
-  if (threadIdx.x < 32) tmem_alloc(&t.tmem, TCOLS);
+  if (threadIdx.x < 32) tmem_alloc(&t.tmem, ncols);
   fence_before();
   __syncthreads();
   fence_after();
+}
+// the network of a packed image (global, 16-byte aligned) by bulk copy
+__device__ __forceinline__ void setup(Tile &t, const Image *img) {
+  setup(t, TCOLS, Copy{&t.net, img, (uint32_t)sizeof(Image)});
+}
+
+// the CTA's shared-memory writes made visible to the tensor cores and
+// ordered, with the tensor-memory loads before them, ahead of the MMAs
+// that follow (every thread)
+__device__ __forceinline__ void to_tensor_cores() {
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+}
+// thread 0: D (+)= A B^T for A of 128 rows and B of N rows, both K-major
+// canonical with K columns, over the first 16 * ksteps of them; then commit
+__device__ __forceinline__ void issue(Tile &t, uint32_t d, const void *A, const void *B, int K, int N, int ksteps,
+                                      bool accumulate) {
+  const uint32_t a = smem_u32(A), b = smem_u32(B), sbo = (uint32_t)K * 16u, id = idesc_bf16(ROWS, N);
+  for (int s = 0; s < ksteps; ++s)
+    mma(d, desc(a + 256 * s, 128, sbo), desc(b + 256 * s, 128, sbo), id, (accumulate || s > 0) ? 1u : 0u);
+  commit(&t.mbar);
+}
+// wait for the MMAs committed last (every thread); false for every thread
+// when they did not complete within the bound
+__device__ __forceinline__ bool wait_mmas(Tile &t, uint32_t &phase) {
+  const bool ok = mbar_wait(&t.mbar, phase);
+  phase ^= 1u;
+  if (__syncthreads_or(!ok)) return false;
+  fence_after();
+  return true;
 }
 
 // wait for the network's bulk copy (the mbarrier phase of parity `phase`);
@@ -214,26 +260,14 @@ __device__ __forceinline__ bool forward_tile(Tile &t, uint32_t &phase, float &y)
   static_assert(NT == 128 || NT == 256, "one or two warps per 32 rows");
   constexpr int CPW = NT == 128 ? 64 : 32;  // columns per warp in the epilogues
   const int tid = threadIdx.x, w = tid >> 5, row = tid & (ROWS - 1), col0 = (w >> 2) * CPW;
-  constexpr uint32_t ID = idesc_bf16(ROWS, 64);
   const uint32_t tm = t.tmem, lanes = (uint32_t)(32 * (w & 3)) << 16;
   // layer 1
-  fence_async_smem();
-  fence_before();
-  __syncthreads();
-  fence_after();
-  if (tid == 0) {
-    const uint32_t a = smem_u32(t.a1), b = smem_u32(t.net.w1);
-#pragma unroll
-    for (int s = 0; s < 2; ++s) mma(tm, desc(a + 256 * s, 128, 512), desc(b + 256 * s, 128, 512), ID, s);
-    commit(&t.mbar);
-  }
-  bool ok = mbar_wait(&t.mbar, phase);
-  phase ^= 1u;
-  if (__syncthreads_or(!ok)) {
+  to_tensor_cores();
+  if (tid == 0) issue(t, tm, t.a1, t.net.w1, 32, 64, 2, false);
+  if (!wait_mmas(t, phase)) {
     y = __int_as_float(0x7fc00000);
     return false;
   }
-  fence_after();
   // epilogue 1: Z1 + b1 -> SiLU -> BF16 into a2 (this warp's columns)
 #pragma unroll
   for (int c = 0; c < CPW / 16; ++c) {
@@ -253,23 +287,12 @@ __device__ __forceinline__ bool forward_tile(Tile &t, uint32_t &phase, float &y)
     }
   }
   // layer 2
-  fence_async_smem();
-  fence_before();
-  __syncthreads();
-  fence_after();
-  if (tid == 0) {
-    const uint32_t a = smem_u32(t.a2), b = smem_u32(t.net.w2);
-#pragma unroll
-    for (int s = 0; s < 4; ++s) mma(tm + 64, desc(a + 256 * s, 128, 1024), desc(b + 256 * s, 128, 1024), ID, s);
-    commit(&t.mbar);
-  }
-  ok = mbar_wait(&t.mbar, phase);
-  phase ^= 1u;
-  if (__syncthreads_or(!ok)) {
+  to_tensor_cores();
+  if (tid == 0) issue(t, tm + 64, t.a2, t.net.w2, 64, 64, 4, false);
+  if (!wait_mmas(t, phase)) {
     y = __int_as_float(0x7fc00000);
     return false;
   }
-  fence_after();
   // epilogue 2: SiLU(Z2 + b2) rounded to BF16, dot with W3, + b3
   float acc = 0.f;
 #pragma unroll
@@ -290,14 +313,14 @@ __device__ __forceinline__ bool forward_tile(Tile &t, uint32_t &phase, float &y)
   return true;
 }
 
-// release the tensor memory (every thread of the CTA); after a timed-out
-// wait the mbarrier is given one more bounded wait first
-__device__ __forceinline__ void teardown(Tile &t, uint32_t phase, bool failed) {
+// release the ncols columns of tensor memory (every thread of the CTA);
+// after a timed-out wait the mbarrier is given one more bounded wait first
+__device__ __forceinline__ void teardown(Tile &t, uint32_t phase, bool failed, uint32_t ncols = TCOLS) {
   if (failed && threadIdx.x == 0) (void)mbar_wait(&t.mbar, phase ^ 1u);
   fence_before();
   __syncthreads();
   fence_after();
-  if (threadIdx.x < 32) tmem_dealloc(t.tmem, TCOLS);
+  if (threadIdx.x < 32) tmem_dealloc(t.tmem, ncols);
 }
 
 }  // namespace tc
