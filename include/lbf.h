@@ -234,8 +234,11 @@ const char *lbf_last_error(void);
  * (dz+1)*9 + (dy+1)*3 + (dx+1); axes reflected so the interface normal is
  * non-negative, then ordered by increasing normal component) -> 64 -> 64 -> 1
  * with SiLU; output y = 4 kappa.  BF16 weights and activations, FP32
- * accumulation, tensor cores.  Parameters theta: 6017 FP32 values, W1 (64x27
- * row-major), b1 (64), W2 (64x64), b2 (64), W3 (64), b3 (1).
+ * accumulation in tensor memory (tcgen05 MMAs on tiles of 128 rows).
+ * Parameters theta: 6017 FP32 values, W1 (64x27 row-major), b1 (64), W2
+ * (64x64), b2 (64), W3 (64), b3 (1).  Every wait of these kernels on the
+ * tensor cores is bounded (about half a second); past the bound a kernel
+ * frees its tensor memory and reports NaN in its outputs or loss.
  */
 typedef struct {
   unsigned long long seed; /* counter-based generator seed                   */
@@ -253,11 +256,14 @@ typedef struct {
 } lbf_mlp_train_cfg;
 
 /* y[i] for n canonical stencils x (device, n x 27 FP32); theta and y are
- * device pointers.  Asynchronous on `stream`.  Errors: LBF_EINVAL. */
+ * device pointers.  Asynchronous on `stream`; allocates nothing.
+ * Errors: LBF_EINVAL. */
 int lbf_mlp_forward(const float *theta, const float *x, int n, float *y, void *stream);
 /* Loss 0.5 mean((y - t)^2) of n stencils x with targets t (all device) and
  * its gradient: grad (device, 6017 FP32) and *loss (device, one double) are
- * overwritten.  Asynchronous.  Errors: LBF_EINVAL. */
+ * overwritten.  Asynchronous; takes a 21 KB packed copy of the network
+ * from the stream's memory pool for the call.  Errors: LBF_EINVAL,
+ * LBF_ECUDA. */
 int lbf_mlp_loss_grad(const float *theta, const float *x, const float *t, int n, float *grad, double *loss,
                       void *stream);
 /* n synthetic training pairs (canonical stencil, y = 4 kappa) into device
