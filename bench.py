@@ -299,12 +299,15 @@ def algorithmic_bytes_step(counts, storage_bytes, Q=19, QA=7):
 
 
 def reduce_max(x: float, world: int) -> float:
+    """The largest x over the ranks (the slowest rank's time); the tensor
+    lives where the process group's backend reduces (NCCL: the GPU)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
