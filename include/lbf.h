@@ -151,7 +151,9 @@ int lbf_set_cells(lbf_sim *s, const uint8_t *type, const double *rho, const doub
  * the first after lbf_mlp_attach or lbf_checkpoint_load) captures and
  * instantiates every graph shape for both parities before any step runs.
  * Synchronises at the end and returns the sticky device error, if any
- * (LBF_ECAPACITY, LBF_ENOTCONV).  Errors: LBF_EINVAL (nsteps < 0). */
+ * (LBF_ECAPACITY, LBF_ENOTCONV; LBF_ECUDA when a wait of the learned
+ * curvature on the tensor cores ran past its bound).  Errors: LBF_EINVAL
+ * (nsteps < 0). */
 int lbf_step(lbf_sim *s, int nsteps);
 
 /* Copy the bubble table to host memory: out has room for capacity rows;

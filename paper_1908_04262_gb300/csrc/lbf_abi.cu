@@ -650,6 +650,7 @@ int check_device_error(lbf_sim *s) {
   if (e & ERR_CAPACITY) return fail(LBF_ECAPACITY, "more bubbles than bubble_capacity");
   if (e & ERR_NOTCONV) return fail(LBF_ENOTCONV, "union-find iteration cap reached");
   if (e & ERR_HASH) return fail(LBF_ECAPACITY, "bubble overlap table full");
+  if (e & ERR_TC_WAIT) return fail(LBF_ECUDA, "learned curvature: a tensor-core wait ran past its bound");
   return 0;
 }
 

@@ -17,7 +17,8 @@ namespace lbf {
 // r.  The least-squares curvature stays where the network is outside its
 // training range (|kappa| outside [0.02, 0.55], i.e. radii beyond [1.8, 50]
 // cells) or the stencil touches a wall, and everywhere once a wait has not
-// completed within its bound.
+// completed within its bound (which also sets ERR_TC_WAIT: lbf_step then
+// fails with LBF_ECUDA).
 constexpr int MLP_THREADS = 256;
 template <int D, class R>
 __global__ void __launch_bounds__(MLP_THREADS) k_mlp_kappa(Params p, const tc::Image *img) {
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_kappa(Params p, const tc::I
       }
       __syncthreads();
     }
+    if (failed && tid == 0) atomicOr(p.err, ERR_TC_WAIT);
     tc::teardown(t, phase, failed);
   }
 }
