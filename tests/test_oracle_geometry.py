@@ -1,6 +1,7 @@
 """Pins of the oracle's geometry (Sec. 2.2 curvature, Sec. 3.3 PLIC and
 disjoining pressure, Appendix A traversal)."""
 import itertools
+import math
 
 import numpy as np
 import pytest
@@ -131,3 +132,77 @@ def test_plic_degenerate_normals(oracle_mod):
         assert abs(oracle_mod.plic_liquid_fraction(3, [0.0, tiny, -1.0], 0.3) - 0.2) < 1e-12
         assert abs(oracle_mod.plic_liquid_fraction(3, [tiny, 1.0, tiny], -0.25) - 0.75) < 1e-12
         assert abs(oracle_mod.plic_liquid_fraction(2, [tiny, -1.0], 0.1) - 0.4) < 1e-12
+
+
+def _cube_fraction_below(t, dim):
+    """Volume of the unit cell [-1/2, 1/2]^dim where u_1 + ... + u_dim <= t:
+    the Irwin-Hall distribution function of dim uniforms at t + dim/2."""
+    x = t + dim / 2.0
+    if x <= 0.0:
+        return 0.0
+    if x >= dim:
+        return 1.0
+    return sum((-1) ** k * math.comb(dim, k) * max(0.0, x - k) ** dim for k in range(dim + 1)) / math.factorial(dim)
+
+
+@pytest.mark.parametrize("dim,axes", [(2, 2), (3, 2), (3, 3)])
+def test_oblique_film_disjoining_pressure(oracle_mod, dim, axes):
+    """A planar film along a lattice diagonal, w = x + y (axes = 2) or
+    w = x + y + z (axes = 3): gas A for w in (1.3, 5.3), the film for
+    (5.3, 8.7), gas B for (8.7, 12.7), liquid elsewhere (period 24 in w, as
+    the periodic box gives).  Fill levels are exact cut volumes
+    (Irwin-Hall over the axes the plane is oblique to), so the Parker-Youngs
+    normal is the diagonal (by the symmetry of its weights) and every PLIC
+    plane is exact.  The ray of Algorithm 1 steps diagonally (w + axes per
+    cell) across the film (Sec. 3.3, Pi = k_Pi (d_max - d)):
+
+    * axes = 2 (D2Q9, or D3Q19 with its xy edge links): every face cell has
+      a gas lattice neighbour, hence a bubble, and its ray meets the other
+      face's plane: d = 3.4 / sqrt(2), the film thickness;
+    * axes = 3 (D3Q19 has no corner links): the face layers at 0.3 from a
+      plane (w = 5, 9) and at 1.3 (w = 4, 10) touch their gas through
+      lattice links, the layers at 0.7 (w = 6, 8) only through corners, so
+      they belong to no bubble (Pi = 0) and rays pass through them.  From
+      w = 4 the ray meets w = 10, a face cell of bubble B: d = 3.4 / sqrt(3).
+      From w = 5 it passes w = 8 and enters B's gas at w = 11, 1.5 sqrt(3)
+      along the ray, whose own plane lies 0.3 / sqrt(3) ahead of the
+      centre: d = 1.5 sqrt(3) - 0.3 / sqrt(3) (and alike from B's side).
+
+    Faces towards the thick liquid (12.6 / sqrt(axes) away, beyond d_max)
+    get Pi = 0.  With axes = 2 in 3D the steps have no z offset, so a
+    distance that mixes up the z component with another fails."""
+    kpi, dmax, N = 2e-3, 4.0, 24
+    gas = [(1.3, 5.3), (8.7, 12.7)]
+    cfg = W.config(nx=N, ny=N, nz=N if dim == 3 else 1, k_pi=kpi, d_max=dmax, atmosphere=0)
+    s = oracle_mod.OracleSim(cfg)
+    idx = np.arange(s.N)
+    x, y, z = idx % N, (idx // N) % N, idx // (N * N)
+    w = np.mod(x + y + (z if axes == 3 else 0), N).astype(float)
+    alpha = np.ones(s.N)
+    for i, wi in enumerate(w):
+        g = 0.0
+        for lo, hi in gas:
+            for img in (-N, 0, N):
+                g += _cube_fraction_below(hi + img - wi, axes) - _cube_fraction_below(lo + img - wi, axes)
+        alpha[i] = 1.0 - g
+    t = np.where(alpha >= 1.0, oracle_mod.LIQ, np.where(alpha <= 0.0, oracle_mod.GAS, oracle_mod.IFC)).astype(np.uint8)
+    s.set_cells(t, np.ones(s.N), np.zeros((s.N, 3)), alpha, np.zeros(s.N))
+    assert s.bubbles()["mass"].size == 2
+    ifc = t == oracle_mod.IFC
+    face_a = ifc & (np.abs(w - 5.3) < axes / 2.0)
+    face_b = ifc & (np.abs(w - 8.7) < axes / 2.0)
+    assert face_a.sum() == face_b.sum() == axes * N ** (dim - 1)
+    diag = np.ones(3) * (np.arange(3) < axes) / math.sqrt(axes)
+    nrm = s.get("normal")
+    assert np.allclose(nrm[face_a], diag, rtol=0, atol=1e-12)
+    assert np.allclose(nrm[face_b], -diag, rtol=0, atol=1e-12)
+    Pi, lab = s.get("pi"), s.labels()
+    film = kpi * (dmax - 3.4 / math.sqrt(axes))
+    want = np.zeros(s.N)
+    if axes == 2:
+        want[face_a | face_b] = film
+    else:
+        want[(w == 4) | (w == 10)] = film
+        want[(w == 5) | (w == 9)] = kpi * (dmax - (1.5 * math.sqrt(3) - 0.3 / math.sqrt(3)))
+        assert np.all(lab[(w == 6) | (w == 8)] == -1)
+    assert np.allclose(Pi, want, rtol=1e-9, atol=0)
