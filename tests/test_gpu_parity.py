@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from paper_1908_04262_gb300 import workloads as W
+from tests import films
 from tests._parity import compare_state, rel_err
 
 pytestmark = pytest.mark.gpu
@@ -142,6 +143,31 @@ def test_geometry_fp64(lbf, oracle_mod):
     assert rel_err(g["kappa"][I], ora.get("kappa")[I]) < 1e-9
     assert rel_err(g["pi"][I], ora.get("pi")[I]) < 1e-9
     assert np.max(ora.get("pi")) > 0  # the pair is within reach
+
+
+@pytest.mark.parametrize("dim,axes", [(2, 2), (3, 2), (3, 3)])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-9), ("fp32", 1e-5)])
+def test_disjoining_diagonal_films(lbf, oracle_mod, dim, axes, storage, tol):
+    """Disjoining pressure of planar films along the lattice diagonals (the
+    oracle's closed-form pin): diagonal ray steps, the hit plane's distance
+    and, along (1,1,1), the corner-only face layers that belong to no bubble
+    and that rays pass through."""
+    N = 24
+    cfg = W.config(nx=N, ny=N, nz=N if dim == 3 else 1, storage=storage, k_pi=2e-3, d_max=4.0, atmosphere=0)
+    w, t, alpha = films.diagonal_film(N, dim, axes, 1, 0, 2)
+    one, zero, zero3 = np.ones(t.size), np.zeros(t.size), np.zeros((t.size, 3))
+    ora = oracle_mod.OracleSim(cfg)
+    ora.set_cells(t, one, zero3, alpha, zero)
+    sim = lbf.Sim(cfg)
+    sim.set_cells(t, one, zero3, alpha, zero)
+    g = sim.fields(["flags", "label", "pi"])
+    assert np.array_equal(g["flags"], ora.types())
+    assert np.array_equal(g["label"], ora.labels())
+    ref = ora.get("pi")
+    assert np.max(ref) > 0
+    assert rel_err(g["pi"], ref) < tol
+    assert np.array_equal(g["pi"] > 0, ref > 0)
+    sim.close()
 
 
 def test_mass_ledger_gpu(lbf):

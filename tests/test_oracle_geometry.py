@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from paper_1908_04262_gb300 import workloads as W
+from tests import films
 
 
 def _gas_fraction_incl_excl(m, a):
@@ -134,16 +135,6 @@ def test_plic_degenerate_normals(oracle_mod):
         assert abs(oracle_mod.plic_liquid_fraction(2, [tiny, -1.0], 0.1) - 0.4) < 1e-12
 
 
-def _cube_fraction_below(t, dim):
-    """Volume of the unit cell [-1/2, 1/2]^dim where u_1 + ... + u_dim <= t:
-    the Irwin-Hall distribution function of dim uniforms at t + dim/2."""
-    x = t + dim / 2.0
-    if x <= 0.0:
-        return 0.0
-    if x >= dim:
-        return 1.0
-    return sum((-1) ** k * math.comb(dim, k) * max(0.0, x - k) ** dim for k in range(dim + 1)) / math.factorial(dim)
-
 
 @pytest.mark.parametrize("dim,axes", [(2, 2), (3, 2), (3, 3)])
 def test_oblique_film_disjoining_pressure(oracle_mod, dim, axes):
@@ -172,20 +163,9 @@ def test_oblique_film_disjoining_pressure(oracle_mod, dim, axes):
     get Pi = 0.  With axes = 2 in 3D the steps have no z offset, so a
     distance that mixes up the z component with another fails."""
     kpi, dmax, N = 2e-3, 4.0, 24
-    gas = [(1.3, 5.3), (8.7, 12.7)]
     cfg = W.config(nx=N, ny=N, nz=N if dim == 3 else 1, k_pi=kpi, d_max=dmax, atmosphere=0)
     s = oracle_mod.OracleSim(cfg)
-    idx = np.arange(s.N)
-    x, y, z = idx % N, (idx // N) % N, idx // (N * N)
-    w = np.mod(x + y + (z if axes == 3 else 0), N).astype(float)
-    alpha = np.ones(s.N)
-    for i, wi in enumerate(w):
-        g = 0.0
-        for lo, hi in gas:
-            for img in (-N, 0, N):
-                g += _cube_fraction_below(hi + img - wi, axes) - _cube_fraction_below(lo + img - wi, axes)
-        alpha[i] = 1.0 - g
-    t = np.where(alpha >= 1.0, oracle_mod.LIQ, np.where(alpha <= 0.0, oracle_mod.GAS, oracle_mod.IFC)).astype(np.uint8)
+    w, t, alpha = films.diagonal_film(N, dim, axes, oracle_mod.LIQ, oracle_mod.GAS, oracle_mod.IFC)
     s.set_cells(t, np.ones(s.N), np.zeros((s.N, 3)), alpha, np.zeros(s.N))
     assert s.bubbles()["mass"].size == 2
     ifc = t == oracle_mod.IFC
