@@ -189,6 +189,51 @@ def test_filling_wins_over_emptying(oracle_mod):
     _check(s, types, mass)
 
 
+@pytest.mark.parametrize("emptying", [False, True])
+def test_new_interface_cells_take_the_mean_of_their_interface_neighbours(oracle_mod, emptying):
+    """(3, 3) fills and the gas cells (2..4, 4) above it turn interface.
+    Each starts at the equilibrium (Sec. 2 Eq. equilibrium) of the mean
+    density, velocity and dissolved gas of its lattice neighbours that were
+    interface and not emptying, the filling cell included (the reading of
+    the paper's silence on new interface cells):
+        (2, 4) <- (1, 3), (2, 3), (3, 3)
+        (3, 4) <- (2, 3), (3, 3), (4, 3)
+        (4, 4) <- (3, 3), (4, 3), (5, 3)
+    with the post-collision moments of those cells (what the oracle holds
+    for them after the step: the conversion changes only masses and fill
+    levels).  Random densities, velocities and concentrations make another
+    neighbour set, a weighted mean or the cell's own old values visible.
+    With `emptying`, (5, 3) (two cells from the filling one, so it may
+    empty) holds -0.3 and drops out of the mean of (4, 4)."""
+    rng = np.random.default_rng(11)
+    t, _, _, alpha = _uniform_case({(3, 3): 1.3, (5, 3): -0.3 if emptying else 0.5})
+    N = NX * NY
+    rho = rng.uniform(0.98, 1.02, N)
+    u = np.zeros((N, 3))
+    u[:, :2] = rng.uniform(-0.01, 0.01, (N, 2))
+    conc = rng.uniform(0.2, 0.8, N)
+    s = oracle_mod.OracleSim(cfg())
+    s.set_cells(t, rho, u.reshape(-1), alpha, conc)
+    s.step(1)
+    ty = s.types()
+    assert ty[idx(3, 3)] == L_
+    R, U, C, F = s.get("rho"), s.get("u"), s.get("conc"), s.get("fpop")
+    sources = {(2, 4): [(1, 3), (2, 3), (3, 3)], (3, 4): [(2, 3), (3, 3), (4, 3)],
+               (4, 4): [(3, 3), (4, 3)] + ([] if emptying else [(5, 3)])}
+    assert ty[idx(5, 3)] == (G_ if emptying else I_)
+    for cell, nbs in sources.items():
+        n = idx(*cell)
+        m = [idx(*c) for c in nbs]
+        assert ty[n] == I_, cell
+        rb, ub, cb = np.mean(R[m]), np.mean(U[m], axis=0), np.mean(C[m])
+        assert abs(R[n] - rb) < 1e-14, cell
+        assert np.max(np.abs(U[n] - ub)) < 1e-14, cell
+        assert abs(C[n] - cb) < 1e-14, cell
+        # the populations are that equilibrium (compared as a set: the
+        # order of the directions is the oracle's own)
+        assert np.max(np.abs(np.sort(F[n]) - np.sort(feq(rb, ub[:2])))) < 1e-14, cell
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_least_squares_curvature_of_exact_quadrics(oracle_mod, dim):
     """The least-squares fit of the curvature (Sec. 2.2 Eq. rhob, the
