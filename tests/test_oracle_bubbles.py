@@ -93,6 +93,34 @@ def test_new_bubble_starts_in_laplace_equilibrium(oracle_mod):
     assert abs(b["mass"][0] - b["pressure"][0] * b["volume"][0] / 0.5) < 1e-12
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_nucleated_volume_matches_the_disk_or_sphere(oracle_mod, dim):
+    """Nucleation carves fill levels from 4^d sub-cell points per cell (the
+    fraction outside the sphere is the liquid fraction): the bubble's
+    volume (gas cells + sum of 1 - alpha over its interface cells) is the
+    disk's or sphere's within a bound that falls like 1/R -- 0.05/R in 2D,
+    0.03/R in 3D, against measured errors of 1.2 % (2D) and 0.16 % (3D) at
+    R = 2.7.  Carving whole cells by their centres (no sub-points) breaks
+    the bound in 8 of the 12 2D cases and 5 of the 12 3D cases below (up to
+    0.14/R and 0.08/R); taking the sampled fraction inside the sphere as the
+    liquid fraction misses by far more."""
+    import math
+
+    rng = np.random.default_rng(3)
+    for R in (2.7, 4.3, 6.1, 9.4):
+        for _ in range(3):
+            n = int(2 * R + 8)
+            cfg = W.config(nx=n, ny=n, nz=n if dim == 3 else 1, atmosphere=0)
+            s = oracle_mod.OracleSim(cfg)
+            c = n / 2 + rng.uniform(-0.5, 0.5, 3)
+            if dim == 2:
+                c[2] = 0.0
+            s.nucleate([list(c)], [R])
+            V = s.bubbles()["volume"][0]
+            exact = math.pi * R * R if dim == 2 else 4.0 / 3.0 * math.pi * R ** 3
+            assert abs(V / exact - 1.0) < (0.05 if dim == 2 else 0.03) / R, (dim, R, V, exact)
+
+
 def _two_bubbles(oracle_mod, RT=0.2):
     """Two disks separated by a thin liquid lamella (2D, periodic)."""
     cfg = W.config(nx=40, ny=24, nz=1, sigma=0.01, RT=RT, atmosphere=0)
