@@ -1,5 +1,6 @@
 """Pins of the oracle's advection-diffusion step (Sec. 3.1-3.2)."""
 import numpy as np
+import pytest
 
 from paper_1908_04262_gb300 import workloads as W
 
@@ -74,3 +75,39 @@ def test_gas_ledger_closes_for_static_interface(oracle_mod):
     t0 = total()
     s.step(300)
     assert abs(total() - t0) < 1e-12
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_advection_moves_the_centroid_at_the_flow_velocity(oracle_mod, dim):
+    """Sec. 3.1 Eq. diffusion with the equilibrium g_eq = w_i c (1 + e_i.u /
+    c_s^2): in a uniform periodic liquid moving at u0 (no force, no walls,
+    density 1.02) the flow stays uniform, and from g = g_eq(c, u0) the
+    collision keeps the lattice-wide first moment at u0 sum(c) (the first
+    moment of g_eq is c u0, and relaxing towards it keeps the sum there), so
+    the centroid of a concentration pulse moves by exactly u0 per step as
+    long as nothing crosses the periodic faces: the populations move one
+    cell per step, so a pulse of radius 4 stays inside radius 14 for 10
+    steps, inside the box of 32.  Fails for a flipped advective sign (-u0),
+    a missing 1/c_s^2 (u0/3 in D2Q5) or the momentum rho u in place of u
+    (1.02 u0)."""
+    n = 32
+    u0 = np.array([0.05, -0.03, 0.02]) * (np.arange(3) < dim)
+    cfg = W.config(nx=n, ny=n, nz=n if dim == 3 else 1, tau=0.8, D=0.05, c0=0.0, kH=0.0, atmosphere=0)
+    s = oracle_mod.OracleSim(cfg)
+    t = s.types()
+    assert np.all(t == oracle_mod.LIQ)
+    idx = np.arange(s.N)
+    X = np.stack([idx % n, (idx // n) % n, idx // (n * n)], 1).astype(float)
+    centre = np.array([n / 2 - 0.3, n / 2 + 0.2, (n / 2 + 0.1) if dim == 3 else 0.0])
+    conc = np.maximum(0.0, 1.0 - np.sum((X - centre) ** 2, 1) / 16.0) ** 2
+    s.set_cells(t, np.full(s.N, 1.02), np.tile(u0, s.N), np.ones(s.N), conc)
+
+    def centroid():
+        c = s.get("conc")
+        return (c @ X) / c.sum()
+
+    x0 = centroid()
+    T = 10
+    s.step(T)
+    assert np.max(np.abs(s.get("u") - u0)) < 1e-14
+    assert np.max(np.abs(centroid() - x0 - T * u0)) < 1e-12
