@@ -111,3 +111,41 @@ def test_advection_moves_the_centroid_at_the_flow_velocity(oracle_mod, dim):
     s.step(T)
     assert np.max(np.abs(s.get("u") - u0)) < 1e-14
     assert np.max(np.abs(centroid() - x0 - T * u0)) < 1e-12
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_diffusion_spreads_the_pulse_by_the_lattice_closed_form(oracle_mod, dim):
+    """Sec. 3.1 Eq. diffusion at rest, worked out on the lattice: with
+    omega = 1 / tau_g, tau_g = 1/2 + D / c_s^2 (c_s^2 = 1/3 on D2Q5, 1/4 on
+    D3Q7) and g = g_eq(c, 0) at the start, the lattice-wide second moment
+    of the ADE populations stays c_s^2 sum(c) and K = sum x J_x obeys
+    K(t+1) = (1 - omega) K(t) + c_s^2 C, K(0) = 0, so along every axis
+
+        Var(t) - Var(0) = sum_{k<t} c_s^2 [1 + 2 (1 - omega) (1 - (1 - omega)^k) / omega]
+
+    (slope 2 D for large t), exactly, while nothing crosses the periodic
+    faces (a pulse of radius 4 for 10 steps in a box of 32).  Fails for a
+    wrong c_s^2 of either lattice, a relaxation rate that misses the 1/2 of
+    tau_g, or equilibrium weights with another second moment."""
+    n, T, D = 32, 10, 0.05
+    cs2 = 1.0 / 3.0 if dim == 2 else 0.25
+    om = 1.0 / (0.5 + D / cs2)
+    cfg = W.config(nx=n, ny=n, nz=n if dim == 3 else 1, tau=0.8, D=D, c0=0.0, kH=0.0, atmosphere=0)
+    s = oracle_mod.OracleSim(cfg)
+    t = s.types()
+    assert np.all(t == oracle_mod.LIQ)
+    idx = np.arange(s.N)
+    X = np.stack([idx % n, (idx // n) % n, idx // (n * n)], 1)[:, :dim].astype(float)
+    centre = np.array([n / 2 - 0.3, n / 2 + 0.2, n / 2 + 0.1])[:dim]
+    conc = np.maximum(0.0, 1.0 - np.sum((X - centre) ** 2, 1) / 16.0) ** 2
+    s.set_cells(t, np.ones(s.N), np.zeros((s.N, 3)), np.ones(s.N), conc)
+
+    def variance():
+        c = s.get("conc")
+        m = (c @ X) / c.sum()
+        return (c @ (X - m) ** 2) / c.sum()
+
+    v0 = variance()
+    s.step(T)
+    grow = sum(cs2 * (1.0 + 2.0 * (1.0 - om) * (1.0 - (1.0 - om) ** k) / om) for k in range(T))
+    assert np.max(np.abs(variance() - v0 - grow)) < 1e-11
