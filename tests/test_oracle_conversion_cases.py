@@ -189,6 +189,18 @@ def test_filling_wins_over_emptying(oracle_mod):
     _check(s, types, mass)
 
 
+@pytest.mark.parametrize("a,kind", [(1.0005, I_), (1.0015, L_), (-0.0005, I_), (-0.0015, G_)])
+def test_conversion_thresholds(oracle_mod, a, kind):
+    """Sec. 2.1's thresholds alpha >= 1 and alpha <= 0 with the margin
+    epsilon = 1e-3 of the reading: a cell fills when M > (1 + eps) rho and
+    empties when M < -eps rho.  In the uniform state every exchange term is
+    zero, so M stays alpha rho through the step: (3, 3) at alpha just inside
+    a threshold keeps its type, just beyond it converts."""
+    t, rho, u, alpha = _uniform_case({(3, 3): a})
+    s, M0 = run_one_step(oracle_mod, t, rho, u, alpha)
+    assert s.types()[idx(3, 3)] == kind
+
+
 @pytest.mark.parametrize("emptying", [False, True])
 def test_new_interface_cells_take_the_mean_of_their_interface_neighbours(oracle_mod, emptying):
     """(3, 3) fills and the gas cells (2..4, 4) above it turn interface.
