@@ -1,11 +1,14 @@
-// lbf_tc.cuh -- the network's two hidden-layer products on the
+// lbf_tc.cuh -- the learned-curvature network's products on the
 // fifth-generation tensor cores (tcgen05): operand tiles in shared memory
 // (K-major, no swizzle), the FP32 accumulators in tensor memory, one
 // elected thread issuing the BF16 MMAs and committing them to an mbarrier,
-// the epilogues reading the accumulators back with tcgen05.ld.  Inline PTX
-// for sm_103a.
+// the epilogues reading the accumulators back with tcgen05.ld, the packed
+// network brought into shared memory by bulk copies.  Inline PTX for
+// sm_103a.  The forward tile below serves inference; the gradient kernel
+// (lbf_mlp.cu) uses the same set-up, issue, wait and load helpers for its
+// own products.
 //
-// Tile of one CTA (128 or 256 threads; in the epilogues thread t holds row
+// Forward tile of one CTA (128 or 256 threads; in the epilogues thread t holds row
 // t mod 128, and with 256 threads each pair of warps on the same rows
 // splits the 64 columns):
 //   layer 1: Z1 (128 x 64) = X (128 x 32, 27 inputs used) W1^T, 2 MMAs of K 16
