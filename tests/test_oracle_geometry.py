@@ -83,12 +83,11 @@ def test_curvature_of_voxelised_bubble(oracle_mod, dim, n, R, lo, hi):
     assert np.allclose(np.linalg.norm(nrm, axis=1), 1.0)
 
 
-def _film(oracle_mod, L, aa, ab, kpi=2e-3, dmax=4.0):
+def _film(oracle_mod, L, aa, ab, kpi=2e-3, dmax=4.0, nz=16, sigma=0.0):
     """Planar lamella between two bubbles: walls at z = 0 and z = nz-1,
     gas A below, interface (alpha_a) at za, L liquid layers, interface
     (alpha_b) at zb = za + L + 1, gas B above."""
-    nz = 16
-    cfg = W.config(nx=4, ny=4, nz=nz, walls=0x30, k_pi=kpi, d_max=dmax, atmosphere=0)
+    cfg = W.config(nx=4, ny=4, nz=nz, walls=0x30, k_pi=kpi, d_max=dmax, atmosphere=0, sigma=sigma)
     s = oracle_mod.OracleSim(cfg)
     z = np.arange(s.N) // 16
     za = 4
@@ -120,6 +119,29 @@ def test_planar_film_disjoining_pressure(oracle_mod, L, aa, ab):
     assert np.allclose(Pi[z == za], want, rtol=0, atol=1e-14)
     assert np.allclose(Pi[z == zb], want, rtol=0, atol=1e-14)
     assert np.all(Pi[(z != za) & (z != zb)] == 0.0)
+
+
+@pytest.mark.parametrize("L,kpi", [(1, 2e-3), (2, 2e-3), (2, 4e-3)])
+def test_film_liquid_settles_at_gas_pressure_minus_disjoining(oracle_mod, L, kpi):
+    """Sec. 3.3 Eq. rhobplusdisjoining at rest: a symmetric planar film (3
+    gas layers on either side, so both bubbles keep one pressure) with
+    sigma = 0.01 -- a plane's curvature is 0, so the Laplace term drops out
+    -- settles to a state with no flow in which the liquid's pressure
+    c_s^2 rho equals p_g - Pi.  Fails for Pi added instead of subtracted
+    (off by 2 Pi), Pi left out (off by Pi), or the gas density without its
+    factor 1 / c_s^2."""
+    s, z, za, zb = _film(oracle_mod, L, 0.5, 0.5, kpi, nz=4 + L + 1 + 3 + 2, sigma=0.01)
+    s.step(500)
+    t = s.types()
+    assert np.sum(t == oracle_mod.IFC) == 32
+    assert np.max(np.abs(s.get("u"))) < 1e-9
+    p = s.bubbles()["pressure"]
+    assert p.size == 2 and abs(p[0] - p[1]) < 1e-12
+    Pi = s.get("pi")[t == oracle_mod.IFC]
+    assert np.all(Pi > 0) and np.ptp(Pi) < 1e-12
+    assert np.all(s.get("kappa")[t == oracle_mod.IFC] == 0.0)
+    rho = s.get("rho")[t == oracle_mod.LIQ]
+    assert np.max(np.abs(rho / 3.0 - (p[0] - Pi[0]))) < 1e-9
 
 
 def test_disjoining_off_beyond_cutoff(oracle_mod):
