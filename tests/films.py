@@ -1,4 +1,4 @@
-"""Seeded-free geometric inputs shared by the oracle pins and the GPU parity
+"""Deterministic geometric inputs shared by the oracle pins and the GPU parity
 tests: planar films along lattice diagonals with exact fill levels."""
 import math
 
