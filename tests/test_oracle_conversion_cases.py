@@ -165,6 +165,61 @@ def test_reconstruction_at_gas_links(oracle_mod):
         assert np.max(np.abs(R[n] * U[n][:2] - j)) < 1e-14, (x, R[n] * U[n][:2], j)
 
 
+def test_henry_reconstruction_and_gas_flux(oracle_mod):
+    """Sec. 3.2 Eq. henryslaw / reconstructdiffusion and Sec. 3.1 Eq.
+    gascurrent (as read: the exchange at the gas links) on the flat
+    interface row, random rho, u and dissolved gas, k_H = 0.7, sigma = 0.02:
+    the D2Q5 populations arriving at an interface cell x from its gas
+    neighbour are g_eq_i(k_H p_g, u_I) + g_eq_ibar(k_H p_g, u_I) - g_ibar(x)
+    (g_eq_i(c, u) = w_i c (1 + 3 e_i.u), w = 1/3, 1/6), the others stream
+    from liquid and interface neighbours; the collision conserves c, so
+    after one step the cell's c is the sum of the arrivals, and the bubble
+    has gained, over its interface cells, what they sent into the gas minus
+    what Henry's law returned: sum (g_ibar(x) - g_i).  Fails for the
+    Henry concentration without k_H or with p0 in place of the bubble's
+    pressure, a missing -g_ibar(x), or a flux of the opposite sign."""
+    rng = np.random.default_rng(17)
+    t = layout()
+    N = NX * NY
+    rho = rng.uniform(0.98, 1.02, N)
+    u = rng.uniform(-0.02, 0.02, (N, 2))
+    u3 = np.zeros((N, 3))
+    u3[:, :2] = u
+    c = rng.uniform(0.1, 0.9, N)
+    alpha = np.where(t == I_, 0.5, 0.0)
+    kH = 0.7
+    s = oracle_mod.OracleSim(dict(cfg(), sigma=0.02, kH=kH))
+    s.set_cells(t, rho, u3.reshape(-1), alpha, c)
+    b0 = s.bubbles()
+    assert b0["pressure"].size == 1 and abs(b0["pressure"][0] - 1.0 / 3.0) > 1e-4
+    cH = kH * b0["pressure"][0]
+    s.step(1)
+    assert np.array_equal(s.types(), t)
+    EA, WA = E[:5], [1 / 3] + [1 / 6] * 4
+
+    def geq(cc, uu):
+        return np.array([WA[i] * cc * (1 + 3 * (ex * uu[0] + ey * uu[1])) for i, (ex, ey) in enumerate(EA)])
+
+    C = s.get("conc")
+    flux = 0.0
+    for x in range(NX):
+        n = idx(x, 3)
+        gin = np.zeros(5)
+        for i, (ex, ey) in enumerate(EA):
+            ib = EA.index((-ex, -ey))
+            m = idx(x - ex, 3 - ey)
+            if i == 0 or t[m] in (L_, I_):
+                gin[i] = geq(c[m], u[m])[i]
+            else:
+                assert t[m] == G_
+                gin[i] = geq(cH, u[n])[i] + geq(cH, u[n])[ib] - geq(c[n], u[n])[ib]
+                flux += geq(c[n], u[n])[ib] - gin[i]
+        assert abs(C[n] - gin.sum()) < 1e-14, (x, C[n], gin.sum())
+    b1 = s.bubbles()
+    assert abs(flux) > 1e-3
+    assert abs(b1["mass"][0] - (b0["mass"][0] + flux)) < 1e-14, (b1["mass"][0], b0["mass"][0] + flux)
+
+
 def _uniform_case(alpha_of):
     """rho = 1 and u = 0 everywhere: every exchange term is w_i - w_i = 0, so
     only the conversion changes the masses."""
