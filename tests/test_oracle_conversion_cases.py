@@ -163,6 +163,8 @@ def test_reconstruction_at_gas_links(oracle_mod):
         j = fin @ np.array(E, float)
         assert abs(R[n] - r) < 1e-14, (x, R[n], r)
         assert np.max(np.abs(R[n] * U[n][:2] - j)) < 1e-14, (x, R[n] * U[n][:2], j)
+        # Sec. 2.1 Eq. alpha: the fill level follows the new mass and density
+        assert abs(s.get("alpha")[n] - s.get("mass")[n] / R[n]) < 1e-15
 
 
 def test_henry_reconstruction_and_gas_flux(oracle_mod):
