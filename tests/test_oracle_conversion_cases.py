@@ -116,19 +116,24 @@ def test_mass_exchange_weights_theta(oracle_mod):
     assert checked == 8
 
 
-def test_reconstruction_at_gas_links(oracle_mod):
+@pytest.mark.parametrize("rippled", [False, True])
+def test_reconstruction_at_gas_links(oracle_mod, rippled):
     """Sec. 2.2 Eq. reconstruct on the flat interface row (alpha = 1/2
-    everywhere, so kappa = 0; k_Pi = 0), sigma = 0.02 so that the bubble's
+    everywhere, so kappa = 0; k_Pi = 0) or a rippled one (alpha random in
+    0.3..0.7, so each cell has the curvature kappa_x its geometry gives),
+    sigma = 0.02 so that the bubble's
     Laplace-equilibrium pressure differs from p0, random rho and u, every
     cell at equilibrium: the populations arriving at an interface cell x
     are the streamed ones from liquid and interface neighbours, the
     bounced-back own outgoing ones from walls, and from gas neighbours
     f_eq_i(rho_g, u_I) + f_eq_ibar(rho_g, u_I) - f_ibar(x) with
-    rho_g = p_g / c_s^2 (p_g the bubble's pressure) and u_I the cell's own
-    velocity.  Collision conserves density and momentum (no force), so
+    rho_g = (p_g - 2 sigma kappa_x) / c_s^2 (p_g the bubble's pressure) and
+    u_I the cell's own velocity.  Collision conserves density and momentum (no force), so
     after one step the cell's rho and rho u are the sums of those arrivals.
     Fails for a gas density without 1/c_s^2, p0 in place of the bubble's
-    pressure, u = 0 in place of u_I, or a missing -f_ibar(x)."""
+    pressure, u = 0 in place of u_I, or a missing -f_ibar(x); rippled, also
+    for sigma kappa in place of 2 sigma kappa or the curvature's sign
+    flipped."""
     rng = np.random.default_rng(13)
     t = layout()
     N = NX * NY
@@ -136,19 +141,23 @@ def test_reconstruction_at_gas_links(oracle_mod):
     u = rng.uniform(-0.02, 0.02, (N, 2))
     u3 = np.zeros((N, 3))
     u3[:, :2] = u
-    alpha = np.where(t == I_, 0.5, 0.0)
+    alpha = np.where(t == I_, rng.uniform(0.3, 0.7, N) if rippled else 0.5, 0.0)
     s = oracle_mod.OracleSim(dict(cfg(), sigma=0.02))
     s.set_cells(t, rho, u3.reshape(-1), alpha, np.zeros(N))
-    assert np.all(s.get("kappa")[t == I_] == 0.0)
+    kap = s.get("kappa")
+    if rippled:
+        assert np.min(np.abs(kap[t == I_])) > 1e-3
+    else:
+        assert np.all(kap[t == I_] == 0.0)
     pg = s.bubbles()["pressure"]
     assert pg.size == 1 and abs(pg[0] - 1.0 / 3.0) > 1e-4
-    rg = pg[0] * 3.0
     s.step(1)
     assert np.array_equal(s.types(), t)
     R, U = s.get("rho"), s.get("u")
     f = {n: feq(rho[n], u[n]) for n in range(N) if t[n] in (L_, I_)}
     for x in range(NX):
         n = idx(x, 3)
+        rg = (pg[0] - 2 * 0.02 * kap[n]) * 3.0
         fin = np.zeros(9)
         for i, (ex, ey) in enumerate(E):
             ib = E.index((-ex, -ey))
