@@ -231,6 +231,51 @@ def test_henry_reconstruction_and_gas_flux(oracle_mod):
     assert abs(b1["mass"][0] - (b0["mass"][0] + flux)) < 1e-14, (b1["mass"][0], b0["mass"][0] + flux)
 
 
+def test_atmosphere_is_held_at_p0_and_books_its_exchange_outside(oracle_mod):
+    """The reading of the headspace: gas touching the top interior layer (the
+    gas row here, under the wall) is the atmosphere, held at p0; its Henry
+    concentration is k_H p0, and what its interface cells exchange with it
+    goes to the outside ledger (entry 5) instead of changing it: after one
+    step its mass is again p0 V / RT and the ledger has taken the old mass
+    plus the exchange minus the new one.  The same hand sums as above give
+    the exchange.  Fails for an atmosphere that keeps the gas it receives
+    or a ledger entry of the opposite sign."""
+    rng = np.random.default_rng(19)
+    t = layout()
+    N = NX * NY
+    rho = rng.uniform(0.98, 1.02, N)
+    u = rng.uniform(-0.02, 0.02, (N, 2))
+    u3 = np.zeros((N, 3))
+    u3[:, :2] = u
+    c = rng.uniform(0.1, 0.9, N)
+    alpha = np.where(t == I_, 0.5, 0.0)
+    kH, p0, RT = 0.7, 1.0 / 3.0, 1.0
+    s = oracle_mod.OracleSim(dict(cfg(), sigma=0.02, kH=kH, atmosphere=1))
+    s.set_cells(t, rho, u3.reshape(-1), alpha, c)
+    b0 = s.bubbles()
+    assert b0["atm"].tolist() == [1] and b0["pressure"][0] == p0
+    led0 = s.ledger()[5]
+    s.step(1)
+    EA, WA = E[:5], [1 / 3] + [1 / 6] * 4
+
+    def geq(cc, uu):
+        return np.array([WA[i] * cc * (1 + 3 * (ex * uu[0] + ey * uu[1])) for i, (ex, ey) in enumerate(EA)])
+
+    flux = 0.0
+    for x in range(NX):
+        n = idx(x, 3)
+        for i, (ex, ey) in enumerate(EA):
+            ib = EA.index((-ex, -ey))
+            if t[idx(x - ex, 3 - ey)] == G_:
+                gin = geq(kH * p0, u[n])[i] + geq(kH * p0, u[n])[ib] - geq(c[n], u[n])[ib]
+                flux += geq(c[n], u[n])[ib] - gin
+    b1 = s.bubbles()
+    assert abs(flux) > 1e-3
+    assert b1["pressure"][0] == p0
+    assert abs(b1["mass"][0] - p0 * b1["volume"][0] / RT) < 1e-15
+    assert abs((s.ledger()[5] - led0) - (b0["mass"][0] + flux - b1["mass"][0])) < 1e-14
+
+
 def _uniform_case(alpha_of):
     """rho = 1 and u = 0 everywhere: every exchange term is w_i - w_i = 0, so
     only the conversion changes the masses."""
