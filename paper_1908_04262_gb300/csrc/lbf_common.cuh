@@ -37,9 +37,7 @@ enum : int { FLD_RHO = 0, FLD_U = 1, FLD_ALPHA = 2, FLD_MASS = 3, FLD_FLAGS = 4,
              FLD_KAPPA = 6, FLD_LABEL = 7, FLD_PI = 8, FLD_NORMAL = 9, FLD_DSTAR = 10 };
 
 // sticky device error bits
-// device error flags (p.err); ERR_TC_WAIT: a tensor-core wait (MMA
-// completion or the network's bulk copy) ran past its bound
-enum : int { ERR_CAPACITY = 1, ERR_NOTCONV = 2, ERR_HASH = 4, ERR_TC_WAIT = 8 };
+enum : int { ERR_CAPACITY = 1, ERR_NOTCONV = 2, ERR_HASH = 4 };
 
 // ---------------------------------------------------------------------------
 // velocity sets (Sec. 2: D2Q9 / D3Q19 with the paper's weights; Sec. 3.1:

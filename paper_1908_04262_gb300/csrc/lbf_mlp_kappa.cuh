@@ -4,6 +4,7 @@
 #pragma once
 #include "lbf_common.cuh"
 #include "lbf_mlp.cuh"
+#include "lbf_ops_api.h"
 #include "lbf_tc.cuh"
 
 namespace lbf {

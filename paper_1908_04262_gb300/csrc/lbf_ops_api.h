@@ -8,6 +8,11 @@
 
 namespace lbf {
 
+// a further sticky device error bit beside those of lbf_common.cuh: a wait
+// of the learned curvature on the tensor cores (MMA completion or the
+// network's bulk copy) ran past its bound
+constexpr int ERR_TC_WAIT = 8;
+
 struct Ops {
   virtual ~Ops() {}
   virtual void init_fill(const Params &p, int par, double h, cudaStream_t s) = 0;
