@@ -61,6 +61,38 @@ def test_create_rejects_bad_configuration(name, bad):
     assert ei.value.code == EINVAL, (name, str(ei.value))
 
 
+def test_network_calls_reject_bad_arguments_on_the_host():
+    """The learned-curvature entry points check their arguments before any
+    CUDA call: NULL pointers, negative or empty counts, radii that are not
+    positive and training configurations outside the header's ranges are
+    LBF_EINVAL; an empty forward pass (n = 0) succeeds without a launch."""
+    import ctypes
+
+    lbf = _lib_or_skip()
+    lib = lbf.load()
+    d = ctypes.c_void_p(16)  # never dereferenced: every call below returns first
+    assert lib.lbf_mlp_forward(None, d, 4, d, None) == EINVAL
+    assert lib.lbf_mlp_forward(d, d, -1, d, None) == EINVAL
+    assert lib.lbf_mlp_forward(d, d, 0, d, None) == 0
+    assert lib.lbf_mlp_loss_grad(d, d, d, 0, d, d, None) == EINVAL
+    assert lib.lbf_mlp_loss_grad(d, None, d, 8, d, d, None) == EINVAL
+    assert lib.lbf_mlp_generate(1, 8, 0.0, 4.0, d, d, None) == EINVAL
+    assert lib.lbf_mlp_generate(1, 8, 5.0, 4.0, d, d, None) == EINVAL
+    assert lib.lbf_mlp_generate(1, -1, 2.0, 4.0, d, d, None) == EINVAL
+    assert lib.lbf_mlp_stencils_from_params(d, 0, d, d, None) == EINVAL
+    assert lib.lbf_mlp_attach(None, None) == EINVAL
+    assert lib.lbf_mlp_harvest(None, d, d, None, 4, ctypes.byref(ctypes.c_int())) == EINVAL
+    theta = (ctypes.c_float * lbf.MLP_NPARAM)()
+    assert lib.lbf_mlp_train(None, theta, None) == EINVAL
+    good = dict(seed=1, n_samples=4096, epochs=1, batch=256, lr=1e-3, rmin=2.0, rmax=20.0, noise=0.0,
+                x_extra=None, y_extra=None, n_extra=0, stream=None)
+    for bad in (dict(batch=8), dict(epochs=0), dict(n_samples=-1), dict(noise=-0.1), dict(n_samples=100),
+                dict(n_extra=5)):
+        cfg = lbf.MlpTrainCfg(**dict(good, **bad))
+        assert lib.lbf_mlp_train(ctypes.byref(cfg), theta, None) == EINVAL, bad
+    assert b"bad" in lib.lbf_last_error() or b"fewer" in lib.lbf_last_error()
+
+
 def test_create_rejects_null_config():
     import ctypes
 
