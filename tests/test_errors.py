@@ -93,6 +93,24 @@ def test_network_calls_reject_bad_arguments_on_the_host():
     assert b"bad" in lib.lbf_last_error() or b"fewer" in lib.lbf_last_error()
 
 
+def test_noalloc_labelling_rejects_bad_sizes_on_the_host():
+    """The labelling entry point that allocates nothing checks its buffers
+    and sizes before any CUDA call: NULL buffers, extents below 3, and
+    lattices beyond its static scratch (1,048,576 cells) are LBF_EINVAL with
+    a message naming the limit."""
+    import ctypes
+
+    lbf = _lib_or_skip()
+    lib = lbf.load()
+    d = ctypes.c_void_p(16)  # never dereferenced
+    assert lib.lbf_label_gas_noalloc(None, 8, 8, 1, d, d, None) == EINVAL
+    assert lib.lbf_label_gas_noalloc(d, 2, 8, 1, d, d, None) == EINVAL
+    assert lib.lbf_label_gas_noalloc(d, 8, 8, 2, d, d, None) == EINVAL
+    assert lib.lbf_label_gas_noalloc(d, 1024, 1025, 1, d, d, None) == EINVAL
+    assert b"1,048,576" in lib.lbf_last_error()
+    assert lib.lbf_label_gas_noalloc(d, 128, 128, 65, d, d, None) == EINVAL
+
+
 def test_create_rejects_null_config():
     import ctypes
 
