@@ -276,6 +276,84 @@ def test_atmosphere_is_held_at_p0_and_books_its_exchange_outside(oracle_mod):
     assert abs((s.ledger()[5] - led0) - (b0["mass"][0] + flux - b1["mass"][0])) < 1e-14
 
 
+def test_mass_exchange_weights_theta_3d(oracle_mod):
+    """The same hand computation of Sec. 2.1 Eq. massexchange on D3Q19 (the
+    paper's 3D lattice: rest 1/3, six faces 1/18, twelve edges 1/36, no
+    corners): a 5 x 5 x 6 box periodic in x and y, walls at z = 0 and 5,
+    liquid at z = 1, 2, interface at z = 3, gas at z = 4, an extra interface
+    cell (2, 2, 4) in the gas and an interior wall (1, 1, 2), random rho, u
+    and fill levels 0.3..0.7: after one step M = alpha rho + sum_i Theta_i
+    (f_ibar(x + e_i) - f_i(x)) over the 18 links, Theta = 1 (liquid),
+    (alpha_x + alpha_nb)/2 (interface), 0 (gas, wall).  Fails for corner
+    links, a missing edge link or other weights."""
+    nx, ny, nz = 5, 5, 6
+    E3 = [(0, 0, 0)] + [v for a in range(3) for v in (tuple(1 if k == a else 0 for k in range(3)),
+                                                       tuple(-1 if k == a else 0 for k in range(3)))]
+    E3 += [(a, b, 0) for a in (1, -1) for b in (1, -1)] + [(a, 0, b) for a in (1, -1) for b in (1, -1)]
+    E3 += [(0, a, b) for a in (1, -1) for b in (1, -1)]
+    W3 = [1 / 3] + [1 / 18] * 6 + [1 / 36] * 12
+    assert len(E3) == 19 and abs(sum(W3) - 1) < 1e-15
+
+    def id3(x, y, z):
+        return (x % nx) + nx * ((y % ny) + ny * z)
+
+    def feq3(r, uu):
+        out = np.zeros(19)
+        for i, e in enumerate(E3):
+            eu = float(np.dot(e, uu))
+            out[i] = W3[i] * r * (1 + 3 * eu + 4.5 * eu * eu - 1.5 * float(np.dot(uu, uu)))
+        return out
+
+    N = nx * ny * nz
+    t = np.full(N, L_, np.uint8)
+    for x in range(nx):
+        for y in range(ny):
+            t[id3(x, y, 0)] = t[id3(x, y, 5)] = W_
+            t[id3(x, y, 4)] = G_
+            t[id3(x, y, 3)] = I_
+    t[id3(2, 2, 4)] = I_
+    t[id3(1, 1, 2)] = W_
+    rng = np.random.default_rng(23)
+    rho = rng.uniform(0.98, 1.02, N)
+    u = rng.uniform(-0.02, 0.02, (N, 3))
+    alpha = np.where(t == I_, rng.uniform(0.3, 0.7, N), 0.0)
+    c3 = W.config(nx=nx, ny=ny, nz=nz, storage="fp64", walls=0x30, atmosphere=0, sigma=0.0, k_pi=0.0,
+                  tau=0.8, rho0=1.0, p0=1.0 / 3.0, RT=1.0, kH=0.0, c0=0.0, eps=1e-3)
+    s = oracle_mod.OracleSim(c3)
+    s.set_cells(t, rho, u.reshape(-1), alpha, np.zeros(N))
+    assert np.array_equal(s.types(), t)
+    M0 = s.get("mass").copy()
+    s.step(1)
+    assert np.array_equal(s.types(), t), "no cell may convert in this case"
+    M1 = s.get("mass")
+    f = {n: feq3(rho[n], u[n]) for n in range(N) if t[n] in (L_, I_)}
+    checked, kinds_seen = 0, set()
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                n = id3(x, y, z)
+                if t[n] != I_:
+                    continue
+                dM = 0.0
+                for i in range(1, 19):
+                    e = E3[i]
+                    m = id3(x + e[0], y + e[1], z + e[2])
+                    ib = E3.index(tuple(-k for k in e))
+                    if t[m] == L_:
+                        theta = 1.0
+                    elif t[m] == I_:
+                        theta = 0.5 * (alpha[n] + alpha[m])
+                    else:
+                        theta = 0.0
+                    kinds_seen.add(int(t[m]))
+                    if theta:
+                        dM += theta * (f[m][ib] - f[n][i])
+                assert abs(M0[n] - alpha[n] * rho[n]) < 1e-15
+                assert abs(M1[n] - (M0[n] + dM)) < 1e-14, ((x, y, z), M1[n], M0[n] + dM)
+                checked += 1
+    assert checked == nx * ny + 1 and kinds_seen == {G_, L_, I_, W_}
+
+
 def _uniform_case(alpha_of):
     """rho = 1 and u = 0 everywhere: every exchange term is w_i - w_i = 0, so
     only the conversion changes the masses."""
