@@ -276,6 +276,52 @@ def test_atmosphere_is_held_at_p0_and_books_its_exchange_outside(oracle_mod):
     assert abs((s.ledger()[5] - led0) - (b0["mass"][0] + flux - b1["mass"][0])) < 1e-14
 
 
+# D3Q19 (the paper's 3D lattice: rest 1/3, six faces 1/18, twelve edges
+# 1/36) and D3Q7 (rest 1/4, faces 1/8) for the 3D hand cases, on a
+# 5 x 5 x 6 box periodic in x and y with walls at z = 0 and 5
+NX3, NY3, NZ3 = 5, 5, 6
+E3 = [(0, 0, 0)] + [v for a in range(3) for v in (tuple(1 if k == a else 0 for k in range(3)),
+                                                   tuple(-1 if k == a else 0 for k in range(3)))]
+E3 += [(a, b, 0) for a in (1, -1) for b in (1, -1)] + [(a, 0, b) for a in (1, -1) for b in (1, -1)]
+E3 += [(0, a, b) for a in (1, -1) for b in (1, -1)]
+W3 = [1 / 3] + [1 / 18] * 6 + [1 / 36] * 12
+EA3, WA3 = E3[:7], [1 / 4] + [1 / 8] * 6
+
+
+def id3(x, y, z):
+    return (x % NX3) + NX3 * ((y % NY3) + NY3 * z)
+
+
+def feq3(r, uu):
+    """D3Q19 equilibrium (Sec. 2 Eq. equilibrium)."""
+    out = np.zeros(19)
+    for i, e in enumerate(E3):
+        eu = float(np.dot(e, uu))
+        out[i] = W3[i] * r * (1 + 3 * eu + 4.5 * eu * eu - 1.5 * float(np.dot(uu, uu)))
+    return out
+
+
+def geq3(cc, uu):
+    """D3Q7 advection-diffusion equilibrium (Sec. 3.1; c_s^2 = 1/4)."""
+    return np.array([WA3[i] * cc * (1 + 4 * float(np.dot(e, uu))) for i, e in enumerate(EA3)])
+
+
+def layout3():
+    """z = 1, 2 liquid, z = 3 interface, z = 4 gas (under the top wall)."""
+    t = np.full(NX3 * NY3 * NZ3, L_, np.uint8)
+    for x in range(NX3):
+        for y in range(NY3):
+            t[id3(x, y, 0)] = t[id3(x, y, 5)] = W_
+            t[id3(x, y, 4)] = G_
+            t[id3(x, y, 3)] = I_
+    return t
+
+
+def cfg3(**kw):
+    return dict(W.config(nx=NX3, ny=NY3, nz=NZ3, storage="fp64", walls=0x30, atmosphere=0, sigma=0.0,
+                         k_pi=0.0, tau=0.8, rho0=1.0, p0=1.0 / 3.0, RT=1.0, kH=0.0, c0=0.0, eps=1e-3), **kw)
+
+
 def test_mass_exchange_weights_theta_3d(oracle_mod):
     """The same hand computation of Sec. 2.1 Eq. massexchange on D3Q19 (the
     paper's 3D lattice: rest 1/3, six faces 1/18, twelve edges 1/36, no
@@ -286,40 +332,17 @@ def test_mass_exchange_weights_theta_3d(oracle_mod):
     (f_ibar(x + e_i) - f_i(x)) over the 18 links, Theta = 1 (liquid),
     (alpha_x + alpha_nb)/2 (interface), 0 (gas, wall).  Fails for corner
     links, a missing edge link or other weights."""
-    nx, ny, nz = 5, 5, 6
-    E3 = [(0, 0, 0)] + [v for a in range(3) for v in (tuple(1 if k == a else 0 for k in range(3)),
-                                                       tuple(-1 if k == a else 0 for k in range(3)))]
-    E3 += [(a, b, 0) for a in (1, -1) for b in (1, -1)] + [(a, 0, b) for a in (1, -1) for b in (1, -1)]
-    E3 += [(0, a, b) for a in (1, -1) for b in (1, -1)]
-    W3 = [1 / 3] + [1 / 18] * 6 + [1 / 36] * 12
+    nx, ny, nz = NX3, NY3, NZ3
     assert len(E3) == 19 and abs(sum(W3) - 1) < 1e-15
-
-    def id3(x, y, z):
-        return (x % nx) + nx * ((y % ny) + ny * z)
-
-    def feq3(r, uu):
-        out = np.zeros(19)
-        for i, e in enumerate(E3):
-            eu = float(np.dot(e, uu))
-            out[i] = W3[i] * r * (1 + 3 * eu + 4.5 * eu * eu - 1.5 * float(np.dot(uu, uu)))
-        return out
-
     N = nx * ny * nz
-    t = np.full(N, L_, np.uint8)
-    for x in range(nx):
-        for y in range(ny):
-            t[id3(x, y, 0)] = t[id3(x, y, 5)] = W_
-            t[id3(x, y, 4)] = G_
-            t[id3(x, y, 3)] = I_
+    t = layout3()
     t[id3(2, 2, 4)] = I_
     t[id3(1, 1, 2)] = W_
     rng = np.random.default_rng(23)
     rho = rng.uniform(0.98, 1.02, N)
     u = rng.uniform(-0.02, 0.02, (N, 3))
     alpha = np.where(t == I_, rng.uniform(0.3, 0.7, N), 0.0)
-    c3 = W.config(nx=nx, ny=ny, nz=nz, storage="fp64", walls=0x30, atmosphere=0, sigma=0.0, k_pi=0.0,
-                  tau=0.8, rho0=1.0, p0=1.0 / 3.0, RT=1.0, kH=0.0, c0=0.0, eps=1e-3)
-    s = oracle_mod.OracleSim(c3)
+    s = oracle_mod.OracleSim(cfg3())
     s.set_cells(t, rho, u.reshape(-1), alpha, np.zeros(N))
     assert np.array_equal(s.types(), t)
     M0 = s.get("mass").copy()
@@ -352,6 +375,66 @@ def test_mass_exchange_weights_theta_3d(oracle_mod):
                 assert abs(M1[n] - (M0[n] + dM)) < 1e-14, ((x, y, z), M1[n], M0[n] + dM)
                 checked += 1
     assert checked == nx * ny + 1 and kinds_seen == {G_, L_, I_, W_}
+
+
+def test_reconstruction_henry_and_gas_flux_3d(oracle_mod):
+    """The 2D hand sums of Eq. reconstruct, Eq. henryslaw /
+    reconstructdiffusion and the gas-link exchange (Eq. gascurrent as read)
+    on D3Q19 and D3Q7: the flat interface layer z = 3 (alpha = 1/2, so
+    kappa = 0) of the 5 x 5 x 6 box under a gas layer, sigma = 0.02,
+    k_H = 0.7, random rho, u and dissolved gas.  After one step each
+    interface cell's rho, rho u and c are the sums of the streamed, bounced
+    and rebuilt populations (five D3Q19 links and one D3Q7 link come from
+    the gas), and the bubble has gained the exchange at its gas links."""
+    t = layout3()
+    N = NX3 * NY3 * NZ3
+    rng = np.random.default_rng(29)
+    rho = rng.uniform(0.98, 1.02, N)
+    u = rng.uniform(-0.02, 0.02, (N, 3))
+    c = rng.uniform(0.1, 0.9, N)
+    alpha = np.where(t == I_, 0.5, 0.0)
+    kH = 0.7
+    s = oracle_mod.OracleSim(cfg3(sigma=0.02, kH=kH))
+    s.set_cells(t, rho, u.reshape(-1), alpha, c)
+    assert np.all(s.get("kappa")[t == I_] == 0.0)
+    b0 = s.bubbles()
+    assert b0["pressure"].size == 1 and abs(b0["pressure"][0] - 1.0 / 3.0) > 1e-4
+    pg = b0["pressure"][0]
+    s.step(1)
+    assert np.array_equal(s.types(), t)
+    R, U, C = s.get("rho"), s.get("u"), s.get("conc")
+    flux = 0.0
+    for x in range(NX3):
+        for y in range(NY3):
+            n = id3(x, y, 3)
+            fin, gin = np.zeros(19), np.zeros(7)
+            gas_links = 0
+            for i, e in enumerate(E3):
+                ib = E3.index(tuple(-k for k in e))
+                m = id3(x - e[0], y - e[1], 3 - e[2])
+                if i == 0 or t[m] in (L_, I_):
+                    fin[i] = feq3(rho[m], u[m])[i]
+                elif t[m] == W_:
+                    fin[i] = feq3(rho[n], u[n])[ib]
+                else:
+                    gas_links += 1
+                    fin[i] = feq3(3 * pg, u[n])[i] + feq3(3 * pg, u[n])[ib] - feq3(rho[n], u[n])[ib]
+            for i, e in enumerate(EA3):
+                ib = EA3.index(tuple(-k for k in e))
+                m = id3(x - e[0], y - e[1], 3 - e[2])
+                if i == 0 or t[m] in (L_, I_):
+                    gin[i] = geq3(c[m], u[m])[i]
+                else:
+                    assert t[m] == G_
+                    gin[i] = geq3(kH * pg, u[n])[i] + geq3(kH * pg, u[n])[ib] - geq3(c[n], u[n])[ib]
+                    flux += geq3(c[n], u[n])[ib] - gin[i]
+            assert gas_links == 5
+            assert abs(R[n] - fin.sum()) < 1e-14
+            assert np.max(np.abs(R[n] * U[n] - fin @ np.array(E3, float))) < 1e-14
+            assert abs(C[n] - gin.sum()) < 1e-14
+    b1 = s.bubbles()
+    assert abs(flux) > 1e-3
+    assert abs(b1["mass"][0] - (b0["mass"][0] + flux)) < 1e-13
 
 
 def _uniform_case(alpha_of):
