@@ -38,7 +38,8 @@ extern "C" {
 #define LBF_ENOMEM (-2)     /* device allocation failed                       */
 #define LBF_ECUDA (-3)      /* a CUDA runtime call failed                     */
 #define LBF_ENOTCONV (-4)   /* union-find iteration cap reached               */
-#define LBF_ENONFINITE (-5) /* non-finite populations found by lbf_ledger     */
+#define LBF_ENONFINITE (-5) /* a NaN or infinity given to lbf_set_cells, or
+                               non-finite populations found by lbf_ledger   */
 #define LBF_ECAPACITY (-6)  /* more bubbles than cfg.bubble_capacity          */
 
 typedef struct lbf_sim lbf_sim;
