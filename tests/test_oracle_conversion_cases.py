@@ -437,6 +437,36 @@ def test_reconstruction_henry_and_gas_flux_3d(oracle_mod):
     assert abs(b1["mass"][0] - (b0["mass"][0] + flux)) < 1e-13
 
 
+def test_filling_cell_3d(oracle_mod):
+    """A filling cell on D3Q19: (2, 2, 3) holds 1.3 in the uniform state
+    (rho = 1, u = 0: no exchange), so it becomes liquid; its gas neighbours
+    along lattice links -- (2, 2, 4) and the four edge neighbours (1, 2, 4),
+    (3, 2, 4), (2, 1, 4), (2, 3, 4) -- become interface, the corner ones
+    ((1, 1, 4) ...) stay gas; the surplus 0.3 goes in equal parts to the 13
+    link neighbours interface after the conversion: the 8 in its layer and
+    the 5 new ones.  Fails for a 26-cell neighbourhood."""
+    t = layout3()
+    N = NX3 * NY3 * NZ3
+    alpha = np.where(t == I_, 0.5, 0.0)
+    alpha[id3(2, 2, 3)] = 1.3
+    s = oracle_mod.OracleSim(cfg3())
+    s.set_cells(t, np.ones(N), np.zeros(3 * N), alpha, np.zeros(N))
+    s.step(1)
+    ty, M = s.types(), s.get("mass")
+    share = 0.3 / 13
+    assert ty[id3(2, 2, 3)] == L_
+    for c in [(2, 2, 4), (1, 2, 4), (3, 2, 4), (2, 1, 4), (2, 3, 4)]:
+        assert ty[id3(*c)] == I_, c
+        assert abs(M[id3(*c)] - share) < 1e-14, c
+    for c in [(1, 1, 4), (3, 3, 4), (1, 3, 4), (3, 1, 4), (0, 2, 4)]:
+        assert ty[id3(*c)] == G_, c
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            if dx or dy:
+                assert abs(M[id3(2 + dx, 2 + dy, 3)] - (0.5 + share)) < 1e-14, (dx, dy)
+    assert abs(M[id3(0, 2, 3)] - 0.5) < 1e-14
+
+
 def _uniform_case(alpha_of):
     """rho = 1 and u = 0 everywhere: every exchange term is w_i - w_i = 0, so
     only the conversion changes the masses."""
