@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "lbf.h")).read()
+    with open(os.path.join(ROOT, "include", "lbf.h")) as fh:
+        src = fh.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(lbf_[a-z_0-9]+)\s*\(", src)))
 
@@ -42,7 +43,8 @@ def test_config_struct_matches_header_layout():
     """The ctypes mirror lists the fields of lbf_config in header order."""
     from paper_1908_04262_gb300 import lbf
 
-    src = open(os.path.join(ROOT, "include", "lbf.h")).read()
+    with open(os.path.join(ROOT, "include", "lbf.h")) as fh:
+        src = fh.read()
     body = src[src.index("typedef struct {\n  int nx, ny, nz;"):src.index("} lbf_config;")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     names = []
